@@ -1,0 +1,246 @@
+/*
+ * flatspin_b300.h - C ABI of the flatspin relax loop on B300 (sm_103a).
+ *
+ * The model is the dipole model of Jensen et al., "flatspin: A Large-Scale
+ * Artificial Spin Ice Simulator" (arXiv 2002.11401):
+ *   - islands are point dipoles with Ising spins s_i in {-1,+1} at fixed
+ *     positions r_i and angles theta_i (Sec. "Magnets as dipoles", Eq. 1);
+ *   - the total field is dipolar + external + thermal (Eq. 2); the dipolar
+ *     field sums Eq. 3 over the neighbours inside a cutoff (Sec. "Magnetic
+ *     dipole-dipole interactions");
+ *   - an island may switch when the left-hand side (LHS) of the generalised
+ *     Stoner-Wohlfarth astroid, Eq. 5, exceeds one and h_i . m_i < 0, Eq. 6;
+ *   - coercive fields h_k^(i) ~ N(h_k, k_disorder h_k) (Sec. "Imperfections and
+ *     disorder");
+ *   - dynamics: flip the flippable island with the largest LHS (ties: lowest
+ *     index), repeat until none is flippable, then move to the next field value
+ *     (Sec. "Dynamics").
+ *
+ * Conventions for every call:
+ *   - Host buffers belong to the caller and are copied in or out before the
+ *     call returns. Device buffers passed to *_dev calls belong to the caller
+ *     and must stay valid until the work queued on the simulation's stream ends.
+ *   - The library owns every device allocation it makes for a simulation and
+ *     frees it in fs_destroy.
+ *   - Calls are synchronous on the simulation's stream unless named *_dev.
+ *   - A fs_sim is not thread-safe; distinct fs_sim objects are independent.
+ *   - Island order is the canonical order: ascending y, then ascending x, for
+ *     generated arrays; the caller's order for custom arrays. Every index in and
+ *     out of the library uses it.
+ *   - On error nothing is committed and fs_last_error() explains.
+ *   - A device fault is reported as FS_ERR_CUDA; the CUDA context is then
+ *     unusable and the process should exit.
+ */
+#ifndef FLATSPIN_B300_H
+#define FLATSPIN_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FS_OK = 0,
+    FS_ERR_INVALID = 1,       /* bad argument or unsupported size */
+    FS_ERR_OOM = 2,           /* device or host allocation failed */
+    FS_ERR_CUDA = 3,          /* a CUDA call failed */
+    FS_ERR_NOT_CONVERGED = 4, /* a relax exceeded max_flips_per_step */
+    FS_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+    FS_ERR_BOUNDS = 6,        /* an index check on device failed */
+    FS_ERR_STATE = 8          /* call out of order (e.g. relax before params) */
+} fs_status;
+
+typedef enum { FS_SQUARE = 0, FS_PINWHEEL = 1, FS_KAGOME = 2 } fs_geom;
+
+/* Arithmetic of the relax loop.
+ * FS_FP64: dipolar sums in 64-bit fixed point (exact integer sums of per-pair
+ *   coefficients rounded to 2^-e64, e64 chosen per system), the astroid in FP64.
+ * FS_FP32_RECHECK: dipolar sums in 32-bit fixed point, the astroid in FP32 with
+ *   rigorous error bounds; a pick whose FP32 margin is within its error band of
+ *   one, of another candidate, or of the sign change of Eq. 6 is re-evaluated
+ *   in the FS_FP64 arithmetic. Both yield the same flip sequence. */
+typedef enum { FS_FP64 = 0, FS_FP32_RECHECK = 1 } fs_precision;
+
+/* Model parameters (Sec. "The flatspin magnetic model"). */
+typedef struct {
+    double alpha;       /* dipolar coupling, Eq. 3 */
+    double hk;          /* mean coercive field h_k */
+    double k_disorder;  /* relative std of h_k^(i) */
+    double b, c;        /* astroid height and width, Eq. 5 */
+    double beta, gamma; /* astroid exponents: 2/gamma on h_par, 2/beta on h_perp (Eq. 5) */
+    double cutoff;      /* neighbourhood radius in lattice spacings (inclusive) */
+    double sigma_th;    /* thermal field std, Sec. "Thermal field" (0 = none) */
+    uint64_t seed;      /* Philox key of the h_k and thermal draws */
+    uint32_t instance;  /* third Philox counter word (ensemble member) */
+    int32_t precision;  /* fs_precision */
+    int64_t max_flips_per_step; /* guard; <= 0 means 16 * n */
+} fs_params;
+
+typedef struct fs_sim fs_sim;
+
+/* Read-only facts about a built system. */
+typedef struct {
+    int64_t n;         /* islands */
+    int64_t nnz;       /* neighbour pairs (ordered) */
+    int64_t nnz_padded;/* stored entries (rows padded to multiples of 4) */
+    int32_t max_degree;
+    int32_t e64, e32;  /* fixed-point exponents: value = integer * 2^-e */
+    int64_t device_bytes;
+    double band_rel, band_abs; /* FP32 error band of the LHS: rel * LHS + abs */
+} fs_info;
+
+/* Last error message of `sim` (or of the last failed create call when sim is
+ * NULL). Valid until the next call on the same object / thread. */
+const char* fs_last_error(const fs_sim* sim);
+
+/* FNV-1a (64-bit) offset basis: the value a fresh flip-sequence hash starts
+ * from. The hash folds the 8 little-endian bytes (u32 step, u32 island) of
+ * every flip, in order. */
+uint64_t fs_hash_init(void);
+
+/* Generated arrays (Sec. "Geometries"): nx x ny cells of spacing a.
+ * Square: closed edges, islands at 0 and 90 degrees, 2 nx ny + nx + ny islands.
+ * Pinwheel: the square's islands turned 45 degrees about their centres.
+ * Kagome: nx x ny flat-top hexagons of edge a, islands at 0/60/120 degrees on
+ *   the edge midpoints, 3 nx ny + 2 nx + 2 ny - 1 islands.
+ * Angles are (deg * pi) / 180 in double. *out receives a new simulation. */
+fs_status fs_create_geometry(int32_t kind, int32_t nx, int32_t ny, double a, fs_sim** out);
+
+/* Any 2D set of identical islands (Sec. "Geometries", last paragraph):
+ * positions x, y and angles theta (radians), n islands, caller's order.
+ * At most 65536 distinct angles. `a` is the unit of the cutoff. */
+fs_status fs_create_custom(int64_t n, const double* x, const double* y, const double* theta,
+                           double a, fs_sim** out);
+
+void fs_destroy(fs_sim* sim);
+
+/* CUDA stream (cudaStream_t) for all later work of `sim`; NULL = legacy default. */
+fs_status fs_set_stream(fs_sim* sim, void* stream);
+
+/* Sets the parameters, draws h_k^(i) (Philox4x32-10 counter (i, r, instance, 0),
+ * Box-Muller, redrawn while <= 0; Sec. "Imperfections and disorder") and builds
+ * the neighbour tensors on the device (cell grid, CSR rows ascending, per-pair
+ * coefficients P_ij = mhat_i . T_ij mhat_j and Q_ij = mhat_perp_i . T_ij mhat_j,
+ * T_ij = alpha (3 rhat rhat^T - I) / r^3, Eq. 3). Resets spins to +1. */
+fs_status fs_set_params(fs_sim* sim, const fs_params* p);
+
+/* Replaces the drawn coercive fields with the caller's (n values, > 0). */
+fs_status fs_set_hk(fs_sim* sim, const double* hk, int64_t n);
+
+/* Spins (n values in {-1,+1}); default after fs_set_params is all +1. */
+fs_status fs_set_spins(fs_sim* sim, const int8_t* s, int64_t n);
+
+/* External field (Sec. "External field", global form) and the field-step index
+ * that keys the thermal draw (Philox counter (i, step, instance, 1)). */
+fs_status fs_set_field(fs_sim* sim, double hx, double hy, uint32_t step);
+
+/* One relax at the current field (Sec. "Dynamics"): recompute every field,
+ * then flip the flippable island with the largest Eq. 5 LHS (lowest index on
+ * ties) until none is flippable. The first log_cap flipped islands go to
+ * log_spin (may be NULL). *n_flips receives the number of flips. */
+fs_status fs_relax(fs_sim* sim, uint32_t* log_spin, int64_t log_cap, int64_t* n_flips);
+
+/* K field steps; step t applies (hx[t], hy[t]) with thermal step index
+ * step0 + t, then relaxes. Host buffers. log_step/log_spin receive the first
+ * log_cap flips (may be NULL), flips_per_step[K] may be NULL, *seq_hash is
+ * updated in place (start from fs_hash_init()), *n_flips receives the total.
+ * resweep != 0 recomputes every dipolar sum from the neighbour tensors at every
+ * field step (the paper's order); resweep == 0 keeps the exact fixed-point sums
+ * that the flips maintain and only re-evaluates Eq. 5/6. Both give identical
+ * results because integer sums are exact. */
+fs_status fs_run_protocol(fs_sim* sim, const double* hx, const double* hy, int64_t K,
+                          uint32_t step0, int32_t resweep, uint32_t* log_step,
+                          uint32_t* log_spin, int64_t log_cap, int64_t* flips_per_step,
+                          uint64_t* seq_hash, int64_t* n_flips);
+
+/* As fs_run_protocol with device buffers, queued on the simulation's stream
+ * without waiting: d_hx/d_hy [K] in; d_log_step/d_log_spin [log_cap] (or NULL),
+ * d_flips_per_step [K] (or NULL), d_out[4] receives {status, n_flips,
+ * seq_hash, 0} as int64/uint64 when the queued work ends (seq_hash starts from
+ * fs_hash_init()). Returns an error only for bad arguments or launch failures. */
+fs_status fs_run_protocol_dev(fs_sim* sim, const double* d_hx, const double* d_hy, int64_t K,
+                              uint32_t step0, int32_t resweep, uint32_t* d_log_step,
+                              uint32_t* d_log_spin, int64_t log_cap,
+                              int64_t* d_flips_per_step, uint64_t* d_out);
+
+/* Current spins, n values. */
+fs_status fs_get_spins(const fs_sim* sim, int8_t* out, int64_t n);
+
+/* Total field (Eq. 2) of every island in its own frame at the current spins,
+ * external field and thermal step: h_par = h . mhat_i, h_perp = h . mhat_perp_i.
+ * In FS_FP32_RECHECK the values are those of the FP32 evaluation. */
+fs_status fs_get_fields(fs_sim* sim, double* h_par, double* h_perp, int64_t n);
+
+/* Eq. 5 LHS of every island at the current state, in the simulation's precision,
+ * with bounds lo <= LHS(FS_FP64) <= hi (for FS_FP64, lo = hi = lhs). Any output
+ * may be NULL. */
+fs_status fs_get_lhs(fs_sim* sim, double* lhs, double* lo, double* hi, int64_t n);
+
+fs_status fs_get_hk(const fs_sim* sim, double* out, int64_t n);
+fs_status fs_get_geometry(const fs_sim* sim, double* x, double* y, double* theta, int64_t n);
+fs_status fs_get_info(const fs_sim* sim, fs_info* out);
+
+/* Neighbour CSR (unpadded): row_ptr[n+1], col[nnz] ascending per row, and the
+ * FP64-path coefficients P[nnz], Q[nnz] (fixed point converted back to double;
+ * field at i per unit spin of j, in i's frame). Any output may be NULL. */
+fs_status fs_get_csr(const fs_sim* sim, int64_t* row_ptr, int32_t* col, double* P, double* Q);
+
+/* ---- Batched ensembles ------------------------------------------------------
+ * Advances n independent simulations through the same protocol together: per
+ * field step one sweep over every member's rows and one relax per member, all
+ * members in flight at once, the whole protocol captured in one CUDA graph on
+ * sims[0]'s stream. Every member must have parameters set and the same
+ * precision. Per member i: n_flips[i], seq_hash[i] (in/out, start from
+ * fs_hash_init()), status[i] (fs_status), flips_per_step[i*K + t] (or NULL).
+ * Results equal those of running each member alone. */
+fs_status fs_batch_run_protocol(fs_sim* const* sims, int32_t n, const double* hx,
+                                const double* hy, int64_t K, int32_t resweep, int64_t* n_flips,
+                                uint64_t* seq_hash, int32_t* status, int64_t* flips_per_step);
+
+/* ---- Continuous-batching server ---------------------------------------------
+ * A host thread admits requests while their device footprint fits the budget,
+ * builds them on a side stream, and advances every admitted simulation one field
+ * step per iteration (one batched sweep and one batched relax launch); requests
+ * that arrive while others run join at the next iteration. Results equal those
+ * of running each request alone. */
+typedef struct fs_server fs_server;
+
+typedef struct {
+    int32_t kind;          /* fs_geom */
+    int32_t nx, ny;
+    double a;
+    fs_params params;
+    int64_t K;             /* field steps */
+    const double* hx;      /* [K], copied at submit */
+    const double* hy;      /* [K], copied at submit */
+    int8_t* spins_out;     /* optional host buffer [n] for the final spins (written before done) */
+} fs_request;
+
+typedef struct {
+    int32_t status;        /* fs_status of the simulation */
+    int32_t done;          /* 1 when finished */
+    int64_t n;             /* islands */
+    int64_t n_flips;
+    uint64_t seq_hash;
+    double t_submit, t_admit, t_done; /* seconds on the server's monotonic clock */
+} fs_result;
+
+/* hbm_budget: bytes of device memory the server may hold for admitted requests. */
+fs_status fs_server_create(size_t hbm_budget, int32_t max_active, fs_server** out);
+fs_status fs_server_submit(fs_server* srv, const fs_request* req, uint64_t* ticket);
+/* FS_ERR_STATE while the request is not done; FS_OK with *out filled when done. */
+fs_status fs_server_poll(fs_server* srv, uint64_t ticket, fs_result* out);
+/* Blocks until every submitted request is done. */
+fs_status fs_server_drain(fs_server* srv);
+/* Seconds on the server's clock (for arrival schedules). */
+double fs_server_now(const fs_server* srv);
+void fs_server_destroy(fs_server* srv);
+const char* fs_server_last_error(const fs_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLATSPIN_B300_H */

@@ -1,0 +1,856 @@
+// fs_api.cu - the C ABI of include/flatspin_b300.h: simulation objects, device
+// memory, the neighbour build, the field-step protocol driver and batches.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/flatspin_b300.h"
+#include "fs_build.h"
+#include "fs_common.cuh"
+#include "fs_host.h"
+#include "fs_internal.h"
+#include "fs_kernels.h"
+
+using namespace fs;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+const char* cuda_msg(cudaError_t e) { return cudaGetErrorString(e); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Device arena
+// ---------------------------------------------------------------------------
+
+namespace fs {
+
+void Arena::release(cudaStream_t st) {
+    for (void* p : blocks) cudaFreeAsync(p, st);
+    blocks.clear();
+    bytes = 0;
+}
+
+cudaError_t Arena::alloc(void** out, size_t n, cudaStream_t st) {
+    *out = nullptr;
+    if (n == 0) n = 16;
+    n = (n + 255) & ~(size_t)255;
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, n, st);
+    if (e != cudaSuccess) return e;
+    blocks.push_back(p);
+    bytes += (int64_t)n;
+    *out = p;
+    return cudaSuccess;
+}
+
+// Largest |z32 - z64| of the FP32 and FP64 Box-Muller normals of one Philox block,
+// with margin (the FP32 draw keeps a relative error of a few ulp in ln u1, sqrt and
+// sincospi; |z| <= 8.7).
+const double kThermalZErr = 2e-5;
+
+int choose_lanes(double avg_groups) {
+    if (avg_groups <= 4.5) return 4;
+    if (avg_groups <= 8.5) return 8;
+    if (avg_groups <= 16.5) return 16;
+    return 8;
+}
+
+}  // namespace fs
+
+static fs_status fail(fs_sim* s, fs_status code, const std::string& msg) {
+    if (s)
+        s->err = msg;
+    else
+        g_last_error = msg;
+    return code;
+}
+
+static fs_status cfail(fs_sim* s, cudaError_t e, const char* where) {
+    return fail(s, FS_ERR_CUDA, std::string(where) + ": " + cuda_msg(e));
+}
+
+#define CK(call, where)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cfail(sim, e_, where); \
+    } while (0)
+
+extern "C" const char* fs_last_error(const fs_sim* sim) {
+    return sim ? sim->err.c_str() : g_last_error.c_str();
+}
+
+extern "C" uint64_t fs_hash_init(void) { return 0xcbf29ce484222325ull; }
+
+// ---------------------------------------------------------------------------
+// Creation
+// ---------------------------------------------------------------------------
+
+static fs_status init_sim(fs_sim* sim, std::vector<double>&& x, std::vector<double>&& y,
+                          std::vector<double>&& th, double a) {
+    sim->n = (int64_t)x.size();
+    sim->a = a;
+    sim->x = std::move(x);
+    sim->y = std::move(y);
+    sim->theta = std::move(th);
+    // angle classes: exact dedup of the angle values; (cos, sin) from the host libm
+    std::map<uint64_t, uint16_t> seen;
+    sim->cls.resize((size_t)sim->n);
+    for (int64_t i = 0; i < sim->n; ++i) {
+        uint64_t bits;
+        memcpy(&bits, &sim->theta[(size_t)i], 8);
+        auto it = seen.find(bits);
+        if (it == seen.end()) {
+            if (seen.size() >= 65536)
+                return fail(sim, FS_ERR_INVALID, "more than 65536 distinct island angles");
+            const uint16_t c = (uint16_t)seen.size();
+            seen.emplace(bits, c);
+            sim->cls_cos.push_back(std::cos(sim->theta[(size_t)i]));
+            sim->cls_sin.push_back(std::sin(sim->theta[(size_t)i]));
+            sim->cls[(size_t)i] = c;
+        } else {
+            sim->cls[(size_t)i] = it->second;
+        }
+    }
+    return FS_OK;
+}
+
+extern "C" fs_status fs_create_geometry(int32_t kind, int32_t nx, int32_t ny, double a,
+                                        fs_sim** out) {
+    if (!out) return fail(nullptr, FS_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (kind < 0 || kind > 2) return fail(nullptr, FS_ERR_INVALID, "unknown geometry kind");
+    if (nx <= 0 || ny <= 0 || nx > 100000 || ny > 100000 || !(a > 0.0))
+        return fail(nullptr, FS_ERR_INVALID, "bad geometry size or spacing");
+    Geometry g;
+    if (!make_geometry(kind, nx, ny, a, g)) return fail(nullptr, FS_ERR_INVALID, "bad geometry");
+    if ((int64_t)g.x.size() >= (1ll << 31) - 64)
+        return fail(nullptr, FS_ERR_INVALID, "too many islands");
+    fs_sim* sim = new fs_sim();
+    const fs_status r = init_sim(sim, std::move(g.x), std::move(g.y), std::move(g.theta), a);
+    if (r != FS_OK) {
+        g_last_error = sim->err;
+        delete sim;
+        return r;
+    }
+    *out = sim;
+    return FS_OK;
+}
+
+extern "C" fs_status fs_create_custom(int64_t n, const double* x, const double* y,
+                                      const double* theta, double a, fs_sim** out) {
+    if (!out) return fail(nullptr, FS_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (n <= 0 || n >= (1ll << 31) - 64 || !x || !y || !theta || !(a > 0.0))
+        return fail(nullptr, FS_ERR_INVALID, "bad custom geometry arguments");
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(x[i]) || !std::isfinite(y[i]) || !std::isfinite(theta[i]))
+            return fail(nullptr, FS_ERR_INVALID, "non-finite position or angle");
+    fs_sim* sim = new fs_sim();
+    const fs_status r =
+        init_sim(sim, std::vector<double>(x, x + n), std::vector<double>(y, y + n),
+                 std::vector<double>(theta, theta + n), a);
+    if (r != FS_OK) {
+        g_last_error = sim->err;
+        delete sim;
+        return r;
+    }
+    *out = sim;
+    return FS_OK;
+}
+
+extern "C" void fs_destroy(fs_sim* sim) {
+    if (!sim) return;
+    if (sim->graph_exec) cudaGraphExecDestroy(sim->graph_exec);
+    sim->run.release(sim->stream);
+    sim->mem.release(sim->stream);
+    cudaStreamSynchronize(sim->stream);
+    delete sim;
+}
+
+extern "C" fs_status fs_set_stream(fs_sim* sim, void* stream) {
+    if (!sim) return fail(nullptr, FS_ERR_INVALID, "sim is NULL");
+    sim->stream = (cudaStream_t)stream;
+    return FS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Parameters and the neighbour build
+// ---------------------------------------------------------------------------
+
+static bool bad_double(double v) { return !std::isfinite(v); }
+
+fs_status fs_build_sim(fs_sim* sim) {
+    cudaStream_t st = sim->stream;
+    const int64_t n = sim->n;
+    const fs_params& p = sim->p;
+    sim->mem.release(st);
+    sim->fields_valid = false;
+
+    // ---- temporaries of the build
+    Arena tmp;
+    auto talloc = [&](void** q, size_t b) { return tmp.alloc(q, b, st); };
+    double *dx = nullptr, *dy = nullptr;
+    uint16_t* dcls = nullptr;
+    double2* dcs = nullptr;
+    const size_t ncls = sim->cls_cos.size();
+    std::vector<double2> cs64(ncls);
+    for (size_t c = 0; c < ncls; ++c) cs64[c] = make_double2(sim->cls_cos[c], sim->cls_sin[c]);
+    CK(talloc((void**)&dx, 8 * n), "alloc");
+    CK(talloc((void**)&dy, 8 * n), "alloc");
+    CK(talloc((void**)&dcls, 2 * n), "alloc");
+    CK(talloc((void**)&dcs, 16 * ncls), "alloc");
+    CK(cudaMemcpyAsync(dx, sim->x.data(), 8 * n, cudaMemcpyHostToDevice, st), "upload");
+    CK(cudaMemcpyAsync(dy, sim->y.data(), 8 * n, cudaMemcpyHostToDevice, st), "upload");
+    CK(cudaMemcpyAsync(dcls, sim->cls.data(), 2 * n, cudaMemcpyHostToDevice, st), "upload");
+    CK(cudaMemcpyAsync(dcs, cs64.data(), 16 * ncls, cudaMemcpyHostToDevice, st), "upload");
+
+    BuildIn in;
+    in.n = n;
+    in.x = dx;
+    in.y = dy;
+    in.cls = dcls;
+    in.cs = dcs;
+    const double rc = p.cutoff * sim->a;
+    in.rc2 = rc * rc * (1.0 + 1e-9);
+    in.alpha = p.alpha;
+
+    BuildWork w;
+    double xmin = sim->x[0], xmax = sim->x[0], ymin = sim->y[0], ymax = sim->y[0];
+    for (int64_t i = 1; i < n; ++i) {
+        xmin = std::min(xmin, sim->x[i]);
+        xmax = std::max(xmax, sim->x[i]);
+        ymin = std::min(ymin, sim->y[i]);
+        ymax = std::max(ymax, sim->y[i]);
+    }
+    double cell = rc * 1.0001;
+    auto dims = [&](double c, int64_t& gx, int64_t& gy) {
+        gx = (int64_t)std::floor((xmax - xmin) / c) + 1;
+        gy = (int64_t)std::floor((ymax - ymin) / c) + 1;
+    };
+    dims(cell, w.gx, w.gy);
+    while ((double)w.gx * (double)w.gy > 4.0 * (double)n + 4096.0) {
+        cell *= 2.0;
+        dims(cell, w.gx, w.gy);
+    }
+    w.xmin = xmin;
+    w.ymin = ymin;
+    w.cell = cell;
+    const int64_t ncell = w.gx * w.gy;
+    CK(talloc((void**)&w.cell_of, 4 * n), "alloc");
+    CK(talloc((void**)&w.cell_cnt, 4 * ncell), "alloc");
+    CK(talloc((void**)&w.cell_start, 4 * (ncell + 1)), "alloc");
+    CK(talloc((void**)&w.items, 4 * n), "alloc");
+    CK(talloc((void**)&w.tmp64, 8 * (ncell + 1)), "alloc");
+    CK(talloc((void**)&w.tmp64b, 8 * (ncell + 1)), "alloc");
+    CK(talloc((void**)&w.deg_pad, 8 * n), "alloc");
+    const int64_t scr = std::max(scan_scratch_elems(ncell + 1), scan_scratch_elems(n + 1)) + 8;
+    CK(talloc((void**)&w.scratch, 8 * scr), "alloc");
+    CK(talloc((void**)&w.stats, sizeof(BuildStats)), "alloc");
+    int64_t* rp_tmp = nullptr;
+    CK(talloc((void**)&rp_tmp, 8 * (n + 1)), "alloc");
+
+    CK(build_cells(in, w, st), "cell grid");
+    CK(build_degrees(in, w, st), "degrees");
+    CK(build_rows(in, w, rp_tmp, st), "row scan");
+    BuildStats stats;
+    int64_t nnzp = 0;
+    CK(cudaMemcpyAsync(&stats, w.stats, sizeof(stats), cudaMemcpyDeviceToHost, st), "stats");
+    CK(cudaMemcpyAsync(&nnzp, rp_tmp + n, 8, cudaMemcpyDeviceToHost, st), "stats");
+    CK(cudaStreamSynchronize(st), "build sync");
+    if (stats.max_deg > kMaxPaddedDegree) {
+        tmp.release(st);
+        return fail(sim, FS_ERR_INVALID,
+                    "neighbourhood too large: " + std::to_string(stats.max_deg) +
+                        " neighbours (max " + std::to_string(kMaxPaddedDegree) +
+                        "); reduce the cutoff");
+    }
+    double bound;
+    memcpy(&bound, &stats.bound_bits, 8);
+    bound *= 1.000001;
+    int e64 = 0, e32 = 0;
+    if (bound > 0.0) {
+        e64 = (int)std::floor(62.0 - std::log2(bound));
+        e32 = (int)std::floor(30.0 - std::log2(bound));
+    }
+    e64 = std::max(-900, std::min(e64, 900));
+    e32 = std::max(-900, std::min(e32, 900));
+    sim->e64 = e64;
+    sim->e32 = e32;
+    sim->nnzp = nnzp;
+    sim->max_deg = stats.max_deg;
+
+    // ---- persistent arrays
+    Inst& I = sim->inst;
+    memset(&I, 0, sizeof(I));
+    I.n = n;
+    I.nnzp = nnzp;
+    I.prec = p.precision;
+    auto palloc = [&](void** q, size_t b) { return sim->mem.alloc(q, b, st); };
+    int64_t* rp = nullptr;
+    int32_t* col = nullptr;
+    longlong2* pq64 = nullptr;
+    long long* qt64 = nullptr;
+    int2* pq32 = nullptr;
+    int* qt32 = nullptr;
+    CK(palloc((void**)&rp, 8 * (n + 1)), "alloc");
+    CK(palloc((void**)&col, 4 * nnzp), "alloc");
+    CK(palloc((void**)&pq64, 16 * nnzp), "alloc");
+    CK(palloc((void**)&qt64, 8 * nnzp), "alloc");
+    if (p.precision == FS_FP32_RECHECK) {
+        CK(palloc((void**)&pq32, 8 * nnzp), "alloc");
+        CK(palloc((void**)&qt32, 4 * nnzp), "alloc");
+    } else {
+        // the fill kernel writes both widths; the 32-bit ones go to scratch
+        CK(talloc((void**)&pq32, 8 * nnzp), "alloc");
+        CK(talloc((void**)&qt32, 4 * nnzp), "alloc");
+    }
+    CK(cudaMemcpyAsync(rp, rp_tmp, 8 * (n + 1), cudaMemcpyDeviceToDevice, st), "copy");
+    BuildOut o;
+    o.scale64 = std::ldexp(1.0, e64);
+    o.scale32 = std::ldexp(1.0, e32);
+    o.rp = rp;
+    o.col = col;
+    o.pq64 = pq64;
+    o.qt64 = qt64;
+    o.pq32 = pq32;
+    o.qt32 = qt32;
+    CK(build_fill(in, w, o, st), "fill");
+    I.rp = rp;
+    I.col = col;
+    I.pq64 = pq64;
+    I.qt64 = qt64;
+    I.pq32 = p.precision == FS_FP32_RECHECK ? pq32 : nullptr;
+    I.qt32 = p.precision == FS_FP32_RECHECK ? qt32 : nullptr;
+
+    // islands
+    int8_t* s = nullptr;
+    double* hk64 = nullptr;
+    float* hk32 = nullptr;
+    uint16_t* cls = nullptr;
+    double2* c64 = nullptr;
+    float2* c32 = nullptr;
+    CK(palloc((void**)&s, n), "alloc");
+    CK(palloc((void**)&hk64, 8 * n), "alloc");
+    CK(palloc((void**)&hk32, 4 * n), "alloc");
+    CK(palloc((void**)&cls, 2 * n), "alloc");
+    CK(palloc((void**)&c64, 16 * ncls), "alloc");
+    CK(palloc((void**)&c32, 8 * ncls), "alloc");
+    std::vector<float2> cs32(ncls);
+    for (size_t c = 0; c < ncls; ++c)
+        cs32[c] = make_float2((float)sim->cls_cos[c], (float)sim->cls_sin[c]);
+    CK(cudaMemsetAsync(s, 1, n, st), "init spins");
+    CK(cudaMemcpyAsync(cls, dcls, 2 * n, cudaMemcpyDeviceToDevice, st), "copy");
+    CK(cudaMemcpyAsync(c64, cs64.data(), 16 * ncls, cudaMemcpyHostToDevice, st), "upload");
+    CK(cudaMemcpyAsync(c32, cs32.data(), 8 * ncls, cudaMemcpyHostToDevice, st), "upload");
+    I.s = s;
+    I.hk64 = hk64;
+    I.hk32 = hk32;
+    I.cls = cls;
+    I.cs64 = c64;
+    I.cs32 = c32;
+
+    CK(palloc((void**)&I.h64, 16 * n), "alloc");
+    if (p.precision == FS_FP32_RECHECK) {
+        CK(palloc((void**)&I.h32, 8 * n), "alloc");
+        CK(palloc((void**)&I.key32, 8 * n), "alloc");
+        CK(palloc((void**)&I.lo32, 4 * n), "alloc");
+    } else {
+        CK(palloc((void**)&I.key64, 8 * n), "alloc");
+    }
+    CK(palloc((void**)&I.ext64, 16 * ncls), "alloc");
+    CK(palloc((void**)&I.ext32, 8 * ncls), "alloc");
+    I.nclass = (int32_t)ncls;
+    if (p.sigma_th > 0.0) CK(palloc((void**)&I.th32, 8 * n), "alloc");
+
+    // max-tree levels above the leaves, fan-out 32
+    int nlev = 0;
+    int64_t cnt = (n + 31) / 32, total = 0;
+    for (;;) {
+        if (nlev >= kMaxLevels) return fail(sim, FS_ERR_INVALID, "system too large for the tree");
+        I.lvl_n[nlev] = (int32_t)cnt;
+        I.lvl_off[nlev] = total;
+        total += cnt;
+        ++nlev;
+        if (cnt == 1) break;
+        cnt = (cnt + 31) / 32;
+    }
+    I.nlev = nlev;
+    CK(palloc((void**)&I.tree, 16 * total), "alloc");
+    CK(palloc((void**)&sim->tcnt, 4 * total), "alloc");
+    CK(cudaMemsetAsync(sim->tcnt, 0, 4 * total, st), "init");
+    CK(palloc((void**)&sim->d_state, sizeof(InstState)), "alloc");
+    CK(palloc((void**)&sim->d_inst, sizeof(Inst)), "alloc");
+    CK(palloc((void**)&sim->d_task_start, 16), "alloc");
+    CK(palloc((void**)&sim->d_tcnts, 8), "alloc");
+    CK(palloc((void**)&sim->d_work, 16), "alloc");
+    CK(palloc((void**)&sim->d_field, 16), "alloc");
+    CK(palloc((void**)&sim->d_eval, 8 * 5 * n), "alloc");
+    const int64_t ts[2] = {0, (n + 31) / 32};
+    CK(cudaMemcpyAsync(sim->d_task_start, ts, 16, cudaMemcpyHostToDevice, st), "upload");
+    CK(cudaMemcpyAsync(sim->d_tcnts, &sim->tcnt, 8, cudaMemcpyHostToDevice, st), "upload");
+    const int32_t wk = 0;
+    CK(cudaMemcpyAsync(sim->d_work, &wk, 4, cudaMemcpyHostToDevice, st), "upload");
+
+    // parameters
+    I.b = p.b;
+    I.c = p.c;
+    I.pexp = 2.0 / p.gamma;
+    I.qexp = 2.0 / p.beta;
+    I.sigma = p.sigma_th;
+    I.bf = (float)p.b;
+    I.cf = (float)p.c;
+    I.pexpf = (float)I.pexp;
+    I.qexpf = (float)I.qexp;
+    I.sigmaf = (float)p.sigma_th;
+    I.inv64 = std::ldexp(1.0, -e64);
+    I.inv64f = (float)std::ldexp(1.0, -e64);
+    I.inv32 = (float)std::ldexp(1.0, -e32);
+    I.seed = p.seed;
+    I.instance = p.instance;
+    I.max_flips = p.max_flips_per_step > 0 ? p.max_flips_per_step : 16 * n;
+    I.st = sim->d_state;
+    // FP32 error model, bounds on |FP32 evaluation - FS_FP64 evaluation|:
+    //  - dh_abs: both fixed-point roundings over the longest row, plus the FP32
+    //    Box-Muller draw against the FP64 one (|z32 - z64| <= kThermalZErr);
+    //  - dh_rel: four float roundings of the field pieces (u = 2^-24);
+    //  - div_rel: the roundings of h_k, b or c, their product, the reciprocal and
+    //    the scaling, against the FP64 division (six u);
+    //  - pow_rel: powf (measured max 1.26 u on this GPU) and the bound arithmetic.
+    const double u = std::ldexp(1.0, -24);
+    const double quant = (double)stats.max_deg * (std::ldexp(1.0, -e32 - 1) +
+                                                  std::ldexp(1.0, -e64 - 1));
+    I.dh_abs = (float)((quant + p.sigma_th * kThermalZErr) * 1.5 + 1e-30);
+    I.dh_rel = (float)(4.0 * u);
+    I.div_rel = (float)(6.0 * u);
+    I.pow_rel = (float)(6.0 * u);
+    sim->lanes = choose_lanes((double)nnzp / (double)n / 4.0);
+
+    // coercive fields
+    CK(cudaMemcpyAsync(hk64, sim->hk.data(), 8 * n, cudaMemcpyHostToDevice, st), "upload");
+    sim->hk32.resize((size_t)n);
+    for (int64_t i = 0; i < n; ++i) sim->hk32[(size_t)i] = (float)sim->hk[(size_t)i];
+    CK(cudaMemcpyAsync(hk32, sim->hk32.data(), 4 * n, cudaMemcpyHostToDevice, st), "upload");
+    CK(cudaMemcpyAsync(sim->d_inst, &I, sizeof(Inst), cudaMemcpyHostToDevice, st), "upload");
+    tmp.release(st);
+    CK(cudaStreamSynchronize(st), "build");
+    sim->built = true;
+    return FS_OK;
+}
+
+extern "C" fs_status fs_set_params(fs_sim* sim, const fs_params* p) {
+    if (!sim || !p) return fail(sim, FS_ERR_INVALID, "NULL argument");
+    if (bad_double(p->alpha) || bad_double(p->hk) || bad_double(p->k_disorder) ||
+        bad_double(p->b) || bad_double(p->c) || bad_double(p->beta) || bad_double(p->gamma) ||
+        bad_double(p->cutoff) || bad_double(p->sigma_th))
+        return fail(sim, FS_ERR_INVALID, "non-finite parameter");
+    if (!(p->hk > 0.0) || !(p->b > 0.0) || !(p->c > 0.0) || !(p->beta > 0.0) ||
+        !(p->gamma > 0.0) || !(p->cutoff > 0.0) || p->sigma_th < 0.0 || p->k_disorder < 0.0 ||
+        p->alpha < 0.0)
+        return fail(sim, FS_ERR_INVALID, "parameter out of range");
+    if (p->precision != FS_FP64 && p->precision != FS_FP32_RECHECK)
+        return fail(sim, FS_ERR_INVALID, "unknown precision");
+    sim->p = *p;
+    draw_hk(sim->n, p->hk, p->k_disorder, p->seed, p->instance, sim->hk);
+    sim->built = false;
+    return fs_build_sim(sim);
+}
+
+static fs_status need_built(fs_sim* sim) {
+    if (!sim) return fail(nullptr, FS_ERR_INVALID, "sim is NULL");
+    if (!sim->built) return fail(sim, FS_ERR_STATE, "parameters not set");
+    return FS_OK;
+}
+
+extern "C" fs_status fs_set_hk(fs_sim* sim, const double* hk, int64_t n) {
+    fs_status r = need_built(sim);
+    if (r != FS_OK) return r;
+    if (!hk || n != sim->n) return fail(sim, FS_ERR_INVALID, "hk must have n values");
+    for (int64_t i = 0; i < n; ++i)
+        if (!(hk[i] > 0.0) || !std::isfinite(hk[i]))
+            return fail(sim, FS_ERR_INVALID, "hk values must be positive and finite");
+    sim->hk.assign(hk, hk + n);
+    sim->hk32.resize((size_t)n);
+    for (int64_t i = 0; i < n; ++i) sim->hk32[(size_t)i] = (float)hk[i];
+    CK(cudaMemcpyAsync((void*)sim->inst.hk64, sim->hk.data(), 8 * n, cudaMemcpyHostToDevice,
+                       sim->stream),
+       "upload");
+    CK(cudaMemcpyAsync((void*)sim->inst.hk32, sim->hk32.data(), 4 * n, cudaMemcpyHostToDevice,
+                       sim->stream),
+       "upload");
+    CK(cudaStreamSynchronize(sim->stream), "sync");
+    return FS_OK;
+}
+
+extern "C" fs_status fs_set_spins(fs_sim* sim, const int8_t* s, int64_t n) {
+    fs_status r = need_built(sim);
+    if (r != FS_OK) return r;
+    if (!s || n != sim->n) return fail(sim, FS_ERR_INVALID, "spins must have n values");
+    for (int64_t i = 0; i < n; ++i)
+        if (s[i] != 1 && s[i] != -1) return fail(sim, FS_ERR_INVALID, "spins must be +1 or -1");
+    CK(cudaMemcpyAsync(sim->inst.s, s, n, cudaMemcpyHostToDevice, sim->stream), "upload");
+    CK(cudaStreamSynchronize(sim->stream), "sync");
+    sim->fields_valid = false;
+    return FS_OK;
+}
+
+extern "C" fs_status fs_set_field(fs_sim* sim, double hx, double hy, uint32_t step) {
+    fs_status r = need_built(sim);
+    if (r != FS_OK) return r;
+    if (bad_double(hx) || bad_double(hy)) return fail(sim, FS_ERR_INVALID, "non-finite field");
+    sim->hx = hx;
+    sim->hy = hy;
+    sim->step = step;
+    return FS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Protocol driver
+// ---------------------------------------------------------------------------
+
+namespace fs {
+
+int relax_smem_budget(int64_t n) {
+    (void)n;
+    return 96 * 1024;
+}
+
+// Queues K field steps of one simulation (sweep + relax per step). The
+// descriptor's protocol fields must already point at device buffers.
+cudaError_t enqueue_steps(fs_sim* sim, int64_t K, int resweep, cudaStream_t st) {
+    SweepLaunch S;
+    S.tab = sim->d_inst;
+    S.task_start = sim->d_task_start;
+    S.n_inst = 1;
+    S.total_tasks = (sim->n + 31) / 32;
+    S.tcnts = sim->d_tcnts;
+    S.prec = sim->p.precision;
+    S.lanes_per_row = sim->lanes;
+    RelaxLaunch R;
+    R.tab = sim->d_inst;
+    R.work = sim->d_work;
+    R.n_work = 1;
+    R.prec = sim->p.precision;
+    R.smem_budget = relax_smem_budget(sim->n);
+    for (int64_t t = 0; t < K; ++t) {
+        S.resweep = resweep ? 1 : 0;
+        cudaError_t e = launch_sweep(S, st);
+        if (e != cudaSuccess) return e;
+        e = launch_relax(R, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace fs
+
+struct RunBufs {
+    double* hx = nullptr;
+    double* hy = nullptr;
+    uint32_t* ls = nullptr;
+    uint32_t* lk = nullptr;
+    int64_t* fps = nullptr;
+};
+
+static fs_status run_device(fs_sim* sim, const double* d_hx, const double* d_hy, int64_t K,
+                            uint32_t step0, int32_t resweep, uint32_t* d_ls, uint32_t* d_lk,
+                            int64_t log_cap, int64_t* d_fps, uint64_t hash0) {
+    cudaStream_t st = sim->stream;
+    Inst I = sim->inst;
+    I.phx = d_hx;
+    I.phy = d_hy;
+    I.K = K;
+    I.step0 = step0;
+    I.resweep = resweep;
+    I.log_step = d_ls;
+    I.log_spin = d_lk;
+    I.log_cap = (d_ls && d_lk) ? log_cap : 0;
+    I.flips_per_step = d_fps;
+    InstState S;
+    memset(&S, 0, sizeof(S));
+    S.hash = hash0;
+    S.init = sim->fields_valid ? 0 : 1;
+    sim->inst_run = I;
+    CK(cudaMemcpyAsync(sim->d_inst, &sim->inst_run, sizeof(Inst), cudaMemcpyHostToDevice, st),
+       "upload");
+    sim->state_host = S;
+    CK(cudaMemcpyAsync(sim->d_state, &sim->state_host, sizeof(S), cudaMemcpyHostToDevice, st),
+       "upload");
+    CK(enqueue_steps(sim, K, resweep, st), "launch");
+    if (K > 0) sim->fields_valid = true;
+    return FS_OK;
+}
+
+static fs_status finish_run(fs_sim* sim, InstState* out) {
+    CK(cudaMemcpyAsync(&sim->state_host, sim->d_state, sizeof(InstState), cudaMemcpyDeviceToHost,
+                       sim->stream),
+       "download");
+    CK(cudaStreamSynchronize(sim->stream), "protocol");
+    *out = sim->state_host;
+    sim->rechecks += out->rechecks;
+    sim->fallbacks += out->fallbacks;
+    if (out->status == ST_NOT_CONVERGED)
+        return fail(sim, FS_ERR_NOT_CONVERGED, "a relax exceeded max_flips_per_step");
+    if (out->status == ST_BOUNDS)
+        return fail(sim, FS_ERR_BOUNDS, "FP64 recheck did not settle (internal error)");
+    if (out->status != ST_OK) return fail(sim, FS_ERR_CUDA, "device status " +
+                                                                std::to_string(out->status));
+    return FS_OK;
+}
+
+extern "C" fs_status fs_run_protocol(fs_sim* sim, const double* hx, const double* hy, int64_t K,
+                                     uint32_t step0, int32_t resweep, uint32_t* log_step,
+                                     uint32_t* log_spin, int64_t log_cap,
+                                     int64_t* flips_per_step, uint64_t* seq_hash,
+                                     int64_t* n_flips) {
+    fs_status r = need_built(sim);
+    if (r != FS_OK) return r;
+    if (K < 0 || (K > 0 && (!hx || !hy)) || !seq_hash || !n_flips)
+        return fail(sim, FS_ERR_INVALID, "bad protocol arguments");
+    if (log_cap < 0) return fail(sim, FS_ERR_INVALID, "log_cap < 0");
+    for (int64_t t = 0; t < K; ++t)
+        if (bad_double(hx[t]) || bad_double(hy[t]))
+            return fail(sim, FS_ERR_INVALID, "non-finite field value");
+    const bool want_log = log_step && log_spin && log_cap > 0;
+    cudaStream_t st = sim->stream;
+    sim->run.release(st);
+    RunBufs b;
+    auto ralloc = [&](void** q, size_t n) { return sim->run.alloc(q, n, st); };
+    CK(ralloc((void**)&b.hx, 8 * std::max<int64_t>(K, 1)), "alloc");
+    CK(ralloc((void**)&b.hy, 8 * std::max<int64_t>(K, 1)), "alloc");
+    if (want_log) {
+        CK(ralloc((void**)&b.ls, 4 * log_cap), "alloc");
+        CK(ralloc((void**)&b.lk, 4 * log_cap), "alloc");
+    }
+    if (flips_per_step) CK(ralloc((void**)&b.fps, 8 * std::max<int64_t>(K, 1)), "alloc");
+    if (K > 0) {
+        CK(cudaMemcpyAsync(b.hx, hx, 8 * K, cudaMemcpyHostToDevice, st), "upload");
+        CK(cudaMemcpyAsync(b.hy, hy, 8 * K, cudaMemcpyHostToDevice, st), "upload");
+    }
+    r = run_device(sim, b.hx, b.hy, K, step0, resweep, b.ls, b.lk, log_cap, b.fps, *seq_hash);
+    if (r != FS_OK) return r;
+    InstState S;
+    r = finish_run(sim, &S);
+    const int64_t m = std::min<int64_t>(S.n_flips, want_log ? log_cap : 0);
+    if (m > 0) {
+        CK(cudaMemcpyAsync(log_step, b.ls, 4 * m, cudaMemcpyDeviceToHost, st), "download");
+        CK(cudaMemcpyAsync(log_spin, b.lk, 4 * m, cudaMemcpyDeviceToHost, st), "download");
+    }
+    if (flips_per_step && K > 0)
+        CK(cudaMemcpyAsync(flips_per_step, b.fps, 8 * K, cudaMemcpyDeviceToHost, st), "download");
+    CK(cudaStreamSynchronize(st), "download");
+    *seq_hash = S.hash;
+    *n_flips = S.n_flips;
+    if (K > 0) {
+        sim->hx = hx[K - 1];
+        sim->hy = hy[K - 1];
+        sim->step = step0 + (uint32_t)(K - 1);
+    }
+    return r;
+}
+
+// d_out: {status, n_flips, hash, rechecks}
+__global__ void k_copy_out(const InstState* st, uint64_t* out) {
+    out[0] = (uint64_t)(int64_t)st->status;
+    out[1] = (uint64_t)st->n_flips;
+    out[2] = st->hash;
+    out[3] = (uint64_t)st->rechecks;
+}
+
+extern "C" fs_status fs_run_protocol_dev(fs_sim* sim, const double* d_hx, const double* d_hy,
+                                         int64_t K, uint32_t step0, int32_t resweep,
+                                         uint32_t* d_log_step, uint32_t* d_log_spin,
+                                         int64_t log_cap, int64_t* d_flips_per_step,
+                                         uint64_t* d_out) {
+    fs_status r = need_built(sim);
+    if (r != FS_OK) return r;
+    if (K < 0 || (K > 0 && (!d_hx || !d_hy)) || !d_out || log_cap < 0)
+        return fail(sim, FS_ERR_INVALID, "bad protocol arguments");
+    r = run_device(sim, d_hx, d_hy, K, step0, resweep, d_log_step, d_log_spin, log_cap,
+                   d_flips_per_step, fs_hash_init());
+    if (r != FS_OK) return r;
+    k_copy_out<<<1, 1, 0, sim->stream>>>(sim->d_state, d_out);
+    CK(cudaGetLastError(), "launch");
+    return FS_OK;
+}
+
+extern "C" fs_status fs_relax(fs_sim* sim, uint32_t* log_spin, int64_t log_cap,
+                              int64_t* n_flips) {
+    fs_status r = need_built(sim);
+    if (r != FS_OK) return r;
+    if (!n_flips || log_cap < 0) return fail(sim, FS_ERR_INVALID, "bad arguments");
+    std::vector<uint32_t> ls((size_t)std::max<int64_t>(log_cap, 0));
+    uint64_t h = fs_hash_init();
+    const double hx = sim->hx, hy = sim->hy;
+    return fs_run_protocol(sim, &hx, &hy, 1, sim->step, 1, log_cap > 0 ? ls.data() : nullptr,
+                           log_cap > 0 ? log_spin : nullptr, log_cap, nullptr, &h, n_flips);
+}
+
+// ---------------------------------------------------------------------------
+// Read-back
+// ---------------------------------------------------------------------------
+
+extern "C" fs_status fs_get_spins(const fs_sim* csim, int8_t* out, int64_t n) {
+    fs_sim* sim = const_cast<fs_sim*>(csim);
+    fs_status r = need_built(sim);
+    if (r != FS_OK) return r;
+    if (!out || n != sim->n) return fail(sim, FS_ERR_INVALID, "out must hold n values");
+    CK(cudaMemcpyAsync(out, sim->inst.s, n, cudaMemcpyDeviceToHost, sim->stream), "download");
+    CK(cudaStreamSynchronize(sim->stream), "sync");
+    return FS_OK;
+}
+
+// Brings the dipolar sums up to date for the current spins (one resweep).
+static fs_status refresh_fields(fs_sim* sim) {
+    if (sim->fields_valid) return FS_OK;
+    cudaStream_t st = sim->stream;
+    double f[2] = {sim->hx, sim->hy};
+    CK(cudaMemcpyAsync(sim->d_field, f, 16, cudaMemcpyHostToDevice, st), "upload");
+    Inst I = sim->inst;
+    I.phx = sim->d_field;
+    I.phy = sim->d_field + 1;
+    I.K = 1;
+    I.step0 = sim->step;
+    sim->inst_run = I;
+    CK(cudaMemcpyAsync(sim->d_inst, &sim->inst_run, sizeof(Inst), cudaMemcpyHostToDevice, st),
+       "upload");
+    memset(&sim->state_host, 0, sizeof(InstState));
+    sim->state_host.init = 1;
+    CK(cudaMemcpyAsync(sim->d_state, &sim->state_host, sizeof(InstState), cudaMemcpyHostToDevice,
+                       st),
+       "upload");
+    SweepLaunch S;
+    S.tab = sim->d_inst;
+    S.task_start = sim->d_task_start;
+    S.n_inst = 1;
+    S.total_tasks = (sim->n + 31) / 32;
+    S.tcnts = sim->d_tcnts;
+    S.prec = sim->p.precision;
+    S.resweep = 1;
+    S.lanes_per_row = sim->lanes;
+    CK(launch_sweep(S, st), "sweep");
+    CK(cudaStreamSynchronize(st), "sweep");
+    sim->fields_valid = true;
+    return FS_OK;
+}
+
+static fs_status eval_into(fs_sim* sim, double* hpar, double* hperp, double* lhs, double* lo,
+                           double* hi, int64_t n) {
+    fs_status r = need_built(sim);
+    if (r != FS_OK) return r;
+    if (n != sim->n) return fail(sim, FS_ERR_INVALID, "outputs must hold n values");
+    r = refresh_fields(sim);
+    if (r != FS_OK) return r;
+    cudaStream_t st = sim->stream;
+    Inst I = sim->inst;
+    sim->inst_run = I;
+    CK(cudaMemcpyAsync(sim->d_inst, &sim->inst_run, sizeof(Inst), cudaMemcpyHostToDevice, st),
+       "upload");
+    double* d = sim->d_eval;
+    CK(launch_eval_all(sim->d_inst, n, sim->hx, sim->hy, sim->step, d, st), "eval");
+    double* outs[5] = {hpar, hperp, lhs, lo, hi};
+    for (int q = 0; q < 5; ++q)
+        if (outs[q])
+            CK(cudaMemcpyAsync(outs[q], d + q * n, 8 * n, cudaMemcpyDeviceToHost, st), "download");
+    CK(cudaStreamSynchronize(st), "download");
+    return FS_OK;
+}
+
+extern "C" fs_status fs_get_fields(fs_sim* sim, double* h_par, double* h_perp, int64_t n) {
+    return eval_into(sim, h_par, h_perp, nullptr, nullptr, nullptr, n);
+}
+
+extern "C" fs_status fs_get_lhs(fs_sim* sim, double* lhs, double* lo, double* hi, int64_t n) {
+    return eval_into(sim, nullptr, nullptr, lhs, lo, hi, n);
+}
+
+extern "C" fs_status fs_get_hk(const fs_sim* csim, double* out, int64_t n) {
+    fs_sim* sim = const_cast<fs_sim*>(csim);
+    fs_status r = need_built(sim);
+    if (r != FS_OK) return r;
+    if (!out || n != sim->n) return fail(sim, FS_ERR_INVALID, "out must hold n values");
+    memcpy(out, sim->hk.data(), 8 * n);
+    return FS_OK;
+}
+
+extern "C" fs_status fs_get_geometry(const fs_sim* csim, double* x, double* y, double* theta,
+                                     int64_t n) {
+    fs_sim* sim = const_cast<fs_sim*>(csim);
+    if (!sim) return fail(nullptr, FS_ERR_INVALID, "sim is NULL");
+    if (n != sim->n) return fail(sim, FS_ERR_INVALID, "outputs must hold n values");
+    if (x) memcpy(x, sim->x.data(), 8 * n);
+    if (y) memcpy(y, sim->y.data(), 8 * n);
+    if (theta) memcpy(theta, sim->theta.data(), 8 * n);
+    return FS_OK;
+}
+
+extern "C" fs_status fs_get_info(const fs_sim* csim, fs_info* out) {
+    fs_sim* sim = const_cast<fs_sim*>(csim);
+    if (!sim || !out) return fail(sim, FS_ERR_INVALID, "NULL argument");
+    memset(out, 0, sizeof(*out));
+    out->n = sim->n;
+    if (!sim->built) return FS_OK;
+    out->nnz_padded = sim->nnzp;
+    out->max_degree = sim->max_deg;
+    out->e64 = sim->e64;
+    out->e32 = sim->e32;
+    out->device_bytes = sim->mem.bytes;
+    out->band_rel = sim->inst.pow_rel + sim->inst.div_rel + sim->inst.dh_rel;
+    out->band_abs = sim->inst.dh_abs;
+    // unpadded nnz: count non-self entries
+    std::vector<int64_t> rp((size_t)sim->n + 1);
+    std::vector<int32_t> col((size_t)sim->nnzp);
+    CK(cudaMemcpyAsync(rp.data(), sim->inst.rp, 8 * (sim->n + 1), cudaMemcpyDeviceToHost,
+                       sim->stream),
+       "download");
+    CK(cudaMemcpyAsync(col.data(), sim->inst.col, 4 * sim->nnzp, cudaMemcpyDeviceToHost,
+                       sim->stream),
+       "download");
+    CK(cudaStreamSynchronize(sim->stream), "sync");
+    int64_t nnz = 0;
+    for (int64_t i = 0; i < sim->n; ++i)
+        for (int64_t e = rp[(size_t)i]; e < rp[(size_t)i + 1]; ++e) nnz += col[(size_t)e] != i;
+    out->nnz = nnz;
+    return FS_OK;
+}
+
+extern "C" fs_status fs_get_csr(const fs_sim* csim, int64_t* row_ptr, int32_t* col_out,
+                                double* P, double* Q) {
+    fs_sim* sim = const_cast<fs_sim*>(csim);
+    fs_status r = need_built(sim);
+    if (r != FS_OK) return r;
+    const int64_t n = sim->n, nnzp = sim->nnzp;
+    std::vector<int64_t> rp((size_t)n + 1);
+    std::vector<int32_t> col((size_t)nnzp);
+    std::vector<longlong2> pq((size_t)nnzp);
+    cudaStream_t st = sim->stream;
+    CK(cudaMemcpyAsync(rp.data(), sim->inst.rp, 8 * (n + 1), cudaMemcpyDeviceToHost, st),
+       "download");
+    CK(cudaMemcpyAsync(col.data(), sim->inst.col, 4 * nnzp, cudaMemcpyDeviceToHost, st),
+       "download");
+    CK(cudaMemcpyAsync(pq.data(), sim->inst.pq64, 16 * nnzp, cudaMemcpyDeviceToHost, st),
+       "download");
+    CK(cudaStreamSynchronize(st), "sync");
+    const double inv = std::ldexp(1.0, -sim->e64);
+    int64_t q = 0;
+    if (row_ptr) row_ptr[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t e = rp[(size_t)i]; e < rp[(size_t)i + 1]; ++e) {
+            if (col[(size_t)e] == i) continue;
+            if (col_out) col_out[q] = col[(size_t)e];
+            if (P) P[q] = (double)pq[(size_t)e].x * inv;
+            if (Q) Q[q] = (double)pq[(size_t)e].y * inv;
+            ++q;
+        }
+        if (row_ptr) row_ptr[i + 1] = q;
+    }
+    return FS_OK;
+}

@@ -1,0 +1,236 @@
+// fs_batch.cu - many independent simulations advanced together (ensembles of
+// disorder realisations, parameter sweeps; Sec. "Simulation framework", runner).
+//
+// Per field step, one sweep launch covers the rows of every member (one warp per
+// 32 islands of any member, so the whole device streams the CSR at once), and one
+// relax launch gives every member its own CTA. The K-step protocol is captured in
+// a CUDA graph and replayed as one launch. Each member's arithmetic is exactly
+// that of a solo run: integer field sums and per-island evaluations do not depend
+// on what else is in flight.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/flatspin_b300.h"
+#include "fs_batch.h"
+#include "fs_common.cuh"
+#include "fs_internal.h"
+#include "fs_kernels.h"
+
+namespace fs {
+
+cudaError_t BatchTable::upload(const std::vector<fs_sim*>& sims,
+                               const std::vector<Inst>& descs, cudaStream_t st) {
+    const int n = (int)sims.size();
+    cudaError_t e;
+    if (n > cap) {
+        mem.release(st);
+        cap = std::max(n, 2 * cap);
+        if ((e = mem.alloc((void**)&tab, sizeof(Inst) * cap, st)) != cudaSuccess) return e;
+        if ((e = mem.alloc((void**)&task_start, 8 * (cap + 1), st)) != cudaSuccess) return e;
+        if ((e = mem.alloc((void**)&tcnts, 8 * cap, st)) != cudaSuccess) return e;
+        if ((e = mem.alloc((void**)&work, 4 * cap, st)) != cudaSuccess) return e;
+    }
+    h_tab = descs;
+    h_task.assign((size_t)n + 1, 0);
+    h_tcnt.resize((size_t)n);
+    h_work.resize((size_t)n);
+    double deg = 0.0, rows = 0.0;
+    for (int i = 0; i < n; ++i) {
+        h_task[(size_t)i + 1] = h_task[(size_t)i] + (sims[(size_t)i]->n + 31) / 32;
+        h_tcnt[(size_t)i] = sims[(size_t)i]->tcnt;
+        deg += (double)sims[(size_t)i]->nnzp;
+        rows += (double)sims[(size_t)i]->n;
+    }
+    // largest members first, so that long relaxes start early
+    std::vector<int> order((size_t)n);
+    for (int i = 0; i < n; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return sims[(size_t)a]->n > sims[(size_t)b]->n; });
+    for (int i = 0; i < n; ++i) h_work[(size_t)i] = order[(size_t)i];
+    total_tasks = h_task[(size_t)n];
+    n_inst = n;
+    lanes = choose_lanes(rows > 0 ? deg / rows / 4.0 : 4.0);
+    if (n == 0) return cudaSuccess;
+    if ((e = cudaMemcpyAsync(tab, h_tab.data(), sizeof(Inst) * n, cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaMemcpyAsync(task_start, h_task.data(), 8 * (n + 1), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpyAsync(tcnts, h_tcnt.data(), 8 * n, cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+        return e;
+    return cudaMemcpyAsync(work, h_work.data(), 4 * n, cudaMemcpyHostToDevice, st);
+}
+
+cudaError_t BatchTable::enqueue_step(int prec, int resweep, int smem, cudaStream_t st) const {
+    if (n_inst == 0) return cudaSuccess;
+    SweepLaunch S;
+    S.tab = tab;
+    S.task_start = task_start;
+    S.n_inst = n_inst;
+    S.total_tasks = total_tasks;
+    S.tcnts = tcnts;
+    S.prec = prec;
+    S.resweep = resweep;
+    S.lanes_per_row = lanes;
+    cudaError_t e = launch_sweep(S, st);
+    if (e != cudaSuccess) return e;
+    RelaxLaunch R;
+    R.tab = tab;
+    R.work = work;
+    R.n_work = n_inst;
+    R.prec = prec;
+    R.smem_budget = smem;
+    return launch_relax(R, st);
+}
+
+}  // namespace fs
+
+using namespace fs;
+
+extern "C" fs_status fs_batch_run_protocol(fs_sim* const* sims, int32_t n, const double* hx,
+                                           const double* hy, int64_t K, int32_t resweep,
+                                           int64_t* n_flips, uint64_t* seq_hash,
+                                           int32_t* status, int64_t* flips_per_step) {
+    if (!sims || n <= 0 || !sims[0]) return FS_ERR_INVALID;
+    fs_sim* lead = sims[0];
+    if (K < 0 || (K > 0 && (!hx || !hy)) || !n_flips || !seq_hash || !status) {
+        lead->err = "bad batch arguments";
+        return FS_ERR_INVALID;
+    }
+    std::vector<fs_sim*> v((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        if (!sims[i] || !sims[i]->built) {
+            lead->err = "batch member " + std::to_string(i) + " has no parameters";
+            return FS_ERR_STATE;
+        }
+        if (sims[i]->p.precision != lead->p.precision) {
+            lead->err = "batch members must share one precision";
+            return FS_ERR_INVALID;
+        }
+        v[(size_t)i] = sims[i];
+    }
+    // graphs cannot be captured on the legacy default stream: run the batch on a
+    // stream of its own, ordered after the lead's queued work
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        lead->err = "could not create a stream";
+        return FS_ERR_CUDA;
+    }
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    } guard{st};
+    Arena tmp;
+    double *dhx = nullptr, *dhy = nullptr;
+    int64_t* dfps = nullptr;
+    cudaError_t e;
+    auto bail = [&](cudaError_t err, const char* where) {
+        tmp.release(st);
+        cudaStreamSynchronize(st);
+        lead->err = std::string(where) + ": " + cudaGetErrorString(err);
+        return FS_ERR_CUDA;
+    };
+    // members' own work must be finished before the batch reuses their buffers
+    for (int i = 0; i < n; ++i)
+        if ((e = cudaStreamSynchronize(v[(size_t)i]->stream)) != cudaSuccess)
+            return bail(e, "sync");
+    if ((e = tmp.alloc((void**)&dhx, 8 * std::max<int64_t>(K, 1), st)) != cudaSuccess)
+        return bail(e, "alloc");
+    if ((e = tmp.alloc((void**)&dhy, 8 * std::max<int64_t>(K, 1), st)) != cudaSuccess)
+        return bail(e, "alloc");
+    if (flips_per_step &&
+        (e = tmp.alloc((void**)&dfps, 8 * std::max<int64_t>(K * n, 1), st)) != cudaSuccess)
+        return bail(e, "alloc");
+    if (K > 0) {
+        if ((e = cudaMemcpyAsync(dhx, hx, 8 * K, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return bail(e, "upload");
+        if ((e = cudaMemcpyAsync(dhy, hy, 8 * K, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return bail(e, "upload");
+    }
+    std::vector<Inst> descs((size_t)n);
+    std::vector<InstState> states((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        Inst I = v[(size_t)i]->inst;
+        I.phx = dhx;
+        I.phy = dhy;
+        I.K = K;
+        I.step0 = 0;
+        I.resweep = resweep;
+        I.log_step = nullptr;
+        I.log_spin = nullptr;
+        I.log_cap = 0;
+        I.flips_per_step = dfps ? dfps + (int64_t)i * K : nullptr;
+        descs[(size_t)i] = I;
+        memset(&states[(size_t)i], 0, sizeof(InstState));
+        states[(size_t)i].hash = seq_hash[i];
+        states[(size_t)i].init = v[(size_t)i]->fields_valid ? 0 : 1;
+        if ((e = cudaMemcpyAsync(v[(size_t)i]->d_state, &states[(size_t)i], sizeof(InstState),
+                                 cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return bail(e, "upload");
+    }
+    BatchTable B;
+    if ((e = B.upload(v, descs, st)) != cudaSuccess) return bail(e, "upload");
+    const int prec = lead->p.precision;
+    const int smem = relax_smem_budget(0);
+    if ((e = prepare_relax(prec, smem)) != cudaSuccess) return bail(e, "relax setup");
+    // capture the whole protocol in one graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return bail(e, "capture");
+    cudaError_t le = cudaSuccess;
+    for (int64_t t = 0; t < K && le == cudaSuccess; ++t)
+        le = B.enqueue_step(prec, resweep ? 1 : 0, smem, st);
+    e = cudaStreamEndCapture(st, &graph);
+    if (le != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return bail(le, "launch");
+    }
+    if (e != cudaSuccess) return bail(e, "capture");
+    if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return bail(e, "instantiate");
+    }
+    e = cudaGraphLaunch(exec, st);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        return bail(e, "graph launch");
+    }
+    for (int i = 0; i < n; ++i)
+        if ((e = cudaMemcpyAsync(&states[(size_t)i], v[(size_t)i]->d_state, sizeof(InstState),
+                                 cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return bail(e, "download");
+    if (flips_per_step && K > 0 &&
+        (e = cudaMemcpyAsync(flips_per_step, dfps, 8 * K * n, cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess)
+        return bail(e, "download");
+    e = cudaStreamSynchronize(st);
+    cudaGraphExecDestroy(exec);
+    if (e != cudaSuccess) return bail(e, "protocol");
+    tmp.release(st);
+    B.mem.release(st);
+    fs_status worst = FS_OK;
+    for (int i = 0; i < n; ++i) {
+        const InstState& S = states[(size_t)i];
+        n_flips[i] = S.n_flips;
+        seq_hash[i] = S.hash;
+        status[i] = S.status;
+        v[(size_t)i]->rechecks += S.rechecks;
+        v[(size_t)i]->fields_valid = K > 0 ? true : v[(size_t)i]->fields_valid;
+        if (S.status != ST_OK && worst == FS_OK) worst = (fs_status)S.status;
+    }
+    cudaStreamSynchronize(st);
+    if (worst != FS_OK) lead->err = "a batch member stopped early (see status[])";
+    return worst;
+}

@@ -1,0 +1,37 @@
+// fs_batch.h - device table of simulations advanced together (batches, server).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "fs_common.cuh"
+#include "fs_internal.h"
+
+namespace fs {
+
+struct BatchTable {
+    Arena mem;
+    int cap = 0;
+    Inst* tab = nullptr;
+    int64_t* task_start = nullptr;
+    unsigned** tcnts = nullptr;
+    int32_t* work = nullptr;
+    int n_inst = 0;
+    int64_t total_tasks = 0;
+    int lanes = 16;
+    std::vector<Inst> h_tab;
+    std::vector<int64_t> h_task;
+    std::vector<unsigned*> h_tcnt;
+    std::vector<int32_t> h_work;
+
+    cudaError_t upload(const std::vector<fs_sim*>& sims, const std::vector<Inst>& descs,
+                       cudaStream_t st);
+    // one field step of every member: a sweep over all rows, then one relax CTA each
+    cudaError_t enqueue_step(int prec, int resweep, int smem, cudaStream_t st) const;
+};
+
+cudaError_t prepare_relax(int prec, int smem);
+
+}  // namespace fs

@@ -1,0 +1,361 @@
+// fs_common.cuh - device-visible instance descriptor and the per-island
+// arithmetic shared by every kernel: Philox4x32-10, Box-Muller, the total field
+// in the island's frame (Eq. 2), the astroid left-hand side (Eq. 5) and the
+// anti-alignment test (Eq. 6), in FP64 and in FP32 with rigorous error bounds.
+//
+// Every floating-point expression that decides a flip is written with explicit
+// round-to-nearest intrinsics so that no compiler contraction can make two
+// kernels evaluate the same island differently.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fs {
+
+constexpr int kRowPad = 4;                // CSR rows padded to multiples of 4 entries
+constexpr int kMaxPaddedDegree = 1024;    // neighbours per island after padding
+constexpr int kFan = 32;                  // max-tree fan-out (one warp)
+constexpr int kMaxLevels = 8;             // tree levels above the leaves
+constexpr int kRelaxThreads = 1024;       // threads of one relax CTA
+constexpr int kRecheckCap = 256;          // FP64 recheck candidates per round
+
+// Device status codes (mirror fs_status).
+enum : int32_t {
+    ST_OK = 0,
+    ST_NOT_CONVERGED = 4,
+    ST_TIMEOUT = 5,
+    ST_BOUNDS = 6,
+};
+
+// Mutable per-simulation state in device memory.
+struct InstState {
+    int64_t t;          // next protocol step (0..K)
+    int64_t n_flips;    // flips so far in this protocol call
+    uint64_t hash;      // FNV-1a of (step, island) so far
+    int32_t status;     // ST_*
+    int32_t init;       // 1: the dipolar sums must be computed from scratch this step
+    double hx, hy;      // external field of the current step
+    uint32_t step;      // thermal step index of the current step
+    uint32_t pad;
+    int64_t rechecks;   // FP64 recheck rounds (FP32 path)
+    int64_t fallbacks;  // full-scan rechecks (candidate overflow)
+};
+
+// Read-only descriptor of one simulation (one entry of a batch table).
+struct Inst {
+    int64_t n;       // islands
+    int64_t nnzp;    // padded CSR entries
+    int32_t prec;    // 0 = FP64, 1 = FP32 + FP64 recheck
+    int32_t nlev;    // tree levels above the leaves; level nlev-1 is the root
+    int32_t nclass;  // distinct island angles
+    int32_t pad1;
+    int32_t lvl_n[kMaxLevels];
+    int64_t lvl_off[kMaxLevels];  // node offset of each level in `tree`
+    // neighbour tensors (rows padded with self-entries of zero weight)
+    const int64_t* rp;
+    const int32_t* col;
+    const longlong2* pq64;  // (P, Q) in 2^-e64 fixed point
+    const long long* qt64;  // transposed Q: field of the row island on col, col's frame
+    const int2* pq32;       // (P, Q) in 2^-e32 fixed point
+    const int* qt32;
+    // islands
+    int8_t* s;
+    const double* hk64;
+    const float* hk32;
+    const uint16_t* cls;    // angle class
+    const double2* cs64;    // (cos, sin) per class
+    const float2* cs32;
+    double2* ext64;         // external field projected on each class, current step
+    float2* ext32;
+    // fields and keys
+    longlong2* h64;         // dipolar (par, perp), exact 64-bit sums (both paths)
+    int2* h32;              // dipolar (par, perp), 32-bit sums (FP32 path)
+    float2* th32;           // thermal (par, perp) of the current step (sigma > 0)
+    unsigned long long* key32;  // FP32 path: (bits(hi) << 32) | ~i, 0 = not a candidate
+    float* lo32;                // FP32 path: certified lower bound of the LHS, -1 if none
+    double* key64;              // FP64 path: LHS when flippable, else 0
+    ulonglong2* tree;           // tree nodes (both paths, 16 B each)
+    // protocol
+    const double* phx;
+    const double* phy;
+    int64_t K;
+    uint32_t step0;
+    int32_t resweep;
+    uint32_t* log_step;
+    uint32_t* log_spin;
+    int64_t log_cap;
+    int64_t* flips_per_step;
+    // parameters
+    double b, c, pexp, qexp, sigma;
+    float bf, cf, pexpf, qexpf, sigmaf;
+    double inv64;   // 2^-e64
+    float inv64f;   // 2^-e64 as a float
+    float inv32;    // 2^-e32
+    uint64_t seed;
+    uint32_t instance;
+    int32_t pad0;
+    int64_t max_flips;
+    // FP32 error model: |h32 - h64| <= dh_abs + dh_rel * (|h_dip| + |h_ext| + |h_th|);
+    // div_rel bounds the relative error of |h| / (b h_k), pow_rel that of powf and of
+    // the bound arithmetic
+    float dh_abs, dh_rel, pow_rel, div_rel;
+    InstState* st;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and Box-Muller
+// ---------------------------------------------------------------------------
+
+__host__ __device__ __forceinline__ void philox_round(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#ifdef __CUDA_ARCH__
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]);
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]);
+#else
+    const uint32_t hi0 = (uint32_t)(((uint64_t)0xD2511F53u * c[0]) >> 32);
+    const uint32_t hi1 = (uint32_t)(((uint64_t)0xCD9E8D57u * c[2]) >> 32);
+#endif
+    const uint32_t lo0 = 0xD2511F53u * c[0];
+    const uint32_t lo1 = 0xCD9E8D57u * c[2];
+    const uint32_t n0 = hi1 ^ c[1] ^ k0;
+    const uint32_t n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+}
+
+// Ten rounds, key advanced by the Weyl constants between rounds.
+__host__ __device__ __forceinline__ void philox10(uint32_t c[4], uint64_t seed) {
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        philox_round(c, k0, k1);
+    }
+}
+
+// The 53-bit uniforms in (0,1): ((w_hi:w_lo) >> 11) + 1/2, times 2^-53.
+__host__ __device__ __forceinline__ uint64_t u53(uint32_t hi, uint32_t lo) {
+    return (((uint64_t)hi << 32) | (uint64_t)lo) >> 11;
+}
+
+// FP64 Box-Muller of one Philox output block.
+__device__ __forceinline__ void box_muller64(const uint32_t w[4], double* z0, double* z1) {
+    const double u1 = __dmul_rn(__dadd_rn((double)u53(w[0], w[1]), 0.5), 0x1.0p-53);
+    const double u2 = __dmul_rn(__dadd_rn((double)u53(w[2], w[3]), 0.5), 0x1.0p-53);
+    const double rad = sqrt(__dmul_rn(-2.0, log(u1)));
+    const double ang = __dmul_rn(2.0 * 3.14159265358979323846, u2);
+    double sn, cs;
+    sincos(ang, &sn, &cs);
+    *z0 = __dmul_rn(rad, cs);
+    *z1 = __dmul_rn(rad, sn);
+}
+
+// FP32 Box-Muller of the same block. ln(u1) is taken from u1 itself when
+// u1 < 1/2 and from log1p(-(1 - u1)) otherwise, with 1 - u1 formed exactly in
+// integers, so the result carries a small relative error at every u1.
+__device__ __forceinline__ void box_muller32(const uint32_t w[4], float* z0, float* z1) {
+    const uint64_t a = u53(w[0], w[1]);
+    const uint64_t b = u53(w[2], w[3]);
+    float l;
+    if (a < (1ull << 52)) {
+        const float u1 = __fmul_rn(__ull2float_rn(a) + 0.5f, 0x1.0p-53f);
+        l = logf(u1);
+    } else {
+        // 1 - u1 = (2^53 - a - 1/2) 2^-53
+        const uint64_t v = (1ull << 53) - a;
+        const float om = __fmul_rn(__fsub_rn(__ull2float_rn(v), 0.5f), 0x1.0p-53f);
+        l = log1pf(-om);
+    }
+    const float rad = sqrtf(__fmul_rn(-2.0f, l));
+    const float u2 = __fmul_rn(__ull2float_rn(b) + 0.5f, 0x1.0p-53f);
+    float sn, cs;
+    sincospif(__fmul_rn(2.0f, u2), &sn, &cs);
+    *z0 = __fmul_rn(rad, cs);
+    *z1 = __fmul_rn(rad, sn);
+}
+
+// Thermal field (par, perp) of island i at thermal step `step`: counter
+// (i, step, instance, 1).
+__device__ __forceinline__ void thermal64(const Inst& I, int64_t i, uint32_t step, double* tp,
+                                          double* tq) {
+    uint32_t c[4] = {(uint32_t)i, step, I.instance, 1u};
+    philox10(c, I.seed);
+    double z0, z1;
+    box_muller64(c, &z0, &z1);
+    *tp = __dmul_rn(I.sigma, z0);
+    *tq = __dmul_rn(I.sigma, z1);
+}
+
+__device__ __forceinline__ float2 thermal32(const Inst& I, int64_t i, uint32_t step) {
+    uint32_t c[4] = {(uint32_t)i, step, I.instance, 1u};
+    philox10(c, I.seed);
+    float z0, z1;
+    box_muller32(c, &z0, &z1);
+    return make_float2(__fmul_rn(I.sigmaf, z0), __fmul_rn(I.sigmaf, z1));
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 2 in the island's frame, Eq. 5 and Eq. 6
+// ---------------------------------------------------------------------------
+
+// Projection of the external field on an island's frame (h_ext . mhat,
+// h_ext . mhat_perp), in FP64. Both evaluations below take this same value (the
+// FP32 one rounded once), so its error is relative to the projection itself.
+__device__ __forceinline__ double2 ext_proj(double hx, double hy, double2 cs) {
+    return make_double2(__dadd_rn(__dmul_rn(hx, cs.x), __dmul_rn(hy, cs.y)),
+                        __dadd_rn(__dmul_rn(-hx, cs.y), __dmul_rn(hy, cs.x)));
+}
+
+// x^p for x >= 0 in FP64. p = 2/3 (gamma or beta = 3, the Stoner-Wohlfarth value)
+// is taken as cbrt(x^2), a few times cheaper than pow on this GPU.
+__device__ __forceinline__ double pow_pos(double x, double p) {
+    if (x <= 0.0) return 0.0;
+    if (p == 2.0 / 3.0) return cbrt(__dmul_rn(x, x));
+    return pow(x, p);
+}
+
+// Exact FP64 evaluation from the 64-bit fixed-point dipolar sums.
+struct Eval64 {
+    double hpar, hperp, lhs;
+    bool flippable;
+};
+
+__device__ __forceinline__ Eval64 eval64(const Inst& I, int s, long long dp, long long dq,
+                                         double hk, double2 ext, double tp, double tq) {
+    Eval64 e;
+    e.hpar = __dadd_rn(__dadd_rn(__dmul_rn((double)dp, I.inv64), ext.x), tp);
+    e.hperp = __dadd_rn(__dadd_rn(__dmul_rn((double)dq, I.inv64), ext.y), tq);
+    const double x = __ddiv_rn(fabs(e.hpar), __dmul_rn(I.b, hk));
+    const double y = __ddiv_rn(fabs(e.hperp), __dmul_rn(I.c, hk));
+    e.lhs = __dadd_rn(pow_pos(x, I.pexp), pow_pos(y, I.qexp));
+    e.flippable = ((double)s * e.hpar < 0.0) && (e.lhs > 1.0);
+    return e;
+}
+
+// FP32 evaluation with bounds: [lo, hi] contains the FS_FP64 value of the LHS;
+// `possible` = the island may be flippable in FP64, `certain` = it surely is.
+struct Eval32 {
+    float hpar, hperp, lhs, hi, lo;
+    bool possible, certain;
+};
+
+__device__ __forceinline__ float pow_nonneg(float x, float p) {
+    return x > 0.0f ? powf(x, p) : 0.0f;
+}
+
+// Bounds of one astroid term a^p, a = |h| / (b h_k), whose FP32 value t = powf(x, p)
+// was taken at x; u bounds the relative error of x. For p <= 1 the concave power
+// gives (x(1+u))^p <= x^p (1 + p u) and (x(1-u))^p >= x^p (1 - p u / (1 - u)); for
+// 1 < p <= 3, (1 + u)^(p-1) <= 2 on u <= 1/4 gives factors 1 + 2 p u and 1 - p u.
+// Outside u <= 1/4 the monotone bounds are evaluated directly. `r` is the
+// relative error of powf and of the factor arithmetic.
+__device__ __forceinline__ void term_bounds(float t, float x, float u, float p, float r,
+                                            float* hi, float* lo) {
+    if (u <= 0.25f && p <= 3.0f) {
+        const float g_hi = p <= 1.0f ? __fmul_rn(p, u) : __fmul_rn(2.0f * p, u);
+        const float g_lo = p <= 1.0f ? __fdiv_rn(__fmul_rn(p, u), __fsub_rn(1.0f, u))
+                                     : __fmul_rn(p, u);
+        *hi = __fmul_rn(__fmul_rn(t, __fadd_rn(1.0f, r)), __fadd_rn(1.0f, g_hi));
+        *lo = __fmul_rn(__fmul_rn(t, __fsub_rn(1.0f, r)), fmaxf(__fsub_rn(1.0f, g_lo), 0.0f));
+    } else {
+        *hi = __fmul_rn(pow_nonneg(__fmul_rn(x, __fadd_rn(1.0f, u)), p), __fadd_rn(1.0f, r));
+        *lo = u < 1.0f ? __fmul_rn(pow_nonneg(__fmul_rn(x, __fsub_rn(1.0f, u)), p),
+                                   __fsub_rn(1.0f, r))
+                       : 0.0f;
+    }
+}
+
+__device__ __forceinline__ Eval32 eval32(const Inst& I, int s, float dp, float dq, float hk,
+                                         float2 ext, float tp, float tq) {
+    Eval32 e;
+    e.hpar = __fadd_rn(__fadd_rn(dp, ext.x), tp);
+    e.hperp = __fadd_rn(__fadd_rn(dq, ext.y), tq);
+    // field error bound: fixed point + thermal draw (absolute), float roundings
+    const float dpar = __fadd_rn(I.dh_abs, __fmul_rn(I.dh_rel, __fadd_rn(__fadd_rn(fabsf(dp),
+                                                                     fabsf(ext.x)), fabsf(tp))));
+    const float dperp = __fadd_rn(I.dh_abs, __fmul_rn(I.dh_rel, __fadd_rn(__fadd_rn(fabsf(dq),
+                                                                      fabsf(ext.y)), fabsf(tq))));
+    const float ap = fabsf(e.hpar), aq = fabsf(e.hperp);
+    const float rb = __frcp_rn(__fmul_rn(I.bf, hk)), rc = __frcp_rn(__fmul_rn(I.cf, hk));
+    const float x = __fmul_rn(ap, rb), y = __fmul_rn(aq, rc);
+    const float tx = pow_nonneg(x, I.pexpf), ty = pow_nonneg(y, I.qexpf);
+    e.lhs = __fadd_rn(tx, ty);
+    // relative error of x and y (field bound + the scaling roundings)
+    const float ux = ap > 0.0f ? __fadd_rn(__fdiv_rn(dpar, ap), I.div_rel) : 2.0f;
+    const float uy = aq > 0.0f ? __fadd_rn(__fdiv_rn(dperp, aq), I.div_rel) : 2.0f;
+    float hx_, lx_, hy_, ly_;
+    if (ap > 0.0f) {
+        term_bounds(tx, x, ux, I.pexpf, I.pow_rel, &hx_, &lx_);
+    } else {  // |h_par| <= dpar
+        hx_ = __fmul_rn(pow_nonneg(__fmul_rn(__fmul_rn(dpar, rb), __fadd_rn(1.0f, I.div_rel)),
+                                   I.pexpf),
+                        __fadd_rn(1.0f, I.pow_rel));
+        lx_ = 0.0f;
+    }
+    if (aq > 0.0f) {
+        term_bounds(ty, y, uy, I.qexpf, I.pow_rel, &hy_, &ly_);
+    } else {
+        hy_ = __fmul_rn(pow_nonneg(__fmul_rn(__fmul_rn(dperp, rc), __fadd_rn(1.0f, I.div_rel)),
+                                   I.qexpf),
+                        __fadd_rn(1.0f, I.pow_rel));
+        ly_ = 0.0f;
+    }
+    e.hi = __fmul_rn(__fadd_rn(hx_, hy_), 1.0f + 0x1.0p-22f);
+    e.lo = __fmul_rn(__fadd_rn(lx_, ly_), 1.0f - 0x1.0p-22f);
+    const float sp = (float)s * e.hpar;
+    e.possible = (sp < dpar) && (e.hi > 1.0f);
+    e.certain = (sp < -dpar) && (e.lo > 1.0f);
+    return e;
+}
+
+// FP32 key: the upper bound of the LHS (order) with the lowest index winning ties.
+__device__ __forceinline__ unsigned long long key32_of(float hi, int64_t i) {
+    return ((unsigned long long)__float_as_uint(hi) << 32) |
+           (unsigned long long)(0xFFFFFFFFu - (uint32_t)i);
+}
+__device__ __forceinline__ float key32_hi(unsigned long long k) {
+    return __uint_as_float((uint32_t)(k >> 32));
+}
+__device__ __forceinline__ uint32_t key32_idx(unsigned long long k) {
+    return 0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFull);
+}
+
+// FP64 node order: larger LHS first, then lower index. (v, idx) packed in a
+// ulonglong2 as (double bits, index). Keys are non-negative doubles, whose bit
+// patterns order like their values, so the compare is integer-only.
+__device__ __forceinline__ bool better64(unsigned long long va, unsigned long long ia,
+                                         unsigned long long vb, unsigned long long ib) {
+    return va > vb || (va == vb && ia < ib);
+}
+
+// FP32 top-2 merge: node = (best, second best) key.
+__device__ __forceinline__ ulonglong2 top2(ulonglong2 a, ulonglong2 b) {
+    ulonglong2 r;
+    r.x = a.x > b.x ? a.x : b.x;
+    const unsigned long long lo = a.x > b.x ? b.x : a.x;
+    const unsigned long long s2 = a.y > b.y ? a.y : b.y;
+    r.y = lo > s2 ? lo : s2;
+    return r;
+}
+
+// FNV-1a over the 8 little-endian bytes of (step, island).
+__device__ __forceinline__ uint64_t fnv_flip(uint64_t h, uint32_t step, uint32_t spin) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        h ^= (step >> (8 * q)) & 0xFFu;
+        h *= 0x100000001b3ull;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        h ^= (spin >> (8 * q)) & 0xFFu;
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
+}  // namespace fs

@@ -1,0 +1,68 @@
+// fs_internal.h - the simulation object behind the opaque fs_sim handle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/flatspin_b300.h"
+#include "fs_common.cuh"
+
+namespace fs {
+
+// Stream-ordered device allocations owned by one object.
+struct Arena {
+    std::vector<void*> blocks;
+    int64_t bytes = 0;
+    cudaError_t alloc(void** out, size_t n, cudaStream_t st);
+    void release(cudaStream_t st);
+};
+
+int choose_lanes(double avg_groups);
+int relax_smem_budget(int64_t n);
+
+}  // namespace fs
+
+struct fs_sim {
+    // geometry (canonical order)
+    int64_t n = 0;
+    double a = 1.0;
+    std::vector<double> x, y, theta;
+    std::vector<uint16_t> cls;
+    std::vector<double> cls_cos, cls_sin;
+    // parameters
+    fs_params p{};
+    std::vector<double> hk;
+    std::vector<float> hk32;
+    bool built = false;
+    bool fields_valid = false;
+    // current external field and thermal step
+    double hx = 0.0, hy = 0.0;
+    uint32_t step = 0;
+    // device
+    cudaStream_t stream = nullptr;
+    fs::Arena mem;  // everything that lives as long as the parameters
+    fs::Arena run;  // per-call protocol buffers
+    fs::Inst inst{};      // descriptor (host copy)
+    fs::Inst inst_run{};  // descriptor of the queued call (host staging)
+    fs::InstState state_host{};
+    fs::Inst* d_inst = nullptr;
+    fs::InstState* d_state = nullptr;
+    int64_t* d_task_start = nullptr;
+    unsigned** d_tcnts = nullptr;
+    unsigned* tcnt = nullptr;
+    int32_t* d_work = nullptr;
+    double* d_field = nullptr;
+    double* d_eval = nullptr;
+    int64_t nnzp = 0;
+    int32_t max_deg = 0;
+    int32_t e64 = 0, e32 = 0;
+    int lanes = 16;
+    int64_t rechecks = 0, fallbacks = 0;
+    cudaGraphExec_t graph_exec = nullptr;
+    std::string err;
+};
+
+fs_status fs_build_sim(fs_sim* sim);

@@ -1,0 +1,39 @@
+// fs_kernels.h - launch interfaces of the sweep and relax kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fs_common.cuh"
+
+namespace fs {
+
+struct SweepLaunch {
+    const Inst* tab;            // device table of simulations
+    const int64_t* task_start;  // device [n_inst + 1]: first 32-island task of each
+    int n_inst;
+    int64_t total_tasks;
+    unsigned* const* tcnts;     // device [n_inst]: per-simulation tree counters
+    int prec;
+    int resweep;                // 0 margins only, 1 recompute the dipolar sums
+    int lanes_per_row;          // 4, 8, 16 or 32
+};
+
+struct RelaxLaunch {
+    const Inst* tab;
+    const int32_t* work;  // device [n_work]: simulation of each CTA
+    int n_work;
+    int prec;
+    int smem_budget;      // dynamic shared memory for the upper tree levels
+};
+
+cudaError_t launch_sweep(const SweepLaunch& L, cudaStream_t st);
+cudaError_t launch_relax(const RelaxLaunch& L, cudaStream_t st);
+cudaError_t prepare_relax(int prec, int smem);
+// out5 = [h_par | h_perp | lhs | lo | hi], 5 n doubles
+cudaError_t launch_eval_all(const Inst* tab, int64_t n, double hx, double hy, uint32_t step,
+                            double* out5, cudaStream_t st);
+int relax_threads();
+size_t relax_static_smem(int prec);
+
+}  // namespace fs

@@ -1,0 +1,293 @@
+// fs_sweep.cu - the full field-and-margin sweep (Sec. "Dynamics": at each
+// simulation step the total field on every island is calculated; Eq. 2, 3, 5, 6).
+//
+// One warp owns 32 consecutive islands (one node of the first tree level).
+// Sub-warps of W lanes stream one CSR row each: every lane reads a group of four
+// entries with 16-byte loads (column indices, then the fixed-point (P, Q)
+// coefficients), gathers the four spins, and accumulates the exact integer sums
+// s_j P_ij and s_j Q_ij; a shuffle butterfly inside the sub-warp finishes the row.
+// The per-row sums are staged in shared memory so that lane q then evaluates
+// island q: external and thermal fields, Eq. 5/6, the argmax key. A warp max
+// gives the first tree level; the last warp to finish a group of 32 sibling
+// nodes builds their parent (fenced counter), so the whole max-tree is ready
+// when the kernel ends.
+//
+// With resweep off, the exact sums kept up to date by the flips are read instead
+// of recomputed; integer sums make both modes bit-identical.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fs_common.cuh"
+#include "fs_kernels.h"
+
+namespace fs {
+
+namespace {
+
+constexpr int kSweepThreads = 256;
+constexpr int kSweepWarps = kSweepThreads / 32;
+
+__device__ __forceinline__ int find_inst(const int64_t* __restrict__ start, int n_inst,
+                                         int64_t task) {
+    int lo = 0, hi = n_inst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= task)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int sgn_sel(int8_t s, int v) { return s > 0 ? v : -v; }
+__device__ __forceinline__ long long sgn_sel(int8_t s, long long v) { return s > 0 ? v : -v; }
+
+// Merge of two FP64 nodes (LHS bits, index).
+__device__ __forceinline__ ulonglong2 best64(ulonglong2 a, ulonglong2 b) {
+    return better64(a.x, a.y, b.x, b.y) ? a : b;
+}
+
+template <int PREC>
+__device__ __forceinline__ ulonglong2 merge_node(ulonglong2 a, ulonglong2 b) {
+    if constexpr (PREC == 1)
+        return top2(a, b);
+    else
+        return best64(a, b);
+}
+
+template <int PREC>
+__device__ __forceinline__ ulonglong2 warp_merge(ulonglong2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ulonglong2 u;
+        u.x = __shfl_xor_sync(0xffffffffu, v.x, o);
+        u.y = __shfl_xor_sync(0xffffffffu, v.y, o);
+        v = merge_node<PREC>(v, u);
+    }
+    return v;
+}
+
+template <int PREC>
+__device__ __forceinline__ ulonglong2 empty_node() {
+    if constexpr (PREC == 1)
+        return make_ulonglong2(0ull, 0ull);
+    else
+        return make_ulonglong2(0ull, 0xFFFFFFFFFFFFFFFFull);
+}
+
+// Called by a full warp after lane 0 wrote node `idx` of level `lev`: the last
+// of its siblings to arrive builds the parent, and so on up to the root.
+template <int PREC>
+__device__ void propagate_up(const Inst& I, unsigned* __restrict__ tcnt, int lev, int64_t idx) {
+    const int lane = threadIdx.x & 31;
+    while (lev + 1 < I.nlev) {
+        const int64_t parent = idx >> 5;
+        const int64_t first = parent << 5;
+        const int64_t last = min((int64_t)I.lvl_n[lev], first + 32);
+        const unsigned nchild = (unsigned)(last - first);
+        __threadfence();
+        unsigned old = 0;
+        if (lane == 0) old = atomicAdd(&tcnt[I.lvl_off[lev + 1] + parent], 1u);
+        old = __shfl_sync(0xffffffffu, old, 0);
+        if (old + 1 != nchild) return;
+        if (lane == 0) tcnt[I.lvl_off[lev + 1] + parent] = 0u;
+        __threadfence();
+        ulonglong2 v = empty_node<PREC>();
+        if (first + lane < last) v = __ldcg(&I.tree[I.lvl_off[lev] + first + lane]);
+        v = warp_merge<PREC>(v);
+        if (lane == 0) I.tree[I.lvl_off[lev + 1] + parent] = v;
+        ++lev;
+        idx = parent;
+    }
+}
+
+// MODE 0: margins only (exact sums kept by the flips); MODE 1: resweep the sums of
+// the simulation's width. A simulation whose state says `init` (sums not set up
+// yet) is swept in any mode, and on the FP32 path both widths are summed.
+template <int PREC, int W, int MODE>
+__global__ void __launch_bounds__(kSweepThreads)
+    k_sweep(const Inst* __restrict__ tab, const int64_t* __restrict__ task_start, int n_inst,
+            int64_t total_tasks, unsigned* const* __restrict__ tcnts) {
+    __shared__ int sums32[PREC == 1 ? kSweepWarps : 1][32][2];
+    __shared__ long long sums64[kSweepWarps][32][2];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t gw = (blockIdx.x * (int64_t)kSweepThreads + threadIdx.x) >> 5;
+    if (gw >= total_tasks) return;
+    const int inst = find_inst(task_start, n_inst, gw);
+    const Inst& I = tab[inst];
+    const InstState* st = I.st;
+    const int64_t t = st->t;
+    if (st->status != ST_OK || t >= I.K) return;
+    const int64_t lt = gw - task_start[inst];
+    const int64_t r0 = lt << 5;
+    const bool init = st->init != 0;
+    const bool SUM32 = PREC == 1 && (MODE == 1 || init);
+    const bool SUM64 = PREC == 0 ? (MODE == 1 || init) : init;
+
+    if (SUM32 || SUM64) {
+        constexpr int R = 32 / W;
+        const int sub = lane / W, sl = lane % W;
+        const int4* __restrict__ col4 = reinterpret_cast<const int4*>(I.col);
+        for (int q = sub; q < 32; q += R) {
+            const int64_t i = r0 + q;
+            int bp = 0, bq = 0;
+            long long ap = 0, aq = 0;
+            if (i < I.n) {
+                const int64_t g0 = __ldg(&I.rp[i]) >> 2, g1 = __ldg(&I.rp[i + 1]) >> 2;
+                for (int64_t g = g0 + sl; g < g1; g += W) {
+                    const int4 c = __ldg(&col4[g]);
+                    const int8_t s0 = __ldg(&I.s[c.x]), s1 = __ldg(&I.s[c.y]);
+                    const int8_t s2 = __ldg(&I.s[c.z]), s3 = __ldg(&I.s[c.w]);
+                    if (PREC == 1 && SUM32) {
+                        const int4* p4 = reinterpret_cast<const int4*>(I.pq32) + 2 * g;
+                        const int4 a = __ldg(p4), b = __ldg(p4 + 1);
+                        bp += sgn_sel(s0, a.x) + sgn_sel(s1, a.z) + sgn_sel(s2, b.x) +
+                              sgn_sel(s3, b.z);
+                        bq += sgn_sel(s0, a.y) + sgn_sel(s1, a.w) + sgn_sel(s2, b.y) +
+                              sgn_sel(s3, b.w);
+                    }
+                    if (SUM64) {
+                        const longlong2* p = I.pq64 + 4 * g;
+                        const longlong2 v0 = __ldg(p), v1 = __ldg(p + 1);
+                        const longlong2 v2 = __ldg(p + 2), v3 = __ldg(p + 3);
+                        ap += sgn_sel(s0, v0.x) + sgn_sel(s1, v1.x) + sgn_sel(s2, v2.x) +
+                              sgn_sel(s3, v3.x);
+                        aq += sgn_sel(s0, v0.y) + sgn_sel(s1, v1.y) + sgn_sel(s2, v2.y) +
+                              sgn_sel(s3, v3.y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = W / 2; o > 0; o >>= 1) {
+                if (SUM32) {
+                    bp += __shfl_xor_sync(0xffffffffu, bp, o);
+                    bq += __shfl_xor_sync(0xffffffffu, bq, o);
+                }
+                if (SUM64) {
+                    ap += __shfl_xor_sync(0xffffffffu, ap, o);
+                    aq += __shfl_xor_sync(0xffffffffu, aq, o);
+                }
+            }
+            if (sl == 0) {
+                if (PREC == 1 && SUM32) {
+                    sums32[wib][q][0] = bp;
+                    sums32[wib][q][1] = bq;
+                }
+                if (SUM64) {
+                    sums64[wib][q][0] = ap;
+                    sums64[wib][q][1] = aq;
+                }
+            }
+        }
+        __syncwarp();
+    }
+
+    const int64_t i = r0 + lane;
+    ulonglong2 node = empty_node<PREC>();
+    if (i < I.n) {
+        const uint32_t step = I.step0 + (uint32_t)t;
+        const int si = I.s[i];
+        const uint16_t ci = I.cls[i];
+        const float2 e32 = I.ext32[ci];
+        float2 th = make_float2(0.0f, 0.0f);
+        if (I.sigma > 0.0) {
+            th = thermal32(I, i, step);
+            I.th32[i] = th;
+        }
+        longlong2 h64;
+        if (SUM64) {
+            h64 = make_longlong2(sums64[wib][lane][0], sums64[wib][lane][1]);
+            I.h64[i] = h64;
+        }
+        if constexpr (PREC == 1) {
+            int2 h;
+            if (SUM32) {
+                h = make_int2(sums32[wib][lane][0], sums32[wib][lane][1]);
+                I.h32[i] = h;
+            } else {
+                h = I.h32[i];
+            }
+            const float dp = __fmul_rn(__int2float_rn(h.x), I.inv32);
+            const float dq = __fmul_rn(__int2float_rn(h.y), I.inv32);
+            const Eval32 e = eval32(I, si, dp, dq, I.hk32[i], e32, th.x, th.y);
+            const unsigned long long key = e.possible ? key32_of(e.hi, i) : 0ull;
+            I.key32[i] = key;
+            I.lo32[i] = e.certain ? e.lo : -1.0f;
+            node = make_ulonglong2(key, 0ull);
+        } else {
+            if (!SUM64) h64 = I.h64[i];
+            const float dp = __fmul_rn(__ll2float_rn(h64.x), I.inv64f);
+            const float dq = __fmul_rn(__ll2float_rn(h64.y), I.inv64f);
+            const Eval32 e = eval32(I, si, dp, dq, I.hk32[i], e32, th.x, th.y);
+            double key = 0.0;
+            if (e.possible) {
+                double tp = 0.0, tq = 0.0;
+                if (I.sigma > 0.0) thermal64(I, i, step, &tp, &tq);
+                const Eval64 f = eval64(I, si, h64.x, h64.y, I.hk64[i], I.ext64[ci], tp, tq);
+                if (f.flippable) key = f.lhs;
+            }
+            I.key64[i] = key;
+            node = make_ulonglong2((unsigned long long)__double_as_longlong(key),
+                                   (unsigned long long)i);
+        }
+    }
+    node = warp_merge<PREC>(node);
+    if (lane == 0) I.tree[I.lvl_off[0] + lt] = node;
+    propagate_up<PREC>(I, tcnts[inst], 0, lt);
+}
+
+// Projections of the current step's external field on every angle class of every
+// active simulation (FP64, and rounded once to FP32), one block per simulation.
+__global__ void k_ext_table(const Inst* __restrict__ tab, int n_inst) {
+    const Inst& I = tab[blockIdx.x];
+    const InstState* st = I.st;
+    const int64_t t = st->t;
+    if (st->status != ST_OK || t >= I.K) return;
+    const double hx = I.phx[t], hy = I.phy[t];
+    for (int c = threadIdx.x; c < I.nclass; c += blockDim.x) {
+        const double2 e = ext_proj(hx, hy, I.cs64[c]);
+        I.ext64[c] = e;
+        I.ext32[c] = make_float2(__double2float_rn(e.x), __double2float_rn(e.y));
+    }
+}
+
+template <int PREC, int MODE>
+cudaError_t launch_w(int W, const SweepLaunch& L, cudaStream_t st) {
+    const unsigned blocks = (unsigned)((L.total_tasks + kSweepWarps - 1) / kSweepWarps);
+    if (blocks == 0) return cudaSuccess;
+    switch (W) {
+        case 4:
+            k_sweep<PREC, 4, MODE><<<blocks, kSweepThreads, 0, st>>>(
+                L.tab, L.task_start, L.n_inst, L.total_tasks, L.tcnts);
+            break;
+        case 8:
+            k_sweep<PREC, 8, MODE><<<blocks, kSweepThreads, 0, st>>>(
+                L.tab, L.task_start, L.n_inst, L.total_tasks, L.tcnts);
+            break;
+        case 16:
+            k_sweep<PREC, 16, MODE><<<blocks, kSweepThreads, 0, st>>>(
+                L.tab, L.task_start, L.n_inst, L.total_tasks, L.tcnts);
+            break;
+        default:
+            k_sweep<PREC, 32, MODE><<<blocks, kSweepThreads, 0, st>>>(
+                L.tab, L.task_start, L.n_inst, L.total_tasks, L.tcnts);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_sweep(const SweepLaunch& L, cudaStream_t st) {
+    if (L.n_inst == 0) return cudaSuccess;
+    k_ext_table<<<L.n_inst, 128, 0, st>>>(L.tab, L.n_inst);
+    if (L.prec == 1)
+        return L.resweep ? launch_w<1, 1>(L.lanes_per_row, L, st)
+                         : launch_w<1, 0>(L.lanes_per_row, L, st);
+    return L.resweep ? launch_w<0, 1>(L.lanes_per_row, L, st)
+                     : launch_w<0, 0>(L.lanes_per_row, L, st);
+}
+
+}  // namespace fs

@@ -1,0 +1,348 @@
+"""CUDA path against the FP64 oracle, element by element, on seeded inputs.
+
+Tolerances: flip sequences (step, island) and spin states bit-exact; coercive
+fields bit-exact (both sides draw them with Philox4x32-10 + Box-Muller in host
+double precision); fields within 1e-12 of max|h| (FS_FP64) or 1e-5 of max|h|
+(FS_FP32_RECHECK, the FP32 evaluation itself).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2002_11401_b300 import inputs as I
+
+from .helpers import first_divergence, lib_sim, oracle_sim, small
+
+pytestmark = pytest.mark.gpu
+
+FP64, FP32 = 0, 1
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2002_11401_b300 import build
+    build.build()
+    from paper_2002_11401_b300 import binding
+    return binding
+
+
+def _pair_field_frame(O, xi, yi, ti, xj, yj, tj, alpha):
+    hx, hy = O.dipole_field(xi - xj, yi - yj, math.cos(tj), math.sin(tj), alpha)
+    c, s = math.cos(ti), math.sin(ti)
+    return hx * c + hy * s, -hx * s + hy * c
+
+
+# ---------------------------------------------------------------------------
+# Inputs and tensors
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,n", [(I.SQUARE, 16), (I.PINWHEEL, 10), (I.KAGOME, 8)])
+def test_hk_and_neighbour_tensor(B, oracle, kind, n):
+    w = small(kind, n)
+    sim = lib_sim(w)
+    S = oracle_sim(oracle, w)
+    np.testing.assert_array_equal(sim.hk(), S.hk)  # bit-exact draws
+    rp, col, P, Q = sim.csr()
+    orp, ocol = S.neighbors()
+    np.testing.assert_array_equal(rp, orp)
+    np.testing.assert_array_equal(col, ocol)
+    x, y, t = S.x, S.y, S.theta
+    scale = 0.0
+    errs = []
+    for i in range(S.n):
+        for e in range(rp[i], rp[i + 1]):
+            j = col[e]
+            ep, eq = _pair_field_frame(oracle, x[i], y[i], t[i], x[j], y[j], t[j], w["alpha"])
+            errs.append(max(abs(P[e] - ep), abs(Q[e] - eq)))
+            scale = max(scale, abs(ep), abs(eq))
+    assert max(errs) <= 1e-14 * scale
+    # P_ij = P_ji exactly (symmetric tensor, symmetric neighbourhood)
+    pos = {(i, int(col[e])): e for i in range(S.n) for e in range(rp[i], rp[i + 1])}
+    for (i, j), e in pos.items():
+        assert P[e] == P[pos[(j, i)]]
+
+
+# ---------------------------------------------------------------------------
+# Fields (Eq. 2, 3) and the astroid (Eq. 5)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-12), (FP32, 1e-5)])
+@pytest.mark.parametrize("kind,n,sigma", [(I.SQUARE, 12, 0.0), (I.PINWHEEL, 9, 0.0),
+                                          (I.KAGOME, 9, 0.005)])
+def test_fields_match_oracle(B, oracle, prec, tol, kind, n, sigma):
+    w = small(kind, n, sigma_th=sigma, alpha=3e-3)
+    sim = lib_sim(w, precision=prec)
+    S = oracle_sim(oracle, w)
+    worst = 0.0
+    for trial in range(4):
+        s = I.random_spins(S.n, 100 + trial)
+        hx, hy = 0.05 * math.cos(trial), -0.07 * math.sin(trial + 1)
+        sim.set_spins(s)
+        sim.set_field(hx, hy, step=trial * 7)
+        hp, hq = sim.fields()
+        op, oq = S.fields(s, hx, hy, step=trial * 7)
+        hmax = max(np.abs(op).max(), np.abs(oq).max())
+        err = max(np.abs(hp - op).max(), np.abs(hq - oq).max()) / hmax
+        worst = max(worst, err)
+        assert err <= tol, (trial, err)
+        lhs = sim.lhs()
+        olhs = np.array([oracle.astroid_lhs(op[i], oq[i], S.hk[i], 1, 1, 3, 3)
+                         for i in range(S.n)])
+        assert np.abs(lhs - olhs).max() <= (1e-11 if prec == FP64 else 1e-4) * olhs.max()
+
+
+# ---------------------------------------------------------------------------
+# Flip sequences (Sec. "Dynamics")
+# ---------------------------------------------------------------------------
+
+def _compare_runs(oracle, w, hx, hy, precs=(FP64, FP32), resweeps=(True,), **over):
+    S = oracle_sim(oracle, w, **over)
+    ref = S.run(np.ones(S.n, dtype=np.int8), hx, hy)
+    assert ref["status"] == 0
+    out = []
+    for prec in precs:
+        for rs in resweeps:
+            sim = lib_sim(w, precision=prec, **over)
+            got = sim.run_protocol(hx, hy, resweep=rs)
+            d = first_divergence(ref["log_step"], ref["log_spin"], got["log_step"],
+                                 got["log_spin"])
+            assert d is None, (prec, rs, d, ref["ties"])
+            assert got["n_flips"] == ref["n_flips"]
+            assert got["hash"] == ref["hash"]
+            np.testing.assert_array_equal(got["flips_per_step"], ref["flips_per_step"])
+            np.testing.assert_array_equal(sim.spins(), ref["spins"])
+            out.append(got)
+    return ref, out
+
+
+def test_square16_sequence(B, oracle):
+    w = I.WORKLOADS["square16"]
+    hx, hy = I.protocol_of(w["protocol"])
+    ref, _ = _compare_runs(oracle, w, hx, hy, resweeps=(True, False))
+    assert ref["n_flips"] == 2 * 544
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_small_systems_sequences(B, oracle, case):
+    rng = np.random.default_rng(1000 + case)
+    kind = [I.SQUARE, I.PINWHEEL, I.KAGOME][case % 3]
+    astroids = [(1, 1, 3, 3), (0.28, 1, 4.8, 3), (0.42, 1, 1.7, 3.4), (0.38, 1, 1.5, 3.2)]
+    b, c, beta, gamma = astroids[case % 4]
+    n = int(rng.integers(5, 14))
+    sigma = 0.004 if case % 2 else 0.0
+    w = small(kind, n, b=b, c=c, beta=beta, gamma=gamma, sigma_th=sigma, seed=case,
+              alpha=[1e-3, 3e-3, 1e-2][case % 3], k_disorder=[0.05, 0.1, 0.02][case % 3])
+    hmax = 0.35 if b >= 1 else 0.2
+    proto = [I.ramp_protocol(60, float(rng.uniform(0, 360)), hmax),
+             I.rotation_protocol(60, 6.0, hmax * 0.6),
+             I.loop_protocol(60, float(rng.uniform(0, 360)), -hmax, hmax)][case % 3]
+    _compare_runs(oracle, w, *proto, resweeps=(True, False))
+
+
+def test_pinwheel_mid_size(B, oracle):
+    w = small(I.PINWHEEL, 48, seed=1)
+    hx, hy = I.loop_protocol(150, 30.0, -0.25, 0.25)
+    ref, _ = _compare_runs(oracle, w, hx, hy)
+    assert ref["n_flips"] > w["nx"] * w["nx"]
+
+
+def test_kagome_thermal_mid_size(B, oracle):
+    w = small(I.KAGOME, 40, sigma_th=0.005, k_disorder=0.08, seed=2)
+    hx, hy = I.rotation_protocol(120, 3.0, 0.11)
+    _compare_runs(oracle, w, hx, hy)
+
+
+# ---------------------------------------------------------------------------
+# Edge cases
+# ---------------------------------------------------------------------------
+
+def test_single_island(B, oracle):
+    sim = B.Sim.custom([0.0], [0.0], [0.3])
+    sim.set_params(B.make_params(alpha=1e-3, cutoff=2.0))
+    hx = np.array([0.0, -0.1, -0.3, 0.3])
+    hy = np.zeros(4)
+    got = sim.run_protocol(hx, hy)
+    S = oracle.Sim([0.0], [0.0], [0.3], sim.hk(), alpha=1e-3, cutoff_abs=2.0)
+    ref = S.run(np.ones(1, dtype=np.int8), hx, hy)
+    assert got["hash"] == ref["hash"] and got["n_flips"] == ref["n_flips"] == 2
+
+
+def test_exact_ties_lowest_index(B, oracle):
+    # identical non-interacting islands with equal h_k: every pick is an exact tie
+    n = 70
+    x = np.arange(n, dtype=np.float64) * 10.0
+    for prec in (FP64, FP32):
+        sim = B.Sim.custom(x, np.zeros(n), np.zeros(n))
+        sim.set_params(B.make_params(alpha=0.0, cutoff=1.0, precision=prec))
+        sim.set_hk(np.full(n, 0.2))
+        got = sim.run_protocol(np.array([-0.3, 0.3]), np.zeros(2))
+        assert got["log_spin"].tolist() == list(range(n)) * 2
+
+
+def test_custom_geometry_matches_oracle(B, oracle):
+    rng = np.random.default_rng(9)
+    n = 300
+    x = rng.uniform(0, 12, n)
+    y = rng.uniform(0, 12, n)
+    t = rng.uniform(0, math.pi, n)
+    hx, hy = I.rotation_protocol(50, 7.0, 0.12)
+    for prec in (FP64, FP32):
+        sim = B.Sim.custom(x, y, t)
+        sim.set_params(B.make_params(alpha=2e-3, cutoff=2.5, k_disorder=0.1, seed=3,
+                                     precision=prec))
+        S = oracle.Sim(x, y, t, sim.hk(), alpha=2e-3, cutoff_abs=2.5)
+        ref = S.run(np.ones(n, dtype=np.int8), hx, hy)
+        got = sim.run_protocol(hx, hy)
+        assert got["hash"] == ref["hash"], first_divergence(
+            ref["log_step"], ref["log_spin"], got["log_step"], got["log_spin"])
+
+
+def test_flip_guard_reports_not_converged(B):
+    w = small(I.SQUARE, 6, max_flips_per_step=5)
+    sim = lib_sim(w)
+    got = sim.run_protocol(np.array([-0.4]), np.array([-0.4]))
+    assert got["status"] == B.FS_ERR_NOT_CONVERGED
+    assert got["n_flips"] == 5
+
+
+def test_empty_protocol_and_relax(B, oracle):
+    w = small(I.SQUARE, 5)
+    sim = lib_sim(w)
+    got = sim.run_protocol(np.zeros(0), np.zeros(0))
+    assert got["n_flips"] == 0 and got["hash"] == B.hash_init()
+    sim.set_field(-0.25, -0.25, step=3)
+    nf, log = sim.relax(log_cap=10_000)
+    S = oracle_sim(oracle, w)
+    ref = S.run(np.ones(S.n, dtype=np.int8), np.array([-0.25]), np.array([-0.25]), step0=3)
+    assert nf == ref["n_flips"]
+    np.testing.assert_array_equal(log, ref["log_spin"])
+
+
+def test_resume_split_protocol(B, oracle):
+    w = small(I.KAGOME, 10, sigma_th=0.01)
+    hx, hy = I.rotation_protocol(80, 4.5, 0.12)
+    for prec in (FP64, FP32):
+        sim = lib_sim(w, precision=prec)
+        full = sim.run_protocol(hx, hy)
+        sim2 = lib_sim(w, precision=prec)
+        a = sim2.run_protocol(hx[:37], hy[:37])
+        spins = sim2.spins()
+        sim3 = lib_sim(w, precision=prec)
+        sim3.set_spins(spins)
+        b = sim3.run_protocol(hx[37:], hy[37:], step0=37, hash_in=a["hash"])
+        assert b["hash"] == full["hash"]
+        np.testing.assert_array_equal(sim3.spins(), sim.spins())
+
+
+def test_log_shorter_than_flips(B):
+    w = small(I.SQUARE, 8)
+    sim = lib_sim(w)
+    hx, hy = I.protocol_of(("ramp", (40, 45.0, 0.3)))
+    full = sim.run_protocol(hx, hy)
+    sim2 = lib_sim(w)
+    part = sim2.run_protocol(hx, hy, log_cap=10)
+    assert part["hash"] == full["hash"] and part["n_flips"] == full["n_flips"]
+    np.testing.assert_array_equal(part["log_spin"], full["log_spin"][:10])
+
+
+# ---------------------------------------------------------------------------
+# Batches
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_batch_equals_solo_and_oracle(B, oracle, prec):
+    rng = np.random.default_rng(4)
+    sides = rng.integers(3, 15, size=12)
+    hx, hy = I.ramp_protocol(50, 45.0, 0.3)
+    members = []
+    for q, s in enumerate(sides):
+        w = small(I.SQUARE, int(s), seed=1000 + q)
+        members.append((w, lib_sim(w, precision=prec)))
+    out = B.batch_run_protocol([m for _, m in members], hx, hy, with_counts=True)
+    for q, (w, _) in enumerate(members):
+        S = oracle_sim(oracle, w)
+        ref = S.run(np.ones(S.n, dtype=np.int8), hx, hy)
+        assert int(out["hash"][q]) == ref["hash"]
+        assert out["n_flips"][q] == ref["n_flips"]
+        np.testing.assert_array_equal(out["flips_per_step"][q], ref["flips_per_step"])
+        solo = lib_sim(w, precision=prec).run_protocol(hx, hy)
+        assert solo["hash"] == ref["hash"]
+
+
+# ---------------------------------------------------------------------------
+# Serving: each result is the same alone and in the mix
+# ---------------------------------------------------------------------------
+
+def test_server_results_equal_solo_runs(B):
+    reqs = I.serving_stream(n_requests=10, n_lo=200, n_hi=6000, steps_lo=20, steps_hi=60,
+                            seed=8)
+    srv = B.Server(hbm_budget=2 << 30, max_active=64)
+    tickets = []
+    spins = []
+    for r in reqs:
+        hx, hy = I.protocol_of(r["protocol"])
+        prec = FP32 if r["seed"] % 2 else FP64
+        p = B.make_params(alpha=r["alpha"], hk=r["hk"], k_disorder=r["k_disorder"],
+                          cutoff=r["cutoff"], seed=r["seed"], precision=prec)
+        sim_n = B.Sim.geometry(r["kind"], r["nx"], r["ny"]).n
+        buf = np.zeros(sim_n, dtype=np.int8)
+        spins.append(buf)
+        tickets.append((srv.submit(r["kind"], r["nx"], r["ny"], p, hx, hy, spins_out=buf), r,
+                        prec, hx, hy))
+    srv.drain()
+    for (t, r, prec, hx, hy), buf in zip(tickets, spins):
+        res = srv.poll(t)
+        assert res is not None and res["status"] == 0
+        w = small(r["kind"], r["nx"], alpha=r["alpha"], cutoff=r["cutoff"], seed=r["seed"])
+        solo_sim = lib_sim(w, precision=prec)
+        solo = solo_sim.run_protocol(hx, hy)
+        assert res["hash"] == solo["hash"]
+        assert res["n_flips"] == solo["n_flips"]
+        np.testing.assert_array_equal(buf, solo_sim.spins())
+    srv.close()
+
+
+@pytest.mark.parametrize("kind,astroid,sigma", [(I.SQUARE, (1, 1, 3, 3), 0.0),
+                                                (I.PINWHEEL, (0.28, 1, 4.8, 3), 0.0),
+                                                (I.KAGOME, (0.42, 1, 1.7, 3.4), 0.006),
+                                                (I.SQUARE, (0.38, 1, 1.5, 3.2), 0.01)])
+def test_fp32_bounds_bracket_fp64(B, kind, astroid, sigma):
+    # the FP32 evaluation's [lo, hi] must contain the FS_FP64 value of the LHS
+    b, c, beta, gamma = astroid
+    w = small(kind, 12, b=b, c=c, beta=beta, gamma=gamma, sigma_th=sigma, alpha=4e-3)
+    s32 = lib_sim(w, precision=FP32)
+    s64 = lib_sim(w, precision=FP64)
+    rng = np.random.default_rng(5)
+    worst = 0.0
+    for trial in range(12):
+        s = I.random_spins(s32.n, trial)
+        ang = rng.uniform(0, 2 * math.pi)
+        mag = [0.0, 0.05, 0.2, 0.4][trial % 4]
+        for sim in (s32, s64):
+            sim.set_spins(s)
+            sim.set_field(mag * math.cos(ang), mag * math.sin(ang), step=trial)
+        l32, lo, hi = s32.lhs(bounds=True)
+        l64 = s64.lhs()
+        assert (lo <= l64).all() and (l64 <= hi).all(), trial
+        near = l64 > 0.5  # the band matters only near the switching threshold
+        if near.any():
+            worst = max(worst, float(np.max(hi[near] - lo[near])))
+    assert worst < 2e-3
+
+
+def test_fp32_thermal_draw_within_bound(B):
+    # alpha = 0 and no external field: the total field is the thermal draw alone,
+    # FP32 Box-Muller in one simulation, FP64 in the other; the error bound of the
+    # FP32 path assumes |z32 - z64| <= 2e-5.
+    w = small(I.KAGOME, 60, sigma_th=1.0, alpha=0.0)
+    s32 = lib_sim(w, precision=FP32)
+    s64 = lib_sim(w, precision=FP64)
+    worst = 0.0
+    for step in range(0, 40, 3):
+        for sim in (s32, s64):
+            sim.set_field(0.0, 0.0, step=step)
+        p32, q32 = s32.fields()
+        p64, q64 = s64.fields()
+        worst = max(worst, float(np.abs(p32 - p64).max()), float(np.abs(q32 - q64).max()))
+    assert worst < 2e-5 / 2, worst

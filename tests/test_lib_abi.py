@@ -1,0 +1,78 @@
+"""The C-ABI library loads and exports every entry point the header declares;
+host-only calls (geometry generation) agree with the oracle bit for bit. No
+device work runs here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2002_11401_b300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names.update(re.findall(r"\b(fs_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2002_11401_b300 import build
+    build.build()
+    from paper_2002_11401_b300 import binding as B
+    return B.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared()
+    assert len(declared) > 20
+    missing = [n for n in sorted(declared) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    from paper_2002_11401_b300 import binding as B
+    assert set(B.EXPORTS) == _declared()
+
+
+def test_hash_init_is_fnv_offset_basis(lib):
+    assert lib.fs_hash_init() == 0xcbf29ce484222325
+
+
+@pytest.mark.parametrize("kind,n", [(I.SQUARE, 16), (I.PINWHEEL, 9), (I.KAGOME, 29),
+                                    (I.KAGOME, 7)])
+def test_geometry_matches_oracle_bitwise(lib, oracle, kind, n):
+    from paper_2002_11401_b300 import binding as B
+    sim = B.Sim.geometry(kind, n, n + 1)
+    x, y, t = sim.geometry_arrays()
+    ox, oy, ot = oracle.geometry(kind, n, n + 1)
+    np.testing.assert_array_equal(x, ox)
+    np.testing.assert_array_equal(y, oy)
+    np.testing.assert_array_equal(t, ot)
+
+
+def test_bad_arguments_are_rejected(lib):
+    from paper_2002_11401_b300 import binding as B
+    with pytest.raises(B.FsError):
+        B.Sim.geometry(7, 4, 4)
+    with pytest.raises(B.FsError):
+        B.Sim.geometry(I.SQUARE, 0, 4)
+    with pytest.raises(B.FsError):
+        B.Sim.custom([0.0, np.nan], [0.0, 1.0], [0.0, 0.0])
+    sim = B.Sim.geometry(I.SQUARE, 2, 2)
+    # calls that need parameters fail with FS_ERR_STATE before any device work
+    h = ctypes.c_uint64(0)
+    nf = ctypes.c_int64(0)
+    st = lib.fs_run_protocol(sim.handle, None, None, 0, 0, 1, None, None, 0, None,
+                             ctypes.byref(h), ctypes.byref(nf))
+    assert st == B.FS_ERR_STATE
+    assert b"parameters" in lib.fs_last_error(sim.handle)
