@@ -165,6 +165,23 @@ fs_status fs_run_protocol_dev(fs_sim* sim, const double* d_hx, const double* d_h
                               uint32_t* d_log_spin, int64_t log_cap,
                               int64_t* d_flips_per_step, uint64_t* d_out);
 
+/* Spins from a device buffer (n int8 values in {-1,+1}, not checked), queued on
+ * the simulation's stream; the next protocol call recomputes every dipolar sum. */
+fs_status fs_set_spins_dev(fs_sim* sim, const int8_t* d_s, int64_t n);
+
+/* Per-kernel timing (profiling subsystem): with profiling on, every field step
+ * of fs_run_protocol / fs_run_protocol_dev brackets its sweep and its relax
+ * launch with CUDA events on the simulation's stream. fs_set_profiling resets
+ * the totals; fs_get_profile waits for the recorded events and returns them. */
+typedef struct {
+    double sweep_ms, relax_ms;  /* summed device time of the sweeps and relaxes */
+    int64_t sweep_launches, relax_launches;
+    int64_t rechecks;           /* FP64 recheck rounds of the FP32 path so far */
+    int64_t fallbacks;          /* rechecks that overflowed into a full scan */
+} fs_profile;
+fs_status fs_set_profiling(fs_sim* sim, int32_t on);
+fs_status fs_get_profile(fs_sim* sim, fs_profile* out);
+
 /* Current spins, n values. */
 fs_status fs_get_spins(const fs_sim* sim, int8_t* out, int64_t n);
 

@@ -26,7 +26,8 @@ EXPORTS = (
     "fs_run_protocol", "fs_run_protocol_dev", "fs_get_spins", "fs_get_fields", "fs_get_lhs",
     "fs_get_hk", "fs_get_geometry", "fs_get_info", "fs_get_csr", "fs_batch_run_protocol",
     "fs_server_create", "fs_server_submit", "fs_server_poll", "fs_server_drain",
-    "fs_server_now", "fs_server_destroy", "fs_server_last_error",
+    "fs_server_now", "fs_server_destroy", "fs_server_last_error", "fs_set_spins_dev",
+    "fs_set_profiling", "fs_get_profile",
 )
 
 
@@ -48,6 +49,12 @@ class fs_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nnz_padded", C.c_int64),
                 ("max_degree", C.c_int32), ("e64", C.c_int32), ("e32", C.c_int32),
                 ("device_bytes", C.c_int64), ("band_rel", C.c_double), ("band_abs", C.c_double)]
+
+
+class fs_profile(C.Structure):
+    _fields_ = [("sweep_ms", C.c_double), ("relax_ms", C.c_double),
+                ("sweep_launches", C.c_int64), ("relax_launches", C.c_int64),
+                ("rechecks", C.c_int64), ("fallbacks", C.c_int64)]
 
 
 class fs_request(C.Structure):
@@ -107,6 +114,9 @@ def load():
             "fs_server_now": ([P], dbl),
             "fs_server_destroy": ([P], None),
             "fs_server_last_error": ([P], C.c_char_p),
+            "fs_set_spins_dev": ([P, P, i64], i32),
+            "fs_set_profiling": ([P, i32], i32),
+            "fs_get_profile": ([P, P], i32),
         }
         for name, (args, res) in sig.items():
             if not hasattr(lib, name):
@@ -192,6 +202,17 @@ class Sim:
     def set_spins(self, s):
         s = np.ascontiguousarray(s, dtype=np.int8)
         self._check(self._lib.fs_set_spins(self._h, _p(s), len(s)))
+
+    def set_spins_dev(self, d_ptr: int):
+        self._check(self._lib.fs_set_spins_dev(self._h, C.c_void_p(d_ptr), self.n))
+
+    def set_profiling(self, on: bool):
+        self._check(self._lib.fs_set_profiling(self._h, int(bool(on))))
+
+    def profile(self) -> dict:
+        out = fs_profile()
+        self._check(self._lib.fs_get_profile(self._h, C.byref(out)))
+        return {k: getattr(out, k) for k, _ in fs_profile._fields_}
 
     def set_field(self, hx: float, hy: float, step: int = 0):
         self._check(self._lib.fs_set_field(self._h, hx, hy, step))

@@ -170,6 +170,8 @@ extern "C" fs_status fs_create_custom(int64_t n, const double* x, const double* 
 extern "C" void fs_destroy(fs_sim* sim) {
     if (!sim) return;
     if (sim->graph_exec) cudaGraphExecDestroy(sim->graph_exec);
+    cudaStreamSynchronize(sim->stream);
+    for (cudaEvent_t e : sim->ev_pool) cudaEventDestroy(e);
     sim->run.release(sim->stream);
     sim->mem.release(sim->stream);
     cudaStreamSynchronize(sim->stream);
@@ -525,6 +527,38 @@ int relax_smem_budget(int64_t n) {
 
 // Queues K field steps of one simulation (sweep + relax per step). The
 // descriptor's protocol fields must already point at device buffers.
+static cudaError_t next_event(fs_sim* sim, cudaEvent_t* ev) {
+    if (sim->ev_used == sim->ev_pool.size()) {
+        cudaEvent_t e;
+        const cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        sim->ev_pool.push_back(e);
+    }
+    *ev = sim->ev_pool[sim->ev_used++];
+    return cudaSuccess;
+}
+
+// Accumulates the durations of the recorded (ext, sweep, relax) launch triples.
+cudaError_t collect_profile(fs_sim* sim) {
+    if (sim->ev_used == 0) return cudaSuccess;
+    cudaError_t e = cudaEventSynchronize(sim->ev_pool[sim->ev_used - 1]);
+    if (e != cudaSuccess) return e;
+    for (size_t q = 0; q + 2 < sim->ev_used; q += 3) {
+        float a = 0.0f, b = 0.0f;
+        cudaEventElapsedTime(&a, sim->ev_pool[q], sim->ev_pool[q + 1]);
+        cudaEventElapsedTime(&b, sim->ev_pool[q + 1], sim->ev_pool[q + 2]);
+        sim->prof_sweep_ms += a;
+        sim->prof_relax_ms += b;
+        ++sim->prof_sweeps;
+        ++sim->prof_relaxes;
+    }
+    sim->ev_used = 0;
+    return cudaSuccess;
+}
+
+// Queues K field steps of one simulation: per step the external-field table,
+// the sweep and the relax. With profiling on, events bracket the sweep and the
+// relax of every step.
 cudaError_t enqueue_steps(fs_sim* sim, int64_t K, int resweep, cudaStream_t st) {
     SweepLaunch S;
     S.tab = sim->d_inst;
@@ -534,18 +568,30 @@ cudaError_t enqueue_steps(fs_sim* sim, int64_t K, int resweep, cudaStream_t st) 
     S.tcnts = sim->d_tcnts;
     S.prec = sim->p.precision;
     S.lanes_per_row = sim->lanes;
+    S.resweep = resweep ? 1 : 0;
     RelaxLaunch R;
     R.tab = sim->d_inst;
     R.work = sim->d_work;
     R.n_work = 1;
     R.prec = sim->p.precision;
     R.smem_budget = relax_smem_budget(sim->n);
+    cudaError_t e;
+    if (sim->profiling && sim->ev_used + 3 * (size_t)K > 30000 &&
+        (e = collect_profile(sim)) != cudaSuccess)
+        return e;
     for (int64_t t = 0; t < K; ++t) {
-        S.resweep = resweep ? 1 : 0;
-        cudaError_t e = launch_sweep(S, st);
-        if (e != cudaSuccess) return e;
-        e = launch_relax(R, st);
-        if (e != cudaSuccess) return e;
+        if ((e = launch_ext_table(S, st)) != cudaSuccess) return e;
+        cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+        if (sim->profiling) {
+            if ((e = next_event(sim, &e0)) != cudaSuccess) return e;
+            if ((e = next_event(sim, &e1)) != cudaSuccess) return e;
+            if ((e = next_event(sim, &e2)) != cudaSuccess) return e;
+            cudaEventRecord(e0, st);
+        }
+        if ((e = launch_sweep(S, st)) != cudaSuccess) return e;
+        if (sim->profiling) cudaEventRecord(e1, st);
+        if ((e = launch_relax(R, st)) != cudaSuccess) return e;
+        if (sim->profiling) cudaEventRecord(e2, st);
     }
     return cudaSuccess;
 }
@@ -736,6 +782,7 @@ static fs_status refresh_fields(fs_sim* sim) {
     S.prec = sim->p.precision;
     S.resweep = 1;
     S.lanes_per_row = sim->lanes;
+    CK(launch_ext_table(S, st), "sweep");
     CK(launch_sweep(S, st), "sweep");
     CK(cudaStreamSynchronize(st), "sweep");
     sim->fields_valid = true;
@@ -852,5 +899,35 @@ extern "C" fs_status fs_get_csr(const fs_sim* csim, int64_t* row_ptr, int32_t* c
         }
         if (row_ptr) row_ptr[i + 1] = q;
     }
+    return FS_OK;
+}
+
+extern "C" fs_status fs_set_spins_dev(fs_sim* sim, const int8_t* d_s, int64_t n) {
+    fs_status r = need_built(sim);
+    if (r != FS_OK) return r;
+    if (!d_s || n != sim->n) return fail(sim, FS_ERR_INVALID, "spins must have n values");
+    CK(cudaMemcpyAsync(sim->inst.s, d_s, n, cudaMemcpyDeviceToDevice, sim->stream), "copy");
+    sim->fields_valid = false;
+    return FS_OK;
+}
+
+extern "C" fs_status fs_set_profiling(fs_sim* sim, int32_t on) {
+    if (!sim) return fail(nullptr, FS_ERR_INVALID, "sim is NULL");
+    CK(collect_profile(sim), "profile");
+    sim->profiling = on != 0;
+    sim->prof_sweep_ms = sim->prof_relax_ms = 0.0;
+    sim->prof_sweeps = sim->prof_relaxes = 0;
+    return FS_OK;
+}
+
+extern "C" fs_status fs_get_profile(fs_sim* sim, fs_profile* out) {
+    if (!sim || !out) return fail(sim, FS_ERR_INVALID, "NULL argument");
+    CK(collect_profile(sim), "profile");
+    out->sweep_ms = sim->prof_sweep_ms;
+    out->relax_ms = sim->prof_relax_ms;
+    out->sweep_launches = sim->prof_sweeps;
+    out->relax_launches = sim->prof_relaxes;
+    out->rechecks = sim->rechecks;
+    out->fallbacks = sim->fallbacks;
     return FS_OK;
 }

@@ -79,7 +79,9 @@ cudaError_t BatchTable::enqueue_step(int prec, int resweep, int smem, cudaStream
     S.prec = prec;
     S.resweep = resweep;
     S.lanes_per_row = lanes;
-    cudaError_t e = launch_sweep(S, st);
+    cudaError_t e = launch_ext_table(S, st);
+    if (e != cudaSuccess) return e;
+    e = launch_sweep(S, st);
     if (e != cudaSuccess) return e;
     RelaxLaunch R;
     R.tab = tab;

@@ -62,6 +62,12 @@ struct fs_sim {
     int lanes = 16;
     int64_t rechecks = 0, fallbacks = 0;
     cudaGraphExec_t graph_exec = nullptr;
+    // profiling: CUDA events around each sweep and relax launch
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    double prof_sweep_ms = 0.0, prof_relax_ms = 0.0;
+    int64_t prof_sweeps = 0, prof_relaxes = 0;
     std::string err;
 };
 

@@ -27,6 +27,7 @@ struct RelaxLaunch {
     int smem_budget;      // dynamic shared memory for the upper tree levels
 };
 
+cudaError_t launch_ext_table(const SweepLaunch& L, cudaStream_t st);
 cudaError_t launch_sweep(const SweepLaunch& L, cudaStream_t st);
 cudaError_t launch_relax(const RelaxLaunch& L, cudaStream_t st);
 cudaError_t prepare_relax(int prec, int smem);

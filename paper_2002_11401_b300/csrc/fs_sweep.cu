@@ -280,9 +280,15 @@ cudaError_t launch_w(int W, const SweepLaunch& L, cudaStream_t st) {
 
 }  // namespace
 
-cudaError_t launch_sweep(const SweepLaunch& L, cudaStream_t st) {
+cudaError_t launch_ext_table(const SweepLaunch& L, cudaStream_t st) {
     if (L.n_inst == 0) return cudaSuccess;
     k_ext_table<<<L.n_inst, 128, 0, st>>>(L.tab, L.n_inst);
+    return cudaGetLastError();
+}
+
+// The sweep proper; launch_ext_table must have run for the same step.
+cudaError_t launch_sweep(const SweepLaunch& L, cudaStream_t st) {
+    if (L.n_inst == 0) return cudaSuccess;
     if (L.prec == 1)
         return L.resweep ? launch_w<1, 1>(L.lanes_per_row, L, st)
                          : launch_w<1, 0>(L.lanes_per_row, L, st);
