@@ -204,6 +204,36 @@ fs_status fs_get_info(const fs_sim* sim, fs_info* out);
  * field at i per unit spin of j, in i's frame). Any output may be NULL. */
 fs_status fs_get_csr(const fs_sim* sim, int64_t* row_ptr, int32_t* col, double* P, double* Q);
 
+/* ---- Allocation-free evaluation ----------------------------------------------
+ * The paper has no counterpart; this is a service for callers that cannot
+ * allocate device memory when they call (a control loop that must not block on
+ * the CUDA allocator, or a process whose device memory is wholly reserved by
+ * another framework's pool).
+ *
+ * One field-and-margin sweep in the FS_FP64 arithmetic (exact 64-bit dipolar sums
+ * over sim's neighbour tensors, external field (hx, hy), thermal draw of `step`,
+ * Eq. 5 and 6) for the caller's spins, and the argmax of the relax rule.
+ *   sim      built simulation (fs_set_params done); its spins are not used or
+ *            changed; n = its island count, at most 2,097,152 (2^21)
+ *   d_spins  device, n int8 in {-1,+1} (values are not checked)
+ *   d_lhs    device output, n doubles: the Eq. 5 LHS of every flippable island,
+ *            0 for the others
+ *   d_best   device output, one int64: the flippable island with the largest
+ *            LHS (lowest index on ties), or -1 when none is flippable
+ *   stream   cudaStream_t to queue on (NULL = legacy default); the call returns
+ *            without waiting, the outputs are valid once the stream gets there
+ * It calls no allocator: its scratch (the max-tree and its arrival counters) is
+ * one static device array of 2 MiB in the library, which every GPU that loads the
+ * library holds until the process exits. The first call on a device looks up that
+ * array's address (once per device, with that device current); later calls only
+ * queue a memset of the counters and one kernel. All calls share the array, so
+ * calls whose work overlaps on the GPU race and give undefined results.
+ * Returns FS_ERR_INVALID (NULL pointer or n above the limit), FS_ERR_STATE
+ * (parameters not set) or FS_ERR_CUDA (lookup or launch failed); no message is
+ * recorded for fs_last_error. */
+fs_status fs_eval_argmax_static(const fs_sim* sim, const int8_t* d_spins, double hx, double hy,
+                                uint32_t step, double* d_lhs, int64_t* d_best, void* stream);
+
 /* ---- Batched ensembles ------------------------------------------------------
  * Advances n independent simulations through the same protocol together: per
  * field step one sweep over every member's rows and one relax per member, all
