@@ -190,6 +190,17 @@ extern "C" fs_status fs_set_stream(fs_sim* sim, void* stream) {
 
 static bool bad_double(double v) { return !std::isfinite(v); }
 
+// Per-island scales of the FP32 evaluation: 1 / (b h_k) and 1 / (c h_k) in double,
+// each rounded once to FP32.
+static void fill_rbc(fs_sim* sim) {
+    sim->rbc32.resize((size_t)sim->n);
+    for (int64_t i = 0; i < sim->n; ++i) {
+        const double h = sim->hk[(size_t)i];
+        sim->rbc32[(size_t)i] = make_float2((float)(1.0 / (sim->p.b * h)),
+                                            (float)(1.0 / (sim->p.c * h)));
+    }
+}
+
 fs_status fs_build_sim(fs_sim* sim) {
     cudaStream_t st = sim->stream;
     const int64_t n = sim->n;
@@ -336,13 +347,13 @@ fs_status fs_build_sim(fs_sim* sim) {
     // islands
     int8_t* s = nullptr;
     double* hk64 = nullptr;
-    float* hk32 = nullptr;
+    float2* rbc32 = nullptr;
     uint16_t* cls = nullptr;
     double2* c64 = nullptr;
     float2* c32 = nullptr;
     CK(palloc((void**)&s, n), "alloc");
     CK(palloc((void**)&hk64, 8 * n), "alloc");
-    CK(palloc((void**)&hk32, 4 * n), "alloc");
+    CK(palloc((void**)&rbc32, 8 * n), "alloc");
     CK(palloc((void**)&cls, 2 * n), "alloc");
     CK(palloc((void**)&c64, 16 * ncls), "alloc");
     CK(palloc((void**)&c32, 8 * ncls), "alloc");
@@ -355,19 +366,18 @@ fs_status fs_build_sim(fs_sim* sim) {
     CK(cudaMemcpyAsync(c32, cs32.data(), 8 * ncls, cudaMemcpyHostToDevice, st), "upload");
     I.s = s;
     I.hk64 = hk64;
-    I.hk32 = hk32;
+    I.rbc32 = rbc32;
     I.cls = cls;
     I.cs64 = c64;
     I.cs32 = c32;
 
     CK(palloc((void**)&I.h64, 16 * n), "alloc");
-    if (p.precision == FS_FP32_RECHECK) {
+    CK(palloc((void**)&I.key32, 8 * n), "alloc");
+    CK(palloc((void**)&I.lo32, 4 * n), "alloc");
+    if (p.precision == FS_FP32_RECHECK)
         CK(palloc((void**)&I.h32, 8 * n), "alloc");
-        CK(palloc((void**)&I.key32, 8 * n), "alloc");
-        CK(palloc((void**)&I.lo32, 4 * n), "alloc");
-    } else {
+    else
         CK(palloc((void**)&I.key64, 8 * n), "alloc");
-    }
     CK(palloc((void**)&I.ext64, 16 * ncls), "alloc");
     CK(palloc((void**)&I.ext32, 8 * ncls), "alloc");
     I.nclass = (int32_t)ncls;
@@ -386,7 +396,7 @@ fs_status fs_build_sim(fs_sim* sim) {
         cnt = (cnt + 31) / 32;
     }
     I.nlev = nlev;
-    CK(palloc((void**)&I.tree, 16 * total), "alloc");
+    CK(palloc((void**)&I.tree, 8 * total), "alloc");
     CK(palloc((void**)&sim->tcnt, 4 * total), "alloc");
     CK(cudaMemsetAsync(sim->tcnt, 0, 4 * total, st), "init");
     CK(palloc((void**)&sim->d_state, sizeof(InstState)), "alloc");
@@ -424,23 +434,23 @@ fs_status fs_build_sim(fs_sim* sim) {
     //  - dh_abs: both fixed-point roundings over the longest row, plus the FP32
     //    Box-Muller draw against the FP64 one (|z32 - z64| <= kThermalZErr);
     //  - dh_rel: four float roundings of the field pieces (u = 2^-24);
-    //  - div_rel: the roundings of h_k, b or c, their product, the reciprocal and
-    //    the scaling, against the FP64 division (six u);
-    //  - pow_rel: powf (measured max 1.26 u on this GPU) and the bound arithmetic.
+    //  - div_rel: the FP32 rounding of 1 / (b h_k) and of the scaling, against the
+    //    FP64 division (two u, taken as three);
+    //  - pow_rel: powf (measured max 1.26 u on this GPU, taken as two); the bound
+    //    arithmetic itself rounds outward.
     const double u = std::ldexp(1.0, -24);
     const double quant = (double)stats.max_deg * (std::ldexp(1.0, -e32 - 1) +
                                                   std::ldexp(1.0, -e64 - 1));
     I.dh_abs = (float)((quant + p.sigma_th * kThermalZErr) * 1.5 + 1e-30);
     I.dh_rel = (float)(4.0 * u);
-    I.div_rel = (float)(6.0 * u);
-    I.pow_rel = (float)(6.0 * u);
+    I.div_rel = (float)(3.0 * u);
+    I.pow_rel = (float)(2.0 * u);
     sim->lanes = choose_lanes((double)nnzp / (double)n / 4.0);
 
     // coercive fields
     CK(cudaMemcpyAsync(hk64, sim->hk.data(), 8 * n, cudaMemcpyHostToDevice, st), "upload");
-    sim->hk32.resize((size_t)n);
-    for (int64_t i = 0; i < n; ++i) sim->hk32[(size_t)i] = (float)sim->hk[(size_t)i];
-    CK(cudaMemcpyAsync(hk32, sim->hk32.data(), 4 * n, cudaMemcpyHostToDevice, st), "upload");
+    fill_rbc(sim);
+    CK(cudaMemcpyAsync(rbc32, sim->rbc32.data(), 8 * n, cudaMemcpyHostToDevice, st), "upload");
     CK(cudaMemcpyAsync(sim->d_inst, &I, sizeof(Inst), cudaMemcpyHostToDevice, st), "upload");
     tmp.release(st);
     CK(cudaStreamSynchronize(st), "build");
@@ -480,12 +490,11 @@ extern "C" fs_status fs_set_hk(fs_sim* sim, const double* hk, int64_t n) {
         if (!(hk[i] > 0.0) || !std::isfinite(hk[i]))
             return fail(sim, FS_ERR_INVALID, "hk values must be positive and finite");
     sim->hk.assign(hk, hk + n);
-    sim->hk32.resize((size_t)n);
-    for (int64_t i = 0; i < n; ++i) sim->hk32[(size_t)i] = (float)hk[i];
+    fill_rbc(sim);
     CK(cudaMemcpyAsync((void*)sim->inst.hk64, sim->hk.data(), 8 * n, cudaMemcpyHostToDevice,
                        sim->stream),
        "upload");
-    CK(cudaMemcpyAsync((void*)sim->inst.hk32, sim->hk32.data(), 4 * n, cudaMemcpyHostToDevice,
+    CK(cudaMemcpyAsync((void*)sim->inst.rbc32, sim->rbc32.data(), 8 * n, cudaMemcpyHostToDevice,
                        sim->stream),
        "upload");
     CK(cudaStreamSynchronize(sim->stream), "sync");

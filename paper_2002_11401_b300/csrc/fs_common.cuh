@@ -62,7 +62,7 @@ struct Inst {
     // islands
     int8_t* s;
     const double* hk64;
-    const float* hk32;
+    const float2* rbc32;    // (1 / (b h_k), 1 / (c h_k)) per island, FP32
     const uint16_t* cls;    // angle class
     const double2* cs64;    // (cos, sin) per class
     const float2* cs32;
@@ -72,10 +72,10 @@ struct Inst {
     longlong2* h64;         // dipolar (par, perp), exact 64-bit sums (both paths)
     int2* h32;              // dipolar (par, perp), 32-bit sums (FP32 path)
     float2* th32;           // thermal (par, perp) of the current step (sigma > 0)
-    unsigned long long* key32;  // FP32 path: (bits(hi) << 32) | ~i, 0 = not a candidate
-    float* lo32;                // FP32 path: certified lower bound of the LHS, -1 if none
-    double* key64;              // FP64 path: LHS when flippable, else 0
-    ulonglong2* tree;           // tree nodes (both paths, 16 B each)
+    unsigned long long* key32;  // (bits(upper bound) << 32) | ~i, 0 = not a candidate
+    float* lo32;                // certified lower bound of the LHS, -1 if none
+    double* key64;              // FP64 path: exact LHS when flippable, else 0
+    unsigned long long* tree;   // max-tree nodes above the keys
     // protocol
     const double* phx;
     const double* phy;
@@ -97,8 +97,8 @@ struct Inst {
     int32_t pad0;
     int64_t max_flips;
     // FP32 error model: |h32 - h64| <= dh_abs + dh_rel * (|h_dip| + |h_ext| + |h_th|);
-    // div_rel bounds the relative error of |h| / (b h_k), pow_rel that of powf and of
-    // the bound arithmetic
+    // div_rel bounds the relative error of |h| / (b h_k) against the FP64 division,
+    // pow_rel that of powf
     float dh_abs, dh_rel, pow_rel, div_rel;
     InstState* st;
 };
@@ -250,63 +250,73 @@ __device__ __forceinline__ float pow_nonneg(float x, float p) {
 
 // Bounds of one astroid term a^p, a = |h| / (b h_k), whose FP32 value t = powf(x, p)
 // was taken at x; u bounds the relative error of x. For p <= 1 the concave power
-// gives (x(1+u))^p <= x^p (1 + p u) and (x(1-u))^p >= x^p (1 - p u / (1 - u)); for
-// 1 < p <= 3, (1 + u)^(p-1) <= 2 on u <= 1/4 gives factors 1 + 2 p u and 1 - p u.
-// Outside u <= 1/4 the monotone bounds are evaluated directly. `r` is the
-// relative error of powf and of the factor arithmetic.
+// gives (x(1+u))^p <= x^p (1 + p u) and (x(1-u))^p >= x^p (1 - p u / (1 - u)), and
+// 1 / (1 - u) <= 1 + 2u on u <= 1/4; for 1 < p <= 3, (1 + u)^(p-1) <= 2 on u <= 1/4
+// gives the factors 1 + 2 p u and 1 - p u. Outside u <= 1/4 the monotone bounds
+// are evaluated directly. `r` bounds the relative error of powf. Upper bounds are
+// formed with round-up and lower bounds with round-down arithmetic.
 __device__ __forceinline__ void term_bounds(float t, float x, float u, float p, float r,
                                             float* hi, float* lo) {
     if (u <= 0.25f && p <= 3.0f) {
-        const float g_hi = p <= 1.0f ? __fmul_rn(p, u) : __fmul_rn(2.0f * p, u);
-        const float g_lo = p <= 1.0f ? __fdiv_rn(__fmul_rn(p, u), __fsub_rn(1.0f, u))
-                                     : __fmul_rn(p, u);
-        *hi = __fmul_rn(__fmul_rn(t, __fadd_rn(1.0f, r)), __fadd_rn(1.0f, g_hi));
-        *lo = __fmul_rn(__fmul_rn(t, __fsub_rn(1.0f, r)), fmaxf(__fsub_rn(1.0f, g_lo), 0.0f));
+        const float pu = __fmul_ru(p, u);
+        const float g_hi = p <= 1.0f ? pu : __fmul_ru(2.0f, pu);
+        const float g_lo = p <= 1.0f ? __fmul_ru(pu, __fadd_ru(1.0f, __fmul_ru(2.0f, u))) : pu;
+        *hi = __fmul_ru(__fmul_ru(t, __fadd_ru(1.0f, r)), __fadd_ru(1.0f, g_hi));
+        *lo = __fmul_rd(__fmul_rd(t, __fsub_rd(1.0f, r)), fmaxf(__fsub_rd(1.0f, g_lo), 0.0f));
     } else {
-        *hi = __fmul_rn(pow_nonneg(__fmul_rn(x, __fadd_rn(1.0f, u)), p), __fadd_rn(1.0f, r));
-        *lo = u < 1.0f ? __fmul_rn(pow_nonneg(__fmul_rn(x, __fsub_rn(1.0f, u)), p),
-                                   __fsub_rn(1.0f, r))
+        *hi = __fmul_ru(pow_nonneg(__fmul_ru(x, __fadd_ru(1.0f, u)), p), __fadd_ru(1.0f, r));
+        *lo = u < 1.0f ? __fmul_rd(pow_nonneg(__fmul_rd(x, __fsub_rd(1.0f, u)), p),
+                                   __fsub_rd(1.0f, r))
                        : 0.0f;
     }
 }
 
-__device__ __forceinline__ Eval32 eval32(const Inst& I, int s, float dp, float dq, float hk,
+// An upper bound of 1 / x for x > 0: the hardware reciprocal (at most 1 ulp off,
+// PTX ISA rcp.approx.f32) widened by 2^-22 and rounded up. A denormal x gives
+// +inf, which the callers treat as "no useful bound".
+__device__ __forceinline__ float rcp_up(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return __fmul_ru(r, 1.0f + 0x1.0p-22f);
+}
+
+// rbc = (1 / (b h_k), 1 / (c h_k)) of the island, each rounded once to FP32.
+__device__ __forceinline__ Eval32 eval32(const Inst& I, int s, float dp, float dq, float2 rbc,
                                          float2 ext, float tp, float tq) {
     Eval32 e;
     e.hpar = __fadd_rn(__fadd_rn(dp, ext.x), tp);
     e.hperp = __fadd_rn(__fadd_rn(dq, ext.y), tq);
     // field error bound: fixed point + thermal draw (absolute), float roundings
-    const float dpar = __fadd_rn(I.dh_abs, __fmul_rn(I.dh_rel, __fadd_rn(__fadd_rn(fabsf(dp),
+    const float dpar = __fadd_ru(I.dh_abs, __fmul_ru(I.dh_rel, __fadd_ru(__fadd_ru(fabsf(dp),
                                                                      fabsf(ext.x)), fabsf(tp))));
-    const float dperp = __fadd_rn(I.dh_abs, __fmul_rn(I.dh_rel, __fadd_rn(__fadd_rn(fabsf(dq),
+    const float dperp = __fadd_ru(I.dh_abs, __fmul_ru(I.dh_rel, __fadd_ru(__fadd_ru(fabsf(dq),
                                                                       fabsf(ext.y)), fabsf(tq))));
     const float ap = fabsf(e.hpar), aq = fabsf(e.hperp);
-    const float rb = __frcp_rn(__fmul_rn(I.bf, hk)), rc = __frcp_rn(__fmul_rn(I.cf, hk));
-    const float x = __fmul_rn(ap, rb), y = __fmul_rn(aq, rc);
+    const float x = __fmul_rn(ap, rbc.x), y = __fmul_rn(aq, rbc.y);
     const float tx = pow_nonneg(x, I.pexpf), ty = pow_nonneg(y, I.qexpf);
     e.lhs = __fadd_rn(tx, ty);
-    // relative error of x and y (field bound + the scaling roundings)
-    const float ux = ap > 0.0f ? __fadd_rn(__fdiv_rn(dpar, ap), I.div_rel) : 2.0f;
-    const float uy = aq > 0.0f ? __fadd_rn(__fdiv_rn(dperp, aq), I.div_rel) : 2.0f;
+    // relative error of x and y: the field bound plus the scaling roundings
+    const float ux = ap > 0.0f ? __fadd_ru(__fmul_ru(dpar, rcp_up(ap)), I.div_rel) : 2.0f;
+    const float uy = aq > 0.0f ? __fadd_ru(__fmul_ru(dperp, rcp_up(aq)), I.div_rel) : 2.0f;
     float hx_, lx_, hy_, ly_;
     if (ap > 0.0f) {
         term_bounds(tx, x, ux, I.pexpf, I.pow_rel, &hx_, &lx_);
     } else {  // |h_par| <= dpar
-        hx_ = __fmul_rn(pow_nonneg(__fmul_rn(__fmul_rn(dpar, rb), __fadd_rn(1.0f, I.div_rel)),
+        hx_ = __fmul_ru(pow_nonneg(__fmul_ru(__fmul_ru(dpar, rbc.x), __fadd_ru(1.0f, I.div_rel)),
                                    I.pexpf),
-                        __fadd_rn(1.0f, I.pow_rel));
+                        __fadd_ru(1.0f, I.pow_rel));
         lx_ = 0.0f;
     }
     if (aq > 0.0f) {
         term_bounds(ty, y, uy, I.qexpf, I.pow_rel, &hy_, &ly_);
     } else {
-        hy_ = __fmul_rn(pow_nonneg(__fmul_rn(__fmul_rn(dperp, rc), __fadd_rn(1.0f, I.div_rel)),
+        hy_ = __fmul_ru(pow_nonneg(__fmul_ru(__fmul_ru(dperp, rbc.y), __fadd_ru(1.0f, I.div_rel)),
                                    I.qexpf),
-                        __fadd_rn(1.0f, I.pow_rel));
+                        __fadd_ru(1.0f, I.pow_rel));
         ly_ = 0.0f;
     }
-    e.hi = __fmul_rn(__fadd_rn(hx_, hy_), 1.0f + 0x1.0p-22f);
-    e.lo = __fmul_rn(__fadd_rn(lx_, ly_), 1.0f - 0x1.0p-22f);
+    e.hi = __fadd_ru(hx_, hy_);
+    e.lo = __fadd_rd(lx_, ly_);
     const float sp = (float)s * e.hpar;
     e.possible = (sp < dpar) && (e.hi > 1.0f);
     e.certain = (sp < -dpar) && (e.lo > 1.0f);

@@ -35,7 +35,7 @@ struct fs_sim {
     // parameters
     fs_params p{};
     std::vector<double> hk;
-    std::vector<float> hk32;
+    std::vector<float2> rbc32;
     bool built = false;
     bool fields_valid = false;
     // current external field and thermal step

@@ -1,19 +1,26 @@
 // fs_relax.cu - the greedy single-flip relaxation (Sec. "Dynamics"), one CTA per
 // simulation, entirely on the device.
 //
-// Per flip: read the root of the max-tree (largest Eq. 5 LHS among flippable
-// islands, lowest index on ties); flip that island k; for every neighbour i of k
-// (row k of the CSR, whose transposed coefficients give the field k puts on i in
-// i's frame) add 2 s_k(new) (P_ik, Q_ik) to i's exact fixed-point dipolar sums and
-// re-evaluate i's key; then rebuild only the tree nodes above the changed leaves,
-// level by level. The fields stay constant over the relax, as the paper states.
+// Keys: one 64-bit key per island, (FP32 upper bound of its Eq. 5 LHS) << 32 |
+// (2^32 - 1 - index), 0 when the island cannot be flippable; a max-tree of fan-out
+// 32 over the keys, its upper levels in shared memory. The largest key is the
+// island with the largest bound, lowest index first.
 //
-// FS_FP32_RECHECK: keys are FP32 upper bounds of the LHS, nodes keep the best two
-// keys. The root's island is accepted when its certified lower bound exceeds one
-// and the runner-up's upper bound; otherwise every island whose upper bound
-// reaches the threshold is re-evaluated with the FS_FP64 arithmetic (exact
-// 64-bit sum of its CSR row), non-flippable ones are demoted, and the FP64 best
-// is taken once no island outside the set can beat it.
+// Per flip: warp 0 reads the root's island w and the largest other key (w's
+// sibling sets at every level). w is taken when its certified lower bound exceeds
+// one and that runner-up's upper bound; otherwise the islands whose bounds reach
+// the threshold are compared exactly (FS_FP64 values), non-flippable ones are
+// demoted, and the exact best is taken once no island outside the set can beat
+// it. Then island k is flipped and every neighbour i of k (row k of the CSR,
+// whose transposed coefficients give the field k puts on i in i's frame) gets
+// 2 s_k(new) (P_ik, Q_ik) added to its exact fixed-point sums and a new key. A key
+// that grows is pushed up the tree with atomic maxima; a node whose maximum was a
+// key that shrank is rebuilt from its children, level by level. Fields are held
+// constant over the relax, as the paper states.
+//
+// FS_FP32_RECHECK computes keys from FP32 bounds and its exact values in FP64;
+// FS_FP64 computes every candidate's exact value when its key is set, and its keys
+// are that value rounded out to FP32.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -24,309 +31,342 @@ namespace fs {
 
 namespace {
 
-constexpr int kT = 512;  // threads per relax CTA
+constexpr int kT = 256;  // threads per relax CTA
+constexpr int kNW = kT / 32;
+constexpr int kDirtyCap = kMaxPaddedDegree + 8;
 
 struct Levels {
-    ulonglong2* p[kMaxLevels];
+    unsigned long long* p[kMaxLevels];
 };
 
-__device__ __forceinline__ ulonglong2 best64n(ulonglong2 a, ulonglong2 b) {
-    return better64(a.x, a.y, b.x, b.y) ? a : b;
+// Warp maximum of 64-bit keys (every lane gets it): the largest upper half, then
+// among those the largest lower half.
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v) {
+    const unsigned hi = (unsigned)(v >> 32), lo = (unsigned)v;
+    const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+    return ((unsigned long long)mh << 32) | ml;
 }
 
-template <int PREC>
-__device__ __forceinline__ ulonglong2 empty_node() {
-    if constexpr (PREC == 1)
-        return make_ulonglong2(0ull, 0ull);
-    else
-        return make_ulonglong2(0ull, 0xFFFFFFFFFFFFFFFFull);
-}
-
-template <int PREC>
-__device__ __forceinline__ ulonglong2 merge_node(ulonglong2 a, ulonglong2 b) {
-    if constexpr (PREC == 1)
-        return top2(a, b);
-    else
-        return best64n(a, b);
-}
-
-// Node `node` of level `lev` from its 32 children (leaves when lev == 0), one
-// child per lane and a shuffle butterfly; every lane returns the node.
-template <int PREC>
-__device__ __forceinline__ ulonglong2 warp_children(const Inst& I, const Levels& L, int lev,
-                                                    int64_t node) {
+// Node `node` of level `lev` from its 32 children (leaves when lev == 0).
+__device__ __forceinline__ unsigned long long warp_node(const Inst& I, const Levels& L, int lev,
+                                                        int64_t node) {
     const int lane = threadIdx.x & 31;
     const int64_t c = (node << 5) + lane;
-    ulonglong2 v = empty_node<PREC>();
+    unsigned long long v = 0ull;
     if (lev == 0) {
-        if (c < I.n) {
-            if constexpr (PREC == 1)
-                v = make_ulonglong2(I.key32[c], 0ull);
-            else
-                v = make_ulonglong2((unsigned long long)__double_as_longlong(I.key64[c]),
-                                    (unsigned long long)c);
-        }
+        if (c < I.n) v = I.key32[c];
     } else if (c < I.lvl_n[lev - 1]) {
         v = L.p[lev - 1][c];
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        ulonglong2 u;
-        u.x = __shfl_xor_sync(0xffffffffu, v.x, o);
-        u.y = __shfl_xor_sync(0xffffffffu, v.y, o);
-        v = merge_node<PREC>(v, u);
-    }
-    return v;
+    return warp_max_key(v);
 }
 
-// Warp-wide: the distinct parents (x >> 5) of in[0..nin) in order, written to
-// out. Entries < 0 are skipped. `in` is ascending except that its last entry may
-// be out of place; that entry's parent is checked against all others.
-__device__ int warp_parents(const int32_t* in, int nin, int32_t* out) {
+// The largest key other than island w's: w's fellow leaves and, at every level,
+// the siblings of w's ancestor. Warp-wide.
+__device__ unsigned long long runner_up(const Inst& I, const Levels& L, int64_t w) {
     const int lane = threadIdx.x & 31;
-    int cnt = 0;
-    int carry = -1;
-    for (int base = 0; base < nin; base += 32) {
-        const int t = base + lane;
-        const int p = (t < nin && in[t] >= 0) ? (in[t] >> 5) : -1;
-        int up = __shfl_up_sync(0xffffffffu, p, 1);
-        if (lane == 0) up = carry;
-        const bool first = p >= 0 && p != up;
-        const unsigned m = __ballot_sync(0xffffffffu, first);
-        if (first) out[cnt + __popc(m & ((1u << lane) - 1u))] = p;
-        cnt += __popc(m);
-        carry = __shfl_sync(0xffffffffu, p, 31);
+    unsigned long long m = 0ull;
+    {
+        const int64_t c = ((w >> 5) << 5) + lane;
+        if (c != w && c < I.n) m = I.key32[c];
     }
-    __syncwarp();
-    if (cnt >= 2) {
-        const int last = out[cnt - 1];
-        bool dup = false;
-        for (int base = 0; base < cnt - 1; base += 32) {
-            const int t = base + lane;
-            dup |= __any_sync(0xffffffffu, t < cnt - 1 && out[t] == last);
+    for (int lev = 1; lev < I.nlev; ++lev) {
+        const int64_t anc = w >> (5 * lev);
+        const int64_t c = ((anc >> 5) << 5) + lane;
+        if (c != anc && c < I.lvl_n[lev - 1]) {
+            const unsigned long long v = L.p[lev - 1][c];
+            m = v > m ? v : m;
         }
-        if (dup) --cnt;
     }
-    __syncwarp();
-    return cnt;
+    return warp_max_key(m);
 }
 
-struct TreeScratch {
-    int32_t nodes[2][kMaxPaddedDegree + 2];
-    int32_t n1;
+struct Dirty {
+    int32_t lv0[kDirtyCap];        // first-level nodes to rebuild
+    int32_t up[2][kDirtyCap];      // upper-level nodes, one level at a time
+    int32_t n0, nup[2];
 };
 
-// Re-derives the tree above the changed leaves list[0..len) (ascending except the
-// last entry; entries < 0 skipped): all warps rebuild the first level, one warp
-// per node; then warp 0 alone climbs the few upper levels. Ends with warp 0 still
-// working; the caller's next block barrier orders it before any reader.
-template <int PREC>
-__device__ void tree_update_sorted(const Inst& I, const Levels& L, TreeScratch& T,
-                                   const int32_t* list, int len) {
+// A leaf's key went from `old` to `nk`: a larger key is pushed up with atomic
+// maxima on every ancestor; if the leaf held its
+// first-level node's maximum and shrank, that node is queued for a rebuild.
+__device__ __forceinline__ void leaf_changed(const Inst& I, const Levels& L, Dirty& D, int64_t i,
+                                             unsigned long long old, unsigned long long nk) {
+    if (nk > old) {
+        int64_t node = i;
+        for (int lev = 0; lev < I.nlev; ++lev) {
+            node >>= 5;
+            atomicMax(&L.p[lev][node], nk);
+        }
+    } else if (nk < old) {
+        const int64_t node = i >> 5;
+        if (L.p[0][node] == old) {
+            const int q = atomicAdd(&D.n0, 1);
+            if (q < kDirtyCap) D.lv0[q] = (int32_t)node;
+        }
+    }
+}
+
+// Rebuilds the queued nodes: all warps the first level, then warp 0 the levels
+// above (few nodes), each queueing its parent when its maximum shrank and the
+// parent held it. Call with every thread; returns with warp 0 possibly still
+// working on the upper levels when `wait` is false.
+__device__ void rebuild_dirty(const Inst& I, const Levels& L, Dirty& D, bool wait) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (wid == 0) {
-        const int n1 = warp_parents(list, len, T.nodes[0]);
-        if (lane == 0) T.n1 = n1;
+    const int n0 = min(D.n0, kDirtyCap);
+    for (int q = wid; q < n0; q += kNW) {
+        const int64_t node = D.lv0[q];
+        const unsigned long long old = L.p[0][node];
+        const unsigned long long nv = warp_node(I, L, 0, node);
+        if (lane == 0) {
+            L.p[0][node] = nv;
+            if (nv < old && I.nlev > 1 && L.p[1][node >> 5] == old) {
+                const int r = atomicAdd(&D.nup[0], 1);
+                if (r < kDirtyCap) D.up[0][r] = (int32_t)(node >> 5);
+            }
+        }
     }
     __syncthreads();
-    const int n1 = T.n1;
-    for (int q = wid; q < n1; q += kT / 32) {
-        const int64_t node = T.nodes[0][q];
-        const ulonglong2 v = warp_children<PREC>(I, L, 0, node);
-        if (lane == 0) L.p[0][node] = v;
-    }
-    __syncthreads();
     if (wid == 0) {
-        int cur = 0, ncur = n1;
+        int cur = 0;
         for (int lev = 1; lev < I.nlev; ++lev) {
-            const int nn = warp_parents(T.nodes[cur], ncur, T.nodes[cur ^ 1]);
+            const int nn = min(D.nup[cur], kDirtyCap);
+            if (lane == 0) D.nup[cur ^ 1] = 0;
+            __syncwarp();
             for (int q = 0; q < nn; ++q) {
-                const int64_t node = T.nodes[cur ^ 1][q];
-                const ulonglong2 v = warp_children<PREC>(I, L, lev, node);
-                if (lane == 0) L.p[lev][node] = v;
+                const int64_t node = D.up[cur][q];
+                const unsigned long long old = L.p[lev][node];
+                const unsigned long long nv = warp_node(I, L, lev, node);
+                if (lane == 0) {
+                    L.p[lev][node] = nv;
+                    if (nv < old && lev + 1 < I.nlev && L.p[lev + 1][node >> 5] == old) {
+                        const int r = D.nup[cur ^ 1]++;
+                        if (r < kDirtyCap) D.up[cur ^ 1][r] = (int32_t)(node >> 5);
+                    }
+                }
                 __syncwarp();
             }
             cur ^= 1;
-            ncur = nn;
+        }
+        if (lane == 0) {
+            D.n0 = 0;
+            D.nup[0] = 0;
+            D.nup[1] = 0;
         }
     }
+    if (wait) __syncthreads();
 }
 
 // Whole tree from the leaves (after a full rescan).
-template <int PREC>
 __device__ void rebuild_tree(const Inst& I, const Levels& L) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int lev = 0; lev < I.nlev; ++lev) {
-        for (int64_t node = wid; node < I.lvl_n[lev]; node += kT / 32) {
-            const ulonglong2 v = warp_children<PREC>(I, L, lev, node);
+        for (int64_t node = wid; node < I.lvl_n[lev]; node += kNW) {
+            const unsigned long long v = warp_node(I, L, lev, node);
             if (lane == 0) L.p[lev][node] = v;
         }
         __syncthreads();
     }
 }
 
-// Key of island i at the current spins and fields (FP32 path writes key32/lo32,
-// FP64 path key64).
+// Key of island i from its current state (already loaded): returns the new key
+// and writes lo (and, on the FP64 path, the exact value x).
 template <int PREC>
-__device__ __forceinline__ void rekey(const Inst& I, int64_t i, uint32_t step) {
-    const int si = I.s[i];
-    const uint16_t ci = I.cls[i];
-    float2 th = make_float2(0.0f, 0.0f);
-    if (I.sigma > 0.0) th = I.th32[i];
-    const float2 e32 = I.ext32[ci];
+__device__ __forceinline__ unsigned long long key_of(const Inst& I, int64_t i, uint32_t step,
+                                                     int si, longlong2 h64, int2 h32,
+                                                     float2 rbc, float2 e32, float2 th,
+                                                     double hk, double2 e64, float* lo,
+                                                     double* x64) {
     if constexpr (PREC == 1) {
-        const int2 h = I.h32[i];
-        const float dp = __fmul_rn(__int2float_rn(h.x), I.inv32);
-        const float dq = __fmul_rn(__int2float_rn(h.y), I.inv32);
-        const Eval32 e = eval32(I, si, dp, dq, I.hk32[i], e32, th.x, th.y);
-        I.key32[i] = e.possible ? key32_of(e.hi, i) : 0ull;
-        I.lo32[i] = e.certain ? e.lo : -1.0f;
+        const float dp = __fmul_rn(__int2float_rn(h32.x), I.inv32);
+        const float dq = __fmul_rn(__int2float_rn(h32.y), I.inv32);
+        const Eval32 e = eval32(I, si, dp, dq, rbc, e32, th.x, th.y);
+        *lo = e.certain ? e.lo : -1.0f;
+        return e.possible ? key32_of(e.hi, i) : 0ull;
     } else {
-        const longlong2 h = I.h64[i];
-        const float dp = __fmul_rn(__ll2float_rn(h.x), I.inv64f);
-        const float dq = __fmul_rn(__ll2float_rn(h.y), I.inv64f);
-        const Eval32 e = eval32(I, si, dp, dq, I.hk32[i], e32, th.x, th.y);
-        double key = 0.0;
+        const float dp = __fmul_rn(__ll2float_rn(h64.x), I.inv64f);
+        const float dq = __fmul_rn(__ll2float_rn(h64.y), I.inv64f);
+        const Eval32 e = eval32(I, si, dp, dq, rbc, e32, th.x, th.y);
+        double x = 0.0;
         if (e.possible) {
             double tp = 0.0, tq = 0.0;
             if (I.sigma > 0.0) thermal64(I, i, step, &tp, &tq);
-            const Eval64 f = eval64(I, si, h.x, h.y, I.hk64[i], I.ext64[ci], tp, tq);
-            if (f.flippable) key = f.lhs;
+            const Eval64 f = eval64(I, si, h64.x, h64.y, hk, e64, tp, tq);
+            if (f.flippable) x = f.lhs;
         }
-        I.key64[i] = key;
+        *x64 = x;
+        *lo = x > 0.0 ? __double2float_rd(x) : -1.0f;
+        return x > 0.0 ? key32_of(__double2float_ru(x), i) : 0ull;
     }
 }
 
-// Exact FP64 evaluation of island i from its exact 64-bit sums.
-__device__ __forceinline__ Eval64 exact_eval(const Inst& I, int64_t i, uint32_t step) {
-    double tp = 0.0, tq = 0.0;
-    if (I.sigma > 0.0) thermal64(I, i, step, &tp, &tq);
-    const longlong2 h = I.h64[i];
-    return eval64(I, I.s[i], h.x, h.y, I.hk64[i], I.ext64[I.cls[i]], tp, tq);
+// Island i's field changes by 2 s_new (dp, dq) (exact 64-bit sums; dp32, dq32 the
+// 32-bit ones); its key is re-evaluated and the tree told. Every load is issued
+// before the first store so that they overlap.
+template <int PREC>
+__device__ __forceinline__ void update_island(const Inst& I, const Levels& L, Dirty& D,
+                                              int64_t i, int snew, long long dp, long long dq,
+                                              int dp32, int dq32, uint32_t step) {
+    longlong2 h = I.h64[i];
+    int2 g = make_int2(0, 0);
+    if constexpr (PREC == 1) g = I.h32[i];
+    const unsigned long long old = I.key32[i];
+    const int si = I.s[i];
+    const uint16_t ci = __ldg(&I.cls[i]);
+    const float2 rbc = __ldg(&I.rbc32[i]);
+    float2 th = make_float2(0.0f, 0.0f);
+    if (I.sigma > 0.0) th = I.th32[i];
+    double hk = 0.0;
+    double2 e64 = make_double2(0.0, 0.0);
+    if constexpr (PREC == 0) {
+        hk = __ldg(&I.hk64[i]);
+        e64 = I.ext64[ci];
+    }
+    const float2 e32 = I.ext32[ci];
+    const unsigned long long up = 2ull * (unsigned long long)dp;
+    const unsigned long long uq = 2ull * (unsigned long long)dq;
+    h.x = (long long)(snew > 0 ? (unsigned long long)h.x + up : (unsigned long long)h.x - up);
+    h.y = (long long)(snew > 0 ? (unsigned long long)h.y + uq : (unsigned long long)h.y - uq);
+    if constexpr (PREC == 1) {
+        const unsigned vp = 2u * (unsigned)dp32, vq = 2u * (unsigned)dq32;
+        g.x = (int)(snew > 0 ? (unsigned)g.x + vp : (unsigned)g.x - vp);
+        g.y = (int)(snew > 0 ? (unsigned)g.y + vq : (unsigned)g.y - vq);
+    }
+    float lo;
+    double x = 0.0;
+    const unsigned long long nk = key_of<PREC>(I, i, step, si, h, g, rbc, e32, th, hk, e64, &lo, &x);
+    I.h64[i] = h;
+    if constexpr (PREC == 1) I.h32[i] = g;
+    if constexpr (PREC == 0) I.key64[i] = x;
+    I.key32[i] = nk;
+    I.lo32[i] = lo;
+    leaf_changed(I, L, D, i, old, nk);
+}
+
+// Exact FP64 value of island i (0 when not flippable): on the FP64 path the value
+// kept with its key, on the FP32 path a fresh FP64 evaluation of its exact sums.
+template <int PREC>
+__device__ __forceinline__ double exact_value(const Inst& I, int64_t i, uint32_t step) {
+    if constexpr (PREC == 0) {
+        return I.key64[i];
+    } else {
+        double tp = 0.0, tq = 0.0;
+        if (I.sigma > 0.0) thermal64(I, i, step, &tp, &tq);
+        const longlong2 h = I.h64[i];
+        const Eval64 e = eval64(I, I.s[i], h.x, h.y, I.hk64[i], I.ext64[I.cls[i]], tp, tq);
+        return e.flippable ? e.lhs : 0.0;
+    }
 }
 
 struct RecheckShared {
     int32_t front[2][kRecheckCap];
-    int32_t nfront[2];
     int32_t cand[kRecheckCap];
-    double cand_lhs[kRecheckCap];
-    int32_t cand_ok[kRecheckCap];
-    int32_t sorted[kRecheckCap];
-    int32_t nsorted;
-    int32_t overflow;
+    double cand_val[kRecheckCap];
+    unsigned long long cand_old[kRecheckCap];
+    unsigned long long cand_new[kRecheckCap];
     int32_t result;
     float tau;
 };
 
-// Finds the FP64 winner among islands whose FP32 upper bound reaches tau, or
-// demotes what it proves non-flippable. Returns the winner, -1 when the caller
-// should look at the root again, -3 on a recheck-round overflow (fallback used).
-__device__ int64_t recheck_round(const Inst& I, const Levels& L, RecheckShared& R,
-                                 TreeScratch& T, float tau, uint32_t step) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+// Exact comparison of the islands whose key bound reaches tau, by warp 0 alone.
+// Returns the winner (its exact value is at least tau, so nothing outside the set
+// can beat it), -2 with R.tau lowered to widen the set, -1 when all of them were
+// demoted, -3 when the set overflowed (nothing changed then).
+template <int PREC>
+__device__ int64_t recheck_warp(const Inst& I, const Levels& L, RecheckShared& R, float tau,
+                                uint32_t step) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     const unsigned long long tkey = (unsigned long long)__float_as_uint(tau) << 32;
-    if (threadIdx.x == 0) {
-        R.front[0][0] = 0;
-        R.nfront[0] = 1;
-        R.nfront[1] = 0;
-        R.overflow = 0;
-    }
-    __syncthreads();
-    int cur = 0;
+    // descent from the root through every node whose maximum reaches tau
+    if (lane == 0) R.front[0][0] = 0;
+    __syncwarp();
+    int cur = 0, nf = 1;
     for (int lev = I.nlev - 1; lev >= 0; --lev) {
-        const int nf = R.nfront[cur];
-        for (int f = wid; f < nf; f += kT / 32) {
-            const int64_t node = R.front[cur][f];
-            const int64_t child = (node << 5) + lane;
-            bool hit = false;
+        int nn = 0;
+        for (int f = 0; f < nf; ++f) {
+            const int64_t child = ((int64_t)R.front[cur][f] << 5) + lane;
+            unsigned long long k = 0ull;
             if (lev > 0) {
-                if (child < I.lvl_n[lev - 1]) hit = L.p[lev - 1][child].x >= tkey;
-            } else {
-                if (child < I.n) {
-                    const unsigned long long k = I.key32[child];
-                    hit = k != 0ull && k >= tkey;
-                }
+                if (child < I.lvl_n[lev - 1]) k = L.p[lev - 1][child];
+            } else if (child < I.n) {
+                k = I.key32[child];
             }
+            const bool hit = k != 0ull && k >= tkey;
             const unsigned m = __ballot_sync(0xffffffffu, hit);
-            int base = 0;
-            if (lane == 0 && m) base = atomicAdd(&R.nfront[cur ^ 1], __popc(m));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (hit) {
-                const int pos = base + __popc(m & ((1u << lane) - 1u));
-                if (pos < kRecheckCap)
-                    R.front[cur ^ 1][pos] = (int32_t)child;
-                else
-                    R.overflow = 1;
-            }
+            const int pos = nn + __popc(m & lt);
+            if (hit && pos < kRecheckCap) R.front[cur ^ 1][pos] = (int32_t)child;
+            nn += __popc(m);
         }
-        __syncthreads();
-        if (R.overflow) break;
-        if (threadIdx.x == 0) R.nfront[cur] = 0;
+        __syncwarp();
+        if (nn > kRecheckCap) return -3;
         cur ^= 1;
-        __syncthreads();
+        nf = nn;
     }
-    if (R.overflow) return -3;
-    const int nc = R.nfront[cur];
-    // exact evaluation, one thread per candidate
-    for (int c = threadIdx.x; c < nc; c += kT) {
+    const int nc = nf;
+    // exact values, one lane per candidate; best by (value, lowest index)
+    unsigned long long bv = 0ull;
+    int64_t bi = -1;
+    for (int c = lane; c < nc; c += 32) {
         const int64_t i = R.front[cur][c];
-        const Eval64 e = exact_eval(I, i, step);
+        const double v = exact_value<PREC>(I, i, step);
         R.cand[c] = (int32_t)i;
-        R.cand_lhs[c] = e.lhs;
-        R.cand_ok[c] = e.flippable;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int64_t best = -1;
-        double bl = 0.0;
-        for (int c = 0; c < nc; ++c) {
-            if (!R.cand_ok[c]) continue;
-            const int64_t i = R.cand[c];
-            if (best < 0 || R.cand_lhs[c] > bl || (R.cand_lhs[c] == bl && i < best)) {
-                best = i;
-                bl = R.cand_lhs[c];
-            }
-        }
-        if (best >= 0 && bl >= (double)tau) {
-            R.result = (int32_t)best;
-        } else if (best >= 0) {
-            // something outside the set might beat it: widen to its value
-            R.result = -2;
-            R.tau = __double2float_rd(bl);
-        } else {
-            R.result = -1;
+        R.cand_val[c] = v;
+        const unsigned long long vb = v > 0.0 ? (unsigned long long)__double_as_longlong(v) : 0ull;
+        if (vb > 0ull && (bi < 0 || vb > bv || (vb == bv && i < bi))) {
+            bv = vb;
+            bi = i;
         }
     }
-    __syncthreads();
-    // Demote proven non-flippable candidates; give the flippable ones the tight
-    // bounds of their exact value (valid until their field changes). Then refresh
-    // the tree above them.
-    for (int c = threadIdx.x; c < nc; c += kT) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    // Demote what proved non-flippable; give the flippable ones keys from their
+    // exact values (valid until their field changes). Both only lower keys.
+    for (int c = lane; c < nc; c += 32) {
         const int64_t i = R.cand[c];
-        if (!R.cand_ok[c]) {
-            I.key32[i] = 0ull;
-            I.lo32[i] = -1.0f;
-        } else {
-            I.key32[i] = key32_of(__double2float_ru(R.cand_lhs[c]), i);
-            I.lo32[i] = __double2float_rd(R.cand_lhs[c]);
+        const double v = R.cand_val[c];
+        const unsigned long long old = I.key32[i];
+        const unsigned long long nk = v > 0.0 ? key32_of(__double2float_ru(v), i) : 0ull;
+        I.key32[i] = nk;
+        I.lo32[i] = v > 0.0 ? __double2float_rd(v) : -1.0f;
+        R.cand_old[c] = old;
+        R.cand_new[c] = nk;
+    }
+    __syncwarp();
+    // rebuild the nodes whose maximum was a lowered key, bottom-up
+    for (int c = 0; c < nc; ++c) {
+        const unsigned long long old = R.cand_old[c];
+        if (R.cand_new[c] >= old) continue;
+        int64_t node = (int64_t)R.cand[c];
+        for (int lev = 0; lev < I.nlev; ++lev) {
+            node >>= 5;
+            if (L.p[lev][node] != old) break;
+            const unsigned long long nv = warp_node(I, L, lev, node);
+            if (lane == 0) L.p[lev][node] = nv;
+            __syncwarp();
         }
     }
-    __syncthreads();
-    for (int c = threadIdx.x; c < nc; c += kT) {
-        const int32_t v = R.cand[c];
-        int rank = 0;
-        for (int u = 0; u < nc; ++u) rank += R.cand[u] < v;
-        R.sorted[rank] = v;
+    const double bl = __longlong_as_double((long long)bv);
+    if (bi >= 0 && bl >= (double)tau) return bi;
+    if (bi >= 0) {
+        if (lane == 0) R.tau = __double2float_rd(bl);  // something outside might beat it
+        __syncwarp();
+        return -2;
     }
-    if (threadIdx.x == 0) R.nsorted = nc;
-    __syncthreads();
-    tree_update_sorted<1>(I, L, T, R.sorted, R.nsorted);
-    __syncthreads();
-    return R.result;
+    return -1;
 }
 
-// Fallback when the candidate set overflows: every island with a key at or above
-// tau is evaluated exactly, by one thread each.
+// Fallback when the candidate set overflows: every island whose key reaches tau
+// is compared exactly, one thread each; the tree is rebuilt afterwards.
+template <int PREC>
 __device__ int64_t recheck_scan(const Inst& I, const Levels& L, RecheckShared& R, float tau,
                                 uint32_t step) {
     __shared__ double sbl[kT];
@@ -337,17 +377,12 @@ __device__ int64_t recheck_scan(const Inst& I, const Levels& L, RecheckShared& R
     for (int64_t i = threadIdx.x; i < I.n; i += kT) {
         const unsigned long long k = I.key32[i];
         if (k == 0ull || k < tkey) continue;
-        const Eval64 e = exact_eval(I, i, step);
-        if (!e.flippable) {
-            I.key32[i] = 0ull;
-            I.lo32[i] = -1.0f;
-        } else {
-            I.key32[i] = key32_of(__double2float_ru(e.lhs), i);
-            I.lo32[i] = __double2float_rd(e.lhs);
-            if (bi < 0 || e.lhs > bl || (e.lhs == bl && i < bi)) {
-                bl = e.lhs;
-                bi = i;
-            }
+        const double v = exact_value<PREC>(I, i, step);
+        I.key32[i] = v > 0.0 ? key32_of(__double2float_ru(v), i) : 0ull;
+        I.lo32[i] = v > 0.0 ? __double2float_rd(v) : -1.0f;
+        if (v > 0.0 && (bi < 0 || v > bl || (v == bl && i < bi))) {
+            bl = v;
+            bi = i;
         }
     }
     sbl[threadIdx.x] = bl;
@@ -371,7 +406,7 @@ __device__ int64_t recheck_scan(const Inst& I, const Levels& L, RecheckShared& R
         }
     }
     __syncthreads();
-    rebuild_tree<1>(I, L);
+    rebuild_tree(I, L);
     return R.result;
 }
 
@@ -379,20 +414,20 @@ template <int PREC>
 __global__ void __launch_bounds__(kT, 1)
     k_relax(const Inst* __restrict__ tab, const int32_t* __restrict__ work, int n_work,
             int smem_budget) {
-    extern __shared__ ulonglong2 sm_levels[];
-    __shared__ int32_t list[kMaxPaddedDegree + 1];
+    extern __shared__ unsigned long long sm_levels[];
     __shared__ int64_t sh_k;
     __shared__ int64_t sh_e0, sh_e1;
     __shared__ int32_t sh_snew;
     __shared__ float sh_tau;
     __shared__ RecheckShared R;
-    __shared__ TreeScratch T;
+    __shared__ Dirty D;
 
     const Inst& I = tab[work[blockIdx.x]];
     InstState* st = I.st;
     const int64_t t = st->t;
     if (st->status != ST_OK || t >= I.K) return;
     const uint32_t step = I.step0 + (uint32_t)t;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 
     // Place the upper tree levels in shared memory while they fit.
     Levels L;
@@ -400,7 +435,7 @@ __global__ void __launch_bounds__(kT, 1)
         int64_t used = 0;
         int first_sm = I.nlev;
         for (int lev = I.nlev - 1; lev >= 0; --lev) {
-            const int64_t b = (int64_t)I.lvl_n[lev] * (int64_t)sizeof(ulonglong2);
+            const int64_t b = (int64_t)I.lvl_n[lev] * (int64_t)sizeof(unsigned long long);
             if (used + b > smem_budget) break;
             used += b;
             first_sm = lev;
@@ -417,6 +452,11 @@ __global__ void __launch_bounds__(kT, 1)
         for (int lev = first_sm; lev < I.nlev; ++lev)
             for (int64_t q = threadIdx.x; q < I.lvl_n[lev]; q += kT)
                 L.p[lev][q] = I.tree[I.lvl_off[lev] + q];
+        if (threadIdx.x == 0) {
+            D.n0 = 0;
+            D.nup[0] = 0;
+            D.nup[1] = 0;
+        }
     }
     __syncthreads();
 
@@ -427,8 +467,7 @@ __global__ void __launch_bounds__(kT, 1)
     const int64_t flips_before = threadIdx.x == 0 ? st->n_flips : 0;
     const int64_t max_flips = I.max_flips;
 
-    // Thread 0: flip island k (Sec. "Dynamics"), log it, fold it into the hash and
-    // publish its CSR row for the neighbour update.
+    // Thread 0: flip island k, log it, fold it into the hash, publish its row.
     auto do_flip = [&](int64_t k, int sk, int64_t a0, int64_t a1) {
         const int snew = -sk;
         I.s[k] = (int8_t)snew;
@@ -444,78 +483,84 @@ __global__ void __launch_bounds__(kT, 1)
     };
 
     for (;;) {
-        // pick (and, when the pick is certain, flip) in one step of thread 0
-        if (threadIdx.x == 0) {
-            const ulonglong2 root = L.p[I.nlev - 1][0];
+        // pick, and flip when the pick is certain: warp 0
+        if (wid == 0) {
+            const unsigned long long root = L.p[I.nlev - 1][0];
             int64_t k = -1;
-            if (root.x != 0ull) {
-                const int64_t w = PREC == 1 ? (int64_t)key32_idx(root.x) : (int64_t)root.y;
-                // independent loads, issued together
-                const int sw = I.s[w];
-                const int64_t a0 = I.rp[w], a1 = I.rp[w + 1];
-                if constexpr (PREC == 1) {
-                    const float lo = I.lo32[w];
-                    const float hi2 = root.y ? key32_hi(root.y) : 0.0f;
+            if (root != 0ull) {
+                const int64_t w = key32_idx(root);
+                float lo = 0.0f;
+                int sw = 0;
+                int64_t a0 = 0, a1 = 0;
+                if (lane == 0) {  // independent loads, in flight during the runner-up scan
+                    lo = I.lo32[w];
+                    sw = I.s[w];
+                    a0 = I.rp[w];
+                    a1 = I.rp[w + 1];
+                }
+                const unsigned long long ru = runner_up(I, L, w);
+                if (lane == 0) {
+                    const float hi2 = ru ? key32_hi(ru) : 0.0f;
                     if (lo > 1.0f && lo > hi2) {
-                        k = w;
+                        if (flips < max_flips) {
+                            do_flip(w, sw, a0, a1);
+                            k = w;
+                        } else {
+                            k = -6;
+                        }
                     } else {
                         k = -2;
                         sh_tau = fmaxf(hi2, lo);
                     }
-                } else {
-                    k = w;
-                }
-                if (k >= 0) {
-                    if (flips < max_flips)
-                        do_flip(k, sw, a0, a1);
-                    else
-                        k = -6;
                 }
             }
-            sh_k = k;
+            if (lane == 0) sh_k = k;
         }
         __syncthreads();
         int64_t k = sh_k;
-        if constexpr (PREC == 1) {
-            if (k == -2) {
-                float tau = sh_tau;
-                while (k == -2) {
-                    if (++rounds > 64) {
-                        k = -4;
-                        break;
-                    }
-                    if (threadIdx.x == 0) atomicAdd((unsigned long long*)&st->rechecks, 1ull);
-                    int64_t r = recheck_round(I, L, R, T, tau, step);
-                    if (r == -3) {
-                        if (threadIdx.x == 0)
-                            atomicAdd((unsigned long long*)&st->fallbacks, 1ull);
-                        r = recheck_scan(I, L, R, tau, step);
-                    }
-                    __syncthreads();
-                    tau = R.tau;
-                    if (r == -1) {
-                        k = -5;  // everything examined was demoted: look at the root again
-                        rounds = 0;
-                    } else {
-                        k = r;  // the winner, or -2 to widen
-                    }
-                    __syncthreads();
-                }
-                if (k == -5) continue;
-                if (k == -4) {
-                    status = ST_BOUNDS;
+        if (k == -2) {
+            float tau = sh_tau;
+            while (k == -2) {
+                if (++rounds > 64) {
+                    k = -4;
                     break;
                 }
-                if (k >= 0) {
-                    if (threadIdx.x == 0) {
-                        if (flips < max_flips)
-                            do_flip(k, I.s[k], I.rp[k], I.rp[k + 1]);
-                        else
-                            sh_k = -6;
+                if (wid == 0) {
+                    const int64_t r = recheck_warp<PREC>(I, L, R, tau, step);
+                    if (lane == 0) {
+                        R.result = (int32_t)r;
+                        atomicAdd((unsigned long long*)&st->rechecks, 1ull);
                     }
-                    __syncthreads();
-                    if (sh_k == -6) k = -6;
                 }
+                __syncthreads();
+                int64_t r = R.result;
+                if (r == -3) {
+                    if (threadIdx.x == 0) atomicAdd((unsigned long long*)&st->fallbacks, 1ull);
+                    r = recheck_scan<PREC>(I, L, R, tau, step);
+                }
+                tau = R.tau;
+                if (r == -1) {
+                    k = -5;  // everything examined was demoted: look at the root again
+                    rounds = 0;
+                } else {
+                    k = r;  // the winner, or -2 to widen
+                }
+                __syncthreads();
+            }
+            if (k == -5) continue;
+            if (k == -4) {
+                status = ST_BOUNDS;
+                break;
+            }
+            if (k >= 0) {
+                if (threadIdx.x == 0) {
+                    if (flips < max_flips)
+                        do_flip(k, I.s[k], I.rp[k], I.rp[k + 1]);
+                    else
+                        sh_k = -6;
+                }
+                __syncthreads();
+                if (sh_k == -6) k = -6;
             }
         }
         rounds = 0;
@@ -525,43 +570,27 @@ __global__ void __launch_bounds__(kT, 1)
         }
         if (k < 0) break;
         ++flips;
-        // every neighbour i of k: add 2 s_k(new) (P_ik, Q_ik) and re-evaluate i
+        // every neighbour i of k: add 2 s_k(new) (P_ik, Q_ik), new key, tree update
         const int snew = sh_snew;
         const int64_t e0 = sh_e0;
         const int len = (int)(sh_e1 - e0);
         for (int q = threadIdx.x; q < len; q += kT) {
             const int64_t e = e0 + q;
-            const int32_t i = I.col[e];
-            if (i == (int32_t)k) {
-                list[q] = -1;  // row padding
-                continue;
-            }
-            {
-                longlong2 h = I.h64[i];
-                const unsigned long long up = 2ull * (unsigned long long)I.pq64[e].x;
-                const unsigned long long uq = 2ull * (unsigned long long)I.qt64[e];
-                h.x = (long long)(snew > 0 ? (unsigned long long)h.x + up
-                                           : (unsigned long long)h.x - up);
-                h.y = (long long)(snew > 0 ? (unsigned long long)h.y + uq
-                                           : (unsigned long long)h.y - uq);
-                I.h64[i] = h;
-            }
+            // the row's entries (read-only), all issued before the padding test
+            const int32_t i = __ldg(&I.col[e]);
+            const long long dp = __ldg(&I.pq64[e].x), dq = __ldg(&I.qt64[e]);
+            int dp32 = 0, dq32 = 0;
             if constexpr (PREC == 1) {
-                int2 h = I.h32[i];
-                const unsigned up = 2u * (unsigned)I.pq32[e].x, uq = 2u * (unsigned)I.qt32[e];
-                h.x = (int)(snew > 0 ? (unsigned)h.x + up : (unsigned)h.x - up);
-                h.y = (int)(snew > 0 ? (unsigned)h.y + uq : (unsigned)h.y - uq);
-                I.h32[i] = h;
+                dp32 = __ldg(&I.pq32[e].x);
+                dq32 = __ldg(&I.qt32[e]);
             }
-            rekey<PREC>(I, i, step);
-            list[q] = i;
+            if (i == (int32_t)k) continue;  // row padding
+            update_island<PREC>(I, L, D, i, snew, dp, dq, dp32, dq32, step);
         }
-        if (threadIdx.x == kT - 1) {
-            rekey<PREC>(I, k, step);
-            list[len] = (int32_t)k;
-        }
+        if (threadIdx.x == kT - 1)  // k's own field is unchanged; its key is not
+            update_island<PREC>(I, L, D, k, snew, 0, 0, 0, 0, step);
         __syncthreads();
-        tree_update_sorted<PREC>(I, L, T, list, len + 1);
+        rebuild_dirty(I, L, D, false);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -591,7 +620,7 @@ __global__ void k_eval_all(const Inst* __restrict__ tab, double hx, double hy, u
         const int2 h = I.h32[i];
         const float2 th = I.sigma > 0.0 ? thermal32(I, i, step) : make_float2(0.0f, 0.0f);
         const Eval32 e = eval32(I, si, __fmul_rn(__int2float_rn(h.x), I.inv32),
-                                __fmul_rn(__int2float_rn(h.y), I.inv32), I.hk32[i],
+                                __fmul_rn(__int2float_rn(h.y), I.inv32), I.rbc32[i],
                                 make_float2(__double2float_rn(ext.x), __double2float_rn(ext.y)),
                                 th.x, th.y);
         hpar[i] = e.hpar;

@@ -43,42 +43,17 @@ __device__ __forceinline__ int find_inst(const int64_t* __restrict__ start, int 
 __device__ __forceinline__ int sgn_sel(int8_t s, int v) { return s > 0 ? v : -v; }
 __device__ __forceinline__ long long sgn_sel(int8_t s, long long v) { return s > 0 ? v : -v; }
 
-// Merge of two FP64 nodes (LHS bits, index).
-__device__ __forceinline__ ulonglong2 best64(ulonglong2 a, ulonglong2 b) {
-    return better64(a.x, a.y, b.x, b.y) ? a : b;
-}
-
-template <int PREC>
-__device__ __forceinline__ ulonglong2 merge_node(ulonglong2 a, ulonglong2 b) {
-    if constexpr (PREC == 1)
-        return top2(a, b);
-    else
-        return best64(a, b);
-}
-
-template <int PREC>
-__device__ __forceinline__ ulonglong2 warp_merge(ulonglong2 v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        ulonglong2 u;
-        u.x = __shfl_xor_sync(0xffffffffu, v.x, o);
-        u.y = __shfl_xor_sync(0xffffffffu, v.y, o);
-        v = merge_node<PREC>(v, u);
-    }
-    return v;
-}
-
-template <int PREC>
-__device__ __forceinline__ ulonglong2 empty_node() {
-    if constexpr (PREC == 1)
-        return make_ulonglong2(0ull, 0ull);
-    else
-        return make_ulonglong2(0ull, 0xFFFFFFFFFFFFFFFFull);
+// Warp maximum of 64-bit keys (every lane gets it): the largest upper half, then
+// among those the largest lower half.
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v) {
+    const unsigned hi = (unsigned)(v >> 32), lo = (unsigned)v;
+    const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+    return ((unsigned long long)mh << 32) | ml;
 }
 
 // Called by a full warp after lane 0 wrote node `idx` of level `lev`: the last
 // of its siblings to arrive builds the parent, and so on up to the root.
-template <int PREC>
 __device__ void propagate_up(const Inst& I, unsigned* __restrict__ tcnt, int lev, int64_t idx) {
     const int lane = threadIdx.x & 31;
     while (lev + 1 < I.nlev) {
@@ -93,9 +68,9 @@ __device__ void propagate_up(const Inst& I, unsigned* __restrict__ tcnt, int lev
         if (old + 1 != nchild) return;
         if (lane == 0) tcnt[I.lvl_off[lev + 1] + parent] = 0u;
         __threadfence();
-        ulonglong2 v = empty_node<PREC>();
+        unsigned long long v = 0ull;
         if (first + lane < last) v = __ldcg(&I.tree[I.lvl_off[lev] + first + lane]);
-        v = warp_merge<PREC>(v);
+        v = warp_max_key(v);
         if (lane == 0) I.tree[I.lvl_off[lev + 1] + parent] = v;
         ++lev;
         idx = parent;
@@ -185,7 +160,7 @@ __global__ void __launch_bounds__(kSweepThreads)
     }
 
     const int64_t i = r0 + lane;
-    ulonglong2 node = empty_node<PREC>();
+    unsigned long long node = 0ull;
     if (i < I.n) {
         const uint32_t step = I.step0 + (uint32_t)t;
         const int si = I.s[i];
@@ -211,31 +186,31 @@ __global__ void __launch_bounds__(kSweepThreads)
             }
             const float dp = __fmul_rn(__int2float_rn(h.x), I.inv32);
             const float dq = __fmul_rn(__int2float_rn(h.y), I.inv32);
-            const Eval32 e = eval32(I, si, dp, dq, I.hk32[i], e32, th.x, th.y);
-            const unsigned long long key = e.possible ? key32_of(e.hi, i) : 0ull;
-            I.key32[i] = key;
+            const Eval32 e = eval32(I, si, dp, dq, I.rbc32[i], e32, th.x, th.y);
+            node = e.possible ? key32_of(e.hi, i) : 0ull;
+            I.key32[i] = node;
             I.lo32[i] = e.certain ? e.lo : -1.0f;
-            node = make_ulonglong2(key, 0ull);
         } else {
             if (!SUM64) h64 = I.h64[i];
             const float dp = __fmul_rn(__ll2float_rn(h64.x), I.inv64f);
             const float dq = __fmul_rn(__ll2float_rn(h64.y), I.inv64f);
-            const Eval32 e = eval32(I, si, dp, dq, I.hk32[i], e32, th.x, th.y);
-            double key = 0.0;
+            const Eval32 e = eval32(I, si, dp, dq, I.rbc32[i], e32, th.x, th.y);
+            double x = 0.0;
             if (e.possible) {
                 double tp = 0.0, tq = 0.0;
                 if (I.sigma > 0.0) thermal64(I, i, step, &tp, &tq);
                 const Eval64 f = eval64(I, si, h64.x, h64.y, I.hk64[i], I.ext64[ci], tp, tq);
-                if (f.flippable) key = f.lhs;
+                if (f.flippable) x = f.lhs;
             }
-            I.key64[i] = key;
-            node = make_ulonglong2((unsigned long long)__double_as_longlong(key),
-                                   (unsigned long long)i);
+            I.key64[i] = x;
+            node = x > 0.0 ? key32_of(__double2float_ru(x), i) : 0ull;
+            I.key32[i] = node;
+            I.lo32[i] = x > 0.0 ? __double2float_rd(x) : -1.0f;
         }
     }
-    node = warp_merge<PREC>(node);
+    node = warp_max_key(node);
     if (lane == 0) I.tree[I.lvl_off[0] + lt] = node;
-    propagate_up<PREC>(I, tcnts[inst], 0, lt);
+    propagate_up(I, tcnts[inst], 0, lt);
 }
 
 // Projections of the current step's external field on every angle class of every
