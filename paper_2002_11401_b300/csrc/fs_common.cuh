@@ -96,10 +96,13 @@ struct Inst {
     uint32_t instance;
     int32_t pad0;
     int64_t max_flips;
-    // FP32 error model: |h32 - h64| <= dh_abs + dh_rel * (|h_dip| + |h_ext| + |h_th|);
+    // FP32 error model: |h32 - h64| <= dh_abs + th_rel * |h_th| + dh_rel * (|h_dip| +
+    // |h_ext| + |h_th|);
     // div_rel bounds the relative error of |h| / (b h_k) against the FP64 division,
     // pow_rel that of powf
     float dh_abs, dh_rel, pow_rel, div_rel;
+    float th_rel;   // |th32 - th64| <= th_rel (|th_par| + |th_perp|)
+    float pad2;
     InstState* st;
 };
 
@@ -155,9 +158,12 @@ __device__ __forceinline__ void box_muller64(const uint32_t w[4], double* z0, do
     *z1 = __dmul_rn(rad, sn);
 }
 
-// FP32 Box-Muller of the same block. ln(u1) is taken from u1 itself when
-// u1 < 1/2 and from log1p(-(1 - u1)) otherwise, with 1 - u1 formed exactly in
-// integers, so the result carries a small relative error at every u1.
+// FP32 Box-Muller of the same block, with an error relative to the radius.
+// ln(u1) is taken from u1 itself when u1 < 1/2 and from log1p(-(1 - u1))
+// otherwise, with 1 - u1 formed exactly in integers. The angle 2 pi u2 = pi x,
+// x = (2b + 1) 2^-53, is split exactly in integers into x_hi (24 bits) + x_lo, and
+// sincospi(x_hi) is corrected to first order in pi x_lo (|pi x_lo| < 4e-7), so the
+// 53-bit uniform is not rounded to 24 bits first.
 __device__ __forceinline__ void box_muller32(const uint32_t w[4], float* z0, float* z1) {
     const uint64_t a = u53(w[0], w[1]);
     const uint64_t b = u53(w[2], w[3]);
@@ -172,11 +178,16 @@ __device__ __forceinline__ void box_muller32(const uint32_t w[4], float* z0, flo
         l = log1pf(-om);
     }
     const float rad = sqrtf(__fmul_rn(-2.0f, l));
-    const float u2 = __fmul_rn(__ull2float_rn(b) + 0.5f, 0x1.0p-53f);
+    const uint64_t x = 2 * b + 1;  // < 2^54
+    const float xh = __fmul_rn(__uint2float_rn((uint32_t)(x >> 30)), 0x1.0p-23f);
+    const float xl = __fmul_rn(__uint2float_rn((uint32_t)(x & ((1u << 30) - 1u))), 0x1.0p-53f);
     float sn, cs;
-    sincospif(__fmul_rn(2.0f, u2), &sn, &cs);
-    *z0 = __fmul_rn(rad, cs);
-    *z1 = __fmul_rn(rad, sn);
+    sincospif(xh, &sn, &cs);
+    const float d = __fmul_rn(3.14159265f, xl);
+    const float c2 = __fsub_rn(cs, __fmul_rn(sn, d));
+    const float s2 = __fadd_rn(sn, __fmul_rn(cs, d));
+    *z0 = __fmul_rn(rad, c2);
+    *z1 = __fmul_rn(rad, s2);
 }
 
 // Thermal field (par, perp) of island i at thermal step `step`: counter
@@ -287,10 +298,14 @@ __device__ __forceinline__ Eval32 eval32(const Inst& I, int s, float dp, float d
     e.hpar = __fadd_rn(__fadd_rn(dp, ext.x), tp);
     e.hperp = __fadd_rn(__fadd_rn(dq, ext.y), tq);
     // field error bound: fixed point + thermal draw (absolute), float roundings
-    const float dpar = __fadd_ru(I.dh_abs, __fmul_ru(I.dh_rel, __fadd_ru(__fadd_ru(fabsf(dp),
-                                                                     fabsf(ext.x)), fabsf(tp))));
-    const float dperp = __fadd_ru(I.dh_abs, __fmul_ru(I.dh_rel, __fadd_ru(__fadd_ru(fabsf(dq),
-                                                                      fabsf(ext.y)), fabsf(tq))));
+    // thermal draw: its FP32 error is relative to the radius |th| <= |tp| + |tq|
+    const float dth = __fmul_ru(I.th_rel, __fadd_ru(fabsf(tp), fabsf(tq)));
+    const float dpar = __fadd_ru(__fadd_ru(I.dh_abs, dth),
+                                 __fmul_ru(I.dh_rel, __fadd_ru(__fadd_ru(fabsf(dp), fabsf(ext.x)),
+                                                               fabsf(tp))));
+    const float dperp = __fadd_ru(__fadd_ru(I.dh_abs, dth),
+                                  __fmul_ru(I.dh_rel, __fadd_ru(__fadd_ru(fabsf(dq), fabsf(ext.y)),
+                                                                fabsf(tq))));
     const float ap = fabsf(e.hpar), aq = fabsf(e.hperp);
     const float x = __fmul_rn(ap, rbc.x), y = __fmul_rn(aq, rbc.y);
     const float tx = pow_nonneg(x, I.pexpf), ty = pow_nonneg(y, I.qexpf);

@@ -182,6 +182,15 @@ __device__ __forceinline__ unsigned long long key_of(const Inst& I, int64_t i, u
         const float dp = __fmul_rn(__int2float_rn(h32.x), I.inv32);
         const float dq = __fmul_rn(__int2float_rn(h32.y), I.inv32);
         const Eval32 e = eval32(I, si, dp, dq, rbc, e32, th.x, th.y);
+        if (e.possible && !e.certain) {
+            // within its band of the threshold or of the sign change: FP64 now
+            double tp = 0.0, tq = 0.0;
+            if (I.sigma > 0.0) thermal64(I, i, step, &tp, &tq);
+            const Eval64 f = eval64(I, si, h64.x, h64.y, hk, e64, tp, tq);
+            const double x = f.flippable ? f.lhs : 0.0;
+            *lo = x > 0.0 ? __double2float_rd(x) : -1.0f;
+            return x > 0.0 ? key32_of(__double2float_ru(x), i) : 0ull;
+        }
         *lo = e.certain ? e.lo : -1.0f;
         return e.possible ? key32_of(e.hi, i) : 0ull;
     } else {
@@ -217,12 +226,8 @@ __device__ __forceinline__ void update_island(const Inst& I, const Levels& L, Di
     const float2 rbc = __ldg(&I.rbc32[i]);
     float2 th = make_float2(0.0f, 0.0f);
     if (I.sigma > 0.0) th = I.th32[i];
-    double hk = 0.0;
-    double2 e64 = make_double2(0.0, 0.0);
-    if constexpr (PREC == 0) {
-        hk = __ldg(&I.hk64[i]);
-        e64 = I.ext64[ci];
-    }
+    const double hk = __ldg(&I.hk64[i]);
+    const double2 e64 = I.ext64[ci];
     const float2 e32 = I.ext32[ci];
     const unsigned long long up = 2ull * (unsigned long long)dp;
     const unsigned long long uq = 2ull * (unsigned long long)dq;
