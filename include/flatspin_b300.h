@@ -182,6 +182,11 @@ typedef struct {
 fs_status fs_set_profiling(fs_sim* sim, int32_t on);
 fs_status fs_get_profile(fs_sim* sim, fs_profile* out);
 
+/* Sweep autotuner: times the field-and-margin sweep with 4, 8, 16 and 32 lanes per
+ * CSR row on this system and keeps the fastest for later calls; *lanes_out (may be
+ * NULL) receives the choice. Every choice gives bit-identical results. */
+fs_status fs_autotune(fs_sim* sim, int32_t* lanes_out);
+
 /* Current spins, n values. */
 fs_status fs_get_spins(const fs_sim* sim, int8_t* out, int64_t n);
 
@@ -247,11 +252,11 @@ fs_status fs_batch_run_protocol(fs_sim* const* sims, int32_t n, const double* hx
                                 uint64_t* seq_hash, int32_t* status, int64_t* flips_per_step);
 
 /* ---- Continuous-batching server ---------------------------------------------
- * A host thread admits requests while their device footprint fits the budget,
- * builds them on a side stream, and advances every admitted simulation one field
- * step per iteration (one batched sweep and one batched relax launch); requests
- * that arrive while others run join at the next iteration. Results equal those
- * of running each request alone. */
+ * Builder threads admit requests while their estimated device footprint fits the
+ * budget and build them on side streams; every admitted request then gets a
+ * stream of its own with its whole protocol queued, so requests that arrive while
+ * others run start as soon as they are built and all of them overlap on the
+ * device. Results equal those of running each request alone. */
 typedef struct fs_server fs_server;
 
 typedef struct {

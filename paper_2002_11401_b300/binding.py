@@ -27,7 +27,7 @@ EXPORTS = (
     "fs_get_hk", "fs_get_geometry", "fs_get_info", "fs_get_csr", "fs_batch_run_protocol",
     "fs_server_create", "fs_server_submit", "fs_server_poll", "fs_server_drain",
     "fs_server_now", "fs_server_destroy", "fs_server_last_error", "fs_set_spins_dev",
-    "fs_set_profiling", "fs_get_profile", "fs_eval_argmax_static",
+    "fs_set_profiling", "fs_get_profile", "fs_eval_argmax_static", "fs_autotune",
 )
 
 
@@ -118,6 +118,7 @@ def load():
             "fs_set_profiling": ([P, i32], i32),
             "fs_get_profile": ([P, P], i32),
             "fs_eval_argmax_static": ([P, P, dbl, dbl, u32, P, P, P], i32),
+            "fs_autotune": ([P, P], i32),
         }
         for name, (args, res) in sig.items():
             if not hasattr(lib, name):
@@ -209,6 +210,11 @@ class Sim:
 
     def set_profiling(self, on: bool):
         self._check(self._lib.fs_set_profiling(self._h, int(bool(on))))
+
+    def autotune(self) -> int:
+        lanes = C.c_int32(0)
+        self._check(self._lib.fs_autotune(self._h, C.byref(lanes)))
+        return int(lanes.value)
 
     def profile(self) -> dict:
         out = fs_profile()

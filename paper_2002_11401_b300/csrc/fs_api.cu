@@ -531,10 +531,27 @@ extern "C" fs_status fs_set_field(fs_sim* sim, double hx, double hy, uint32_t st
 
 namespace fs {
 
+// Dynamic shared memory of a relax CTA: the tree levels above the keys that fit
+// in 96 KiB, counted from the root down (the kernel places them the same way).
+// Small systems take little, so several relax CTAs share an SM.
 int relax_smem_budget(int64_t n) {
-    (void)n;
-    return 96 * 1024;
+    const int64_t cap = 96 * 1024;
+    std::vector<int64_t> lv;
+    int64_t cnt = (n + 31) / 32;
+    for (;;) {
+        lv.push_back(8 * cnt);
+        if (cnt <= 1) break;
+        cnt = (cnt + 31) / 32;
+    }
+    int64_t used = 0;
+    for (size_t q = lv.size(); q-- > 0;) {
+        if (used + lv[q] > cap) break;
+        used += lv[q];
+    }
+    return (int)std::max<int64_t>(1024, used);
 }
+
+int relax_smem_max() { return 96 * 1024; }
 
 // Queues K field steps of one simulation (sweep + relax per step). The
 // descriptor's protocol fields must already point at device buffers.
@@ -940,5 +957,68 @@ extern "C" fs_status fs_get_profile(fs_sim* sim, fs_profile* out) {
     out->relax_launches = sim->prof_relaxes;
     out->rechecks = sim->rechecks;
     out->fallbacks = sim->fallbacks;
+    return FS_OK;
+}
+
+// Sweep autotuner: times the sweep with 4, 8, 16 and 32 lanes per CSR row (CUDA
+// events, best of three after one warm-up each) at the current spins and field and
+// keeps the fastest. Every choice gives bit-identical results (integer sums).
+extern "C" fs_status fs_autotune(fs_sim* sim, int32_t* lanes_out) {
+    fs_status r = need_built(sim);
+    if (r != FS_OK) return r;
+    r = refresh_fields(sim);
+    if (r != FS_OK) return r;
+    cudaStream_t st = sim->stream;
+    double f[2] = {sim->hx, sim->hy};
+    CK(cudaMemcpyAsync(sim->d_field, f, 16, cudaMemcpyHostToDevice, st), "upload");
+    Inst I = sim->inst;
+    I.phx = sim->d_field;
+    I.phy = sim->d_field + 1;
+    I.K = 1;
+    I.step0 = sim->step;
+    sim->inst_run = I;
+    CK(cudaMemcpyAsync(sim->d_inst, &sim->inst_run, sizeof(Inst), cudaMemcpyHostToDevice, st),
+       "upload");
+    memset(&sim->state_host, 0, sizeof(InstState));
+    CK(cudaMemcpyAsync(sim->d_state, &sim->state_host, sizeof(InstState), cudaMemcpyHostToDevice,
+                       st),
+       "upload");
+    SweepLaunch S;
+    S.tab = sim->d_inst;
+    S.task_start = sim->d_task_start;
+    S.n_inst = 1;
+    S.total_tasks = (sim->n + 31) / 32;
+    S.tcnts = sim->d_tcnts;
+    S.prec = sim->p.precision;
+    S.resweep = 1;
+    CK(launch_ext_table(S, st), "sweep");
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    const int cands[4] = {4, 8, 16, 32};
+    int best = sim->lanes;
+    float best_ms = 1e30f;
+    for (int c = 0; c < 4; ++c) {
+        S.lanes_per_row = cands[c];
+        CK(launch_sweep(S, st), "sweep");
+        float ms = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, st);
+            CK(launch_sweep(S, st), "sweep");
+            cudaEventRecord(e1, st);
+            CK(cudaEventSynchronize(e1), "sweep");
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            ms = std::min(ms, t);
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = cands[c];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    sim->lanes = best;
+    if (lanes_out) *lanes_out = best;
     return FS_OK;
 }

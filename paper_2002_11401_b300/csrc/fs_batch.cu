@@ -183,7 +183,8 @@ extern "C" fs_status fs_batch_run_protocol(fs_sim* const* sims, int32_t n, const
     BatchTable B;
     if ((e = B.upload(v, descs, st)) != cudaSuccess) return bail(e, "upload");
     const int prec = lead->p.precision;
-    const int smem = relax_smem_budget(0);
+    int smem = 1024;
+    for (int i = 0; i < n; ++i) smem = std::max(smem, relax_smem_budget(v[(size_t)i]->n));
     if ((e = prepare_relax(prec, smem)) != cudaSuccess) return bail(e, "relax setup");
     // capture the whole protocol in one graph
     cudaGraph_t graph = nullptr;

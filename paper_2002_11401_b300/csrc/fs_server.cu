@@ -2,14 +2,17 @@
 //
 // Three parties:
 //   - callers submit requests (geometry, parameters, field protocol) and poll;
-//   - a builder thread admits pending requests while their estimated device
-//     footprint fits the budget, and builds each (geometry, h_k draw, neighbour
-//     tensors) on its own stream, overlapping the running iterations;
-//   - a worker thread owns the active set and advances it one field step per
-//     iteration (one batched sweep launch over every active member's rows, one
-//     relax CTA per member), re-uploading the batch table only when members join
-//     or leave. Finished members are retired between iterations: final state
-//     read back, memory freed, budget returned.
+//   - builder threads admit pending requests while their estimated device
+//     footprint fits the budget, and build each (geometry, h_k draw, neighbour
+//     tensors) on their own streams, overlapping the running iterations;
+//   - the builder also captures the request's whole protocol (per field step:
+//     external-field table, sweep, relax) as one CUDA graph;
+//   - a worker thread launches every admitted request's graph on a stream of its
+//     own, so requests advance independently and their
+//     sweeps and relaxes overlap on the device (requests that arrive while others
+//     run start as soon as they are built); finished requests are retired as their
+//     completion events fire: final state read back, memory freed, budget
+//     returned.
 // Device waits are all host-side stream synchronisations; no kernel waits on the
 // host.
 #include <cuda_runtime.h>
@@ -30,7 +33,6 @@
 #include <vector>
 
 #include "../../include/flatspin_b300.h"
-#include "fs_batch.h"
 #include "fs_common.cuh"
 #include "fs_internal.h"
 #include "fs_kernels.h"
@@ -49,12 +51,13 @@ struct Job {
     fs_result res{};
     double* d_hx = nullptr;
     double* d_hy = nullptr;
+    cudaGraphExec_t exec = nullptr;  // the request's whole protocol, one launch
 };
 
-// Device bytes of one request before it is built: per island ~80 B of state and,
-// per neighbour pair, the CSR entry (4 B), both coefficient widths and the
-// transposed copies (44 B); the degree is the cutoff disc's area times the
-// array's island density, with 25% slack.
+// Device bytes of one request before it is built: per island ~120 B of state
+// and, per neighbour pair, the CSR entry and both coefficient widths with their
+// transposed copies (40 B); the degree is the cutoff disc's area times the array's
+// island density, plus a margin for the rounding of the rows to multiples of 4.
 size_t estimate_bytes(const fs_request& r) {
     const double rc = r.params.cutoff;
     double n, density;
@@ -65,8 +68,8 @@ size_t estimate_bytes(const fs_request& r) {
         n = 2.0 * r.nx * r.ny + r.nx + r.ny;
         density = 2.0;
     }
-    const double deg = 1.25 * M_PI * rc * rc * density + 8.0;
-    return (size_t)(n * (deg * 44.0 + 96.0) + 8.0 * r.K * 2.0 + (1 << 20));
+    const double deg = 1.05 * M_PI * rc * rc * density + 8.0;
+    return (size_t)(n * (deg * 40.0 + 120.0) + 16.0 * r.K + (1 << 20));
 }
 
 }  // namespace
@@ -76,7 +79,8 @@ struct fs_server {
     int max_active = 256;
     std::atomic<size_t> used{0};
     std::chrono::steady_clock::time_point t0;
-    cudaStream_t main_st = nullptr, build_st = nullptr;
+    cudaStream_t main_st = nullptr;
+    std::vector<cudaStream_t> build_st;
     std::mutex mu;
     std::condition_variable cv_build, cv_work, cv_done;
     std::deque<std::shared_ptr<Job>> pending;
@@ -85,7 +89,8 @@ struct fs_server {
     uint64_t next_ticket = 1;
     int64_t outstanding = 0;
     bool stop = false;
-    std::thread builder, worker;
+    std::vector<std::thread> builders;
+    std::thread worker;
     std::string err;
     int device = 0;
 
@@ -105,8 +110,9 @@ void finish(fs_server* S, const std::shared_ptr<Job>& j, int32_t status) {
     S->cv_done.notify_all();
 }
 
-void builder_loop(fs_server* S) {
+void builder_loop(fs_server* S, int which) {
     cudaSetDevice(S->device);
+    cudaStream_t bst = S->build_st[(size_t)which];
     for (;;) {
         std::shared_ptr<Job> j;
         {
@@ -128,23 +134,68 @@ void builder_loop(fs_server* S) {
         fs_sim* sim = nullptr;
         fs_status st = fs_create_geometry(j->req.kind, j->req.nx, j->req.ny, j->req.a, &sim);
         if (st == FS_OK) {
-            fs_set_stream(sim, S->build_st);
+            fs_set_stream(sim, bst);
             st = fs_set_params(sim, &j->req.params);
         }
         if (st == FS_OK) {
             // protocol buffers live in the simulation's per-call arena
             Arena& A = sim->run;
             const int64_t K = std::max<int64_t>(j->req.K, 1);
-            if (A.alloc((void**)&j->d_hx, 8 * K, S->build_st) != cudaSuccess ||
-                A.alloc((void**)&j->d_hy, 8 * K, S->build_st) != cudaSuccess)
+            if (A.alloc((void**)&j->d_hx, 8 * K, bst) != cudaSuccess ||
+                A.alloc((void**)&j->d_hy, 8 * K, bst) != cudaSuccess)
                 st = FS_ERR_OOM;
             else if (j->req.K > 0 &&
                      (cudaMemcpyAsync(j->d_hx, j->hx.data(), 8 * j->req.K, cudaMemcpyHostToDevice,
-                                      S->build_st) != cudaSuccess ||
+                                      bst) != cudaSuccess ||
                       cudaMemcpyAsync(j->d_hy, j->hy.data(), 8 * j->req.K, cudaMemcpyHostToDevice,
-                                      S->build_st) != cudaSuccess))
+                                      bst) != cudaSuccess))
                 st = FS_ERR_CUDA;
-            if (cudaStreamSynchronize(S->build_st) != cudaSuccess) st = FS_ERR_CUDA;
+            if (cudaStreamSynchronize(bst) != cudaSuccess) st = FS_ERR_CUDA;
+        }
+        if (st != FS_OK) {
+            if (sim) fs_destroy(sim);
+            S->used -= j->reserved;
+            j->res.n = 0;
+            finish(S, j, st);
+            S->cv_build.notify_all();
+            continue;
+        }
+        // descriptor and fresh state on the device, then the protocol captured as one
+        // graph (K field steps: external-field table, sweep, relax)
+        if (st == FS_OK) {
+            Inst I = sim->inst;
+            I.phx = j->d_hx;
+            I.phy = j->d_hy;
+            I.K = j->req.K;
+            I.step0 = 0;
+            I.resweep = 1;
+            I.log_step = nullptr;
+            I.log_spin = nullptr;
+            I.log_cap = 0;
+            I.flips_per_step = nullptr;
+            sim->inst_run = I;
+            memset(&sim->state_host, 0, sizeof(InstState));
+            sim->state_host.hash = fs_hash_init();
+            sim->state_host.init = 1;
+            cudaGraph_t graph = nullptr;
+            bool ok = cudaMemcpy(sim->d_inst, &sim->inst_run, sizeof(Inst),
+                                 cudaMemcpyHostToDevice) == cudaSuccess &&
+                      cudaMemcpy(sim->d_state, &sim->state_host, sizeof(InstState),
+                                 cudaMemcpyHostToDevice) == cudaSuccess &&
+                      cudaStreamBeginCapture(bst, cudaStreamCaptureModeThreadLocal) ==
+                          cudaSuccess;
+            if (ok) {
+                const cudaError_t le = enqueue_steps(sim, j->req.K, 1, bst);
+                const cudaError_t ce = cudaStreamEndCapture(bst, &graph);
+                ok = le == cudaSuccess && ce == cudaSuccess && graph &&
+                     cudaGraphInstantiate(&j->exec, graph, 0) == cudaSuccess;
+            }
+            if (graph) cudaGraphDestroy(graph);
+            if (!ok) {
+                if (j->exec) cudaGraphExecDestroy(j->exec);
+                j->exec = nullptr;
+                st = FS_ERR_CUDA;
+            }
         }
         if (st != FS_OK) {
             if (sim) fs_destroy(sim);
@@ -170,112 +221,116 @@ void builder_loop(fs_server* S) {
     }
 }
 
+// The worker: every admitted request's protocol graph is launched on a stream of
+// its own, followed by an event; requests therefore advance independently and
+// their kernels overlap on the device. Completion is found by polling the events.
 void worker_loop(fs_server* S) {
     cudaSetDevice(S->device);
-    std::vector<std::shared_ptr<Job>> active[2];  // by precision
-    BatchTable table[2];
-    bool dirty[2] = {false, false};
-    std::vector<InstState> states;
-    const int smem = relax_smem_budget(0);
-    prepare_relax(0, smem);
-    prepare_relax(1, smem);
+    struct Active {
+        std::shared_ptr<Job> job;
+        cudaStream_t stream;
+        cudaEvent_t done;
+    };
+    std::vector<Active> active;
+    std::vector<cudaStream_t> free_streams;
+    std::vector<cudaEvent_t> free_events;
     for (;;) {
+        std::vector<std::shared_ptr<Job>> joining;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            S->cv_work.wait(lk, [&] {
-                return S->stop || !S->ready.empty() || !active[0].empty() || !active[1].empty();
-            });
+            if (active.empty())
+                S->cv_work.wait(lk, [&] { return S->stop || !S->ready.empty(); });
+            else
+                S->cv_work.wait_for(lk, std::chrono::microseconds(200),
+                                    [&] { return S->stop || !S->ready.empty(); });
             if (S->stop) break;
             while (!S->ready.empty() &&
-                   (int)(active[0].size() + active[1].size()) < S->max_active) {
-                auto j = S->ready.front();
+                   (int)(active.size() + joining.size()) < S->max_active) {
+                joining.push_back(S->ready.front());
                 S->ready.pop_front();
-                const int p = j->req.params.precision == FS_FP32_RECHECK ? 1 : 0;
-                // fresh protocol state of the joining member
-                Inst I = j->sim->inst;
-                I.phx = j->d_hx;
-                I.phy = j->d_hy;
-                I.K = j->req.K;
-                I.step0 = 0;
-                I.resweep = 1;
-                I.log_step = nullptr;
-                I.log_spin = nullptr;
-                I.log_cap = 0;
-                I.flips_per_step = nullptr;
-                j->sim->inst_run = I;
-                InstState st0;
-                memset(&st0, 0, sizeof(st0));
-                st0.hash = fs_hash_init();
-                st0.init = 1;
-                j->sim->state_host = st0;
-                cudaMemcpyAsync(j->sim->d_state, &j->sim->state_host, sizeof(InstState),
-                                cudaMemcpyHostToDevice, S->main_st);
-                active[p].push_back(j);
-                dirty[p] = true;
             }
         }
-        // a chunk of iterations on both precision groups
-        for (int p = 0; p < 2; ++p) {
-            if (!dirty[p]) continue;
-            std::vector<fs_sim*> sims;
-            std::vector<Inst> descs;
-            for (auto& j : active[p]) {
-                sims.push_back(j->sim);
-                descs.push_back(j->sim->inst_run);
+        for (auto& j : joining) {
+            Active a{j, nullptr, nullptr};
+            if (!free_streams.empty()) {
+                a.stream = free_streams.back();
+                free_streams.pop_back();
+            } else if (cudaStreamCreateWithFlags(&a.stream, cudaStreamNonBlocking) !=
+                       cudaSuccess) {
+                a.stream = nullptr;
             }
-            table[p].upload(sims, descs, S->main_st);
-            dirty[p] = false;
-        }
-        int64_t left = 0;
-        for (int p = 0; p < 2; ++p)
-            for (auto& j : active[p]) {
-                (void)j;
-                ++left;
+            if (!free_events.empty()) {
+                a.done = free_events.back();
+                free_events.pop_back();
+            } else if (cudaEventCreateWithFlags(&a.done, cudaEventDisableTiming) != cudaSuccess) {
+                a.done = nullptr;
             }
-        const int chunk = 4;
-        cudaError_t e = cudaSuccess;
-        for (int it = 0; it < chunk && e == cudaSuccess; ++it)
-            for (int p = 0; p < 2 && e == cudaSuccess; ++p)
-                e = table[p].enqueue_step(p, 1, smem, S->main_st);
-        // read every member's progress
-        for (int p = 0; p < 2; ++p) {
-            states.resize(active[p].size());
-            for (size_t q = 0; q < active[p].size(); ++q)
-                cudaMemcpyAsync(&states[q], active[p][q]->sim->d_state, sizeof(InstState),
-                                cudaMemcpyDeviceToHost, S->main_st);
-            if (cudaStreamSynchronize(S->main_st) != cudaSuccess) e = cudaErrorUnknown;
-            std::vector<std::shared_ptr<Job>> keep;
-            for (size_t q = 0; q < active[p].size(); ++q) {
-                auto& j = active[p][q];
-                const InstState& s = states[q];
-                if (e == cudaSuccess && s.t < j->req.K && s.status == ST_OK) {
-                    keep.push_back(j);
-                    continue;
-                }
-                j->res.n_flips = s.n_flips;
-                j->res.seq_hash = s.hash;
-                if (j->spins_out)
-                    cudaMemcpy(j->spins_out, j->sim->inst.s, j->sim->n, cudaMemcpyDeviceToHost);
-                const size_t bytes = j->reserved;
-                fs_destroy(j->sim);
+            fs_sim* sim = j->sim;
+            bool ok = a.stream && a.done;
+            if (ok) {
+                sim->stream = a.stream;
+                ok = cudaGraphLaunch(j->exec, a.stream) == cudaSuccess &&
+                     cudaEventRecord(a.done, a.stream) == cudaSuccess;
+            }
+            if (!ok) {
+                if (a.stream) cudaStreamSynchronize(a.stream);
+                if (j->exec) cudaGraphExecDestroy(j->exec);
+                j->exec = nullptr;
+                fs_destroy(sim);
                 j->sim = nullptr;
-                S->used -= bytes;
+                S->used -= j->reserved;
                 S->cv_build.notify_all();
-                finish(S, j, e != cudaSuccess ? FS_ERR_CUDA : s.status);
-                dirty[p] = true;
+                finish(S, j, FS_ERR_CUDA);
+                if (a.stream) free_streams.push_back(a.stream);
+                if (a.done) free_events.push_back(a.done);
+                continue;
             }
-            active[p].swap(keep);
+            active.push_back(a);
         }
-        (void)left;
-    }
-    for (int p = 0; p < 2; ++p) {
-        for (auto& j : active[p]) {
-            if (j->sim) fs_destroy(j->sim);
-            finish(S, j, FS_ERR_STATE);
+        // retire finished requests
+        std::vector<Active> keep;
+        for (auto& a : active) {
+            const cudaError_t q = cudaEventQuery(a.done);
+            if (q == cudaErrorNotReady) {
+                keep.push_back(a);
+                continue;
+            }
+            auto& j = a.job;
+            // the request's work has ended: read its state (and spins) back now; a
+            // copy into pageable memory queued earlier would have blocked this thread
+            InstState& st = j->sim->state_host;
+            cudaError_t e = q;
+            if (e == cudaSuccess)
+                e = cudaMemcpy(&st, j->sim->d_state, sizeof(InstState), cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess && j->spins_out)
+                e = cudaMemcpy(j->spins_out, j->sim->inst.s, j->sim->n, cudaMemcpyDeviceToHost);
+            j->res.n_flips = st.n_flips;
+            j->res.seq_hash = st.hash;
+            const int32_t status = e != cudaSuccess ? FS_ERR_CUDA : st.status;
+            const size_t bytes = j->reserved;
+            cudaGraphExecDestroy(j->exec);
+            j->exec = nullptr;
+            fs_destroy(j->sim);
+            j->sim = nullptr;
+            S->used -= bytes;
+            S->cv_build.notify_all();
+            finish(S, j, status);
+            free_streams.push_back(a.stream);
+            free_events.push_back(a.done);
         }
-        table[p].mem.release(S->main_st);
+        active.swap(keep);
     }
-    cudaStreamSynchronize(S->main_st);
+    for (auto& a : active) {
+        cudaStreamSynchronize(a.stream);
+        if (a.job->exec) cudaGraphExecDestroy(a.job->exec);
+        fs_destroy(a.job->sim);
+        a.job->sim = nullptr;
+        finish(S, a.job, FS_ERR_STATE);
+        free_streams.push_back(a.stream);
+        free_events.push_back(a.done);
+    }
+    for (cudaStream_t st : free_streams) cudaStreamDestroy(st);
+    for (cudaEvent_t e : free_events) cudaEventDestroy(e);
 }
 
 }  // namespace
@@ -287,12 +342,23 @@ extern "C" fs_status fs_server_create(size_t hbm_budget, int32_t max_active, fs_
     S->max_active = max_active;
     S->t0 = std::chrono::steady_clock::now();
     cudaGetDevice(&S->device);
-    if (cudaStreamCreateWithFlags(&S->main_st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&S->build_st, cudaStreamNonBlocking) != cudaSuccess) {
+    // the relax kernel's shared-memory limit is set before any capture
+    if (prepare_relax(0, relax_smem_max()) != cudaSuccess ||
+        prepare_relax(1, relax_smem_max()) != cudaSuccess) {
         delete S;
         return FS_ERR_CUDA;
     }
-    S->builder = std::thread(builder_loop, S);
+    const int nb = 4;  // builder threads, each with its own stream
+    S->build_st.resize(nb, nullptr);
+    bool ok = cudaStreamCreateWithFlags(&S->main_st, cudaStreamNonBlocking) == cudaSuccess;
+    for (int b = 0; b < nb && ok; ++b)
+        ok = cudaStreamCreateWithFlags(&S->build_st[(size_t)b], cudaStreamNonBlocking) ==
+             cudaSuccess;
+    if (!ok) {
+        delete S;
+        return FS_ERR_CUDA;
+    }
+    for (int b = 0; b < nb; ++b) S->builders.emplace_back(builder_loop, S, b);
     S->worker = std::thread(worker_loop, S);
     *out = S;
     return FS_OK;
@@ -360,12 +426,14 @@ extern "C" void fs_server_destroy(fs_server* S) {
     }
     S->cv_build.notify_all();
     S->cv_work.notify_all();
-    if (S->builder.joinable()) S->builder.join();
+    for (auto& t : S->builders)
+        if (t.joinable()) t.join();
     if (S->worker.joinable()) S->worker.join();
-    for (auto& j : S->pending) (void)j;
-    for (auto& j : S->ready)
+    for (auto& j : S->ready) {
+        if (j->exec) cudaGraphExecDestroy(j->exec);
         if (j->sim) fs_destroy(j->sim);
+    }
     cudaStreamDestroy(S->main_st);
-    cudaStreamDestroy(S->build_st);
+    for (cudaStream_t b : S->build_st) cudaStreamDestroy(b);
     delete S;
 }
