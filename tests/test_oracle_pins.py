@@ -521,3 +521,20 @@ def test_resume_is_exact(oracle):
     assert b["hash"] == full["hash"]
     np.testing.assert_array_equal(b["spins"], full["spins"])
     assert a["n_flips"] + b["n_flips"] == full["n_flips"]
+
+
+def test_golden_square16_reproduces(oracle):
+    # the stored square16 values were written by tests/golden/make_golden.py from the
+    # oracle; recomputing them must give the same sequence
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "square16.json")))
+    w = I.WORKLOADS["square16"]
+    x, y, th = oracle.geometry(w["kind"], w["nx"], w["ny"])
+    hk = oracle.draw_hk(len(x), w["hk"], w["k_disorder"], w["seed"])
+    S = oracle.Sim(x, y, th, hk, alpha=w["alpha"], cutoff_abs=w["cutoff"])
+    hx, hy = I.protocol_of(w["protocol"])
+    r = S.run(np.ones(len(x), dtype=np.int8), hx, hy)
+    assert f"{r['hash']:#018x}" == g["seq_hash"]
+    assert r["log_spin"].tolist() == g["log_spin"]
+    assert r["flips_per_step"].tolist() == g["flips_per_step"]
