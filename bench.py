@@ -99,6 +99,20 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def aggregate(ms: float, units: float, dist=None, device: str = "cpu"):
+    """Whole-job figures over independent replicas: the slowest rank's time and
+    the units of all ranks (no data-path collective; one all-reduce each for
+    the timing and the count)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms, units
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def cpu_baseline(w, budget_s=20.0):
     """The FP64 oracle on the host cores, on a bounded prefix of the protocol (the
     first field steps, including the initial avalanche), in flips per second."""
@@ -189,6 +203,7 @@ def main():
                                  cutoff=w["cutoff"], sigma_th=w["sigma_th"], seed=w["seed"],
                                  precision=prec))
     info = sim.info()
+    lanes = sim.autotune()
     hx, hy = I.protocol_of(w["protocol"])
     K = len(hx)
     with torch.cuda.stream(stream):
@@ -232,11 +247,7 @@ def main():
     assert int(out1[0]) == 0, f"protocol status {out1[0]}"
     assert int(out1[1]) == flips_per_protocol and (int(out1[2]) & 0xFFFFFFFFFFFFFFFF) == hash0, \
         "timed steps diverged from the warm-up steps"
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    units = flips_per_protocol * args.steps * world
+    ms, units = aggregate(ms, flips_per_protocol * args.steps, dist, device="cuda")
     value = units / (ms / 1000.0)
     field_steps = K * args.steps * world / (ms / 1000.0)
 
@@ -288,11 +299,12 @@ def main():
                        "flips_per_step": flips_per_protocol, "seq_hash": f"{hash0:#018x}",
                        "l2": "inputs larger than L2 (neighbour tensors "
                              f"{info.device_bytes / 1e9:.2f} GB on the device)",
-                       "parallelism": "replicas" if world > 1 else "single"},
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "sweep_lanes_per_row": lanes},
             "field_steps_per_s": field_steps,
             "roofline": roof_relax, "roofline_sweep": roof_sweep,
             "gpu_launches": args.steps * (3 * K + 1),
-            "rechecks_per_flip": prof["rechecks"] / max(units, 1)}
+            "rechecks_per_flip": int(out1[3]) / max(flips_per_protocol, 1)}
     if clk:
         line["clocks"] = clk
 
