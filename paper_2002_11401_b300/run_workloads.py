@@ -3,7 +3,7 @@ runner, Sec. "Simulation framework"): builds each workload from `inputs.py`,
 runs it through the C ABI and prints one JSON line of measurements.
 
   python -m paper_2002_11401_b300.run_workloads square16|pinwheel300|kagome1000 \
-      [--precision fp32|fp64] [--steps K] [--resweep 0|1]
+      [--precision fp32|fp64] [--steps K] [--resweep 0|1] [--cells N]
   python -m paper_2002_11401_b300.run_workloads ensemble512 [--members M]
   python -m paper_2002_11401_b300.run_workloads serving [--requests R] [--rate HZ]
 """
@@ -51,8 +51,10 @@ def sweep_bytes(info, fp32: bool, resweep: bool) -> int:
     return (12 if fp32 else 20) * nnz + 8 * (n + 1) + n * per_island
 
 
-def run_single(name, precision, steps, resweep):
-    w = I.WORKLOADS[name]
+def run_single(name, precision, steps, resweep, cells=0):
+    w = dict(I.WORKLOADS[name])
+    if cells:
+        w["nx"] = w["ny"] = cells
     fp32 = precision == B.FS_FP32_RECHECK
     t0 = time.perf_counter()
     sim = make_sim(w, precision)
@@ -181,6 +183,7 @@ def main(argv=None):
     ap.add_argument("workload")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--steps", type=int, default=0)
+    ap.add_argument("--cells", type=int, default=0, help="override the array side (cells)")
     ap.add_argument("--resweep", type=int, default=1)
     ap.add_argument("--members", type=int, default=512)
     ap.add_argument("--sample", type=int, default=12)
@@ -194,7 +197,7 @@ def main(argv=None):
     B.load()
     prec = B.FS_FP32_RECHECK if a.precision == "fp32" else B.FS_FP64
     if a.workload in I.WORKLOADS:
-        out = run_single(a.workload, prec, a.steps, bool(a.resweep))
+        out = run_single(a.workload, prec, a.steps, bool(a.resweep), a.cells)
     elif a.workload == "ensemble512":
         out = run_ensemble(a.members, a.sample)
     elif a.workload == "serving":
