@@ -374,14 +374,18 @@ fs_status fs_build_sim(fs_sim* sim) {
     CK(palloc((void**)&I.h64, 16 * n), "alloc");
     CK(palloc((void**)&I.key32, 8 * n), "alloc");
     CK(palloc((void**)&I.lo32, 4 * n), "alloc");
-    if (p.precision == FS_FP32_RECHECK)
-        CK(palloc((void**)&I.h32, 8 * n), "alloc");
-    else
-        CK(palloc((void**)&I.key64, 8 * n), "alloc");
+    if (p.precision == FS_FP32_RECHECK) CK(palloc((void**)&I.h32, 8 * n), "alloc");
+    CK(palloc((void**)&I.key64, 8 * n), "alloc");
     CK(palloc((void**)&I.ext64, 16 * ncls), "alloc");
     CK(palloc((void**)&I.ext32, 8 * ncls), "alloc");
     I.nclass = (int32_t)ncls;
-    if (p.sigma_th > 0.0) CK(palloc((void**)&I.th32, 8 * n), "alloc");
+    I.row_cap = std::min<int32_t>(sim->max_deg, kRowBufMax);
+    if (p.sigma_th > 0.0) {
+        CK(palloc((void**)&I.th32, 8 * n), "alloc");
+        CK(palloc((void**)&I.th64, 16 * n), "alloc");
+        CK(palloc((void**)&I.th_step, 4 * n), "alloc");
+        CK(cudaMemsetAsync(I.th_step, 0xFF, 4 * n, st), "init");
+    }
 
     // max-tree levels above the leaves, fan-out 32
     int nlev = 0;
@@ -534,7 +538,7 @@ namespace fs {
 // Dynamic shared memory of a relax CTA: the tree levels above the keys that fit
 // in 96 KiB, counted from the root down (the kernel places them the same way).
 // Small systems take little, so several relax CTAs share an SM.
-int relax_smem_budget(int64_t n) {
+int relax_smem_levels(int64_t n) {
     const int64_t cap = 96 * 1024;
     std::vector<int64_t> lv;
     int64_t cnt = (n + 31) / 32;
@@ -551,7 +555,7 @@ int relax_smem_budget(int64_t n) {
     return (int)std::max<int64_t>(1024, used);
 }
 
-int relax_smem_max() { return 96 * 1024; }
+int relax_smem_max() { return relax_smem_total(96 * 1024, kRowBufMax); }
 
 // Queues K field steps of one simulation (sweep + relax per step). The
 // descriptor's protocol fields must already point at device buffers.
@@ -602,7 +606,8 @@ cudaError_t enqueue_steps(fs_sim* sim, int64_t K, int resweep, cudaStream_t st) 
     R.work = sim->d_work;
     R.n_work = 1;
     R.prec = sim->p.precision;
-    R.smem_budget = relax_smem_budget(sim->n);
+    R.smem_levels = relax_smem_levels(sim->n);
+    R.smem_total = relax_smem_total(R.smem_levels, sim->inst.row_cap);
     cudaError_t e;
     if (sim->profiling && sim->ev_used + 3 * (size_t)K > 30000 &&
         (e = collect_profile(sim)) != cudaSuccess)

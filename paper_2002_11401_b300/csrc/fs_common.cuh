@@ -17,8 +17,10 @@ constexpr int kRowPad = 4;                // CSR rows padded to multiples of 4 e
 constexpr int kMaxPaddedDegree = 1024;    // neighbours per island after padding
 constexpr int kFan = 32;                  // max-tree fan-out (one warp)
 constexpr int kMaxLevels = 8;             // tree levels above the leaves
-constexpr int kRelaxThreads = 1024;       // threads of one relax CTA
 constexpr int kRecheckCap = 256;          // FP64 recheck candidates per round
+constexpr int kRowBufs = 1;               // relax: rows staged in shared memory per flip
+constexpr int kRowBufMax = 256;           // relax: longest row that is staged
+constexpr int kRowBufEntry = 40;          // bytes per staged entry (col, P/Q, Q^T, both widths)
 
 // Device status codes (mirror fs_status).
 enum : int32_t {
@@ -49,6 +51,7 @@ struct Inst {
     int32_t prec;    // 0 = FP64, 1 = FP32 + FP64 recheck
     int32_t nlev;    // tree levels above the leaves; level nlev-1 is the root
     int32_t nclass;  // distinct island angles
+    int32_t row_cap; // entries per staged row buffer: min(max padded degree, kRowBufMax)
     int32_t pad1;
     int32_t lvl_n[kMaxLevels];
     int64_t lvl_off[kMaxLevels];  // node offset of each level in `tree`
@@ -72,9 +75,12 @@ struct Inst {
     longlong2* h64;         // dipolar (par, perp), exact 64-bit sums (both paths)
     int2* h32;              // dipolar (par, perp), 32-bit sums (FP32 path)
     float2* th32;           // thermal (par, perp) of the current step (sigma > 0)
+    double2* th64;          // FP64 thermal (par, perp) drawn for step th_step[i]
+    uint32_t* th_step;      // (sigma > 0; all ones before the first draw)
     unsigned long long* key32;  // (bits(upper bound) << 32) | ~i, 0 = not a candidate
     float* lo32;                // certified lower bound of the LHS, -1 if none
-    double* key64;              // FP64 path: exact LHS when flippable, else 0
+    double* key64;              // exact LHS when flippable, 0 when not; FP32 path: -1
+                                // while the current fields have not been evaluated in FP64
     unsigned long long* tree;   // max-tree nodes above the keys
     // protocol
     const double* phx;
@@ -200,6 +206,22 @@ __device__ __forceinline__ void thermal64(const Inst& I, int64_t i, uint32_t ste
     box_muller64(c, &z0, &z1);
     *tp = __dmul_rn(I.sigma, z0);
     *tq = __dmul_rn(I.sigma, z1);
+}
+
+// thermal64 of island i, drawn once per island and step: the draw is kept with
+// its step number, and later evaluations of the same step reuse it. Callers
+// never evaluate one island from two threads at the same time.
+__device__ __forceinline__ void thermal64_kept(const Inst& I, int64_t i, uint32_t step, double* tp,
+                                               double* tq) {
+    if (I.th_step[i] == step) {
+        const double2 v = I.th64[i];
+        *tp = v.x;
+        *tq = v.y;
+        return;
+    }
+    thermal64(I, i, step, tp, tq);
+    I.th64[i] = make_double2(*tp, *tq);
+    I.th_step[i] = step;
 }
 
 __device__ __forceinline__ float2 thermal32(const Inst& I, int64_t i, uint32_t step) {
@@ -356,16 +378,6 @@ __device__ __forceinline__ uint32_t key32_idx(unsigned long long k) {
 __device__ __forceinline__ bool better64(unsigned long long va, unsigned long long ia,
                                          unsigned long long vb, unsigned long long ib) {
     return va > vb || (va == vb && ia < ib);
-}
-
-// FP32 top-2 merge: node = (best, second best) key.
-__device__ __forceinline__ ulonglong2 top2(ulonglong2 a, ulonglong2 b) {
-    ulonglong2 r;
-    r.x = a.x > b.x ? a.x : b.x;
-    const unsigned long long lo = a.x > b.x ? b.x : a.x;
-    const unsigned long long s2 = a.y > b.y ? a.y : b.y;
-    r.y = lo > s2 ? lo : s2;
-    return r;
 }
 
 // FNV-1a over the 8 little-endian bytes of (step, island).

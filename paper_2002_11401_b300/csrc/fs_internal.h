@@ -21,8 +21,8 @@ struct Arena {
 };
 
 int choose_lanes(double avg_groups);
-int relax_smem_budget(int64_t n);
-int relax_smem_max();
+int relax_smem_levels(int64_t n);  // bytes of upper tree levels kept in shared memory
+int relax_smem_max();              // largest dynamic shared memory of any relax launch
 // Queues K field steps (external-field table, sweep, relax) of one simulation on
 // `st`; the descriptor and state must already be on the device.
 cudaError_t enqueue_steps(fs_sim* sim, int64_t K, int resweep, cudaStream_t st);

@@ -83,14 +83,15 @@ __device__ unsigned long long runner_up(const Inst& I, const Levels& L, int64_t 
 }
 
 struct Dirty {
-    int32_t lv0[kDirtyCap];        // first-level nodes to rebuild
-    int32_t up[2][kDirtyCap];      // upper-level nodes, one level at a time
-    int32_t n0, nup[2];
+    int32_t lv0[kDirtyCap];    // first-level nodes to rebuild
+    int32_t up[2][kDirtyCap];  // upper-level nodes, ping-pong by level parity
+    int32_t n0;
+    int32_t nup[kMaxLevels];   // queued nodes of each upper level
 };
 
 // A leaf's key went from `old` to `nk`: a larger key is pushed up with atomic
-// maxima on every ancestor; if the leaf held its
-// first-level node's maximum and shrank, that node is queued for a rebuild.
+// maxima on every ancestor; if the leaf held its first-level node's maximum and
+// shrank, that node is queued for a rebuild.
 __device__ __forceinline__ void leaf_changed(const Inst& I, const Levels& L, Dirty& D, int64_t i,
                                              unsigned long long old, unsigned long long nk) {
     if (nk > old) {
@@ -108,54 +109,122 @@ __device__ __forceinline__ void leaf_changed(const Inst& I, const Levels& L, Dir
     }
 }
 
-// Rebuilds the queued nodes: all warps the first level, then warp 0 the levels
-// above (few nodes), each queueing its parent when its maximum shrank and the
-// parent held it. Call with every thread; returns with warp 0 possibly still
-// working on the upper levels when `wait` is false.
-__device__ void rebuild_dirty(const Inst& I, const Levels& L, Dirty& D, bool wait) {
+// Rebuilds node `node` of level `lev` (lev >= 0) from its children and, when its
+// maximum shrank and its parent held it, queues the parent. Warp-wide.
+__device__ __forceinline__ void rebuild_node(const Inst& I, const Levels& L, Dirty& D, int lev,
+                                             int64_t node) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long old = L.p[lev][node];
+    const unsigned long long nv = warp_node(I, L, lev, node);
+    if (lane == 0) {
+        L.p[lev][node] = nv;
+        if (nv < old && lev + 1 < I.nlev && L.p[lev + 1][node >> 5] == old) {
+            const int r = atomicAdd(&D.nup[lev + 1], 1);
+            if (r < kDirtyCap) D.up[(lev + 1) & 1][r] = (int32_t)(node >> 5);
+        }
+    }
+}
+
+// The row of the predicted next pick, staged in shared memory. The next pick is
+// the larger of the largest key the flip left untouched (the runner-up, when the
+// flip was certified from bounds) and the largest new key among the flip's
+// neighbours: both are folded into best[parity] with atomic maxima during the
+// neighbour updates, and while warp 0 repairs the tree and picks, warp 1 copies
+// that island's row into the buffer (asynchronous copies). Double-buffered by
+// flip parity.
+struct RowStage {
+    unsigned long long best[2];
+    int32_t buf_id;   // island whose row the buffer holds, -1 for none
+    int32_t buf_len;
+};
+
+struct RowBuf {
+    longlong2* pq64;
+    long long* qt64;
+    int2* pq32;
+    int32_t* col;
+    int32_t* qt32;
+};
+
+// Buffer b of `cap` entries (cap a multiple of 4: every array is a whole number
+// of 16-byte chunks, each starting 16-byte aligned).
+__device__ __forceinline__ RowBuf row_buf(unsigned char* base, int cap, int b) {
+    unsigned char* p = base + (size_t)b * (size_t)cap * kRowBufEntry;
+    RowBuf r;
+    r.pq64 = reinterpret_cast<longlong2*>(p);
+    p += 16 * cap;
+    r.qt64 = reinterpret_cast<long long*>(p);
+    p += 8 * cap;
+    r.pq32 = reinterpret_cast<int2*>(p);
+    p += 8 * cap;
+    r.col = reinterpret_cast<int32_t*>(p);
+    p += 4 * cap;
+    r.qt32 = reinterpret_cast<int32_t*>(p);
+    return r;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Warp-wide: starts the copy of row [a0, a0 + m) into B (m <= cap, multiple of 4).
+template <int PREC>
+__device__ __forceinline__ void stage_row(const Inst& I, const RowBuf& B, int64_t a0, int m) {
+    const int lane = threadIdx.x & 31;
+    for (int c = lane; c < m; c += 32) cp_async16(&B.pq64[c], &I.pq64[a0 + c]);
+    for (int c = lane; c < m / 2; c += 32) cp_async16(&B.qt64[2 * c], &I.qt64[a0 + 2 * c]);
+    for (int c = lane; c < m / 4; c += 32) cp_async16(&B.col[4 * c], &I.col[a0 + 4 * c]);
+    if constexpr (PREC == 1) {
+        for (int c = lane; c < m / 2; c += 32) cp_async16(&B.pq32[2 * c], &I.pq32[a0 + 2 * c]);
+        for (int c = lane; c < m / 4; c += 32) cp_async16(&B.qt32[4 * c], &I.qt32[a0 + 4 * c]);
+    }
+}
+
+// After the neighbour updates, every thread: all warps rebuild the queued
+// first-level nodes; then warp 0 rebuilds the queued nodes above, level by level
+// (few nodes, so one warp without barriers), while warp 1 stages the predicted
+// row. Returns with warp 0 done with the tree and warp 1's copies landed; the
+// caller's next barrier publishes both.
+template <int PREC>
+__device__ void tree_phase(const Inst& I, const Levels& L, Dirty& D, RowStage& P,
+                           unsigned char* bufs, int par) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int n0 = min(D.n0, kDirtyCap);
-    for (int q = wid; q < n0; q += kNW) {
-        const int64_t node = D.lv0[q];
-        const unsigned long long old = L.p[0][node];
-        const unsigned long long nv = warp_node(I, L, 0, node);
-        if (lane == 0) {
-            L.p[0][node] = nv;
-            if (nv < old && I.nlev > 1 && L.p[1][node >> 5] == old) {
-                const int r = atomicAdd(&D.nup[0], 1);
-                if (r < kDirtyCap) D.up[0][r] = (int32_t)(node >> 5);
-            }
-        }
-    }
+    for (int q = wid; q < n0; q += kNW) rebuild_node(I, L, D, 0, D.lv0[q]);
     __syncthreads();
     if (wid == 0) {
-        int cur = 0;
         for (int lev = 1; lev < I.nlev; ++lev) {
-            const int nn = min(D.nup[cur], kDirtyCap);
-            if (lane == 0) D.nup[cur ^ 1] = 0;
-            __syncwarp();
+            const int nn = min(D.nup[lev], kDirtyCap);
             for (int q = 0; q < nn; ++q) {
-                const int64_t node = D.up[cur][q];
-                const unsigned long long old = L.p[lev][node];
-                const unsigned long long nv = warp_node(I, L, lev, node);
-                if (lane == 0) {
-                    L.p[lev][node] = nv;
-                    if (nv < old && lev + 1 < I.nlev && L.p[lev + 1][node >> 5] == old) {
-                        const int r = D.nup[cur ^ 1]++;
-                        if (r < kDirtyCap) D.up[cur ^ 1][r] = (int32_t)(node >> 5);
-                    }
-                }
+                rebuild_node(I, L, D, lev, D.up[lev & 1][q]);
                 __syncwarp();
             }
-            cur ^= 1;
+        }
+    } else if (wid == 1) {
+        const unsigned long long pred = P.best[par];
+        int32_t id = -1, len = 0;
+        if (pred != 0ull) {
+            const int64_t j = key32_idx(pred);
+            const int64_t a0 = __ldg(&I.rp[j]);
+            const int m = (int)(__ldg(&I.rp[j + 1]) - a0);
+            if (m > 0 && m <= I.row_cap) {
+                stage_row<PREC>(I, row_buf(bufs, I.row_cap, 0), a0, m);
+                id = (int32_t)j;
+                len = m;
+            }
         }
         if (lane == 0) {
-            D.n0 = 0;
-            D.nup[0] = 0;
-            D.nup[1] = 0;
+            P.buf_id = id;
+            P.buf_len = len;
+            P.best[par ^ 1] = 0ull;  // the next flip's prediction
         }
+        cp_async_wait_all();
     }
-    if (wait) __syncthreads();
 }
 
 // Whole tree from the leaves (after a full rescan).
@@ -171,10 +240,11 @@ __device__ void rebuild_tree(const Inst& I, const Levels& L) {
 }
 
 // Key of island i from its current state (already loaded): returns the new key
-// and writes lo (and, on the FP64 path, the exact value x).
+// and writes lo and the exact value x (the FS_FP64 LHS when flippable, 0 when
+// not; on the FP32 path -1 when only the FP32 bounds were taken).
 template <int PREC>
 __device__ __forceinline__ unsigned long long key_of(const Inst& I, int64_t i, uint32_t step,
-                                                     int si, longlong2 h64, int2 h32,
+                                                     int si, uint16_t ci, longlong2 h64, int2 h32,
                                                      float2 rbc, float2 e32, float2 th,
                                                      double hk, double2 e64, float* lo,
                                                      double* x64) {
@@ -185,12 +255,15 @@ __device__ __forceinline__ unsigned long long key_of(const Inst& I, int64_t i, u
         if (e.possible && !e.certain) {
             // within its band of the threshold or of the sign change: FP64 now
             double tp = 0.0, tq = 0.0;
-            if (I.sigma > 0.0) thermal64(I, i, step, &tp, &tq);
-            const Eval64 f = eval64(I, si, h64.x, h64.y, hk, e64, tp, tq);
+            if (I.sigma > 0.0) thermal64_kept(I, i, step, &tp, &tq);
+            const Eval64 f =
+                eval64(I, si, h64.x, h64.y, __ldg(&I.hk64[i]), __ldg(&I.ext64[ci]), tp, tq);
             const double x = f.flippable ? f.lhs : 0.0;
+            *x64 = x;
             *lo = x > 0.0 ? __double2float_rd(x) : -1.0f;
             return x > 0.0 ? key32_of(__double2float_ru(x), i) : 0ull;
         }
+        *x64 = e.possible ? -1.0 : 0.0;
         *lo = e.certain ? e.lo : -1.0f;
         return e.possible ? key32_of(e.hi, i) : 0ull;
     } else {
@@ -200,7 +273,7 @@ __device__ __forceinline__ unsigned long long key_of(const Inst& I, int64_t i, u
         double x = 0.0;
         if (e.possible) {
             double tp = 0.0, tq = 0.0;
-            if (I.sigma > 0.0) thermal64(I, i, step, &tp, &tq);
+            if (I.sigma > 0.0) thermal64_kept(I, i, step, &tp, &tq);
             const Eval64 f = eval64(I, si, h64.x, h64.y, hk, e64, tp, tq);
             if (f.flippable) x = f.lhs;
         }
@@ -210,13 +283,47 @@ __device__ __forceinline__ unsigned long long key_of(const Inst& I, int64_t i, u
     }
 }
 
+// Asks L2 for bytes [p, p + n) ahead of their use (TMA bulk prefetch: p 16-byte
+// aligned, n a multiple of 16; no completion to wait for).
+__device__ __forceinline__ void bulk_prefetch_l2(const void* p, uint32_t n) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(n) : "memory");
+}
+
+// Row [a0, a1) of the neighbour tensors that a flip of its island reads. Rows
+// start and end on multiples of 4 entries, so every array's range is 16-byte
+// aligned with a length that is a multiple of 16 bytes.
+template <int PREC>
+__device__ __forceinline__ void prefetch_row(const Inst& I, int64_t a0, int64_t a1) {
+    const uint32_t m = (uint32_t)(a1 - a0);
+    if (m == 0u) return;
+    bulk_prefetch_l2(I.col + a0, 4u * m);
+    bulk_prefetch_l2(I.pq64 + a0, 16u * m);
+    bulk_prefetch_l2(I.qt64 + a0, 8u * m);
+    if constexpr (PREC == 1) {
+        bulk_prefetch_l2(I.pq32 + a0, 8u * m);
+        bulk_prefetch_l2(I.qt32 + a0, 4u * m);
+    }
+}
+
+// Island j (key kj), whose row is [a0, a1), may be the next pick: its row is
+// asked into L2 now and its key enters the prediction.
+template <int PREC>
+__device__ __forceinline__ void stage_candidate(const Inst& I, RowStage& P, int par,
+                                                unsigned long long kj, int64_t a0, int64_t a1) {
+    prefetch_row<PREC>(I, a0, a1);
+    atomicMax(&P.best[par], kj);
+}
+
 // Island i's field changes by 2 s_new (dp, dq) (exact 64-bit sums; dp32, dq32 the
 // 32-bit ones); its key is re-evaluated and the tree told. Every load is issued
-// before the first store so that they overlap.
-template <int PREC>
+// before the first store so that they overlap. When the new key exceeds
+// `pf_above` (the largest key the flip did not touch), i may be the next pick and
+// its row is staged.
+template <int PREC, bool PF>
 __device__ __forceinline__ void update_island(const Inst& I, const Levels& L, Dirty& D,
-                                              int64_t i, int snew, long long dp, long long dq,
-                                              int dp32, int dq32, uint32_t step) {
+                                              RowStage& P, int par, int64_t i, int snew,
+                                              long long dp, long long dq, int dp32, int dq32,
+                                              uint32_t step, unsigned long long pf_above) {
     longlong2 h = I.h64[i];
     int2 g = make_int2(0, 0);
     if constexpr (PREC == 1) g = I.h32[i];
@@ -226,9 +333,18 @@ __device__ __forceinline__ void update_island(const Inst& I, const Levels& L, Di
     const float2 rbc = __ldg(&I.rbc32[i]);
     float2 th = make_float2(0.0f, 0.0f);
     if (I.sigma > 0.0) th = I.th32[i];
-    const double hk = __ldg(&I.hk64[i]);
-    const double2 e64 = I.ext64[ci];
-    const float2 e32 = I.ext32[ci];
+    int64_t r0 = 0, r1 = 0;
+    if constexpr (PF) {
+        r0 = __ldg(&I.rp[i]);
+        r1 = __ldg(&I.rp[i + 1]);
+    }
+    double hk = 0.0;
+    double2 e64 = make_double2(0.0, 0.0);
+    if constexpr (PREC == 0) {
+        hk = __ldg(&I.hk64[i]);
+        e64 = __ldg(&I.ext64[ci]);
+    }
+    const float2 e32 = __ldg(&I.ext32[ci]);
     const unsigned long long up = 2ull * (unsigned long long)dp;
     const unsigned long long uq = 2ull * (unsigned long long)dq;
     h.x = (long long)(snew > 0 ? (unsigned long long)h.x + up : (unsigned long long)h.x - up);
@@ -240,47 +356,75 @@ __device__ __forceinline__ void update_island(const Inst& I, const Levels& L, Di
     }
     float lo;
     double x = 0.0;
-    const unsigned long long nk = key_of<PREC>(I, i, step, si, h, g, rbc, e32, th, hk, e64, &lo, &x);
+    const unsigned long long nk =
+        key_of<PREC>(I, i, step, si, ci, h, g, rbc, e32, th, hk, e64, &lo, &x);
     I.h64[i] = h;
     if constexpr (PREC == 1) I.h32[i] = g;
-    if constexpr (PREC == 0) I.key64[i] = x;
+    I.key64[i] = x;
     I.key32[i] = nk;
     I.lo32[i] = lo;
     leaf_changed(I, L, D, i, old, nk);
+    if constexpr (PF) {
+        if (nk > pf_above) stage_candidate<PREC>(I, P, par, nk, r0, r1);
+    }
 }
 
-// Exact FP64 value of island i (0 when not flippable): on the FP64 path the value
-// kept with its key, on the FP32 path a fresh FP64 evaluation of its exact sums.
+// Exact FP64 value of island i (0 when not flippable): the value kept with its
+// key when its current fields were evaluated in FP64, else (FP32 path) a fresh
+// FP64 evaluation of its exact sums, which is then kept. The island's state is
+// loaded before the kept value is looked at, so that a miss costs no extra trip.
 template <int PREC>
 __device__ __forceinline__ double exact_value(const Inst& I, int64_t i, uint32_t step) {
+    const double kept = I.key64[i];
     if constexpr (PREC == 0) {
-        return I.key64[i];
+        return kept;
     } else {
-        double tp = 0.0, tq = 0.0;
-        if (I.sigma > 0.0) thermal64(I, i, step, &tp, &tq);
         const longlong2 h = I.h64[i];
-        const Eval64 e = eval64(I, I.s[i], h.x, h.y, I.hk64[i], I.ext64[I.cls[i]], tp, tq);
-        return e.flippable ? e.lhs : 0.0;
+        const int si = I.s[i];
+        const double hk = __ldg(&I.hk64[i]);
+        const uint16_t ci = __ldg(&I.cls[i]);
+        if (kept >= 0.0) return kept;
+        double tp = 0.0, tq = 0.0;
+        if (I.sigma > 0.0) thermal64_kept(I, i, step, &tp, &tq);
+        const Eval64 e = eval64(I, si, h.x, h.y, hk, __ldg(&I.ext64[ci]), tp, tq);
+        const double v = e.flippable ? e.lhs : 0.0;
+        I.key64[i] = v;
+        return v;
     }
 }
 
 struct RecheckShared {
     int32_t front[2][kRecheckCap];
-    int32_t cand[kRecheckCap];
-    double cand_val[kRecheckCap];
-    unsigned long long cand_old[kRecheckCap];
-    unsigned long long cand_new[kRecheckCap];
+    unsigned long long leaf_key[kRecheckCap];  // candidates' keys when collected
+    unsigned long long new_key[kRecheckCap];
     int32_t result;
     float tau;
 };
 
+// Rebuilds every node on island w's path to the root from its children. Warp-wide.
+__device__ void rebuild_path(const Inst& I, const Levels& L, int64_t w) {
+    int64_t node = w;
+    for (int lev = 0; lev < I.nlev; ++lev) {
+        node >>= 5;
+        const unsigned long long v = warp_node(I, L, lev, node);
+        if ((threadIdx.x & 31) == 0) L.p[lev][node] = v;
+        __syncwarp();
+    }
+}
+
 // Exact comparison of the islands whose key bound reaches tau, by warp 0 alone.
 // Returns the winner (its exact value is at least tau, so nothing outside the set
-// can beat it), -2 with R.tau lowered to widen the set, -1 when all of them were
-// demoted, -3 when the set overflowed (nothing changed then).
+// can beat it) with its spin and row in *sk, *a0, *a1 on every lane; -2 with R.tau
+// lowered to widen the set; -1 when none of them is flippable; -3 when the set
+// overflowed (nothing changed then). The candidates' keys become their exact
+// values rounded out; the first-level nodes that held a lowered key are queued for
+// the rebuild after the flip (the tree keeps upper bounds meanwhile, which every
+// later comparison tolerates), except on -1, when their paths are repaired at once
+// for the next look at the root.
 template <int PREC>
-__device__ int64_t recheck_warp(const Inst& I, const Levels& L, RecheckShared& R, float tau,
-                                uint32_t step) {
+__device__ int64_t recheck_warp(const Inst& I, const Levels& L, RecheckShared& R, Dirty& D,
+                                float tau, uint32_t step, int* sk, int64_t* a0, int64_t* a1) {
+    constexpr int kBatch = 4;  // frontier nodes whose children are loaded together
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const unsigned long long tkey = (unsigned long long)__float_as_uint(tau) << 32;
@@ -289,20 +433,28 @@ __device__ int64_t recheck_warp(const Inst& I, const Levels& L, RecheckShared& R
     __syncwarp();
     int cur = 0, nf = 1;
     for (int lev = I.nlev - 1; lev >= 0; --lev) {
+        const unsigned long long* src = lev > 0 ? L.p[lev - 1] : I.key32;
+        const int64_t lim = lev > 0 ? (int64_t)I.lvl_n[lev - 1] : I.n;
         int nn = 0;
-        for (int f = 0; f < nf; ++f) {
-            const int64_t child = ((int64_t)R.front[cur][f] << 5) + lane;
-            unsigned long long k = 0ull;
-            if (lev > 0) {
-                if (child < I.lvl_n[lev - 1]) k = L.p[lev - 1][child];
-            } else if (child < I.n) {
-                k = I.key32[child];
+        for (int f0 = 0; f0 < nf; f0 += kBatch) {
+            unsigned long long k[kBatch];
+            int64_t child[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                child[u] = f0 + u < nf ? ((int64_t)R.front[cur][f0 + u] << 5) + lane : lim;
+                k[u] = child[u] < lim ? src[child[u]] : 0ull;
             }
-            const bool hit = k != 0ull && k >= tkey;
-            const unsigned m = __ballot_sync(0xffffffffu, hit);
-            const int pos = nn + __popc(m & lt);
-            if (hit && pos < kRecheckCap) R.front[cur ^ 1][pos] = (int32_t)child;
-            nn += __popc(m);
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const bool hit = k[u] != 0ull && k[u] >= tkey;
+                const unsigned m = __ballot_sync(0xffffffffu, hit);
+                const int pos = nn + __popc(m & lt);
+                if (hit && pos < kRecheckCap) {
+                    R.front[cur ^ 1][pos] = (int32_t)child[u];
+                    if (lev == 0) R.leaf_key[pos] = k[u];
+                }
+                nn += __popc(m);
+            }
         }
         __syncwarp();
         if (nn > kRecheckCap) return -3;
@@ -310,20 +462,36 @@ __device__ int64_t recheck_warp(const Inst& I, const Levels& L, RecheckShared& R
         nf = nn;
     }
     const int nc = nf;
-    // exact values, one lane per candidate; best by (value, lowest index)
+    // Per candidate, one lane each: the exact value, best by (value, lowest index);
+    // the new key (exact value rounded out: only ever lower), queued rebuild.
     unsigned long long bv = 0ull;
     int64_t bi = -1;
+    int bs = 0;
+    int64_t b0 = 0, b1 = 0;
     for (int c = lane; c < nc; c += 32) {
         const int64_t i = R.front[cur][c];
+        const int si = I.s[i];
+        const int64_t r0 = __ldg(&I.rp[i]), r1 = __ldg(&I.rp[i + 1]);
         const double v = exact_value<PREC>(I, i, step);
-        R.cand[c] = (int32_t)i;
-        R.cand_val[c] = v;
         const unsigned long long vb = v > 0.0 ? (unsigned long long)__double_as_longlong(v) : 0ull;
         if (vb > 0ull && (bi < 0 || vb > bv || (vb == bv && i < bi))) {
             bv = vb;
             bi = i;
+            bs = si;
+            b0 = r0;
+            b1 = r1;
+        }
+        const unsigned long long old = R.leaf_key[c];
+        const unsigned long long nk = v > 0.0 ? key32_of(__double2float_ru(v), i) : 0ull;
+        I.key32[i] = nk;
+        I.lo32[i] = v > 0.0 ? __double2float_rd(v) : -1.0f;
+        R.new_key[c] = nk;
+        if (nk < old && L.p[0][i >> 5] == old) {
+            const int q = atomicAdd(&D.n0, 1);
+            if (q < kDirtyCap) D.lv0[q] = (int32_t)(i >> 5);
         }
     }
+    const int64_t my_bi = bi;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
@@ -333,24 +501,25 @@ __device__ int64_t recheck_warp(const Inst& I, const Levels& L, RecheckShared& R
             bi = oi;
         }
     }
-    // Demote what proved non-flippable; give the flippable ones keys from their
-    // exact values (valid until their field changes). Both only lower keys.
-    for (int c = lane; c < nc; c += 32) {
-        const int64_t i = R.cand[c];
-        const double v = R.cand_val[c];
-        const unsigned long long old = I.key32[i];
-        const unsigned long long nk = v > 0.0 ? key32_of(__double2float_ru(v), i) : 0ull;
-        I.key32[i] = nk;
-        I.lo32[i] = v > 0.0 ? __double2float_rd(v) : -1.0f;
-        R.cand_old[c] = old;
-        R.cand_new[c] = nk;
-    }
     __syncwarp();
-    // rebuild the nodes whose maximum was a lowered key, bottom-up
+    const double bl = __longlong_as_double((long long)bv);
+    if (bi >= 0 && bl >= (double)tau) {
+        const int src = __ffs(__ballot_sync(0xffffffffu, my_bi == bi)) - 1;
+        *sk = __shfl_sync(0xffffffffu, bs, src);
+        *a0 = __shfl_sync(0xffffffffu, b0, src);
+        *a1 = __shfl_sync(0xffffffffu, b1, src);
+        return bi;
+    }
+    if (bi >= 0) {
+        if (lane == 0) R.tau = __double2float_rd(bl);  // something outside might beat it
+        __syncwarp();
+        return -2;
+    }
+    // none flippable: rebuild the nodes whose maximum was a lowered key, bottom-up
     for (int c = 0; c < nc; ++c) {
-        const unsigned long long old = R.cand_old[c];
-        if (R.cand_new[c] >= old) continue;
-        int64_t node = (int64_t)R.cand[c];
+        const unsigned long long old = R.leaf_key[c];
+        if (R.new_key[c] >= old) continue;
+        int64_t node = (int64_t)R.front[cur][c];
         for (int lev = 0; lev < I.nlev; ++lev) {
             node >>= 5;
             if (L.p[lev][node] != old) break;
@@ -358,13 +527,6 @@ __device__ int64_t recheck_warp(const Inst& I, const Levels& L, RecheckShared& R
             if (lane == 0) L.p[lev][node] = nv;
             __syncwarp();
         }
-    }
-    const double bl = __longlong_as_double((long long)bv);
-    if (bi >= 0 && bl >= (double)tau) return bi;
-    if (bi >= 0) {
-        if (lane == 0) R.tau = __double2float_rd(bl);  // something outside might beat it
-        __syncwarp();
-        return -2;
     }
     return -1;
 }
@@ -415,13 +577,82 @@ __device__ int64_t recheck_scan(const Inst& I, const Levels& L, RecheckShared& R
     return R.result;
 }
 
+// Pick codes besides an island index.
+constexpr int64_t kPickNone = -1;      // no flippable island: the relax is done
+constexpr int64_t kPickOverflow = -3;  // exact comparison needs the CTA-wide scan
+constexpr int64_t kPickBounds = -4;    // the comparison did not settle
+constexpr int64_t kPickMaxFlips = -6;  // flip budget of the step spent
+
+// Warp 0: the island to flip next. Reads the root's island w and the largest other
+// key; takes w when its certified lower bound exceeds one and that key's upper
+// bound, else compares the contenders exactly. On return lane 0 holds the pick's
+// spin and row, and `ru` the largest key other than the pick's when it was
+// certified from bounds (all ones otherwise).
+template <int PREC>
+__device__ int64_t pick_warp(const Inst& I, const Levels& L, RecheckShared& R, Dirty& D,
+                             InstState* st, uint32_t step, int* sk, int64_t* a0, int64_t* a1,
+                             unsigned long long* ru_out, float* tau_out) {
+    const int lane = threadIdx.x & 31;
+    *ru_out = ~0ull;
+    if (lane == 0) {  // the last repair has read its queues
+        D.n0 = 0;
+        for (int lev = 0; lev < kMaxLevels; ++lev) D.nup[lev] = 0;
+    }
+    __syncwarp();
+    for (int guard = 0; guard < 4 * kRecheckCap + 64; ++guard) {
+        const unsigned long long root = L.p[I.nlev - 1][0];
+        if (root == 0ull) return kPickNone;
+        const int64_t w = key32_idx(root);
+        unsigned long long kw = 0ull;
+        float lo = 0.0f;
+        if (lane == 0) {  // independent loads, in flight during the runner-up scan
+            kw = I.key32[w];
+            lo = I.lo32[w];
+            *sk = I.s[w];
+            *a0 = I.rp[w];
+            *a1 = I.rp[w + 1];
+        }
+        const unsigned long long ru = runner_up(I, L, w);
+        kw = __shfl_sync(0xffffffffu, kw, 0);
+        lo = __shfl_sync(0xffffffffu, lo, 0);
+        if (kw != root) {  // a lowered key still held by its ancestors
+            rebuild_path(I, L, w);
+            continue;
+        }
+        const float hi2 = ru ? key32_hi(ru) : 0.0f;
+        if (lo > 1.0f && lo > hi2) {
+            *ru_out = ru;
+            return w;
+        }
+        // With tau = lo(w) > 1 the set holds w, whose exact value is at least tau,
+        // so one round settles it; at the threshold, start from the runner-up.
+        float tau = lo > 1.0f ? lo : fmaxf(hi2, lo);
+        int64_t k = -2;
+        for (int rounds = 0; k == -2;) {
+            if (++rounds > 64) return kPickBounds;
+            k = recheck_warp<PREC>(I, L, R, D, tau, step, sk, a0, a1);
+            if (lane == 0) atomicAdd((unsigned long long*)&st->rechecks, 1ull);
+            if (k == -2) tau = R.tau;
+        }
+        if (k == -1) continue;  // every contender was demoted: look at the root again
+        if (k == kPickOverflow) {
+            *tau_out = tau;
+            return k;
+        }
+        return k;
+    }
+    return kPickBounds;
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(kT, 1)
     k_relax(const Inst* __restrict__ tab, const int32_t* __restrict__ work, int n_work,
-            int smem_budget) {
-    extern __shared__ unsigned long long sm_levels[];
+            int smem_levels) {
+    extern __shared__ __align__(16) unsigned long long sm_levels[];
     __shared__ int64_t sh_k;
+    __shared__ RowStage P;
     __shared__ int64_t sh_e0, sh_e1;
+    __shared__ unsigned long long sh_ru;
     __shared__ int32_t sh_snew;
     __shared__ float sh_tau;
     __shared__ RecheckShared R;
@@ -441,7 +672,7 @@ __global__ void __launch_bounds__(kT, 1)
         int first_sm = I.nlev;
         for (int lev = I.nlev - 1; lev >= 0; --lev) {
             const int64_t b = (int64_t)I.lvl_n[lev] * (int64_t)sizeof(unsigned long long);
-            if (used + b > smem_budget) break;
+            if (used + b > smem_levels) break;
             used += b;
             first_sm = lev;
         }
@@ -458,16 +689,19 @@ __global__ void __launch_bounds__(kT, 1)
             for (int64_t q = threadIdx.x; q < I.lvl_n[lev]; q += kT)
                 L.p[lev][q] = I.tree[I.lvl_off[lev] + q];
         if (threadIdx.x == 0) {
-            D.n0 = 0;
-            D.nup[0] = 0;
-            D.nup[1] = 0;
+            P.best[0] = 0ull;
+            P.best[1] = 0ull;
+            P.buf_id = -1;
+            P.buf_len = 0;
         }
     }
     __syncthreads();
+    // staged rows follow the levels' budget, 16-byte aligned
+    unsigned char* const bufs =
+        reinterpret_cast<unsigned char*>(sm_levels) + ((smem_levels + 15) & ~15);
 
     int64_t flips = 0;
     int32_t status = ST_OK;
-    int rounds = 0;
     uint64_t hash = threadIdx.x == 0 ? st->hash : 0ull;
     const int64_t flips_before = threadIdx.x == 0 ? st->n_flips : 0;
     const int64_t max_flips = I.max_flips;
@@ -488,88 +722,61 @@ __global__ void __launch_bounds__(kT, 1)
     };
 
     for (;;) {
-        // pick, and flip when the pick is certain: warp 0
+        // pick, and flip: warp 0
         if (wid == 0) {
-            const unsigned long long root = L.p[I.nlev - 1][0];
-            int64_t k = -1;
-            if (root != 0ull) {
-                const int64_t w = key32_idx(root);
-                float lo = 0.0f;
-                int sw = 0;
-                int64_t a0 = 0, a1 = 0;
-                if (lane == 0) {  // independent loads, in flight during the runner-up scan
-                    lo = I.lo32[w];
-                    sw = I.s[w];
-                    a0 = I.rp[w];
-                    a1 = I.rp[w + 1];
+            int sk = 0;
+            int64_t a0 = 0, a1 = 0;
+            unsigned long long ru = ~0ull;
+            float tau = 0.0f;
+            int64_t k = pick_warp<PREC>(I, L, R, D, st, step, &sk, &a0, &a1, &ru, &tau);
+            if (lane == 0) {
+                if (k >= 0) {
+                    if (flips < max_flips)
+                        do_flip(k, sk, a0, a1);
+                    else
+                        k = kPickMaxFlips;
                 }
-                const unsigned long long ru = runner_up(I, L, w);
-                if (lane == 0) {
-                    const float hi2 = ru ? key32_hi(ru) : 0.0f;
-                    if (lo > 1.0f && lo > hi2) {
-                        if (flips < max_flips) {
-                            do_flip(w, sw, a0, a1);
-                            k = w;
-                        } else {
-                            k = -6;
-                        }
-                    } else {
-                        k = -2;
-                        sh_tau = fmaxf(hi2, lo);
-                    }
-                }
+                sh_k = k;
+                sh_ru = ru;
+                sh_tau = tau;
             }
-            if (lane == 0) sh_k = k;
         }
         __syncthreads();
         int64_t k = sh_k;
-        if (k == -2) {
+        if (k == kPickOverflow) {
+            // too many contenders for one warp: every thread compares exactly
             float tau = sh_tau;
-            while (k == -2) {
-                if (++rounds > 64) {
-                    k = -4;
-                    break;
-                }
-                if (wid == 0) {
-                    const int64_t r = recheck_warp<PREC>(I, L, R, tau, step);
-                    if (lane == 0) {
-                        R.result = (int32_t)r;
-                        atomicAdd((unsigned long long*)&st->rechecks, 1ull);
-                    }
-                }
-                __syncthreads();
-                int64_t r = R.result;
-                if (r == -3) {
-                    if (threadIdx.x == 0) atomicAdd((unsigned long long*)&st->fallbacks, 1ull);
-                    r = recheck_scan<PREC>(I, L, R, tau, step);
-                }
+            int64_t r = -2;
+            for (int rounds = 0; r == -2 && rounds < 64; ++rounds) {
+                if (threadIdx.x == 0) atomicAdd((unsigned long long*)&st->fallbacks, 1ull);
+                r = recheck_scan<PREC>(I, L, R, tau, step);
                 tau = R.tau;
-                if (r == -1) {
-                    k = -5;  // everything examined was demoted: look at the root again
-                    rounds = 0;
-                } else {
-                    k = r;  // the winner, or -2 to widen
-                }
+            }
+            if (r == -1) {
                 __syncthreads();
+                continue;  // everything examined was demoted: look at the root again
             }
-            if (k == -5) continue;
-            if (k == -4) {
-                status = ST_BOUNDS;
-                break;
-            }
-            if (k >= 0) {
+            if (r == -2) {
+                k = kPickBounds;
+            } else {
                 if (threadIdx.x == 0) {
-                    if (flips < max_flips)
-                        do_flip(k, I.s[k], I.rp[k], I.rp[k + 1]);
-                    else
-                        sh_k = -6;
+                    if (flips < max_flips) {
+                        do_flip(r, I.s[r], I.rp[r], I.rp[r + 1]);
+                        sh_k = r;
+                    } else {
+                        sh_k = kPickMaxFlips;
+                    }
+                    sh_ru = ~0ull;
                 }
                 __syncthreads();
-                if (sh_k == -6) k = -6;
+                k = sh_k;
             }
         }
-        rounds = 0;
-        if (k == -6) {
+        if (k == kPickBounds) {
+            status = ST_BOUNDS;
+            break;
+        }
+        if (k == kPickMaxFlips) {
             status = ST_NOT_CONVERGED;
             break;
         }
@@ -577,25 +784,48 @@ __global__ void __launch_bounds__(kT, 1)
         ++flips;
         // every neighbour i of k: add 2 s_k(new) (P_ik, Q_ik), new key, tree update
         const int snew = sh_snew;
-        const int64_t e0 = sh_e0;
-        const int len = (int)(sh_e1 - e0);
-        for (int q = threadIdx.x; q < len; q += kT) {
-            const int64_t e = e0 + q;
-            // the row's entries (read-only), all issued before the padding test
-            const int32_t i = __ldg(&I.col[e]);
-            const long long dp = __ldg(&I.pq64[e].x), dq = __ldg(&I.qt64[e]);
-            int dp32 = 0, dq32 = 0;
-            if constexpr (PREC == 1) {
-                dp32 = __ldg(&I.pq32[e].x);
-                dq32 = __ldg(&I.qt32[e]);
+        const int par = (int)(flips & 1);
+        const unsigned long long ru = sh_ru;
+        if (P.buf_id == (int32_t)k) {  // k's row was staged in shared memory
+            const RowBuf B = row_buf(bufs, I.row_cap, 0);
+            const int len = P.buf_len;
+            for (int q = threadIdx.x; q < len; q += kT) {
+                const int32_t i = B.col[q];
+                const long long dp = B.pq64[q].x, dq = B.qt64[q];
+                int dp32 = 0, dq32 = 0;
+                if constexpr (PREC == 1) {
+                    dp32 = B.pq32[q].x;
+                    dq32 = B.qt32[q];
+                }
+                if (i == (int32_t)k) continue;  // row padding
+                update_island<PREC, true>(I, L, D, P, par, i, snew, dp, dq, dp32, dq32, step, ru);
             }
-            if (i == (int32_t)k) continue;  // row padding
-            update_island<PREC>(I, L, D, i, snew, dp, dq, dp32, dq32, step);
+        } else {
+            const int64_t e0 = sh_e0;
+            const int len = (int)(sh_e1 - e0);
+            for (int q = threadIdx.x; q < len; q += kT) {
+                const int64_t e = e0 + q;
+                // the row's entries (read-only), all issued before the padding test
+                const int32_t i = __ldg(&I.col[e]);
+                const long long dp = __ldg(&I.pq64[e].x), dq = __ldg(&I.qt64[e]);
+                int dp32 = 0, dq32 = 0;
+                if constexpr (PREC == 1) {
+                    dp32 = __ldg(&I.pq32[e].x);
+                    dq32 = __ldg(&I.qt32[e]);
+                }
+                if (i == (int32_t)k) continue;  // row padding
+                update_island<PREC, true>(I, L, D, P, par, i, snew, dp, dq, dp32, dq32, step, ru);
+            }
         }
         if (threadIdx.x == kT - 1)  // k's own field is unchanged; its key is not
-            update_island<PREC>(I, L, D, k, snew, 0, 0, 0, 0, step);
+            update_island<PREC, false>(I, L, D, P, par, k, snew, 0, 0, 0, 0, step, ~0ull);
+        if (threadIdx.x == kT - 2 && ru != ~0ull && ru != 0ull) {
+            // the runner-up is the next pick unless a neighbour rises above it
+            const int64_t j = key32_idx(ru);
+            stage_candidate<PREC>(I, P, par, ru, __ldg(&I.rp[j]), __ldg(&I.rp[j + 1]));
+        }
         __syncthreads();
-        rebuild_dirty(I, L, D, false);
+        tree_phase<PREC>(I, L, D, P, bufs, par);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -674,14 +904,20 @@ cudaError_t prepare_relax(int prec, int smem) {
     return e;
 }
 
+int relax_smem_total(int levels, int row_cap) {
+    return ((levels + 15) & ~15) + kRowBufs * row_cap * kRowBufEntry;
+}
+
+// The launch's dynamic shared memory must hold the levels' budget (rounded up to
+// 16 bytes) and kRowBufs buffers of every simulation's row_cap entries.
 cudaError_t launch_relax(const RelaxLaunch& L, cudaStream_t st) {
     if (L.n_work == 0) return cudaSuccess;
-    const cudaError_t e = prepare_relax(L.prec, L.smem_budget);
+    const cudaError_t e = prepare_relax(L.prec, L.smem_total);
     if (e != cudaSuccess) return e;
     if (L.prec == 1)
-        k_relax<1><<<L.n_work, kT, L.smem_budget, st>>>(L.tab, L.work, L.n_work, L.smem_budget);
+        k_relax<1><<<L.n_work, kT, L.smem_total, st>>>(L.tab, L.work, L.n_work, L.smem_levels);
     else
-        k_relax<0><<<L.n_work, kT, L.smem_budget, st>>>(L.tab, L.work, L.n_work, L.smem_budget);
+        k_relax<0><<<L.n_work, kT, L.smem_total, st>>>(L.tab, L.work, L.n_work, L.smem_levels);
     return cudaGetLastError();
 }
 

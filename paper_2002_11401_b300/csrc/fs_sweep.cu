@@ -189,18 +189,20 @@ __global__ void __launch_bounds__(kSweepThreads)
             const Eval32 e = eval32(I, si, dp, dq, I.rbc32[i], e32, th.x, th.y);
             float lo = e.certain ? e.lo : -1.0f;
             node = e.possible ? key32_of(e.hi, i) : 0ull;
+            double x = e.possible ? -1.0 : 0.0;
             if (e.possible && !e.certain) {
                 // within its band of the threshold or of the sign change: FP64 now
                 if (!SUM64) h64 = I.h64[i];
                 double tp = 0.0, tq = 0.0;
-                if (I.sigma > 0.0) thermal64(I, i, step, &tp, &tq);
+                if (I.sigma > 0.0) thermal64_kept(I, i, step, &tp, &tq);
                 const Eval64 f = eval64(I, si, h64.x, h64.y, I.hk64[i], I.ext64[ci], tp, tq);
-                const double x = f.flippable ? f.lhs : 0.0;
+                x = f.flippable ? f.lhs : 0.0;
                 node = x > 0.0 ? key32_of(__double2float_ru(x), i) : 0ull;
                 lo = x > 0.0 ? __double2float_rd(x) : -1.0f;
             }
             I.key32[i] = node;
             I.lo32[i] = lo;
+            I.key64[i] = x;
         } else {
             if (!SUM64) h64 = I.h64[i];
             const float dp = __fmul_rn(__ll2float_rn(h64.x), I.inv64f);
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(kSweepThreads)
             double x = 0.0;
             if (e.possible) {
                 double tp = 0.0, tq = 0.0;
-                if (I.sigma > 0.0) thermal64(I, i, step, &tp, &tq);
+                if (I.sigma > 0.0) thermal64_kept(I, i, step, &tp, &tq);
                 const Eval64 f = eval64(I, si, h64.x, h64.y, I.hk64[i], I.ext64[ci], tp, tq);
                 if (f.flippable) x = f.lhs;
             }
