@@ -600,6 +600,7 @@ cudaError_t enqueue_steps(fs_sim* sim, int64_t K, int resweep, cudaStream_t st) 
     S.tcnts = sim->d_tcnts;
     S.prec = sim->p.precision;
     S.lanes_per_row = sim->lanes;
+    S.occupancy = sim->sweep_occ;
     S.resweep = resweep ? 1 : 0;
     RelaxLaunch R;
     R.tab = sim->d_inst;
@@ -815,6 +816,7 @@ static fs_status refresh_fields(fs_sim* sim) {
     S.prec = sim->p.precision;
     S.resweep = 1;
     S.lanes_per_row = sim->lanes;
+    S.occupancy = sim->sweep_occ;
     CK(launch_ext_table(S, st), "sweep");
     CK(launch_sweep(S, st), "sweep");
     CK(cudaStreamSynchronize(st), "sweep");
@@ -1001,10 +1003,11 @@ extern "C" fs_status fs_autotune(fs_sim* sim, int32_t* lanes_out) {
     CK(cudaEventCreate(&e0), "event");
     CK(cudaEventCreate(&e1), "event");
     const int cands[4] = {4, 8, 16, 32};
-    int best = sim->lanes;
+    int best = sim->lanes, best_occ = sim->sweep_occ;
     float best_ms = 1e30f;
-    for (int c = 0; c < 4; ++c) {
-        S.lanes_per_row = cands[c];
+    for (int c = 0; c < 8; ++c) {
+        S.lanes_per_row = cands[c & 3];
+        S.occupancy = c < 4 ? 4 : 5;
         CK(launch_sweep(S, st), "sweep");
         float ms = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
@@ -1018,12 +1021,14 @@ extern "C" fs_status fs_autotune(fs_sim* sim, int32_t* lanes_out) {
         }
         if (ms < best_ms) {
             best_ms = ms;
-            best = cands[c];
+            best = cands[c & 3];
+            best_occ = S.occupancy;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     sim->lanes = best;
+    sim->sweep_occ = best_occ;
     if (lanes_out) *lanes_out = best;
     return FS_OK;
 }

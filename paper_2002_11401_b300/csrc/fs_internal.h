@@ -64,6 +64,7 @@ struct fs_sim {
     int32_t max_deg = 0;
     int32_t e64 = 0, e32 = 0;
     int lanes = 16;
+    int sweep_occ = 4;  // resident sweep CTAs per SM (4 or 5), set by the autotuner
     int64_t rechecks = 0, fallbacks = 0;
     cudaGraphExec_t graph_exec = nullptr;
     // profiling: CUDA events around each sweep and relax launch

@@ -17,6 +17,7 @@ struct SweepLaunch {
     int prec;
     int resweep;                // 0 margins only, 1 recompute the dipolar sums
     int lanes_per_row;          // 4, 8, 16 or 32
+    int occupancy = 4;          // resident CTAs per SM the kernel is built for: 4 or 5
 };
 
 struct RelaxLaunch {

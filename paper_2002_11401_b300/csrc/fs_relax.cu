@@ -198,12 +198,27 @@ __device__ void tree_phase(const Inst& I, const Levels& L, Dirty& D, RowStage& P
     for (int q = wid; q < n0; q += kNW) rebuild_node(I, L, D, 0, D.lv0[q]);
     __syncthreads();
     if (wid == 0) {
-        for (int lev = 1; lev < I.nlev; ++lev) {
-            const int nn = min(D.nup[lev], kDirtyCap);
+        // Every lane reads the same node values, so the decision to queue a parent
+        // is warp-uniform: the queue lengths stay in registers.
+        int nn = min(D.nup[1], kDirtyCap);
+        for (int lev = 1; lev < I.nlev && nn > 0; ++lev) {
+            const int32_t* qin = D.up[lev & 1];
+            int32_t* qout = D.up[(lev + 1) & 1];
+            const int64_t nchild = I.lvl_n[lev - 1];
+            int nout = 0;
             for (int q = 0; q < nn; ++q) {
-                rebuild_node(I, L, D, lev, D.up[lev & 1][q]);
-                __syncwarp();
+                const int64_t node = qin[q];
+                const unsigned long long old = L.p[lev][node];
+                const int64_t c = (node << 5) + lane;
+                const unsigned long long nv = warp_max_key(c < nchild ? L.p[lev - 1][c] : 0ull);
+                if (lane == 0) L.p[lev][node] = nv;
+                if (nv < old && lev + 1 < I.nlev && L.p[lev + 1][node >> 5] == old) {
+                    if (lane == 0 && nout < kDirtyCap) qout[nout] = (int32_t)(node >> 5);
+                    ++nout;
+                }
             }
+            __syncwarp();
+            nn = min(nout, kDirtyCap);
         }
     } else if (wid == 1) {
         const unsigned long long pred = P.best[par];

@@ -80,8 +80,11 @@ __device__ void propagate_up(const Inst& I, unsigned* __restrict__ tcnt, int lev
 // MODE 0: margins only (exact sums kept by the flips); MODE 1: resweep the sums of
 // the simulation's width. A simulation whose state says `init` (sums not set up
 // yet) is swept in any mode, and on the FP32 path both widths are summed.
-template <int PREC, int W, int MODE>
-__global__ void __launch_bounds__(kSweepThreads)
+// OCC resident CTAs per SM: 4 (registers as needed) or 5 (at most 51 registers a
+// thread, some spilled): the latter puts 5920 warps on the 148 SMs, one wave for
+// an array of up to 189,000 islands. The autotuner picks.
+template <int PREC, int W, int MODE, int OCC>
+__global__ void __launch_bounds__(kSweepThreads, OCC)
     k_sweep(const Inst* __restrict__ tab, const int64_t* __restrict__ task_start, int n_inst,
             int64_t total_tasks, unsigned* const* __restrict__ tcnts) {
     __shared__ int sums32[PREC == 1 ? kSweepWarps : 1][32][2];
@@ -241,29 +244,31 @@ __global__ void k_ext_table(const Inst* __restrict__ tab, int n_inst) {
     }
 }
 
+template <int PREC, int MODE, int W>
+cudaError_t launch_wo(unsigned blocks, const SweepLaunch& L, cudaStream_t st) {
+    if (L.occupancy == 5)
+        k_sweep<PREC, W, MODE, 5><<<blocks, kSweepThreads, 0, st>>>(
+            L.tab, L.task_start, L.n_inst, L.total_tasks, L.tcnts);
+    else
+        k_sweep<PREC, W, MODE, 4><<<blocks, kSweepThreads, 0, st>>>(
+            L.tab, L.task_start, L.n_inst, L.total_tasks, L.tcnts);
+    return cudaGetLastError();
+}
+
 template <int PREC, int MODE>
-cudaError_t launch_w(int W, const SweepLaunch& L, cudaStream_t st) {
+cudaError_t launch_w(const SweepLaunch& L, cudaStream_t st) {
     const unsigned blocks = (unsigned)((L.total_tasks + kSweepWarps - 1) / kSweepWarps);
     if (blocks == 0) return cudaSuccess;
-    switch (W) {
+    switch (L.lanes_per_row) {
         case 4:
-            k_sweep<PREC, 4, MODE><<<blocks, kSweepThreads, 0, st>>>(
-                L.tab, L.task_start, L.n_inst, L.total_tasks, L.tcnts);
-            break;
+            return launch_wo<PREC, MODE, 4>(blocks, L, st);
         case 8:
-            k_sweep<PREC, 8, MODE><<<blocks, kSweepThreads, 0, st>>>(
-                L.tab, L.task_start, L.n_inst, L.total_tasks, L.tcnts);
-            break;
+            return launch_wo<PREC, MODE, 8>(blocks, L, st);
         case 16:
-            k_sweep<PREC, 16, MODE><<<blocks, kSweepThreads, 0, st>>>(
-                L.tab, L.task_start, L.n_inst, L.total_tasks, L.tcnts);
-            break;
+            return launch_wo<PREC, MODE, 16>(blocks, L, st);
         default:
-            k_sweep<PREC, 32, MODE><<<blocks, kSweepThreads, 0, st>>>(
-                L.tab, L.task_start, L.n_inst, L.total_tasks, L.tcnts);
-            break;
+            return launch_wo<PREC, MODE, 32>(blocks, L, st);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace
@@ -278,10 +283,8 @@ cudaError_t launch_ext_table(const SweepLaunch& L, cudaStream_t st) {
 cudaError_t launch_sweep(const SweepLaunch& L, cudaStream_t st) {
     if (L.n_inst == 0) return cudaSuccess;
     if (L.prec == 1)
-        return L.resweep ? launch_w<1, 1>(L.lanes_per_row, L, st)
-                         : launch_w<1, 0>(L.lanes_per_row, L, st);
-    return L.resweep ? launch_w<0, 1>(L.lanes_per_row, L, st)
-                     : launch_w<0, 0>(L.lanes_per_row, L, st);
+        return L.resweep ? launch_w<1, 1>(L, st) : launch_w<1, 0>(L, st);
+    return L.resweep ? launch_w<0, 1>(L, st) : launch_w<0, 0>(L, st);
 }
 
 }  // namespace fs
