@@ -379,7 +379,6 @@ fs_status fs_build_sim(fs_sim* sim) {
     CK(palloc((void**)&I.ext64, 16 * ncls), "alloc");
     CK(palloc((void**)&I.ext32, 8 * ncls), "alloc");
     I.nclass = (int32_t)ncls;
-    I.row_cap = std::min<int32_t>(sim->max_deg, kRowBufMax);
     if (p.sigma_th > 0.0) {
         CK(palloc((void**)&I.th32, 8 * n), "alloc");
         CK(palloc((void**)&I.th64, 16 * n), "alloc");
@@ -555,7 +554,7 @@ int relax_smem_levels(int64_t n) {
     return (int)std::max<int64_t>(1024, used);
 }
 
-int relax_smem_max() { return relax_smem_total(96 * 1024, kRowBufMax); }
+int relax_smem_max() { return 96 * 1024; }
 
 // Queues K field steps of one simulation (sweep + relax per step). The
 // descriptor's protocol fields must already point at device buffers.
@@ -608,7 +607,6 @@ cudaError_t enqueue_steps(fs_sim* sim, int64_t K, int resweep, cudaStream_t st) 
     R.n_work = 1;
     R.prec = sim->p.precision;
     R.smem_levels = relax_smem_levels(sim->n);
-    R.smem_total = relax_smem_total(R.smem_levels, sim->inst.row_cap);
     cudaError_t e;
     if (sim->profiling && sim->ev_used + 3 * (size_t)K > 30000 &&
         (e = collect_profile(sim)) != cudaSuccess)

@@ -68,8 +68,7 @@ cudaError_t BatchTable::upload(const std::vector<fs_sim*>& sims,
     return cudaMemcpyAsync(work, h_work.data(), 4 * n, cudaMemcpyHostToDevice, st);
 }
 
-cudaError_t BatchTable::enqueue_step(int prec, int resweep, int levels, int smem,
-                                      cudaStream_t st) const {
+cudaError_t BatchTable::enqueue_step(int prec, int resweep, int levels, cudaStream_t st) const {
     if (n_inst == 0) return cudaSuccess;
     SweepLaunch S;
     S.tab = tab;
@@ -90,7 +89,6 @@ cudaError_t BatchTable::enqueue_step(int prec, int resweep, int levels, int smem
     R.n_work = n_inst;
     R.prec = prec;
     R.smem_levels = levels;
-    R.smem_total = smem;
     return launch_relax(R, st);
 }
 
@@ -185,13 +183,9 @@ extern "C" fs_status fs_batch_run_protocol(fs_sim* const* sims, int32_t n, const
     BatchTable B;
     if ((e = B.upload(v, descs, st)) != cudaSuccess) return bail(e, "upload");
     const int prec = lead->p.precision;
-    int levels = 1024, row_cap = 0;
-    for (int i = 0; i < n; ++i) {
-        levels = std::max(levels, relax_smem_levels(v[(size_t)i]->n));
-        row_cap = std::max(row_cap, v[(size_t)i]->inst.row_cap);
-    }
-    const int smem = relax_smem_total(levels, row_cap);
-    if ((e = prepare_relax(prec, smem)) != cudaSuccess) return bail(e, "relax setup");
+    int levels = 1024;
+    for (int i = 0; i < n; ++i) levels = std::max(levels, relax_smem_levels(v[(size_t)i]->n));
+    if ((e = prepare_relax(prec, levels)) != cudaSuccess) return bail(e, "relax setup");
     // capture the whole protocol in one graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -199,7 +193,7 @@ extern "C" fs_status fs_batch_run_protocol(fs_sim* const* sims, int32_t n, const
         return bail(e, "capture");
     cudaError_t le = cudaSuccess;
     for (int64_t t = 0; t < K && le == cudaSuccess; ++t)
-        le = B.enqueue_step(prec, resweep ? 1 : 0, levels, smem, st);
+        le = B.enqueue_step(prec, resweep ? 1 : 0, levels, st);
     e = cudaStreamEndCapture(st, &graph);
     if (le != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);

@@ -29,7 +29,7 @@ struct BatchTable {
     cudaError_t upload(const std::vector<fs_sim*>& sims, const std::vector<Inst>& descs,
                        cudaStream_t st);
     // one field step of every member: a sweep over all rows, then one relax CTA each
-    cudaError_t enqueue_step(int prec, int resweep, int levels, int smem, cudaStream_t st) const;
+    cudaError_t enqueue_step(int prec, int resweep, int levels, cudaStream_t st) const;
 };
 
 cudaError_t prepare_relax(int prec, int smem);

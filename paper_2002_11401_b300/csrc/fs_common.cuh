@@ -18,9 +18,6 @@ constexpr int kMaxPaddedDegree = 1024;    // neighbours per island after padding
 constexpr int kFan = 32;                  // max-tree fan-out (one warp)
 constexpr int kMaxLevels = 8;             // tree levels above the leaves
 constexpr int kRecheckCap = 256;          // FP64 recheck candidates per round
-constexpr int kRowBufs = 1;               // relax: rows staged in shared memory per flip
-constexpr int kRowBufMax = 256;           // relax: longest row that is staged
-constexpr int kRowBufEntry = 40;          // bytes per staged entry (col, P/Q, Q^T, both widths)
 
 // Device status codes (mirror fs_status).
 enum : int32_t {
@@ -51,7 +48,6 @@ struct Inst {
     int32_t prec;    // 0 = FP64, 1 = FP32 + FP64 recheck
     int32_t nlev;    // tree levels above the leaves; level nlev-1 is the root
     int32_t nclass;  // distinct island angles
-    int32_t row_cap; // entries per staged row buffer: min(max padded degree, kRowBufMax)
     int32_t pad1;
     int32_t lvl_n[kMaxLevels];
     int64_t lvl_off[kMaxLevels];  // node offset of each level in `tree`
@@ -222,6 +218,22 @@ __device__ __forceinline__ void thermal64_kept(const Inst& I, int64_t i, uint32_
     thermal64(I, i, step, tp, tq);
     I.th64[i] = make_double2(*tp, *tq);
     I.th_step[i] = step;
+}
+
+// thermal64 of island i at `step`, kept (KEEP) or only looked up among the kept
+// draws (otherwise drawn afresh without keeping it).
+template <bool KEEP>
+__device__ __forceinline__ void thermal64_at(const Inst& I, int64_t i, uint32_t step, double* tp,
+                                             double* tq) {
+    if constexpr (KEEP) {
+        thermal64_kept(I, i, step, tp, tq);
+    } else if (I.th_step[i] == step) {
+        const double2 v = I.th64[i];
+        *tp = v.x;
+        *tq = v.y;
+    } else {
+        thermal64(I, i, step, tp, tq);
+    }
 }
 
 __device__ __forceinline__ float2 thermal32(const Inst& I, int64_t i, uint32_t step) {

@@ -26,16 +26,12 @@ struct RelaxLaunch {
     int n_work;
     int prec;
     int smem_levels;      // dynamic shared memory for the upper tree levels
-    int smem_total;       // levels (16-byte aligned) + staged row buffers
 };
 
 cudaError_t launch_ext_table(const SweepLaunch& L, cudaStream_t st);
 cudaError_t launch_sweep(const SweepLaunch& L, cudaStream_t st);
 cudaError_t launch_relax(const RelaxLaunch& L, cudaStream_t st);
 cudaError_t prepare_relax(int prec, int smem);
-// Dynamic shared memory of a relax launch whose simulations have at most
-// `levels` bytes of tree levels and `row_cap` entries per staged row.
-int relax_smem_total(int levels, int row_cap);
 // out5 = [h_par | h_perp | lhs | lo | hi], 5 n doubles
 cudaError_t launch_eval_all(const Inst* tab, int64_t n, double hx, double hy, uint32_t step,
                             double* out5, cudaStream_t st);

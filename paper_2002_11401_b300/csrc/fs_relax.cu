@@ -86,7 +86,6 @@ struct Dirty {
     int32_t lv0[kDirtyCap];    // first-level nodes to rebuild
     int32_t up[2][kDirtyCap];  // upper-level nodes, ping-pong by level parity
     int32_t n0;
-    int32_t nup[kMaxLevels];   // queued nodes of each upper level
 };
 
 // A leaf's key went from `old` to `nk`: a larger key is pushed up with atomic
@@ -109,137 +108,70 @@ __device__ __forceinline__ void leaf_changed(const Inst& I, const Levels& L, Dir
     }
 }
 
-// Rebuilds node `node` of level `lev` (lev >= 0) from its children and, when its
-// maximum shrank and its parent held it, queues the parent. Warp-wide.
-__device__ __forceinline__ void rebuild_node(const Inst& I, const Levels& L, Dirty& D, int lev,
-                                             int64_t node) {
-    const int lane = threadIdx.x & 31;
-    const unsigned long long old = L.p[lev][node];
-    const unsigned long long nv = warp_node(I, L, lev, node);
-    if (lane == 0) {
-        L.p[lev][node] = nv;
-        if (nv < old && lev + 1 < I.nlev && L.p[lev + 1][node >> 5] == old) {
-            const int r = atomicAdd(&D.nup[lev + 1], 1);
-            if (r < kDirtyCap) D.up[(lev + 1) & 1][r] = (int32_t)(node >> 5);
-        }
-    }
-}
-
-// The row of the predicted next pick, staged in shared memory. The next pick is
-// the larger of the largest key the flip left untouched (the runner-up, when the
-// flip was certified from bounds) and the largest new key among the flip's
-// neighbours: both are folded into best[parity] with atomic maxima during the
-// neighbour updates, and while warp 0 repairs the tree and picks, warp 1 copies
-// that island's row into the buffer (asynchronous copies). Double-buffered by
-// flip parity.
+// The prediction of the next pick: the larger of the largest key the flip left
+// untouched (the runner-up, when the flip was certified from bounds) and the
+// largest new key among the flip's neighbours, folded into best[parity] with
+// atomic maxima during the neighbour updates. Double-buffered by flip parity.
 struct RowStage {
     unsigned long long best[2];
-    int32_t buf_id;   // island whose row the buffer holds, -1 for none
-    int32_t buf_len;
 };
 
-struct RowBuf {
-    longlong2* pq64;
-    long long* qt64;
-    int2* pq32;
-    int32_t* col;
-    int32_t* qt32;
-};
-
-// Buffer b of `cap` entries (cap a multiple of 4: every array is a whole number
-// of 16-byte chunks, each starting 16-byte aligned).
-__device__ __forceinline__ RowBuf row_buf(unsigned char* base, int cap, int b) {
-    unsigned char* p = base + (size_t)b * (size_t)cap * kRowBufEntry;
-    RowBuf r;
-    r.pq64 = reinterpret_cast<longlong2*>(p);
-    p += 16 * cap;
-    r.qt64 = reinterpret_cast<long long*>(p);
-    p += 8 * cap;
-    r.pq32 = reinterpret_cast<int2*>(p);
-    p += 8 * cap;
-    r.col = reinterpret_cast<int32_t*>(p);
-    p += 4 * cap;
-    r.qt32 = reinterpret_cast<int32_t*>(p);
-    return r;
-}
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
-// Warp-wide: starts the copy of row [a0, a0 + m) into B (m <= cap, multiple of 4).
-template <int PREC>
-__device__ __forceinline__ void stage_row(const Inst& I, const RowBuf& B, int64_t a0, int m) {
+// Warp 0 after the neighbour updates: rebuilds the queued first-level nodes (their
+// leaves loaded four nodes at a time) and then, level by level, every node above
+// whose maximum was a key that shrank. Every lane reads the same node values, so
+// the decision to queue a parent is warp-uniform and the queues' lengths stay in
+// registers. Empties the first-level queue.
+__device__ void repair_warp(const Inst& I, const Levels& L, Dirty& D) {
+    constexpr int kBatch = 4;
     const int lane = threadIdx.x & 31;
-    for (int c = lane; c < m; c += 32) cp_async16(&B.pq64[c], &I.pq64[a0 + c]);
-    for (int c = lane; c < m / 2; c += 32) cp_async16(&B.qt64[2 * c], &I.qt64[a0 + 2 * c]);
-    for (int c = lane; c < m / 4; c += 32) cp_async16(&B.col[4 * c], &I.col[a0 + 4 * c]);
-    if constexpr (PREC == 1) {
-        for (int c = lane; c < m / 2; c += 32) cp_async16(&B.pq32[2 * c], &I.pq32[a0 + 2 * c]);
-        for (int c = lane; c < m / 4; c += 32) cp_async16(&B.qt32[4 * c], &I.qt32[a0 + 4 * c]);
-    }
-}
-
-// After the neighbour updates, every thread: all warps rebuild the queued
-// first-level nodes; then warp 0 rebuilds the queued nodes above, level by level
-// (few nodes, so one warp without barriers), while warp 1 stages the predicted
-// row. Returns with warp 0 done with the tree and warp 1's copies landed; the
-// caller's next barrier publishes both.
-template <int PREC>
-__device__ void tree_phase(const Inst& I, const Levels& L, Dirty& D, RowStage& P,
-                           unsigned char* bufs, int par) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int n0 = min(D.n0, kDirtyCap);
-    for (int q = wid; q < n0; q += kNW) rebuild_node(I, L, D, 0, D.lv0[q]);
-    __syncthreads();
-    if (wid == 0) {
-        // Every lane reads the same node values, so the decision to queue a parent
-        // is warp-uniform: the queue lengths stay in registers.
-        int nn = min(D.nup[1], kDirtyCap);
-        for (int lev = 1; lev < I.nlev && nn > 0; ++lev) {
-            const int32_t* qin = D.up[lev & 1];
-            int32_t* qout = D.up[(lev + 1) & 1];
-            const int64_t nchild = I.lvl_n[lev - 1];
-            int nout = 0;
-            for (int q = 0; q < nn; ++q) {
-                const int64_t node = qin[q];
-                const unsigned long long old = L.p[lev][node];
-                const int64_t c = (node << 5) + lane;
-                const unsigned long long nv = warp_max_key(c < nchild ? L.p[lev - 1][c] : 0ull);
-                if (lane == 0) L.p[lev][node] = nv;
-                if (nv < old && lev + 1 < I.nlev && L.p[lev + 1][node >> 5] == old) {
-                    if (lane == 0 && nout < kDirtyCap) qout[nout] = (int32_t)(node >> 5);
-                    ++nout;
-                }
+    int32_t* qout = D.up[1];
+    int nout = 0;
+    for (int q0 = 0; q0 < n0; q0 += kBatch) {
+        unsigned long long v[kBatch];
+        int64_t node[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            node[u] = q0 + u < n0 ? (int64_t)D.lv0[q0 + u] : -1;
+            const int64_t c = (node[u] << 5) + lane;
+            v[u] = node[u] >= 0 && c < I.n ? I.key32[c] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            if (node[u] < 0) break;
+            const unsigned long long old = L.p[0][node[u]];
+            const unsigned long long nv = warp_max_key(v[u]);
+            if (lane == 0) L.p[0][node[u]] = nv;
+            if (nv < old && I.nlev > 1 && L.p[1][node[u] >> 5] == old) {
+                if (lane == 0 && nout < kDirtyCap) qout[nout] = (int32_t)(node[u] >> 5);
+                ++nout;
             }
             __syncwarp();
-            nn = min(nout, kDirtyCap);
         }
-    } else if (wid == 1) {
-        const unsigned long long pred = P.best[par];
-        int32_t id = -1, len = 0;
-        if (pred != 0ull) {
-            const int64_t j = key32_idx(pred);
-            const int64_t a0 = __ldg(&I.rp[j]);
-            const int m = (int)(__ldg(&I.rp[j + 1]) - a0);
-            if (m > 0 && m <= I.row_cap) {
-                stage_row<PREC>(I, row_buf(bufs, I.row_cap, 0), a0, m);
-                id = (int32_t)j;
-                len = m;
+    }
+    int nn = min(nout, kDirtyCap);
+    __syncwarp();
+    for (int lev = 1; lev < I.nlev && nn > 0; ++lev) {
+        const int32_t* qin = D.up[lev & 1];
+        qout = D.up[(lev + 1) & 1];
+        const int64_t nchild = I.lvl_n[lev - 1];
+        nout = 0;
+        for (int q = 0; q < nn; ++q) {
+            const int64_t node = qin[q];
+            const unsigned long long old = L.p[lev][node];
+            const int64_t c = (node << 5) + lane;
+            const unsigned long long nv = warp_max_key(c < nchild ? L.p[lev - 1][c] : 0ull);
+            if (lane == 0) L.p[lev][node] = nv;
+            if (nv < old && lev + 1 < I.nlev && L.p[lev + 1][node >> 5] == old) {
+                if (lane == 0 && nout < kDirtyCap) qout[nout] = (int32_t)(node >> 5);
+                ++nout;
             }
         }
-        if (lane == 0) {
-            P.buf_id = id;
-            P.buf_len = len;
-            P.best[par ^ 1] = 0ull;  // the next flip's prediction
-        }
-        cp_async_wait_all();
+        __syncwarp();
+        nn = min(nout, kDirtyCap);
     }
+    if (lane == 0) D.n0 = 0;
+    __syncwarp();
 }
 
 // Whole tree from the leaves (after a full rescan).
@@ -256,8 +188,10 @@ __device__ void rebuild_tree(const Inst& I, const Levels& L) {
 
 // Key of island i from its current state (already loaded): returns the new key
 // and writes lo and the exact value x (the FS_FP64 LHS when flippable, 0 when
-// not; on the FP32 path -1 when only the FP32 bounds were taken).
-template <int PREC>
+// not; on the FP32 path -1 when only the FP32 bounds were taken). KEEP: an FP64
+// thermal draw taken here is kept for later evaluations; without it the kept
+// draws are only read (for evaluations ahead of the pick, which store nothing).
+template <int PREC, bool KEEP>
 __device__ __forceinline__ unsigned long long key_of(const Inst& I, int64_t i, uint32_t step,
                                                      int si, uint16_t ci, longlong2 h64, int2 h32,
                                                      float2 rbc, float2 e32, float2 th,
@@ -270,7 +204,7 @@ __device__ __forceinline__ unsigned long long key_of(const Inst& I, int64_t i, u
         if (e.possible && !e.certain) {
             // within its band of the threshold or of the sign change: FP64 now
             double tp = 0.0, tq = 0.0;
-            if (I.sigma > 0.0) thermal64_kept(I, i, step, &tp, &tq);
+            if (I.sigma > 0.0) thermal64_at<KEEP>(I, i, step, &tp, &tq);
             const Eval64 f =
                 eval64(I, si, h64.x, h64.y, __ldg(&I.hk64[i]), __ldg(&I.ext64[ci]), tp, tq);
             const double x = f.flippable ? f.lhs : 0.0;
@@ -288,7 +222,7 @@ __device__ __forceinline__ unsigned long long key_of(const Inst& I, int64_t i, u
         double x = 0.0;
         if (e.possible) {
             double tp = 0.0, tq = 0.0;
-            if (I.sigma > 0.0) thermal64_kept(I, i, step, &tp, &tq);
+            if (I.sigma > 0.0) thermal64_at<KEEP>(I, i, step, &tp, &tq);
             const Eval64 f = eval64(I, si, h64.x, h64.y, hk, e64, tp, tq);
             if (f.flippable) x = f.lhs;
         }
@@ -329,30 +263,38 @@ __device__ __forceinline__ void stage_candidate(const Inst& I, RowStage& P, int 
     atomicMax(&P.best[par], kj);
 }
 
-// Island i's field changes by 2 s_new (dp, dq) (exact 64-bit sums; dp32, dq32 the
-// 32-bit ones); its key is re-evaluated and the tree told. Every load is issued
-// before the first store so that they overlap. When the new key exceeds
-// `pf_above` (the largest key the flip did not touch), i may be the next pick and
-// its row is staged.
-template <int PREC, bool PF>
-__device__ __forceinline__ void update_island(const Inst& I, const Levels& L, Dirty& D,
-                                              RowStage& P, int par, int64_t i, int snew,
-                                              long long dp, long long dq, int dp32, int dq32,
-                                              uint32_t step, unsigned long long pf_above) {
+// One neighbour update: island i's field changes by 2 s_new (dp, dq) (exact 64-bit
+// sums; dp32, dq32 the 32-bit ones) and its key is re-evaluated. Computing it
+// (loads and arithmetic) is kept apart from its effects (stores, tree, prediction)
+// so that it can be computed ahead of the pick and committed once the pick is
+// known; both ways run the same code.
+struct Upd {
+    int64_t i;  // -1: none
+    longlong2 h;
+    int2 g;
+    unsigned long long old, nk;
+    float lo;
+    double x;
+    int64_t r0, r1;  // island i's row, for the prediction
+};
+
+// Every load is issued before any result is needed so that they overlap.
+template <int PREC, bool KEEP>
+__device__ __forceinline__ Upd compute_update(const Inst& I, int64_t i, int snew, long long dp,
+                                              long long dq, int dp32, int dq32, uint32_t step) {
+    Upd u;
+    u.i = i;
     longlong2 h = I.h64[i];
     int2 g = make_int2(0, 0);
     if constexpr (PREC == 1) g = I.h32[i];
-    const unsigned long long old = I.key32[i];
+    u.old = I.key32[i];
     const int si = I.s[i];
     const uint16_t ci = __ldg(&I.cls[i]);
     const float2 rbc = __ldg(&I.rbc32[i]);
     float2 th = make_float2(0.0f, 0.0f);
     if (I.sigma > 0.0) th = I.th32[i];
-    int64_t r0 = 0, r1 = 0;
-    if constexpr (PF) {
-        r0 = __ldg(&I.rp[i]);
-        r1 = __ldg(&I.rp[i + 1]);
-    }
+    u.r0 = __ldg(&I.rp[i]);
+    u.r1 = __ldg(&I.rp[i + 1]);
     double hk = 0.0;
     double2 e64 = make_double2(0.0, 0.0);
     if constexpr (PREC == 0) {
@@ -369,19 +311,27 @@ __device__ __forceinline__ void update_island(const Inst& I, const Levels& L, Di
         g.x = (int)(snew > 0 ? (unsigned)g.x + vp : (unsigned)g.x - vp);
         g.y = (int)(snew > 0 ? (unsigned)g.y + vq : (unsigned)g.y - vq);
     }
-    float lo;
-    double x = 0.0;
-    const unsigned long long nk =
-        key_of<PREC>(I, i, step, si, ci, h, g, rbc, e32, th, hk, e64, &lo, &x);
-    I.h64[i] = h;
-    if constexpr (PREC == 1) I.h32[i] = g;
-    I.key64[i] = x;
-    I.key32[i] = nk;
-    I.lo32[i] = lo;
-    leaf_changed(I, L, D, i, old, nk);
-    if constexpr (PF) {
-        if (nk > pf_above) stage_candidate<PREC>(I, P, par, nk, r0, r1);
-    }
+    u.h = h;
+    u.g = g;
+    u.x = 0.0;
+    u.nk = key_of<PREC, KEEP>(I, i, step, si, ci, h, g, rbc, e32, th, hk, e64, &u.lo, &u.x);
+    return u;
+}
+
+// The update's effects: new sums, key, bounds and kept value; the tree told; and,
+// when the new key exceeds `pf_above` (the largest key the flip did not touch),
+// the island enters the prediction of the next pick.
+template <int PREC>
+__device__ __forceinline__ void commit_update(const Inst& I, const Levels& L, Dirty& D,
+                                              RowStage& P, int par, const Upd& u,
+                                              unsigned long long pf_above) {
+    I.h64[u.i] = u.h;
+    if constexpr (PREC == 1) I.h32[u.i] = u.g;
+    I.key64[u.i] = u.x;
+    I.key32[u.i] = u.nk;
+    I.lo32[u.i] = u.lo;
+    leaf_changed(I, L, D, u.i, u.old, u.nk);
+    if (u.nk > pf_above) stage_candidate<PREC>(I, P, par, u.nk, u.r0, u.r1);
 }
 
 // Exact FP64 value of island i (0 when not flippable): the value kept with its
@@ -601,19 +551,16 @@ constexpr int64_t kPickMaxFlips = -6;  // flip budget of the step spent
 // Warp 0: the island to flip next. Reads the root's island w and the largest other
 // key; takes w when its certified lower bound exceeds one and that key's upper
 // bound, else compares the contenders exactly. On return lane 0 holds the pick's
-// spin and row, and `ru` the largest key other than the pick's when it was
-// certified from bounds (all ones otherwise).
+// spin and row, `ru` the largest key other than the pick's when it was certified
+// from bounds (all ones otherwise), and `clean` whether no key changed on the way
+// (no exact comparison ran).
 template <int PREC>
 __device__ int64_t pick_warp(const Inst& I, const Levels& L, RecheckShared& R, Dirty& D,
                              InstState* st, uint32_t step, int* sk, int64_t* a0, int64_t* a1,
-                             unsigned long long* ru_out, float* tau_out) {
+                             unsigned long long* ru_out, float* tau_out, bool* clean) {
     const int lane = threadIdx.x & 31;
     *ru_out = ~0ull;
-    if (lane == 0) {  // the last repair has read its queues
-        D.n0 = 0;
-        for (int lev = 0; lev < kMaxLevels; ++lev) D.nup[lev] = 0;
-    }
-    __syncwarp();
+    *clean = true;
     for (int guard = 0; guard < 4 * kRecheckCap + 64; ++guard) {
         const unsigned long long root = L.p[I.nlev - 1][0];
         if (root == 0ull) return kPickNone;
@@ -645,6 +592,7 @@ __device__ int64_t pick_warp(const Inst& I, const Levels& L, RecheckShared& R, D
         int64_t k = -2;
         for (int rounds = 0; k == -2;) {
             if (++rounds > 64) return kPickBounds;
+            *clean = false;
             k = recheck_warp<PREC>(I, L, R, D, tau, step, sk, a0, a1);
             if (lane == 0) atomicAdd((unsigned long long*)&st->rechecks, 1ull);
             if (k == -2) tau = R.tau;
@@ -663,13 +611,16 @@ template <int PREC>
 __global__ void __launch_bounds__(kT, 1)
     k_relax(const Inst* __restrict__ tab, const int32_t* __restrict__ work, int n_work,
             int smem_levels) {
-    extern __shared__ __align__(16) unsigned long long sm_levels[];
+    extern __shared__ unsigned long long sm_levels[];
     __shared__ int64_t sh_k;
     __shared__ RowStage P;
     __shared__ int64_t sh_e0, sh_e1;
     __shared__ unsigned long long sh_ru;
     __shared__ int32_t sh_snew;
+    __shared__ int32_t sh_clean;
     __shared__ float sh_tau;
+    __shared__ int32_t sh_spec_snew[kNW];  // spin after the flip each speculating warp assumed
+    __shared__ int32_t sh_spec_len;
     __shared__ RecheckShared R;
     __shared__ Dirty D;
 
@@ -704,22 +655,19 @@ __global__ void __launch_bounds__(kT, 1)
             for (int64_t q = threadIdx.x; q < I.lvl_n[lev]; q += kT)
                 L.p[lev][q] = I.tree[I.lvl_off[lev] + q];
         if (threadIdx.x == 0) {
+            D.n0 = 0;
             P.best[0] = 0ull;
             P.best[1] = 0ull;
-            P.buf_id = -1;
-            P.buf_len = 0;
         }
     }
     __syncthreads();
-    // staged rows follow the levels' budget, 16-byte aligned
-    unsigned char* const bufs =
-        reinterpret_cast<unsigned char*>(sm_levels) + ((smem_levels + 15) & ~15);
 
     int64_t flips = 0;
     int32_t status = ST_OK;
     uint64_t hash = threadIdx.x == 0 ? st->hash : 0ull;
     const int64_t flips_before = threadIdx.x == 0 ? st->n_flips : 0;
     const int64_t max_flips = I.max_flips;
+    int par = 0;  // parity of the flip whose neighbour updates ran last
 
     // Thread 0: flip island k, log it, fold it into the hash, publish its row.
     auto do_flip = [&](int64_t k, int sk, int64_t a0, int64_t a1) {
@@ -737,13 +685,21 @@ __global__ void __launch_bounds__(kT, 1)
     };
 
     for (;;) {
-        // pick, and flip: warp 0
+        // Predicted next pick (from the last neighbour updates), read by every thread.
+        const unsigned long long pk = P.best[par];
+        const int64_t pred = pk != 0ull ? (int64_t)key32_idx(pk) : -1;
+        Upd spec;
+        spec.i = -1;
         if (wid == 0) {
+            // repair the tree, pick, and flip
+            repair_warp(I, L, D);
             int sk = 0;
             int64_t a0 = 0, a1 = 0;
             unsigned long long ru = ~0ull;
             float tau = 0.0f;
-            int64_t k = pick_warp<PREC>(I, L, R, D, st, step, &sk, &a0, &a1, &ru, &tau);
+            bool clean = true;
+            int64_t k =
+                pick_warp<PREC>(I, L, R, D, st, step, &sk, &a0, &a1, &ru, &tau, &clean);
             if (lane == 0) {
                 if (k >= 0) {
                     if (flips < max_flips)
@@ -754,6 +710,29 @@ __global__ void __launch_bounds__(kT, 1)
                 sh_k = k;
                 sh_ru = ru;
                 sh_tau = tau;
+                sh_clean = clean ? 1 : 0;
+                P.best[par ^ 1] = 0ull;  // the next updates' prediction
+            }
+        } else if (pred >= 0) {
+            // Meanwhile warps 1..7 compute the predicted flip's neighbour updates
+            // (loads and arithmetic only), one entry of its row per thread.
+            const int sp = I.s[pred];
+            const int64_t a0 = __ldg(&I.rp[pred]);
+            const int len = (int)(__ldg(&I.rp[pred + 1]) - a0);
+            if (lane == 0) sh_spec_snew[wid] = -sp;
+            if (threadIdx.x == 32) sh_spec_len = len;
+            const int q = threadIdx.x - 32;
+            if (len <= kT - 32 && q < len) {
+                const int64_t e = a0 + q;
+                const int32_t i = __ldg(&I.col[e]);
+                const long long dp = __ldg(&I.pq64[e].x), dq = __ldg(&I.qt64[e]);
+                int dp32 = 0, dq32 = 0;
+                if constexpr (PREC == 1) {
+                    dp32 = __ldg(&I.pq32[e].x);
+                    dq32 = __ldg(&I.qt32[e]);
+                }
+                if (i != (int32_t)pred)  // not row padding
+                    spec = compute_update<PREC, false>(I, i, -sp, dp, dq, dp32, dq32, step);
             }
         }
         __syncthreads();
@@ -782,6 +761,7 @@ __global__ void __launch_bounds__(kT, 1)
                         sh_k = kPickMaxFlips;
                     }
                     sh_ru = ~0ull;
+                    sh_clean = 0;
                 }
                 __syncthreads();
                 k = sh_k;
@@ -797,24 +777,15 @@ __global__ void __launch_bounds__(kT, 1)
         }
         if (k < 0) break;
         ++flips;
+        par ^= 1;
         // every neighbour i of k: add 2 s_k(new) (P_ik, Q_ik), new key, tree update
         const int snew = sh_snew;
-        const int par = (int)(flips & 1);
         const unsigned long long ru = sh_ru;
-        if (P.buf_id == (int32_t)k) {  // k's row was staged in shared memory
-            const RowBuf B = row_buf(bufs, I.row_cap, 0);
-            const int len = P.buf_len;
-            for (int q = threadIdx.x; q < len; q += kT) {
-                const int32_t i = B.col[q];
-                const long long dp = B.pq64[q].x, dq = B.qt64[q];
-                int dp32 = 0, dq32 = 0;
-                if constexpr (PREC == 1) {
-                    dp32 = B.pq32[q].x;
-                    dq32 = B.qt32[q];
-                }
-                if (i == (int32_t)k) continue;  // row padding
-                update_island<PREC, true>(I, L, D, P, par, i, snew, dp, dq, dp32, dq32, step, ru);
-            }
+        bool use_spec = k == pred && sh_clean != 0 && sh_spec_len <= kT - 32;
+#pragma unroll
+        for (int w = 1; w < kNW; ++w) use_spec = use_spec && sh_spec_snew[w] == snew;
+        if (use_spec) {
+            if (spec.i >= 0) commit_update<PREC>(I, L, D, P, par, spec, ru);
         } else {
             const int64_t e0 = sh_e0;
             const int len = (int)(sh_e1 - e0);
@@ -829,18 +800,22 @@ __global__ void __launch_bounds__(kT, 1)
                     dq32 = __ldg(&I.qt32[e]);
                 }
                 if (i == (int32_t)k) continue;  // row padding
-                update_island<PREC, true>(I, L, D, P, par, i, snew, dp, dq, dp32, dq32, step, ru);
+                const Upd u = compute_update<PREC, true>(I, i, snew, dp, dq, dp32, dq32, step);
+                commit_update<PREC>(I, L, D, P, par, u, ru);
             }
         }
-        if (threadIdx.x == kT - 1)  // k's own field is unchanged; its key is not
-            update_island<PREC, false>(I, L, D, P, par, k, snew, 0, 0, 0, 0, step, ~0ull);
-        if (threadIdx.x == kT - 2 && ru != ~0ull && ru != 0ull) {
+        // k's own field is unchanged; its key is not. Warp 0 holds no neighbour
+        // update on the speculative path; on the other, the last thread seldom does.
+        if (threadIdx.x == (use_spec ? 0 : kT - 1)) {
+            const Upd u = compute_update<PREC, true>(I, k, snew, 0, 0, 0, 0, step);
+            commit_update<PREC>(I, L, D, P, par, u, ~0ull);
+        }
+        if (threadIdx.x == (use_spec ? 1 : kT - 2) && ru != ~0ull && ru != 0ull) {
             // the runner-up is the next pick unless a neighbour rises above it
             const int64_t j = key32_idx(ru);
             stage_candidate<PREC>(I, P, par, ru, __ldg(&I.rp[j]), __ldg(&I.rp[j + 1]));
         }
         __syncthreads();
-        tree_phase<PREC>(I, L, D, P, bufs, par);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -919,20 +894,14 @@ cudaError_t prepare_relax(int prec, int smem) {
     return e;
 }
 
-int relax_smem_total(int levels, int row_cap) {
-    return ((levels + 15) & ~15) + kRowBufs * row_cap * kRowBufEntry;
-}
-
-// The launch's dynamic shared memory must hold the levels' budget (rounded up to
-// 16 bytes) and kRowBufs buffers of every simulation's row_cap entries.
 cudaError_t launch_relax(const RelaxLaunch& L, cudaStream_t st) {
     if (L.n_work == 0) return cudaSuccess;
-    const cudaError_t e = prepare_relax(L.prec, L.smem_total);
+    const cudaError_t e = prepare_relax(L.prec, L.smem_levels);
     if (e != cudaSuccess) return e;
     if (L.prec == 1)
-        k_relax<1><<<L.n_work, kT, L.smem_total, st>>>(L.tab, L.work, L.n_work, L.smem_levels);
+        k_relax<1><<<L.n_work, kT, L.smem_levels, st>>>(L.tab, L.work, L.n_work, L.smem_levels);
     else
-        k_relax<0><<<L.n_work, kT, L.smem_total, st>>>(L.tab, L.work, L.n_work, L.smem_levels);
+        k_relax<0><<<L.n_work, kT, L.smem_levels, st>>>(L.tab, L.work, L.n_work, L.smem_levels);
     return cudaGetLastError();
 }
 
