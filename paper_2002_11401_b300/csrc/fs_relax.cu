@@ -37,6 +37,7 @@ constexpr int kDirtyCap = kMaxPaddedDegree + 8;
 
 struct Levels {
     unsigned long long* p[kMaxLevels];
+    int first_sm;  // levels first_sm.. are in shared memory, those below in global
 };
 
 // Warp maximum of 64-bit keys (every lane gets it): the largest upper half, then
@@ -89,15 +90,21 @@ struct Dirty {
 };
 
 // A leaf's key went from `old` to `nk`: a larger key is pushed up with atomic
-// maxima on every ancestor; if the leaf held its first-level node's maximum and
-// shrank, that node is queued for a rebuild.
+// maxima on its ancestors, up to the first shared-memory one that already holds at
+// least nk (nodes only grow while leaves change, so a stale read costs at most one
+// more atomic; stopping early keeps most of the flip's keys off the few upper
+// nodes, where same-address atomics serialise); if the leaf held its first-level
+// node's maximum and shrank, that node is queued for a rebuild.
 __device__ __forceinline__ void leaf_changed(const Inst& I, const Levels& L, Dirty& D, int64_t i,
                                              unsigned long long old, unsigned long long nk) {
     if (nk > old) {
         int64_t node = i;
         for (int lev = 0; lev < I.nlev; ++lev) {
             node >>= 5;
-            atomicMax(&L.p[lev][node], nk);
+            unsigned long long* a = &L.p[lev][node];
+            // (a global node is not read first: the read would wait for L2)
+            if (lev >= L.first_sm && *(volatile unsigned long long*)a >= nk) break;
+            atomicMax(a, nk);
         }
     } else if (nk < old) {
         const int64_t node = i >> 5;
@@ -260,7 +267,7 @@ template <int PREC>
 __device__ __forceinline__ void stage_candidate(const Inst& I, RowStage& P, int par,
                                                 unsigned long long kj, int64_t a0, int64_t a1) {
     prefetch_row<PREC>(I, a0, a1);
-    atomicMax(&P.best[par], kj);
+    if (*(volatile unsigned long long*)&P.best[par] < kj) atomicMax(&P.best[par], kj);
 }
 
 // One neighbour update: island i's field changes by 2 s_new (dp, dq) (exact 64-bit
@@ -278,17 +285,19 @@ struct Upd {
     int64_t r0, r1;  // island i's row, for the prediction
 };
 
-// Every load is issued before any result is needed so that they overlap.
+// Every load is issued before any result is needed so that they overlap. `own`:
+// island i's spin when given (nonzero), else read from memory.
 template <int PREC, bool KEEP>
 __device__ __forceinline__ Upd compute_update(const Inst& I, int64_t i, int snew, long long dp,
-                                              long long dq, int dp32, int dq32, uint32_t step) {
+                                              long long dq, int dp32, int dq32, uint32_t step,
+                                              int own = 0) {
     Upd u;
     u.i = i;
     longlong2 h = I.h64[i];
     int2 g = make_int2(0, 0);
     if constexpr (PREC == 1) g = I.h32[i];
     u.old = I.key32[i];
-    const int si = I.s[i];
+    const int si = own != 0 ? own : I.s[i];
     const uint16_t ci = __ldg(&I.cls[i]);
     const float2 rbc = __ldg(&I.rbc32[i]);
     float2 th = make_float2(0.0f, 0.0f);
@@ -642,6 +651,7 @@ __global__ void __launch_bounds__(kT, 1)
             used += b;
             first_sm = lev;
         }
+        L.first_sm = first_sm;
         int64_t off = 0;
         for (int lev = I.nlev - 1; lev >= 0; --lev) {
             if (lev >= first_sm) {
@@ -722,7 +732,7 @@ __global__ void __launch_bounds__(kT, 1)
             if (lane == 0) sh_spec_snew[wid] = -sp;
             if (threadIdx.x == 32) sh_spec_len = len;
             const int q = threadIdx.x - 32;
-            if (len <= kT - 32 && q < len) {
+            if (len < kT - 32 && q < len) {
                 const int64_t e = a0 + q;
                 const int32_t i = __ldg(&I.col[e]);
                 const long long dp = __ldg(&I.pq64[e].x), dq = __ldg(&I.qt64[e]);
@@ -733,6 +743,9 @@ __global__ void __launch_bounds__(kT, 1)
                 }
                 if (i != (int32_t)pred)  // not row padding
                     spec = compute_update<PREC, false>(I, i, -sp, dp, dq, dp32, dq32, step);
+            } else if (len < kT - 32 && q == len) {
+                // the predicted island itself: its field unchanged, its spin flipped
+                spec = compute_update<PREC, false>(I, pred, -sp, 0, 0, 0, 0, step, -sp);
             }
         }
         __syncthreads();
@@ -781,11 +794,11 @@ __global__ void __launch_bounds__(kT, 1)
         // every neighbour i of k: add 2 s_k(new) (P_ik, Q_ik), new key, tree update
         const int snew = sh_snew;
         const unsigned long long ru = sh_ru;
-        bool use_spec = k == pred && sh_clean != 0 && sh_spec_len <= kT - 32;
+        bool use_spec = k == pred && sh_clean != 0 && sh_spec_len < kT - 32;
 #pragma unroll
         for (int w = 1; w < kNW; ++w) use_spec = use_spec && sh_spec_snew[w] == snew;
         if (use_spec) {
-            if (spec.i >= 0) commit_update<PREC>(I, L, D, P, par, spec, ru);
+            if (spec.i >= 0) commit_update<PREC>(I, L, D, P, par, spec, spec.i == k ? ~0ull : ru);
         } else {
             const int64_t e0 = sh_e0;
             const int len = (int)(sh_e1 - e0);
@@ -804,17 +817,14 @@ __global__ void __launch_bounds__(kT, 1)
                 commit_update<PREC>(I, L, D, P, par, u, ru);
             }
         }
-        // k's own field is unchanged; its key is not. Warp 0 holds no neighbour
-        // update on the speculative path; on the other, the last thread seldom does.
-        if (threadIdx.x == (use_spec ? 0 : kT - 1)) {
+        // k's own field is unchanged; its key is not (already computed ahead on the
+        // speculative path; on the other, the last thread seldom holds an entry).
+        if (!use_spec && threadIdx.x == kT - 1) {
             const Upd u = compute_update<PREC, true>(I, k, snew, 0, 0, 0, 0, step);
             commit_update<PREC>(I, L, D, P, par, u, ~0ull);
         }
-        if (threadIdx.x == (use_spec ? 1 : kT - 2) && ru != ~0ull && ru != 0ull) {
-            // the runner-up is the next pick unless a neighbour rises above it
-            const int64_t j = key32_idx(ru);
-            stage_candidate<PREC>(I, P, par, ru, __ldg(&I.rp[j]), __ldg(&I.rp[j + 1]));
-        }
+        // the runner-up is the next pick unless a neighbour rises above it
+        if (threadIdx.x == 0 && ru != ~0ull && ru != 0ull) atomicMax(&P.best[par], ru);
         __syncthreads();
     }
     __syncthreads();
