@@ -102,9 +102,15 @@ __device__ __forceinline__ void leaf_changed(const Inst& I, const Levels& L, Dir
         for (int lev = 0; lev < I.nlev; ++lev) {
             node >>= 5;
             unsigned long long* a = &L.p[lev][node];
-            // (a global node is not read first: the read would wait for L2)
-            if (lev >= L.first_sm && *(volatile unsigned long long*)a >= nk) break;
-            atomicMax(a, nk);
+            if (lev >= L.first_sm) {  // shared-memory instructions, not generic ones
+                const unsigned sa = (unsigned)__cvta_generic_to_shared(a);
+                unsigned long long cur;
+                asm volatile("ld.volatile.shared.u64 %0, [%1];" : "=l"(cur) : "r"(sa));
+                if (cur >= nk) break;
+                asm volatile("red.shared.max.u64 [%0], %1;" ::"r"(sa), "l"(nk) : "memory");
+            } else {  // (not read first: the read would wait for L2)
+                atomicMax(a, nk);
+            }
         }
     } else if (nk < old) {
         const int64_t node = i >> 5;
@@ -245,20 +251,15 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* p, uint32_t n) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(n) : "memory");
 }
 
-// Row [a0, a1) of the neighbour tensors that a flip of its island reads. Rows
-// start and end on multiples of 4 entries, so every array's range is 16-byte
-// aligned with a length that is a multiple of 16 bytes.
+// Column indices of row [a0, a1), which a flip of its island reads first. Rows
+// start and end on multiples of 4 entries, so the range is 16-byte aligned with a
+// length that is a multiple of 16 bytes. (The coefficient arrays are left to the
+// speculating warps' own loads: asking for all five arrays queues five bulk
+// requests per candidate on the flip's critical path, which measured slower.)
 template <int PREC>
 __device__ __forceinline__ void prefetch_row(const Inst& I, int64_t a0, int64_t a1) {
     const uint32_t m = (uint32_t)(a1 - a0);
-    if (m == 0u) return;
-    bulk_prefetch_l2(I.col + a0, 4u * m);
-    bulk_prefetch_l2(I.pq64 + a0, 16u * m);
-    bulk_prefetch_l2(I.qt64 + a0, 8u * m);
-    if constexpr (PREC == 1) {
-        bulk_prefetch_l2(I.pq32 + a0, 8u * m);
-        bulk_prefetch_l2(I.qt32 + a0, 4u * m);
-    }
+    if (m != 0u) bulk_prefetch_l2(I.col + a0, 4u * m);
 }
 
 // Island j (key kj), whose row is [a0, a1), may be the next pick: its row is
