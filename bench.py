@@ -256,10 +256,12 @@ def main():
     n, nnz = info.n, info.nnz
     avg_deg = nnz / n
     fp32 = prec == B.FS_FP32_RECHECK
-    # per flip: every neighbour's CSR entry (column, P and transposed Q in both
-    # widths on the FP32 path), its state read-modify-write, and its new key
-    per_nb = (4 + 4 + 4 + 8 + 8 + 16 + 32 + 1 + 2 + 4 + 8 + 4) if fp32 else \
-             (4 + 8 + 8 + 32 + 1 + 2 + 4 + 8 + 8)
+    # per flip and neighbour: the row entry (column, P and transposed Q; both
+    # widths on the FP32 path), the neighbour's state read (exact sums, 32-bit sums,
+    # key, spin, angle class, 1/(b h_k) and 1/(c h_k) or h_k, row pointers for the
+    # next-pick prediction) and written back (sums, key, lower bound, exact value)
+    per_nb = (4 + 4 + 4 + 8 + 8) + (16 + 8 + 8 + 1 + 2 + 8 + 16) + (16 + 8 + 8 + 8 + 4) \
+        if fp32 else (4 + 8 + 8) + (16 + 8 + 1 + 2 + 8 + 8 + 16) + (16 + 8 + 8 + 4)
     relax_bytes = flips_per_protocol * avg_deg * per_nb * args.steps
     relax_s = prof["relax_ms"] / 1000.0
     # per sweep: row pointers, every entry's column and (P, Q), and per island the
