@@ -43,6 +43,19 @@ def workload_desc(w, prec_name, resweep):
             f"{prec_name}, {'full dipolar resweep every field step' if resweep else 'exact incremental sums'}")
 
 
+def sweep_bytes(n: int, nnz: int, fp32: bool, resweep: bool, thermal: bool) -> int:
+    """Algorithmic bytes of one field-and-margin sweep. Per pair: the column index
+    and the (P, Q) coefficients of the path's width (4 + 8 or 4 + 16); per row: its
+    pointer (8). Per island: spin, angle class, 1/(b h_k) and 1/(c h_k) read
+    (1 + 2 + 8); the sums of the path's width written (or, without the resweep,
+    read: 8 or 16); key, lower bound and exact value written (8 + 4 + 8); with
+    thermal noise, the step's FP32 draw written (8)."""
+    per_island = 1 + 2 + 8 + (8 if fp32 else 16) + 8 + 4 + 8 + (8 if thermal else 0)
+    if not resweep:
+        return n * per_island
+    return (12 if fp32 else 20) * nnz + 8 * (n + 1) + n * per_island
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -264,13 +277,7 @@ def main():
         if fp32 else (4 + 8 + 8) + (16 + 8 + 1 + 2 + 8 + 8 + 16) + (16 + 8 + 8 + 4)
     relax_bytes = flips_per_protocol * avg_deg * per_nb * args.steps
     relax_s = prof["relax_ms"] / 1000.0
-    # per sweep: row pointers, every entry's column and (P, Q), and per island the
-    # gathered spin, angle class, h_k, the new sums, key (and lo bound)
-    if args.resweep:
-        sweep_unit = (12 * nnz + 8 * (n + 1) + n * (1 + 2 + 4 + 8 + 8 + 4)) if fp32 else \
-                     (20 * nnz + 8 * (n + 1) + n * (1 + 2 + 4 + 16 + 8))
-    else:
-        sweep_unit = n * (1 + 2 + 4 + 8 + 8 + 4) if fp32 else n * (1 + 2 + 4 + 16 + 8)
+    sweep_unit = sweep_bytes(n, nnz, fp32, bool(args.resweep), w["sigma_th"] > 0)
     sweep_s = prof["sweep_ms"] / 1000.0
     n_sweeps = max(prof["sweep_launches"], 1)
     relax_launch_ms = prof["relax_ms"] / max(prof["relax_launches"], 1)

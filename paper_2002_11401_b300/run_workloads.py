@@ -40,12 +40,15 @@ def make_sim(w, precision):
     return sim
 
 
-def sweep_bytes(info, fp32: bool, resweep: bool) -> int:
-    """Algorithmic bytes of one field-and-margin sweep: row pointers, every entry's
-    column and (P, Q), per island the spin, angle class, scales, new sums, key and
-    bound (FP32 path) or exact value (FP64 path)."""
+def sweep_bytes(info, fp32: bool, resweep: bool, thermal: bool) -> int:
+    """Algorithmic bytes of one field-and-margin sweep. Per pair: the column index
+    and the (P, Q) coefficients of the path's width (4 + 8 or 4 + 16); per row: its
+    pointer (8). Per island: spin, angle class, 1/(b h_k) and 1/(c h_k) read
+    (1 + 2 + 8); the sums of the path's width written (or, without the resweep,
+    read: 8 or 16); key, lower bound and exact value written (8 + 4 + 8); with
+    thermal noise, the step's FP32 draw written (8)."""
     n, nnz = info.n, info.nnz
-    per_island = (1 + 2 + 8 + 8 + 8 + 4) if fp32 else (1 + 2 + 8 + 16 + 8 + 4 + 8)
+    per_island = 1 + 2 + 8 + (8 if fp32 else 16) + 8 + 4 + 8 + (8 if thermal else 0)
     if not resweep:
         return n * per_island
     return (12 if fp32 else 20) * nnz + 8 * (n + 1) + n * per_island
@@ -72,7 +75,7 @@ def run_single(name, precision, steps, resweep, cells=0):
     info = sim.info()
     peak, kind = _peak()
     sw_ms = prof["sweep_ms"] / max(prof["sweep_launches"], 1)
-    sb = sweep_bytes(info, fp32, resweep)
+    sb = sweep_bytes(info, fp32, resweep, w["sigma_th"] > 0)
     return {"workload": name, "precision": "fp32+fp64-recheck" if fp32 else "fp64",
             "islands": info.n, "neighbour_pairs": info.nnz, "field_steps": len(hx),
             "resweep": bool(resweep), "build_s": build_s, "lanes_per_row": lanes,
