@@ -257,7 +257,9 @@ fs_status fs_batch_run_protocol(fs_sim* const* sims, int32_t n, const double* hx
  * budget and build them on side streams; every admitted request then gets a
  * stream of its own with its whole protocol queued, so requests that arrive while
  * others run start as soon as they are built and all of them overlap on the
- * device. Results equal those of running each request alone. */
+ * device. Admission order: a request waiting longer than 10 s first (oldest
+ * first), else the least estimated work (islands x field steps). Results equal
+ * those of running each request alone. */
 typedef struct fs_server fs_server;
 
 typedef struct {

@@ -58,19 +58,25 @@ struct Job {
 // and, per neighbour pair, the CSR entry and both coefficient widths with their
 // transposed copies (40 B); the degree is the cutoff disc's area times the array's
 // island density, plus a margin for the rounding of the rows to multiples of 4.
+double islands_of(const fs_request& r) {
+    return r.kind == FS_KAGOME ? 3.0 * r.nx * r.ny + 2.0 * r.nx + 2.0 * r.ny
+                               : 2.0 * r.nx * r.ny + r.nx + r.ny;
+}
+
 size_t estimate_bytes(const fs_request& r) {
     const double rc = r.params.cutoff;
-    double n, density;
-    if (r.kind == FS_KAGOME) {
-        n = 3.0 * r.nx * r.ny + 2.0 * r.nx + 2.0 * r.ny;
-        density = 3.0 / (1.5 * std::sqrt(3.0));
-    } else {
-        n = 2.0 * r.nx * r.ny + r.nx + r.ny;
-        density = 2.0;
-    }
+    const double n = islands_of(r);
+    const double density = r.kind == FS_KAGOME ? 3.0 / (1.5 * std::sqrt(3.0)) : 2.0;
     const double deg = 1.05 * M_PI * rc * rc * density + 8.0;
     return (size_t)(n * (deg * 40.0 + 128.0) + 16.0 * r.K + (1 << 20));
 }
+
+// Admission order: a request that has waited longer than kAgeS goes first (oldest
+// first), else the one with the least estimated work (islands x field steps), so
+// that short requests are not queued behind long ones and long ones still start.
+constexpr double kAgeS = 10.0;
+
+double work_of(const fs_request& r) { return islands_of(r) * (double)std::max<int64_t>(r.K, 1); }
 
 }  // namespace
 
@@ -110,6 +116,18 @@ void finish(fs_server* S, const std::shared_ptr<Job>& j, int32_t status) {
     S->cv_done.notify_all();
 }
 
+// The pending request to admit next (index into S->pending; call with S->mu held).
+size_t next_pending(const fs_server* S) {
+    const double now = S->now();
+    size_t best = 0;
+    for (size_t q = 0; q < S->pending.size(); ++q) {
+        const Job& j = *S->pending[q];
+        if (now - j.res.t_submit > kAgeS) return q;  // the oldest aged request
+        if (work_of(j.req) < work_of(S->pending[best]->req)) best = q;
+    }
+    return best;
+}
+
 void builder_loop(fs_server* S, int which) {
     cudaSetDevice(S->device);
     cudaStream_t bst = S->build_st[(size_t)which];
@@ -117,16 +135,22 @@ void builder_loop(fs_server* S, int which) {
         std::shared_ptr<Job> j;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            S->cv_build.wait(lk, [&] {
+            size_t pick = 0;
+            S->cv_build.wait_for(lk, std::chrono::milliseconds(100), [&] {
                 if (S->stop) return true;
                 if (S->pending.empty()) return false;
-                const size_t need = estimate_bytes(S->pending.front()->req);
+                pick = next_pending(S);
+                const size_t need = estimate_bytes(S->pending[pick]->req);
                 // admit when it fits, or when nothing else holds memory
                 return S->used.load() + need <= S->budget || S->used.load() == 0;
             });
             if (S->stop) return;
-            j = S->pending.front();
-            S->pending.pop_front();
+            if (S->pending.empty()) continue;
+            pick = next_pending(S);
+            const size_t need = estimate_bytes(S->pending[pick]->req);
+            if (!(S->used.load() + need <= S->budget || S->used.load() == 0)) continue;
+            j = S->pending[pick];
+            S->pending.erase(S->pending.begin() + (std::ptrdiff_t)pick);
             j->reserved = estimate_bytes(j->req);
             S->used += j->reserved;
         }
@@ -348,7 +372,7 @@ extern "C" fs_status fs_server_create(size_t hbm_budget, int32_t max_active, fs_
         delete S;
         return FS_ERR_CUDA;
     }
-    const int nb = 4;  // builder threads, each with its own stream
+    const int nb = 8;  // builder threads, each with its own stream
     S->build_st.resize(nb, nullptr);
     bool ok = cudaStreamCreateWithFlags(&S->main_st, cudaStreamNonBlocking) == cudaSuccess;
     for (int b = 0; b < nb && ok; ++b)

@@ -193,11 +193,13 @@ __global__ void __launch_bounds__(kSweepThreads, OCC)
             float lo = e.certain ? e.lo : -1.0f;
             node = e.possible ? key32_of(e.hi, i) : 0ull;
             double x = e.possible ? -1.0 : 0.0;
+            // An island that may be flippable may meet an exact comparison in the
+            // relax: its FP64 thermal draw is taken and kept here, off the flip chain.
+            double tp = 0.0, tq = 0.0;
+            if (I.sigma > 0.0 && e.possible) thermal64_kept(I, i, step, &tp, &tq);
             if (e.possible && !e.certain) {
                 // within its band of the threshold or of the sign change: FP64 now
                 if (!SUM64) h64 = I.h64[i];
-                double tp = 0.0, tq = 0.0;
-                if (I.sigma > 0.0) thermal64_kept(I, i, step, &tp, &tq);
                 const Eval64 f = eval64(I, si, h64.x, h64.y, I.hk64[i], I.ext64[ci], tp, tq);
                 x = f.flippable ? f.lhs : 0.0;
                 node = x > 0.0 ? key32_of(__double2float_ru(x), i) : 0ull;
