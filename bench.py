@@ -56,6 +56,27 @@ def sweep_bytes(n: int, nnz: int, fp32: bool, resweep: bool, thermal: bool) -> i
     return (12 if fp32 else 20) * nnz + 8 * (n + 1) + n * per_island
 
 
+# DRAM bytes per launch (read + write) of the dominant kernels on this workload, from
+# one ncu capture of every launch of one protocol (profiles/traffic_pinwheel300.md),
+# with a hash of the kernel sources that were profiled: a changed kernel reports null.
+TRAFFIC = {
+    "k_relax": {"bytes_per_launch": 2.149e6, "sources": ("fs_relax.cu", "fs_common.cuh"),
+                "sha256_16": "2c590c0a931b5b89"},
+    "k_sweep": {"bytes_per_launch": 360.674e6, "sources": ("fs_sweep.cu", "fs_common.cuh"),
+                "sha256_16": "46c2962bc6f1236b"},
+}
+
+
+def traffic_of(kernel: str):
+    import hashlib
+    t = TRAFFIC[kernel]
+    m = hashlib.sha256()
+    for name in t["sources"]:
+        with open(os.path.join(ROOT, "paper_2002_11401_b300", "csrc", name), "rb") as f:
+            m.update(f.read())
+    return t["bytes_per_launch"] if m.hexdigest()[:16] == t["sha256_16"] else None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -258,6 +279,9 @@ def main():
     sim.set_profiling(False)
     out1 = d_out.cpu().tolist()
     assert int(out1[0]) == 0, f"protocol status {out1[0]}"
+    if args.warmup <= 0:  # nothing to compare with: the timed steps define the figures
+        flips_per_protocol = int(out1[1])
+        hash0 = int(out1[2]) & 0xFFFFFFFFFFFFFFFF
     assert int(out1[1]) == flips_per_protocol and (int(out1[2]) & 0xFFFFFFFFFFFFFFFF) == hash0, \
         "timed steps diverged from the warm-up steps"
     ms, units = aggregate(ms, flips_per_protocol * args.steps, dist, device="cuda")
@@ -286,16 +310,20 @@ def main():
                   "achieved": relax_bytes / relax_s / 1e9 if relax_s > 0 else 0.0,
                   "peak": peak, "unit": "GB/s",
                   "frac": (relax_bytes / relax_s / 1e9) / peak if relax_s > 0 else 0.0,
-                  "traffic": None, "peak_kind": peak_kind,
+                  "traffic": traffic_of("k_relax") if fp32 and args.resweep else None,
+                  "peak_kind": peak_kind,
                   "avg_launch_ms": relax_launch_ms,
                   "share_of_step": prof["relax_ms"] / ms if ms > 0 else None,
+                  "bytes_per_launch": relax_bytes / max(prof["relax_launches"], 1),
                   "note": "serial flip chain: latency-bound; bytes per flip = "
-                          f"{avg_deg:.1f} neighbours x {per_nb} B"}
+                          f"{avg_deg:.1f} neighbours x {per_nb} B; traffic below them "
+                          "means L2 hits"}
     roof_sweep = {"kernel": "k_sweep", "bound": "hbm",
                   "achieved": sweep_unit / (sweep_launch_ms / 1000.0) / 1e9,
                   "peak": peak, "unit": "GB/s",
                   "frac": sweep_unit / (sweep_launch_ms / 1000.0) / 1e9 / peak,
-                  "traffic": None, "peak_kind": peak_kind, "avg_launch_ms": sweep_launch_ms,
+                  "traffic": traffic_of("k_sweep") if fp32 and args.resweep else None,
+                  "peak_kind": peak_kind, "avg_launch_ms": sweep_launch_ms,
                   "bytes_per_launch": sweep_unit,
                   "share_of_step": prof["sweep_ms"] / ms if ms > 0 else None}
 
