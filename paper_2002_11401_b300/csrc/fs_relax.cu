@@ -35,10 +35,29 @@ constexpr int kT = 256;  // threads per relax CTA
 constexpr int kNW = kT / 32;
 constexpr int kDirtyCap = kMaxPaddedDegree + 8;
 
+// The tree's levels above the leaves. Held in registers: every access goes through
+// lp()/ln(), which select with compile-time indices (a run-time index into these
+// arrays would put them in local memory, one more dependent load per level step).
 struct Levels {
-    unsigned long long* p[kMaxLevels];
+    unsigned long long* p[kMaxLevels];  // base of each level
+    int32_t n[kMaxLevels];              // nodes per level
+    int nlev;
     int first_sm;  // levels first_sm.. are in shared memory, those below in global
 };
+
+__device__ __forceinline__ unsigned long long* lp(const Levels& L, int lev) {
+    unsigned long long* r = L.p[0];
+#pragma unroll
+    for (int q = 1; q < kMaxLevels; ++q) r = lev == q ? L.p[q] : r;
+    return r;
+}
+
+__device__ __forceinline__ int64_t ln(const Levels& L, int lev) {
+    int32_t r = L.n[0];
+#pragma unroll
+    for (int q = 1; q < kMaxLevels; ++q) r = lev == q ? L.n[q] : r;
+    return r;
+}
 
 // Warp maximum of 64-bit keys (every lane gets it): the largest upper half, then
 // among those the largest lower half.
@@ -57,8 +76,8 @@ __device__ __forceinline__ unsigned long long warp_node(const Inst& I, const Lev
     unsigned long long v = 0ull;
     if (lev == 0) {
         if (c < I.n) v = I.key32[c];
-    } else if (c < I.lvl_n[lev - 1]) {
-        v = L.p[lev - 1][c];
+    } else if (c < ln(L, lev - 1)) {
+        v = lp(L, lev - 1)[c];
     }
     return warp_max_key(v);
 }
@@ -72,11 +91,11 @@ __device__ unsigned long long runner_up(const Inst& I, const Levels& L, int64_t 
         const int64_t c = ((w >> 5) << 5) + lane;
         if (c != w && c < I.n) m = I.key32[c];
     }
-    for (int lev = 1; lev < I.nlev; ++lev) {
+    for (int lev = 1; lev < L.nlev; ++lev) {
         const int64_t anc = w >> (5 * lev);
         const int64_t c = ((anc >> 5) << 5) + lane;
-        if (c != anc && c < I.lvl_n[lev - 1]) {
-            const unsigned long long v = L.p[lev - 1][c];
+        if (c != anc && c < ln(L, lev - 1)) {
+            const unsigned long long v = lp(L, lev - 1)[c];
             m = v > m ? v : m;
         }
     }
@@ -99,9 +118,9 @@ __device__ __forceinline__ void leaf_changed(const Inst& I, const Levels& L, Dir
                                              unsigned long long old, unsigned long long nk) {
     if (nk > old) {
         int64_t node = i;
-        for (int lev = 0; lev < I.nlev; ++lev) {
+        for (int lev = 0; lev < L.nlev; ++lev) {
             node >>= 5;
-            unsigned long long* a = &L.p[lev][node];
+            unsigned long long* a = lp(L, lev) + node;
             if (lev >= L.first_sm) {  // shared-memory instructions, not generic ones
                 const unsigned sa = (unsigned)__cvta_generic_to_shared(a);
                 unsigned long long cur;
@@ -114,7 +133,7 @@ __device__ __forceinline__ void leaf_changed(const Inst& I, const Levels& L, Dir
         }
     } else if (nk < old) {
         const int64_t node = i >> 5;
-        if (L.p[0][node] == old) {
+        if (lp(L, 0)[node] == old) {
             const int q = atomicAdd(&D.n0, 1);
             if (q < kDirtyCap) D.lv0[q] = (int32_t)node;
         }
@@ -152,10 +171,10 @@ __device__ void repair_warp(const Inst& I, const Levels& L, Dirty& D) {
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             if (node[u] < 0) break;
-            const unsigned long long old = L.p[0][node[u]];
+            const unsigned long long old = lp(L, 0)[node[u]];
             const unsigned long long nv = warp_max_key(v[u]);
-            if (lane == 0) L.p[0][node[u]] = nv;
-            if (nv < old && I.nlev > 1 && L.p[1][node[u] >> 5] == old) {
+            if (lane == 0) lp(L, 0)[node[u]] = nv;
+            if (nv < old && L.nlev > 1 && lp(L, 1)[node[u] >> 5] == old) {
                 if (lane == 0 && nout < kDirtyCap) qout[nout] = (int32_t)(node[u] >> 5);
                 ++nout;
             }
@@ -164,18 +183,18 @@ __device__ void repair_warp(const Inst& I, const Levels& L, Dirty& D) {
     }
     int nn = min(nout, kDirtyCap);
     __syncwarp();
-    for (int lev = 1; lev < I.nlev && nn > 0; ++lev) {
+    for (int lev = 1; lev < L.nlev && nn > 0; ++lev) {
         const int32_t* qin = D.up[lev & 1];
         qout = D.up[(lev + 1) & 1];
-        const int64_t nchild = I.lvl_n[lev - 1];
+        const int64_t nchild = ln(L, lev - 1);
         nout = 0;
         for (int q = 0; q < nn; ++q) {
             const int64_t node = qin[q];
-            const unsigned long long old = L.p[lev][node];
+            const unsigned long long old = lp(L, lev)[node];
             const int64_t c = (node << 5) + lane;
-            const unsigned long long nv = warp_max_key(c < nchild ? L.p[lev - 1][c] : 0ull);
-            if (lane == 0) L.p[lev][node] = nv;
-            if (nv < old && lev + 1 < I.nlev && L.p[lev + 1][node >> 5] == old) {
+            const unsigned long long nv = warp_max_key(c < nchild ? lp(L, lev - 1)[c] : 0ull);
+            if (lane == 0) lp(L, lev)[node] = nv;
+            if (nv < old && lev + 1 < L.nlev && lp(L, lev + 1)[node >> 5] == old) {
                 if (lane == 0 && nout < kDirtyCap) qout[nout] = (int32_t)(node >> 5);
                 ++nout;
             }
@@ -190,10 +209,10 @@ __device__ void repair_warp(const Inst& I, const Levels& L, Dirty& D) {
 // Whole tree from the leaves (after a full rescan).
 __device__ void rebuild_tree(const Inst& I, const Levels& L) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int lev = 0; lev < I.nlev; ++lev) {
-        for (int64_t node = wid; node < I.lvl_n[lev]; node += kNW) {
+    for (int lev = 0; lev < L.nlev; ++lev) {
+        for (int64_t node = wid; node < ln(L, lev); node += kNW) {
             const unsigned long long v = warp_node(I, L, lev, node);
-            if (lane == 0) L.p[lev][node] = v;
+            if (lane == 0) lp(L, lev)[node] = v;
         }
         __syncthreads();
     }
@@ -379,10 +398,10 @@ struct RecheckShared {
 // Rebuilds every node on island w's path to the root from its children. Warp-wide.
 __device__ void rebuild_path(const Inst& I, const Levels& L, int64_t w) {
     int64_t node = w;
-    for (int lev = 0; lev < I.nlev; ++lev) {
+    for (int lev = 0; lev < L.nlev; ++lev) {
         node >>= 5;
         const unsigned long long v = warp_node(I, L, lev, node);
-        if ((threadIdx.x & 31) == 0) L.p[lev][node] = v;
+        if ((threadIdx.x & 31) == 0) lp(L, lev)[node] = v;
         __syncwarp();
     }
 }
@@ -407,9 +426,9 @@ __device__ int64_t recheck_warp(const Inst& I, const Levels& L, RecheckShared& R
     if (lane == 0) R.front[0][0] = 0;
     __syncwarp();
     int cur = 0, nf = 1;
-    for (int lev = I.nlev - 1; lev >= 0; --lev) {
-        const unsigned long long* src = lev > 0 ? L.p[lev - 1] : I.key32;
-        const int64_t lim = lev > 0 ? (int64_t)I.lvl_n[lev - 1] : I.n;
+    for (int lev = L.nlev - 1; lev >= 0; --lev) {
+        const unsigned long long* src = lev > 0 ? lp(L, lev - 1) : I.key32;
+        const int64_t lim = lev > 0 ? ln(L, lev - 1) : I.n;
         int nn = 0;
         for (int f0 = 0; f0 < nf; f0 += kBatch) {
             unsigned long long k[kBatch];
@@ -461,7 +480,7 @@ __device__ int64_t recheck_warp(const Inst& I, const Levels& L, RecheckShared& R
         I.key32[i] = nk;
         I.lo32[i] = v > 0.0 ? __double2float_rd(v) : -1.0f;
         R.new_key[c] = nk;
-        if (nk < old && L.p[0][i >> 5] == old) {
+        if (nk < old && lp(L, 0)[i >> 5] == old) {
             const int q = atomicAdd(&D.n0, 1);
             if (q < kDirtyCap) D.lv0[q] = (int32_t)(i >> 5);
         }
@@ -495,11 +514,11 @@ __device__ int64_t recheck_warp(const Inst& I, const Levels& L, RecheckShared& R
         const unsigned long long old = R.leaf_key[c];
         if (R.new_key[c] >= old) continue;
         int64_t node = (int64_t)R.front[cur][c];
-        for (int lev = 0; lev < I.nlev; ++lev) {
+        for (int lev = 0; lev < L.nlev; ++lev) {
             node >>= 5;
-            if (L.p[lev][node] != old) break;
+            if (lp(L, lev)[node] != old) break;
             const unsigned long long nv = warp_node(I, L, lev, node);
-            if (lane == 0) L.p[lev][node] = nv;
+            if (lane == 0) lp(L, lev)[node] = nv;
             __syncwarp();
         }
     }
@@ -572,7 +591,7 @@ __device__ int64_t pick_warp(const Inst& I, const Levels& L, RecheckShared& R, D
     *ru_out = ~0ull;
     *clean = true;
     for (int guard = 0; guard < 4 * kRecheckCap + 64; ++guard) {
-        const unsigned long long root = L.p[I.nlev - 1][0];
+        const unsigned long long root = lp(L, L.nlev - 1)[0];
         if (root == 0ull) return kPickNone;
         const int64_t w = key32_idx(root);
         unsigned long long kw = 0ull;
@@ -653,18 +672,22 @@ __global__ void __launch_bounds__(kT, 1)
             first_sm = lev;
         }
         L.first_sm = first_sm;
+        L.nlev = I.nlev;
+        // (static indices only: the descriptor stays in registers)
         int64_t off = 0;
-        for (int lev = I.nlev - 1; lev >= 0; --lev) {
-            if (lev >= first_sm) {
+#pragma unroll
+        for (int lev = kMaxLevels - 1; lev >= 0; --lev) {
+            L.n[lev] = lev < I.nlev ? I.lvl_n[lev] : 0;
+            if (lev < I.nlev && lev >= first_sm) {
                 L.p[lev] = sm_levels + off;
                 off += I.lvl_n[lev];
             } else {
-                L.p[lev] = I.tree + I.lvl_off[lev];
+                L.p[lev] = lev < I.nlev ? I.tree + I.lvl_off[lev] : nullptr;
             }
         }
-        for (int lev = first_sm; lev < I.nlev; ++lev)
-            for (int64_t q = threadIdx.x; q < I.lvl_n[lev]; q += kT)
-                L.p[lev][q] = I.tree[I.lvl_off[lev] + q];
+        for (int lev = first_sm; lev < L.nlev; ++lev)
+            for (int64_t q = threadIdx.x; q < ln(L, lev); q += kT)
+                lp(L, lev)[q] = I.tree[I.lvl_off[lev] + q];
         if (threadIdx.x == 0) {
             D.n0 = 0;
             P.best[0] = 0ull;

@@ -1,8 +1,10 @@
 """Writes the stored expected values under tests/golden/ from the FP64 oracle
 alone (no library code): the square16 protocol in full, and prefixes of the
-pinwheel, kagome and ensemble workloads at their full sizes.
+pinwheel, kagome and ensemble workloads at their full sizes. With --full, the
+whole pinwheel 300x300 and kagome 1000x1000 protocols instead (flip counts per
+step and the sequence hash; minutes to tens of minutes on a few cores).
 
-    python tests/golden/make_golden.py [--threads N]
+    python tests/golden/make_golden.py [--threads N] [--full pinwheel300,kagome1000]
 """
 import argparse
 import json
@@ -51,9 +53,16 @@ def record(name, w, hx, hy, keep_log):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--threads", type=int, default=os.cpu_count() or 1)
+    ap.add_argument("--full", default="", help="comma-separated workloads to record in full")
     a = ap.parse_args()
     O.build()
     O.set_threads(a.threads)
+    if a.full:
+        for name in a.full.split(","):
+            w = I.WORKLOADS[name]
+            hx, hy = I.protocol_of(w["protocol"])
+            record(f"{name}_full", w, hx, hy, keep_log=0)
+        return
     w = I.WORKLOADS["square16"]
     hx, hy = I.protocol_of(w["protocol"])
     record("square16", w, hx, hy, keep_log=10_000)
