@@ -65,8 +65,9 @@ def test_kagome1000_prefix_matches_oracle(B, prec):
 
 def test_pinwheel300_full_protocol_invariants_and_fields(B, oracle):
     # the whole 1000-step protocol on both paths, with and without the resweep:
-    # one sequence; the final state is saturated along +0.25 T at 30 degrees; the
-    # fields at the final state agree with the oracle's recomputation from positions
+    # the oracle's sequence (flips per step and hash); the final state is saturated
+    # along +0.25 T at 30 degrees; the fields at the final state agree with the
+    # oracle's recomputation from positions
     w = I.WORKLOADS["pinwheel300"]
     hx, hy = I.protocol_of(w["protocol"])
     runs = {}
@@ -78,6 +79,10 @@ def test_pinwheel300_full_protocol_invariants_and_fields(B, oracle):
             runs[(prec, rs)] = (r, sim)
     hashes = {k: v[0]["hash"] for k, v in runs.items()}
     assert len(set(hashes.values())) == 1, hashes
+    # the whole protocol as the oracle ran it (tests/golden/make_golden.py --full)
+    g = gold("pinwheel300_full")
+    for (r, _) in runs.values():
+        _check_against(g, r)
     r, sim = runs[(0, True)]
     assert r["n_flips"] == 270900
     s = sim.spins()
