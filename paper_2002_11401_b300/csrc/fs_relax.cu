@@ -91,11 +91,13 @@ __device__ unsigned long long runner_up(const Inst& I, const Levels& L, int64_t 
         const int64_t c = ((w >> 5) << 5) + lane;
         if (c != w && c < I.n) m = I.key32[c];
     }
-    for (int lev = 1; lev < L.nlev; ++lev) {
+    // every level's load in flight at once (unrolled; the levels are independent)
+#pragma unroll
+    for (int lev = 1; lev < kMaxLevels; ++lev) {
         const int64_t anc = w >> (5 * lev);
         const int64_t c = ((anc >> 5) << 5) + lane;
-        if (c != anc && c < ln(L, lev - 1)) {
-            const unsigned long long v = lp(L, lev - 1)[c];
+        if (lev < L.nlev && c != anc && c < L.n[lev - 1]) {
+            const unsigned long long v = L.p[lev - 1][c];
             m = v > m ? v : m;
         }
     }
@@ -188,13 +190,19 @@ __device__ void repair_warp(const Inst& I, const Levels& L, Dirty& D) {
         qout = D.up[(lev + 1) & 1];
         const int64_t nchild = ln(L, lev - 1);
         nout = 0;
+        unsigned long long* const here = lp(L, lev);
+        const unsigned long long* const below = lp(L, lev - 1);
+        unsigned long long* const above = lev + 1 < L.nlev ? lp(L, lev + 1) : nullptr;
         for (int q = 0; q < nn; ++q) {
             const int64_t node = qin[q];
-            const unsigned long long old = lp(L, lev)[node];
             const int64_t c = (node << 5) + lane;
-            const unsigned long long nv = warp_max_key(c < nchild ? lp(L, lev - 1)[c] : 0ull);
-            if (lane == 0) lp(L, lev)[node] = nv;
-            if (nv < old && lev + 1 < L.nlev && lp(L, lev + 1)[node >> 5] == old) {
+            // the node, its children and its parent, loaded together
+            const unsigned long long old = here[node];
+            const unsigned long long cv = c < nchild ? below[c] : 0ull;
+            const unsigned long long pv = above ? above[node >> 5] : 0ull;
+            const unsigned long long nv = warp_max_key(cv);
+            if (lane == 0) here[node] = nv;
+            if (nv < old && above && pv == old) {
                 if (lane == 0 && nout < kDirtyCap) qout[nout] = (int32_t)(node >> 5);
                 ++nout;
             }

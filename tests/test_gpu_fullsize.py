@@ -99,6 +99,19 @@ def test_pinwheel300_full_protocol_invariants_and_fields(B, oracle):
     assert max(np.abs(p32 - op).max(), np.abs(q32 - oq).max()) <= 1e-5 * scale
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_kagome1000_full_protocol_matches_oracle(B, prec):
+    # the whole 720-step rotation with thermal noise (3.0M islands, 3,146,771 flips):
+    # flips per step and the sequence hash as the oracle ran it
+    g = gold("kagome1000_full")
+    w = I.WORKLOADS["kagome1000"]
+    hx, hy = I.protocol_of(w["protocol"])
+    sim = lib_sim(w, precision=prec)
+    got = sim.run_protocol(hx, hy, log_cap=0)
+    assert got["status"] == 0
+    _check_against(g, got)
+
+
 def test_kagome1000_fields_at_full_size(B, oracle):
     # a random state of the 3.0M-island array with its thermal draw: every field
     w = I.WORKLOADS["kagome1000"]
