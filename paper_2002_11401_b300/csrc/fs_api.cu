@@ -373,8 +373,7 @@ fs_status fs_build_sim(fs_sim* sim) {
 
     CK(palloc((void**)&I.h64, 16 * n), "alloc");
     CK(palloc((void**)&I.key32, 8 * n), "alloc");
-    CK(palloc((void**)&I.lo32, 4 * n), "alloc");
-    if (p.precision == FS_FP32_RECHECK) CK(palloc((void**)&I.h32, 8 * n), "alloc");
+    CK(palloc((void**)&I.rec, sizeof(IslandRec) * n), "alloc");
     CK(palloc((void**)&I.key64, 8 * n), "alloc");
     CK(palloc((void**)&I.ext64, 16 * ncls), "alloc");
     CK(palloc((void**)&I.ext32, 8 * ncls), "alloc");

@@ -42,6 +42,22 @@ struct InstState {
 };
 
 // Read-only descriptor of one simulation (one entry of a batch table).
+// Per-island state that the relax reads and writes together, 32 bytes (one sector):
+// the first half (32-bit sums, lower bound, spin) is written by the flips; the
+// second half (FP32 1/(b h_k), 1/(c h_k), row, angle class) is constant over a
+// relax. Every field-and-margin sweep rewrites the whole record from the
+// per-island arrays, so a relax always starts from a fresh one.
+struct __align__(32) IslandRec {
+    int2 h32;          // dipolar (par, perp), 32-bit fixed-point sums (FP32 path; else 0)
+    float lo;          // certified lower bound of the LHS, -1 if none
+    int32_t s;         // spin
+    float2 rbc;        // 1 / (b h_k), 1 / (c h_k)
+    uint32_t rowq;     // first entry of the island's CSR row / 4
+    uint16_t cls;      // angle class
+    uint16_t rowlenq;  // entries of the row / 4
+};
+static_assert(sizeof(IslandRec) == 32, "one 32-byte sector per island");
+
 struct Inst {
     int64_t n;       // islands
     int64_t nnzp;    // padded CSR entries
@@ -69,12 +85,11 @@ struct Inst {
     float2* ext32;
     // fields and keys
     longlong2* h64;         // dipolar (par, perp), exact 64-bit sums (both paths)
-    int2* h32;              // dipolar (par, perp), 32-bit sums (FP32 path)
+    IslandRec* rec;         // the relax's per-island record (see IslandRec)
     float2* th32;           // thermal (par, perp) of the current step (sigma > 0)
     double2* th64;          // FP64 thermal (par, perp) drawn for step th_step[i]
     uint32_t* th_step;      // (sigma > 0; all ones before the first draw)
     unsigned long long* key32;  // (bits(upper bound) << 32) | ~i, 0 = not a candidate
-    float* lo32;                // certified lower bound of the LHS, -1 if none
     double* key64;              // exact LHS when flippable, 0 when not; FP32 path: -1
                                 // while the current fields have not been evaluated in FP64
     unsigned long long* tree;   // max-tree nodes above the keys
@@ -390,6 +405,36 @@ __device__ __forceinline__ uint32_t key32_idx(unsigned long long k) {
 __device__ __forceinline__ bool better64(unsigned long long va, unsigned long long ia,
                                          unsigned long long vb, unsigned long long ib) {
     return va > vb || (va == vb && ia < ib);
+}
+
+// IslandRec access in 16-byte halves.
+__device__ __forceinline__ IslandRec rec_load(const Inst& I, int64_t i) {
+    const int4* p = reinterpret_cast<const int4*>(I.rec + i);
+    const int4 a = p[0], b = p[1];
+    IslandRec r;
+    r.h32 = make_int2(a.x, a.y);
+    r.lo = __int_as_float(a.z);
+    r.s = a.w;
+    r.rbc = make_float2(__int_as_float(b.x), __int_as_float(b.y));
+    r.rowq = (uint32_t)b.z;
+    r.cls = (uint16_t)((uint32_t)b.w & 0xFFFFu);
+    r.rowlenq = (uint16_t)((uint32_t)b.w >> 16);
+    return r;
+}
+
+// The half the flips change: 32-bit sums, lower bound, spin.
+__device__ __forceinline__ void rec_store_dyn(const Inst& I, int64_t i, int2 h32, float lo,
+                                              int s) {
+    *reinterpret_cast<int4*>(I.rec + i) = make_int4(h32.x, h32.y, __float_as_int(lo), s);
+}
+
+// The whole record; row [ra, rb) (multiples of 4 entries).
+__device__ __forceinline__ void rec_store(const Inst& I, int64_t i, int2 h32, float lo, int s,
+                                          float2 rbc, int64_t ra, int64_t rb, uint16_t cls) {
+    int4* p = reinterpret_cast<int4*>(I.rec + i);
+    p[0] = make_int4(h32.x, h32.y, __float_as_int(lo), s);
+    p[1] = make_int4(__float_as_int(rbc.x), __float_as_int(rbc.y), (int)(uint32_t)(ra >> 2),
+                     (int)((uint32_t)cls | ((uint32_t)((rb - ra) >> 2) << 16)));
 }
 
 // FNV-1a over the 8 little-endian bytes of (step, island).

@@ -311,6 +311,7 @@ struct Upd {
     float lo;
     double x;
     int64_t r0, r1;  // island i's row, for the prediction
+    int s;           // island i's spin (written back with the sums)
 };
 
 // Every load is issued before any result is needed so that they overlap. `own`:
@@ -322,16 +323,18 @@ __device__ __forceinline__ Upd compute_update(const Inst& I, int64_t i, int snew
     Upd u;
     u.i = i;
     longlong2 h = I.h64[i];
+    const IslandRec r = rec_load(I, i);
     int2 g = make_int2(0, 0);
-    if constexpr (PREC == 1) g = I.h32[i];
+    if constexpr (PREC == 1) g = r.h32;
     u.old = I.key32[i];
-    const int si = own != 0 ? own : I.s[i];
-    const uint16_t ci = __ldg(&I.cls[i]);
-    const float2 rbc = __ldg(&I.rbc32[i]);
+    const int si = own != 0 ? own : r.s;
+    u.s = si;
+    const uint16_t ci = r.cls;
+    const float2 rbc = r.rbc;
     float2 th = make_float2(0.0f, 0.0f);
     if (I.sigma > 0.0) th = I.th32[i];
-    u.r0 = __ldg(&I.rp[i]);
-    u.r1 = __ldg(&I.rp[i + 1]);
+    u.r0 = (int64_t)r.rowq << 2;
+    u.r1 = u.r0 + ((int64_t)r.rowlenq << 2);
     double hk = 0.0;
     double2 e64 = make_double2(0.0, 0.0);
     if constexpr (PREC == 0) {
@@ -363,10 +366,9 @@ __device__ __forceinline__ void commit_update(const Inst& I, const Levels& L, Di
                                               RowStage& P, int par, const Upd& u,
                                               unsigned long long pf_above) {
     I.h64[u.i] = u.h;
-    if constexpr (PREC == 1) I.h32[u.i] = u.g;
+    rec_store_dyn(I, u.i, u.g, u.lo, u.s);
     I.key64[u.i] = u.x;
     I.key32[u.i] = u.nk;
-    I.lo32[u.i] = u.lo;
     leaf_changed(I, L, D, u.i, u.old, u.nk);
     if (u.nk > pf_above) stage_candidate<PREC>(I, P, par, u.nk, u.r0, u.r1);
 }
@@ -382,9 +384,10 @@ __device__ __forceinline__ double exact_value(const Inst& I, int64_t i, uint32_t
         return kept;
     } else {
         const longlong2 h = I.h64[i];
-        const int si = I.s[i];
+        const IslandRec r = rec_load(I, i);
+        const int si = r.s;
         const double hk = __ldg(&I.hk64[i]);
-        const uint16_t ci = __ldg(&I.cls[i]);
+        const uint16_t ci = r.cls;
         if (kept >= 0.0) return kept;
         double tp = 0.0, tq = 0.0;
         if (I.sigma > 0.0) thermal64_kept(I, i, step, &tp, &tq);
@@ -472,8 +475,9 @@ __device__ int64_t recheck_warp(const Inst& I, const Levels& L, RecheckShared& R
     int64_t b0 = 0, b1 = 0;
     for (int c = lane; c < nc; c += 32) {
         const int64_t i = R.front[cur][c];
-        const int si = I.s[i];
-        const int64_t r0 = __ldg(&I.rp[i]), r1 = __ldg(&I.rp[i + 1]);
+        const IslandRec rc = rec_load(I, i);
+        const int si = rc.s;
+        const int64_t r0 = (int64_t)rc.rowq << 2, r1 = r0 + ((int64_t)rc.rowlenq << 2);
         const double v = exact_value<PREC>(I, i, step);
         const unsigned long long vb = v > 0.0 ? (unsigned long long)__double_as_longlong(v) : 0ull;
         if (vb > 0ull && (bi < 0 || vb > bv || (vb == bv && i < bi))) {
@@ -486,7 +490,7 @@ __device__ int64_t recheck_warp(const Inst& I, const Levels& L, RecheckShared& R
         const unsigned long long old = R.leaf_key[c];
         const unsigned long long nk = v > 0.0 ? key32_of(__double2float_ru(v), i) : 0ull;
         I.key32[i] = nk;
-        I.lo32[i] = v > 0.0 ? __double2float_rd(v) : -1.0f;
+        I.rec[i].lo = v > 0.0 ? __double2float_rd(v) : -1.0f;
         R.new_key[c] = nk;
         if (nk < old && lp(L, 0)[i >> 5] == old) {
             const int q = atomicAdd(&D.n0, 1);
@@ -548,7 +552,7 @@ __device__ int64_t recheck_scan(const Inst& I, const Levels& L, RecheckShared& R
         if (k == 0ull || k < tkey) continue;
         const double v = exact_value<PREC>(I, i, step);
         I.key32[i] = v > 0.0 ? key32_of(__double2float_ru(v), i) : 0ull;
-        I.lo32[i] = v > 0.0 ? __double2float_rd(v) : -1.0f;
+        I.rec[i].lo = v > 0.0 ? __double2float_rd(v) : -1.0f;
         if (v > 0.0 && (bi < 0 || v > bl || (v == bl && i < bi))) {
             bl = v;
             bi = i;
@@ -606,10 +610,11 @@ __device__ int64_t pick_warp(const Inst& I, const Levels& L, RecheckShared& R, D
         float lo = 0.0f;
         if (lane == 0) {  // independent loads, in flight during the runner-up scan
             kw = I.key32[w];
-            lo = I.lo32[w];
-            *sk = I.s[w];
-            *a0 = I.rp[w];
-            *a1 = I.rp[w + 1];
+            const IslandRec r = rec_load(I, w);
+            lo = r.lo;
+            *sk = r.s;
+            *a0 = (int64_t)r.rowq << 2;
+            *a1 = *a0 + ((int64_t)r.rowlenq << 2);
         }
         const unsigned long long ru = runner_up(I, L, w);
         kw = __shfl_sync(0xffffffffu, kw, 0);
@@ -715,6 +720,7 @@ __global__ void __launch_bounds__(kT, 1)
     auto do_flip = [&](int64_t k, int sk, int64_t a0, int64_t a1) {
         const int snew = -sk;
         I.s[k] = (int8_t)snew;
+        I.rec[k].s = snew;
         sh_snew = snew;
         sh_e0 = a0;
         sh_e1 = a1;
@@ -758,9 +764,10 @@ __global__ void __launch_bounds__(kT, 1)
         } else if (pred >= 0) {
             // Meanwhile warps 1..7 compute the predicted flip's neighbour updates
             // (loads and arithmetic only), one entry of its row per thread.
-            const int sp = I.s[pred];
-            const int64_t a0 = __ldg(&I.rp[pred]);
-            const int len = (int)(__ldg(&I.rp[pred + 1]) - a0);
+            const IslandRec rpr = rec_load(I, pred);
+            const int sp = rpr.s;
+            const int64_t a0 = (int64_t)rpr.rowq << 2;
+            const int len = (int)rpr.rowlenq << 2;
             if (lane == 0) sh_spec_snew[wid] = -sp;
             if (threadIdx.x == 32) sh_spec_len = len;
             const int q = threadIdx.x - 32;
@@ -800,7 +807,9 @@ __global__ void __launch_bounds__(kT, 1)
             } else {
                 if (threadIdx.x == 0) {
                     if (flips < max_flips) {
-                        do_flip(r, I.s[r], I.rp[r], I.rp[r + 1]);
+                        const IslandRec rr = rec_load(I, r);
+                        const int64_t ra = (int64_t)rr.rowq << 2;
+                        do_flip(r, rr.s, ra, ra + ((int64_t)rr.rowlenq << 2));
                         sh_k = r;
                     } else {
                         sh_k = kPickMaxFlips;
@@ -880,14 +889,15 @@ __global__ void k_eval_all(const Inst* __restrict__ tab, double hx, double hy, u
     const Inst& I = tab[0];
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= I.n) return;
-    const int si = I.s[i];
-    const uint16_t ci = I.cls[i];
+    const IslandRec r = rec_load(I, i);
+    const int si = r.s;
+    const uint16_t ci = r.cls;
     const double2 ext = ext_proj(hx, hy, I.cs64[ci]);
     if (I.prec == 1) {
-        const int2 h = I.h32[i];
+        const int2 h = r.h32;
         const float2 th = I.sigma > 0.0 ? thermal32(I, i, step) : make_float2(0.0f, 0.0f);
         const Eval32 e = eval32(I, si, __fmul_rn(__int2float_rn(h.x), I.inv32),
-                                __fmul_rn(__int2float_rn(h.y), I.inv32), I.rbc32[i],
+                                __fmul_rn(__int2float_rn(h.y), I.inv32), r.rbc,
                                 make_float2(__double2float_rn(ext.x), __double2float_rn(ext.y)),
                                 th.x, th.y);
         hpar[i] = e.hpar;

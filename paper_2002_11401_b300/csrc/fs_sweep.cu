@@ -168,6 +168,8 @@ __global__ void __launch_bounds__(kSweepThreads, OCC)
         const uint32_t step = I.step0 + (uint32_t)t;
         const int si = I.s[i];
         const uint16_t ci = I.cls[i];
+        const float2 rbc = I.rbc32[i];
+        const int64_t ra = __ldg(&I.rp[i]), rb = __ldg(&I.rp[i + 1]);
         const float2 e32 = I.ext32[ci];
         float2 th = make_float2(0.0f, 0.0f);
         if (I.sigma > 0.0) {
@@ -180,16 +182,12 @@ __global__ void __launch_bounds__(kSweepThreads, OCC)
             I.h64[i] = h64;
         }
         if constexpr (PREC == 1) {
-            int2 h;
-            if (SUM32) {
-                h = make_int2(sums32[wib][lane][0], sums32[wib][lane][1]);
-                I.h32[i] = h;
-            } else {
-                h = I.h32[i];
-            }
+            // (without the resweep, the 32-bit sums kept by the flips)
+            const int2 h = SUM32 ? make_int2(sums32[wib][lane][0], sums32[wib][lane][1])
+                                 : rec_load(I, i).h32;
             const float dp = __fmul_rn(__int2float_rn(h.x), I.inv32);
             const float dq = __fmul_rn(__int2float_rn(h.y), I.inv32);
-            const Eval32 e = eval32(I, si, dp, dq, I.rbc32[i], e32, th.x, th.y);
+            const Eval32 e = eval32(I, si, dp, dq, rbc, e32, th.x, th.y);
             float lo = e.certain ? e.lo : -1.0f;
             node = e.possible ? key32_of(e.hi, i) : 0ull;
             double x = e.possible ? -1.0 : 0.0;
@@ -206,13 +204,13 @@ __global__ void __launch_bounds__(kSweepThreads, OCC)
                 lo = x > 0.0 ? __double2float_rd(x) : -1.0f;
             }
             I.key32[i] = node;
-            I.lo32[i] = lo;
             I.key64[i] = x;
+            rec_store(I, i, h, lo, si, rbc, ra, rb, ci);
         } else {
             if (!SUM64) h64 = I.h64[i];
             const float dp = __fmul_rn(__ll2float_rn(h64.x), I.inv64f);
             const float dq = __fmul_rn(__ll2float_rn(h64.y), I.inv64f);
-            const Eval32 e = eval32(I, si, dp, dq, I.rbc32[i], e32, th.x, th.y);
+            const Eval32 e = eval32(I, si, dp, dq, rbc, e32, th.x, th.y);
             double x = 0.0;
             if (e.possible) {
                 double tp = 0.0, tq = 0.0;
@@ -223,7 +221,8 @@ __global__ void __launch_bounds__(kSweepThreads, OCC)
             I.key64[i] = x;
             node = x > 0.0 ? key32_of(__double2float_ru(x), i) : 0ull;
             I.key32[i] = node;
-            I.lo32[i] = x > 0.0 ? __double2float_rd(x) : -1.0f;
+            rec_store(I, i, make_int2(0, 0), x > 0.0 ? __double2float_rd(x) : -1.0f, si, rbc, ra,
+                      rb, ci);
         }
     }
     node = warp_max_key(node);
