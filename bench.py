@@ -47,10 +47,12 @@ def sweep_bytes(n: int, nnz: int, fp32: bool, resweep: bool, thermal: bool) -> i
     """Algorithmic bytes of one field-and-margin sweep. Per pair: the column index
     and the (P, Q) coefficients of the path's width (4 + 8 or 4 + 16); per row: its
     pointer (8). Per island: spin, angle class, 1/(b h_k) and 1/(c h_k) read
-    (1 + 2 + 8); the sums of the path's width written (or, without the resweep,
-    read: 8 or 16); key, lower bound and exact value written (8 + 4 + 8); with
-    thermal noise, the step's FP32 draw written (8)."""
-    per_island = 1 + 2 + 8 + (8 if fp32 else 16) + 8 + 4 + 8 + (8 if thermal else 0)
+    (1 + 2 + 8); the relax's 32-byte record, key and exact value written
+    (32 + 8 + 8); on the FP64 path the 64-bit sums written (or, without the
+    resweep, read: 16), on the FP32 path without the resweep the 32-bit sums read
+    (8); with thermal noise, the step's FP32 draw written (8)."""
+    per_island = (1 + 2 + 8 + 32 + 8 + 8 + (0 if fp32 else 16)
+                  + (8 if fp32 and not resweep else 0) + (8 if thermal else 0))
     if not resweep:
         return n * per_island
     return (12 if fp32 else 20) * nnz + 8 * (n + 1) + n * per_island
