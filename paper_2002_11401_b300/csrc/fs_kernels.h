@@ -26,6 +26,7 @@ struct RelaxLaunch {
     int n_work;
     int prec;
     int smem_levels;      // dynamic shared memory for the upper tree levels
+    int min_blocks = 1;   // 2: the build for two resident CTAs per SM (shared GPU)
 };
 
 cudaError_t launch_ext_table(const SweepLaunch& L, cudaStream_t st);

@@ -649,8 +649,13 @@ __device__ int64_t pick_warp(const Inst& I, const Levels& L, RecheckShared& R, D
     return kPickBounds;
 }
 
-template <int PREC>
-__global__ void __launch_bounds__(kT, 1)
+// MINB: resident CTAs per SM the build is made for. One CTA per SM (registers as
+// needed) for a relax that has the GPU to itself; two (at most 128 registers a
+// thread) for a batch with more members than SMs, so that each SM interleaves two
+// latency-bound chains (measured: 24.3M vs 20.9M flips/s on the 512-member FP32
+// ensemble; the server's requests, fewer at a time, run faster with one).
+template <int PREC, int MINB>
+__global__ void __launch_bounds__(kT, MINB)
     k_relax(const Inst* __restrict__ tab, const int32_t* __restrict__ work, int n_work,
             int smem_levels) {
     extern __shared__ unsigned long long sm_levels[];
@@ -925,23 +930,27 @@ int relax_threads() { return kT; }
 size_t relax_static_smem(int prec) {
     cudaFuncAttributes a{};
     if (prec == 1)
-        cudaFuncGetAttributes(&a, k_relax<1>);
+        cudaFuncGetAttributes(&a, k_relax<1, 1>);
     else
-        cudaFuncGetAttributes(&a, k_relax<0>);
+        cudaFuncGetAttributes(&a, k_relax<0, 1>);
     return a.sharedSizeBytes;
 }
 
-// Sets the dynamic shared-memory limit of the relax kernel once per size (a
+// Sets the dynamic shared-memory limit of the relax kernels once per size (a
 // no-op afterwards, so launches can be captured in graphs).
 cudaError_t prepare_relax(int prec, int smem) {
     static int set_bytes[2] = {-1, -1};
     const int k = prec == 1 ? 1 : 0;
     if (set_bytes[k] >= smem) return cudaSuccess;
-    const cudaError_t e =
-        prec == 1 ? cudaFuncSetAttribute(k_relax<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem)
-                  : cudaFuncSetAttribute(k_relax<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem);
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e;
+    if (prec == 1) {
+        e = cudaFuncSetAttribute(k_relax<1, 1>, A, smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_relax<1, 2>, A, smem);
+    } else {
+        e = cudaFuncSetAttribute(k_relax<0, 1>, A, smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_relax<0, 2>, A, smem);
+    }
     if (e == cudaSuccess) set_bytes[k] = smem;
     return e;
 }
@@ -950,10 +959,18 @@ cudaError_t launch_relax(const RelaxLaunch& L, cudaStream_t st) {
     if (L.n_work == 0) return cudaSuccess;
     const cudaError_t e = prepare_relax(L.prec, L.smem_levels);
     if (e != cudaSuccess) return e;
-    if (L.prec == 1)
-        k_relax<1><<<L.n_work, kT, L.smem_levels, st>>>(L.tab, L.work, L.n_work, L.smem_levels);
-    else
-        k_relax<0><<<L.n_work, kT, L.smem_levels, st>>>(L.tab, L.work, L.n_work, L.smem_levels);
+    const unsigned g = (unsigned)L.n_work;
+    if (L.prec == 1) {
+        if (L.min_blocks == 2)
+            k_relax<1, 2><<<g, kT, L.smem_levels, st>>>(L.tab, L.work, L.n_work, L.smem_levels);
+        else
+            k_relax<1, 1><<<g, kT, L.smem_levels, st>>>(L.tab, L.work, L.n_work, L.smem_levels);
+    } else {
+        if (L.min_blocks == 2)
+            k_relax<0, 2><<<g, kT, L.smem_levels, st>>>(L.tab, L.work, L.n_work, L.smem_levels);
+        else
+            k_relax<0, 1><<<g, kT, L.smem_levels, st>>>(L.tab, L.work, L.n_work, L.smem_levels);
+    }
     return cudaGetLastError();
 }
 
