@@ -6,17 +6,24 @@
 // 32 over the keys, its upper levels in shared memory. The largest key is the
 // island with the largest bound, lowest index first.
 //
-// Per flip: warp 0 reads the root's island w and the largest other key (w's
-// sibling sets at every level). w is taken when its certified lower bound exceeds
-// one and that runner-up's upper bound; otherwise the islands whose bounds reach
-// the threshold are compared exactly (FS_FP64 values), non-flippable ones are
-// demoted, and the exact best is taken once no island outside the set can beat
-// it. Then island k is flipped and every neighbour i of k (row k of the CSR,
-// whose transposed coefficients give the field k puts on i in i's frame) gets
-// 2 s_k(new) (P_ik, Q_ik) added to its exact fixed-point sums and a new key. A key
-// that grows is pushed up the tree with atomic maxima; a node whose maximum was a
-// key that shrank is rebuilt from its children, level by level. Fields are held
-// constant over the relax, as the paper states.
+// Per flip, two phases and two barriers:
+//  - Warp 0 repairs the tree (nodes whose maximum was a key that shrank are
+//    rebuilt from their children, level by level), reads the root's island w and
+//    the largest other key (w's sibling sets at every level), and takes w when its
+//    certified lower bound exceeds one and that runner-up's upper bound; otherwise
+//    the islands whose bounds reach the threshold are compared exactly (FS_FP64
+//    values) and the exact best is taken. It flips the pick k.
+//  - Meanwhile warps 1..7 compute the neighbour updates of the predicted pick
+//    (loads and arithmetic only): every neighbour i of it (its CSR row, whose
+//    transposed coefficients give the field it puts on i in i's frame) gets
+//    2 s(new) (P, Q) added to its exact fixed-point sums and a new key.
+//  - After the barrier the precomputed updates are committed when k is the
+//    predicted island and no key changed on the way; otherwise k's updates are
+//    computed and committed now. A key that grows is pushed up the tree with
+//    atomic maxima; one that shrank queues its node for the next repair. The
+//    prediction for the next flip is the largest of the untouched runner-up and
+//    the neighbours' new keys.
+// Fields are held constant over the relax, as the paper states.
 //
 // FS_FP32_RECHECK computes keys from FP32 bounds and its exact values in FP64;
 // FS_FP64 computes every candidate's exact value when its key is set, and its keys
@@ -146,7 +153,7 @@ __device__ __forceinline__ void leaf_changed(const Inst& I, const Levels& L, Dir
 // untouched (the runner-up, when the flip was certified from bounds) and the
 // largest new key among the flip's neighbours, folded into best[parity] with
 // atomic maxima during the neighbour updates. Double-buffered by flip parity.
-struct RowStage {
+struct Prediction {
     unsigned long long best[2];
 };
 
@@ -289,11 +296,12 @@ __device__ __forceinline__ void prefetch_row(const Inst& I, int64_t a0, int64_t 
     if (m != 0u) bulk_prefetch_l2(I.col + a0, 4u * m);
 }
 
-// Island j (key kj), whose row is [a0, a1), may be the next pick: its row is
-// asked into L2 now and its key enters the prediction.
+// Island j (key kj), whose row is [a0, a1), may be the next pick: its row's column
+// indices are asked into L2 now and its key enters the prediction.
 template <int PREC>
-__device__ __forceinline__ void stage_candidate(const Inst& I, RowStage& P, int par,
-                                                unsigned long long kj, int64_t a0, int64_t a1) {
+__device__ __forceinline__ void predict_candidate(const Inst& I, Prediction& P, int par,
+                                                  unsigned long long kj, int64_t a0,
+                                                  int64_t a1) {
     prefetch_row<PREC>(I, a0, a1);
     if (*(volatile unsigned long long*)&P.best[par] < kj) atomicMax(&P.best[par], kj);
 }
@@ -363,14 +371,14 @@ __device__ __forceinline__ Upd compute_update(const Inst& I, int64_t i, int snew
 // the island enters the prediction of the next pick.
 template <int PREC>
 __device__ __forceinline__ void commit_update(const Inst& I, const Levels& L, Dirty& D,
-                                              RowStage& P, int par, const Upd& u,
+                                              Prediction& P, int par, const Upd& u,
                                               unsigned long long pf_above) {
     I.h64[u.i] = u.h;
     rec_store_dyn(I, u.i, u.g, u.lo, u.s);
     I.key64[u.i] = u.x;
     I.key32[u.i] = u.nk;
     leaf_changed(I, L, D, u.i, u.old, u.nk);
-    if (u.nk > pf_above) stage_candidate<PREC>(I, P, par, u.nk, u.r0, u.r1);
+    if (u.nk > pf_above) predict_candidate<PREC>(I, P, par, u.nk, u.r0, u.r1);
 }
 
 // Exact FP64 value of island i (0 when not flippable): the value kept with its
@@ -660,7 +668,7 @@ __global__ void __launch_bounds__(kT, MINB)
             int smem_levels) {
     extern __shared__ unsigned long long sm_levels[];
     __shared__ int64_t sh_k;
-    __shared__ RowStage P;
+    __shared__ Prediction P;
     __shared__ int64_t sh_e0, sh_e1;
     __shared__ unsigned long long sh_ru;
     __shared__ int32_t sh_snew;
