@@ -111,6 +111,38 @@ __device__ unsigned long long runner_up(const Inst& I, const Levels& L, int64_t 
     return warp_max_key(m);
 }
 
+// An upper bound of every key other than islands w's and r's (r != w): the groups
+// of leaves, and at every level the sibling sets, that hold w's or r's ancestors,
+// less those ancestors. Warp-wide.
+__device__ unsigned long long third_key(const Inst& I, const Levels& L, int64_t w, int64_t r) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long m = 0ull;
+    {
+        const int64_t c = ((w >> 5) << 5) + lane, c2 = ((r >> 5) << 5) + lane;
+        if (c != w && c != r && c < I.n) m = I.key32[c];
+        if ((r >> 5) != (w >> 5) && c2 != r && c2 != w && c2 < I.n) {
+            const unsigned long long v = I.key32[c2];
+            m = v > m ? v : m;
+        }
+    }
+#pragma unroll
+    for (int lev = 1; lev < kMaxLevels; ++lev) {
+        if (lev >= L.nlev) break;
+        const int64_t aw = w >> (5 * lev), ar = r >> (5 * lev);
+        const int64_t c = ((aw >> 5) << 5) + lane, c2 = ((ar >> 5) << 5) + lane;
+        const int64_t lim = L.n[lev - 1];
+        if (c != aw && c != ar && c < lim) {
+            const unsigned long long v = L.p[lev - 1][c];
+            m = v > m ? v : m;
+        }
+        if ((ar >> 5) != (aw >> 5) && c2 != ar && c2 != aw && c2 < lim) {
+            const unsigned long long v = L.p[lev - 1][c2];
+            m = v > m ? v : m;
+        }
+    }
+    return warp_max_key(m);
+}
+
 struct Dirty {
     int32_t lv0[kDirtyCap];    // first-level nodes to rebuild
     int32_t up[2][kDirtyCap];  // upper-level nodes, ping-pong by level parity
@@ -591,6 +623,45 @@ __device__ int64_t recheck_scan(const Inst& I, const Levels& L, RecheckShared& R
     return R.result;
 }
 
+// Exact comparison of islands w and r when no other key reaches tau <= x(w) (the
+// caller has checked): the exact best of the two is the pick. Both get keys from
+// their exact values (lowered; their first-level nodes queued for the repair when
+// they held the old key). Warp-wide; returns the pick with its spin and row.
+template <int PREC>
+__device__ int64_t pair_compare(const Inst& I, const Levels& L, Dirty& D, int64_t w, int64_t r,
+                                unsigned long long kw, unsigned long long kr, uint32_t step,
+                                int* sk, int64_t* a0, int64_t* a1) {
+    const int lane = threadIdx.x & 31;
+    double v = 0.0;
+    int si = 0;
+    int64_t r0 = 0, r1 = 0;
+    if (lane < 2) {
+        const int64_t i = lane == 0 ? w : r;
+        const unsigned long long old = lane == 0 ? kw : kr;
+        const IslandRec rc = rec_load(I, i);
+        si = rc.s;
+        r0 = (int64_t)rc.rowq << 2;
+        r1 = r0 + ((int64_t)rc.rowlenq << 2);
+        v = exact_value<PREC>(I, i, step);
+        const unsigned long long nk = v > 0.0 ? key32_of(__double2float_ru(v), i) : 0ull;
+        I.key32[i] = nk;
+        I.rec[i].lo = v > 0.0 ? __double2float_rd(v) : -1.0f;
+        if (nk < old && lp(L, 0)[i >> 5] == old) {
+            const int q = atomicAdd(&D.n0, 1);
+            if (q < kDirtyCap) D.lv0[q] = (int32_t)(i >> 5);
+        }
+    }
+    const double vw = __shfl_sync(0xffffffffu, v, 0), vr = __shfl_sync(0xffffffffu, v, 1);
+    // w is flippable (its lower bound exceeds one); r wins on a larger value, or an
+    // equal one with a lower index
+    const int src = (vr > vw || (vr == vw && r < w)) ? 1 : 0;
+    *sk = __shfl_sync(0xffffffffu, si, src);
+    *a0 = __shfl_sync(0xffffffffu, r0, src);
+    *a1 = __shfl_sync(0xffffffffu, r1, src);
+    __syncwarp();
+    return src == 1 ? r : w;
+}
+
 // Pick codes besides an island index.
 constexpr int64_t kPickNone = -1;      // no flippable island: the relax is done
 constexpr int64_t kPickOverflow = -3;  // exact comparison needs the CTA-wide scan
@@ -639,6 +710,17 @@ __device__ int64_t pick_warp(const Inst& I, const Levels& L, RecheckShared& R, D
         // With tau = lo(w) > 1 the set holds w, whose exact value is at least tau,
         // so one round settles it; at the threshold, start from the runner-up.
         float tau = lo > 1.0f ? lo : fmaxf(hi2, lo);
+        if (lo > 1.0f && ru != 0ull && (int64_t)key32_idx(ru) != w) {
+            // When no key but w's and the runner-up's reaches tau, those two alone are
+            // compared exactly (no descent through the tree).
+            const int64_t r = key32_idx(ru);
+            const unsigned long long k3 = third_key(I, L, w, r);
+            if (k3 < ((unsigned long long)__float_as_uint(tau) << 32)) {
+                *clean = false;
+                if (lane == 0) atomicAdd((unsigned long long*)&st->rechecks, 1ull);
+                return pair_compare<PREC>(I, L, D, w, r, kw, ru, step, sk, a0, a1);
+            }
+        }
         int64_t k = -2;
         for (int rounds = 0; k == -2;) {
             if (++rounds > 64) return kPickBounds;

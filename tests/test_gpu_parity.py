@@ -180,6 +180,22 @@ def test_exact_ties_lowest_index(B, oracle):
         assert got["log_spin"].tolist() == list(range(n)) * 2
 
 
+def test_exact_ties_beyond_the_candidate_cap(B):
+    # 400 identical non-interacting islands: every pick is an exact tie among more
+    # islands than one warp's exact comparison holds (256), so the block-wide scan
+    # settles them; the order is still the lowest index first
+    n = 400
+    x = np.arange(n, dtype=np.float64) * 10.0
+    for prec in (FP64, FP32):
+        sim = B.Sim.custom(x, np.zeros(n), np.zeros(n))
+        sim.set_params(B.make_params(alpha=0.0, cutoff=1.0, precision=prec))
+        sim.set_hk(np.full(n, 0.2))
+        got = sim.run_protocol(np.array([-0.3, 0.3]), np.zeros(2), log_cap=2 * n)
+        assert got["status"] == 0
+        assert got["log_spin"].tolist() == list(range(n)) * 2
+        assert sim.profile()["fallbacks"] > 0
+
+
 def test_custom_geometry_matches_oracle(B, oracle):
     rng = np.random.default_rng(9)
     n = 300
