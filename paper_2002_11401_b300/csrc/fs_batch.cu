@@ -79,6 +79,7 @@ cudaError_t BatchTable::enqueue_step(int prec, int resweep, int levels, cudaStre
     S.prec = prec;
     S.resweep = resweep;
     S.lanes_per_row = lanes;
+    S.occupancy = occ;
     cudaError_t e = launch_ext_table(S, st);
     if (e != cudaSuccess) return e;
     e = launch_sweep(S, st);
@@ -99,6 +100,52 @@ cudaError_t BatchTable::enqueue_step(int prec, int resweep, int levels, cudaStre
     }
     R.min_blocks = n_inst > nsm ? 2 : 1;
     return launch_relax(R, st);
+}
+
+cudaError_t BatchTable::autotune(int prec, int resweep, cudaStream_t st) {
+    // The trial sweeps compute what the protocol's first sweep computes (the same
+    // field step of the same states): they change nothing the protocol reads.
+    SweepLaunch S;
+    S.tab = tab;
+    S.task_start = task_start;
+    S.n_inst = n_inst;
+    S.total_tasks = total_tasks;
+    S.tcnts = tcnts;
+    S.prec = prec;
+    S.resweep = resweep;
+    cudaError_t e = launch_ext_table(S, st);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t e0, e1;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return e;
+    }
+    const int cands[4] = {4, 8, 16, 32};
+    float best_ms = 1e30f;
+    for (int c = 0; c < 8 && e == cudaSuccess; ++c) {
+        S.lanes_per_row = cands[c & 3];
+        S.occupancy = c < 4 ? 4 : 5;
+        if ((e = launch_sweep(S, st)) != cudaSuccess) break;  // warm-up
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+            cudaEventRecord(e0, st);
+            e = launch_sweep(S, st);
+            cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0.0f;
+            if (e == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+            ms = std::min(ms, t);
+        }
+        if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            lanes = S.lanes_per_row;
+            occ = S.occupancy;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return e;
 }
 
 }  // namespace fs
@@ -191,6 +238,11 @@ extern "C" fs_status fs_batch_run_protocol(fs_sim* const* sims, int32_t n, const
     }
     BatchTable B;
     if ((e = B.upload(v, descs, st)) != cudaSuccess) return bail(e, "upload");
+    // a batch whose sweep is long enough to matter times its own sweep builds
+    // (about 20 sweeps); smaller ones keep the row-length rule
+    if (K >= 16 && B.total_tasks >= 8192 &&
+        (e = B.autotune(lead->p.precision, resweep ? 1 : 0, st)) != cudaSuccess)
+        return bail(e, "autotune");
     const int prec = lead->p.precision;
     int levels = 1024;
     for (int i = 0; i < n; ++i) levels = std::max(levels, relax_smem_levels(v[(size_t)i]->n));

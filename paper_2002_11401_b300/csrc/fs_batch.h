@@ -21,6 +21,7 @@ struct BatchTable {
     int n_inst = 0;
     int64_t total_tasks = 0;
     int lanes = 16;
+    int occ = 4;  // sweep build: resident CTAs per SM
     std::vector<Inst> h_tab;
     std::vector<int64_t> h_task;
     std::vector<unsigned*> h_tcnt;
@@ -30,6 +31,9 @@ struct BatchTable {
                        cudaStream_t st);
     // one field step of every member: a sweep over all rows, then one relax CTA each
     cudaError_t enqueue_step(int prec, int resweep, int levels, cudaStream_t st) const;
+    // times the batched sweep's builds (lanes per row x resident CTAs per SM) on
+    // the batch's own rows and keeps the fastest; every build gives the same bits
+    cudaError_t autotune(int prec, int resweep, cudaStream_t st);
 };
 
 cudaError_t prepare_relax(int prec, int smem);
