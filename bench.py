@@ -361,6 +361,24 @@ def main():
         line["e2e"] = {"value": r["n_flips"] * args.steps / dt, "unit": UNIT,
                        "h2d_bytes_per_step": int(init.nbytes + hx.nbytes + hy.nbytes),
                        "d2h_bytes_per_step": int(8 * K + 8 + 8 + 64)}
+    # ---- the FP32 path's field error against the FS_FP64 path, at the final state ---
+    if fp32 and rank == 0 and not args.no_e2e:
+        ref = B.Sim.geometry(w["kind"], w["nx"], w["ny"], w["a"])
+        ref.set_params(B.make_params(alpha=w["alpha"], hk=w["hk"], k_disorder=w["k_disorder"],
+                                     b=w["b"], c=w["c"], beta=w["beta"], gamma=w["gamma"],
+                                     cutoff=w["cutoff"], sigma_th=w["sigma_th"], seed=w["seed"],
+                                     precision=B.FS_FP64))
+        final = sim.spins()
+        ref.set_spins(final)
+        ref.set_field(float(hx[-1]), float(hy[-1]), step=K - 1)
+        sim.set_field(float(hx[-1]), float(hy[-1]), step=K - 1)
+        p64, q64 = ref.fields()
+        p32, q32 = sim.fields()
+        scale = max(float(np.abs(p64).max()), float(np.abs(q64).max()))
+        err = max(float(np.abs(p32 - p64).max()), float(np.abs(q32 - q64).max()))
+        line["fp32_field_error"] = {"max_abs_over_max_h": err / scale, "bound": 1e-5,
+                                    "vs": "FS_FP64 path (= oracle to 1e-12) at the final state"}
+        ref.close()
     if rank == 0 and not args.no_cpu and world >= 1:
         try:
             line["cpu_baseline"] = cpu_baseline(w)

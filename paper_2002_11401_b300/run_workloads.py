@@ -170,8 +170,9 @@ def run_serving(n_requests, rate, budget_gb, check):
            "build_and_run_p99_s": float(np.percentile(run, 99)),
            "largest_request_islands": int(max(res["n"] for res, _, _, _ in results)),
            "hbm_budget_gb": budget_gb}
-    # the same requests alone (a sample): identical results
-    same = 0
+    # the same requests alone (a sample): identical results; and the plain
+    # one-simulation-at-a-time FP64 path on them (build not timed), for comparison
+    same, same64, t64, f64 = 0, 0, 0.0, 0
     for res, r, hx, hy in results[:check]:
         w = dict(r)
         w.pop("protocol")
@@ -179,7 +180,18 @@ def run_serving(n_requests, rate, budget_gb, check):
         alone = s.run_protocol(hx, hy, log_cap=0)
         same += int(alone["hash"] == res["hash"] and alone["n_flips"] == res["n_flips"])
         s.close()
-    out["alone_equals_mix"] = f"{same}/{min(check, len(results))}"
+        s = make_sim(w, B.FS_FP64)
+        t0 = time.perf_counter()
+        r64 = s.run_protocol(hx, hy, log_cap=0)
+        t64 += time.perf_counter() - t0
+        f64 += r64["n_flips"]
+        same64 += int(r64["hash"] == res["hash"] and r64["n_flips"] == res["n_flips"])
+        s.close()
+    n_chk = min(check, len(results))
+    out["alone_equals_mix"] = f"{same}/{n_chk}"
+    out["fp64_alone_equals_mix"] = f"{same64}/{n_chk}"
+    out["one_at_a_time_fp64_flips_per_s"] = f64 / t64 if t64 > 0 else None
+    out["served_vs_one_at_a_time_fp64"] = out["flips_per_s"] / (f64 / t64) if f64 else None
     return out
 
 
