@@ -91,14 +91,10 @@ cudaError_t BatchTable::enqueue_step(int prec, int resweep, int levels, cudaStre
     R.prec = prec;
     R.smem_levels = levels;
     // more members than SMs: two latency-bound relaxes per SM
-    static int nsm = 0;
-    if (nsm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (nsm <= 0) nsm = 1;
-    }
-    R.min_blocks = n_inst > nsm ? 2 : 1;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    R.min_blocks = n_inst > std::max(nsm, 1) ? 2 : 1;
     return launch_relax(R, st);
 }
 

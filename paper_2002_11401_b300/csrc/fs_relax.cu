@@ -31,6 +31,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "fs_common.cuh"
 #include "fs_kernels.h"
 
@@ -1027,11 +1030,15 @@ size_t relax_static_smem(int prec) {
 }
 
 // Sets the dynamic shared-memory limit of the relax kernels once per size (a
-// no-op afterwards, so launches can be captured in graphs).
+// no-op afterwards, so launches can be captured in graphs). Thread-safe: the
+// server's builder threads reach it concurrently.
 cudaError_t prepare_relax(int prec, int smem) {
-    static int set_bytes[2] = {-1, -1};
+    static std::atomic<int> set_bytes[2] = {{-1}, {-1}};
+    static std::mutex mu;
     const int k = prec == 1 ? 1 : 0;
-    if (set_bytes[k] >= smem) return cudaSuccess;
+    if (set_bytes[k].load() >= smem) return cudaSuccess;
+    std::lock_guard<std::mutex> g(mu);
+    if (set_bytes[k].load() >= smem) return cudaSuccess;
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e;
     if (prec == 1) {
@@ -1041,7 +1048,7 @@ cudaError_t prepare_relax(int prec, int smem) {
         e = cudaFuncSetAttribute(k_relax<0, 1>, A, smem);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_relax<0, 2>, A, smem);
     }
-    if (e == cudaSuccess) set_bytes[k] = smem;
+    if (e == cudaSuccess) set_bytes[k].store(smem);
     return e;
 }
 
