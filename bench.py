@@ -36,11 +36,11 @@ UNIT = "spin-flips/s"
 WORKLOAD = "pinwheel300"
 
 
-def workload_desc(w, prec_name, resweep):
+def workload_desc(w):
+    """The workload alone (both arms run it; the arithmetic is in config["path"])."""
     return (f"pinwheel {w['nx']}x{w['ny']} cells (180,600 islands), cutoff {w['cutoff']:g}a, "
             f"alpha {w['alpha']:g}, h_k N(0.2 T, 5%) seed {w['seed']}, b=c=1 beta=gamma=3, "
-            f"field loop -0.25 -> +0.25 T at 30 deg in 1000 steps from all +1, "
-            f"{prec_name}, {'full dipolar resweep every field step' if resweep else 'exact incremental sums'}")
+            f"field loop -0.25 -> +0.25 T at 30 deg in 1000 steps from all +1")
 
 
 def sweep_bytes(n: int, nnz: int, fp32: bool, resweep: bool, thermal: bool) -> int:
@@ -190,7 +190,9 @@ def run_reference(args, w, rank):
             "steps": steps, "warmup": warm, "ms_per_step": dt * 1000 / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": workload_desc(w, "FP64 oracle", True)},
+            "config": {"workload": workload_desc(w),
+                       "path": "FP64 oracle on the host cores, dipolar fields recomputed "
+                               "from scratch every field step"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"],
                              "kind": "oracle", "sample": vals[0]["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -333,7 +335,10 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "i32+f32, f64 recheck" if fp32 else "i64+f64", "data": "synthetic",
-            "config": {"workload": workload_desc(w, prec_name, args.resweep), "islands": n,
+            "config": {"workload": workload_desc(w),
+                       "path": f"{prec_name}, " + ("full dipolar resweep every field step"
+                                                   if args.resweep else "exact incremental sums"),
+                       "islands": n,
                        "neighbour_pairs": nnz, "field_steps_per_step": K,
                        "flips_per_step": flips_per_protocol, "seq_hash": f"{hash0:#018x}",
                        "l2": "inputs larger than L2 (neighbour tensors "
