@@ -533,16 +533,17 @@ extern "C" fs_status fs_set_field(fs_sim* sim, double hx, double hy, uint32_t st
 
 namespace fs {
 
-// Dynamic shared memory of a relax CTA: the tree levels above the keys that fit
-// in 96 KiB, counted from the root down (the kernel places them the same way).
-// Small systems take little, so several relax CTAs share an SM.
+// Dynamic shared memory of a relax CTA: the tree levels above the keys that the
+// relax keeps (up to the first with at most kRelaxTopNodes nodes) and that fit in
+// 96 KiB, counted from the top down (the kernel places them the same way). Small
+// systems take little, so several relax CTAs share an SM.
 int relax_smem_levels(int64_t n) {
     const int64_t cap = 96 * 1024;
     std::vector<int64_t> lv;
     int64_t cnt = (n + 31) / 32;
     for (;;) {
         lv.push_back(8 * cnt);
-        if (cnt <= 1) break;
+        if (cnt <= kRelaxTopNodes) break;
         cnt = (cnt + 31) / 32;
     }
     int64_t used = 0;
@@ -550,7 +551,7 @@ int relax_smem_levels(int64_t n) {
         if (used + lv[q] > cap) break;
         used += lv[q];
     }
-    return (int)std::max<int64_t>(1024, used);
+    return (int)std::max<int64_t>(8 * kRelaxTopNodes, used);
 }
 
 int relax_smem_max() { return 96 * 1024; }

@@ -20,6 +20,10 @@ struct SweepLaunch {
     int occupancy = 4;          // resident CTAs per SM the kernel is built for: 4 or 5
 };
 
+// The relax keeps the tree's levels up to the first one with at most this many
+// nodes (one warp reduces it, 8 nodes a lane, in place of the levels above).
+constexpr int kRelaxTopNodes = 256;
+
 struct RelaxLaunch {
     const Inst* tab;
     const int32_t* work;  // device [n_work]: simulation of each CTA

@@ -3,8 +3,10 @@
 //
 // Keys: one 64-bit key per island, (FP32 upper bound of its Eq. 5 LHS) << 32 |
 // (2^32 - 1 - index), 0 when the island cannot be flippable; a max-tree of fan-out
-// 32 over the keys, its upper levels in shared memory. The largest key is the
-// island with the largest bound, lowest index first.
+// 32 over the keys up to the first level of at most 256 nodes (the top), its upper
+// levels in shared memory. The root is not stored: warp 0 reduces the top level
+// when it picks. The largest key is the island with the largest bound, lowest
+// index first.
 //
 // Per flip, two phases and two barriers:
 //  - Warp 0 repairs the tree (nodes whose maximum was a key that shrank are
@@ -44,28 +46,32 @@ namespace {
 constexpr int kT = 256;  // threads per relax CTA
 constexpr int kNW = kT / 32;
 constexpr int kDirtyCap = kMaxPaddedDegree + 8;
+// Levels the relax keeps: fewer than 2^31 islands need at most five (the fifth
+// has at most 64 nodes).
+constexpr int kRelaxLevels = 5;
+constexpr int kTopPerLane = kRelaxTopNodes / 32;
 
 // The tree's levels above the leaves. Held in registers: every access goes through
 // lp()/ln(), which select with compile-time indices (a run-time index into these
 // arrays would put them in local memory, one more dependent load per level step).
 struct Levels {
-    unsigned long long* p[kMaxLevels];  // base of each level
-    int32_t n[kMaxLevels];              // nodes per level
-    int nlev;
+    unsigned long long* p[kRelaxLevels];  // base of each level
+    int32_t n[kRelaxLevels];              // nodes per level
+    int nlev;                             // level nlev - 1 is the top
     int first_sm;  // levels first_sm.. are in shared memory, those below in global
 };
 
 __device__ __forceinline__ unsigned long long* lp(const Levels& L, int lev) {
     unsigned long long* r = L.p[0];
 #pragma unroll
-    for (int q = 1; q < kMaxLevels; ++q) r = lev == q ? L.p[q] : r;
+    for (int q = 1; q < kRelaxLevels; ++q) r = lev == q ? L.p[q] : r;
     return r;
 }
 
 __device__ __forceinline__ int64_t ln(const Levels& L, int lev) {
     int32_t r = L.n[0];
 #pragma unroll
-    for (int q = 1; q < kMaxLevels; ++q) r = lev == q ? L.n[q] : r;
+    for (int q = 1; q < kRelaxLevels; ++q) r = lev == q ? L.n[q] : r;
     return r;
 }
 
@@ -92,9 +98,20 @@ __device__ __forceinline__ unsigned long long warp_node(const Inst& I, const Lev
     return warp_max_key(v);
 }
 
-// The largest key other than island w's: w's fellow leaves and, at every level,
-// the siblings of w's ancestor. Warp-wide.
-__device__ unsigned long long runner_up(const Inst& I, const Levels& L, int64_t w) {
+// The top level's nodes, lane + 32 u in tv[u] (0 past its end).
+__device__ __forceinline__ void load_top(const Levels& L, unsigned long long (&tv)[kTopPerLane]) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long* top = lp(L, L.nlev - 1);
+    const int ntop = (int)ln(L, L.nlev - 1);
+#pragma unroll
+    for (int u = 0; u < kTopPerLane; ++u) tv[u] = lane + 32 * u < ntop ? top[lane + 32 * u] : 0ull;
+}
+
+// The largest key other than island w's: w's fellow leaves, at every level below
+// the top the siblings of w's ancestor, and every top node but w's ancestor (from
+// tv, the top as loaded by the caller). Warp-wide.
+__device__ unsigned long long runner_up(const Inst& I, const Levels& L, int64_t w,
+                                        const unsigned long long (&tv)[kTopPerLane]) {
     const int lane = threadIdx.x & 31;
     unsigned long long m = 0ull;
     {
@@ -103,7 +120,7 @@ __device__ unsigned long long runner_up(const Inst& I, const Levels& L, int64_t 
     }
     // every level's load in flight at once (unrolled; the levels are independent)
 #pragma unroll
-    for (int lev = 1; lev < kMaxLevels; ++lev) {
+    for (int lev = 1; lev < kRelaxLevels; ++lev) {
         const int64_t anc = w >> (5 * lev);
         const int64_t c = ((anc >> 5) << 5) + lane;
         if (lev < L.nlev && c != anc && c < L.n[lev - 1]) {
@@ -111,13 +128,18 @@ __device__ unsigned long long runner_up(const Inst& I, const Levels& L, int64_t 
             m = v > m ? v : m;
         }
     }
+    const int64_t at = w >> (5 * L.nlev);
+#pragma unroll
+    for (int u = 0; u < kTopPerLane; ++u)
+        if (lane + 32 * u != at) m = tv[u] > m ? tv[u] : m;
     return warp_max_key(m);
 }
 
 // An upper bound of every key other than islands w's and r's (r != w): the groups
-// of leaves, and at every level the sibling sets, that hold w's or r's ancestors,
-// less those ancestors. Warp-wide.
-__device__ unsigned long long third_key(const Inst& I, const Levels& L, int64_t w, int64_t r) {
+// of leaves, at every level below the top the sibling sets, and the top, that hold
+// w's or r's ancestors, less those ancestors. Warp-wide.
+__device__ unsigned long long third_key(const Inst& I, const Levels& L, int64_t w, int64_t r,
+                                        const unsigned long long (&tv)[kTopPerLane]) {
     const int lane = threadIdx.x & 31;
     unsigned long long m = 0ull;
     {
@@ -129,7 +151,7 @@ __device__ unsigned long long third_key(const Inst& I, const Levels& L, int64_t 
         }
     }
 #pragma unroll
-    for (int lev = 1; lev < kMaxLevels; ++lev) {
+    for (int lev = 1; lev < kRelaxLevels; ++lev) {
         if (lev >= L.nlev) break;
         const int64_t aw = w >> (5 * lev), ar = r >> (5 * lev);
         const int64_t c = ((aw >> 5) << 5) + lane, c2 = ((ar >> 5) << 5) + lane;
@@ -143,6 +165,10 @@ __device__ unsigned long long third_key(const Inst& I, const Levels& L, int64_t 
             m = v > m ? v : m;
         }
     }
+    const int64_t tw = w >> (5 * L.nlev), tr = r >> (5 * L.nlev);
+#pragma unroll
+    for (int u = 0; u < kTopPerLane; ++u)
+        if (lane + 32 * u != tw && lane + 32 * u != tr) m = tv[u] > m ? tv[u] : m;
     return warp_max_key(m);
 }
 
@@ -476,10 +502,22 @@ __device__ int64_t recheck_warp(const Inst& I, const Levels& L, RecheckShared& R
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const unsigned long long tkey = (unsigned long long)__float_as_uint(tau) << 32;
-    // descent from the root through every node whose maximum reaches tau
-    if (lane == 0) R.front[0][0] = 0;
-    __syncwarp();
-    int cur = 0, nf = 1;
+    // descent from the top through every node whose maximum reaches tau
+    int cur = 0, nf = 0;
+    {
+        unsigned long long tv[kTopPerLane];
+        load_top(L, tv);
+#pragma unroll
+        for (int u = 0; u < kTopPerLane; ++u) {
+            const bool hit = tv[u] != 0ull && tv[u] >= tkey;
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            const int pos = nf + __popc(m & lt);
+            if (hit && pos < kRecheckCap) R.front[0][pos] = lane + 32 * u;
+            nf += __popc(m);
+        }
+        __syncwarp();
+        if (nf > kRecheckCap) return -3;
+    }
     for (int lev = L.nlev - 1; lev >= 0; --lev) {
         const unsigned long long* src = lev > 0 ? lp(L, lev - 1) : I.key32;
         const int64_t lim = lev > 0 ? ln(L, lev - 1) : I.n;
@@ -685,7 +723,12 @@ __device__ int64_t pick_warp(const Inst& I, const Levels& L, RecheckShared& R, D
     *ru_out = ~0ull;
     *clean = true;
     for (int guard = 0; guard < 4 * kRecheckCap + 64; ++guard) {
-        const unsigned long long root = lp(L, L.nlev - 1)[0];
+        unsigned long long tv[kTopPerLane];
+        load_top(L, tv);
+        unsigned long long tm = tv[0];
+#pragma unroll
+        for (int u = 1; u < kTopPerLane; ++u) tm = tv[u] > tm ? tv[u] : tm;
+        const unsigned long long root = warp_max_key(tm);
         if (root == 0ull) return kPickNone;
         const int64_t w = key32_idx(root);
         unsigned long long kw = 0ull;
@@ -698,7 +741,7 @@ __device__ int64_t pick_warp(const Inst& I, const Levels& L, RecheckShared& R, D
             *a0 = (int64_t)r.rowq << 2;
             *a1 = *a0 + ((int64_t)r.rowlenq << 2);
         }
-        const unsigned long long ru = runner_up(I, L, w);
+        const unsigned long long ru = runner_up(I, L, w, tv);
         kw = __shfl_sync(0xffffffffu, kw, 0);
         lo = __shfl_sync(0xffffffffu, lo, 0);
         if (kw != root) {  // a lowered key still held by its ancestors
@@ -717,7 +760,7 @@ __device__ int64_t pick_warp(const Inst& I, const Levels& L, RecheckShared& R, D
             // When no key but w's and the runner-up's reaches tau, those two alone are
             // compared exactly (no descent through the tree).
             const int64_t r = key32_idx(ru);
-            const unsigned long long k3 = third_key(I, L, w, r);
+            const unsigned long long k3 = third_key(I, L, w, r, tv);
             if (k3 < ((unsigned long long)__float_as_uint(tau) << 32)) {
                 *clean = false;
                 if (lane == 0) atomicAdd((unsigned long long*)&st->rechecks, 1ull);
@@ -771,29 +814,36 @@ __global__ void __launch_bounds__(kT, MINB)
     const uint32_t step = I.step0 + (uint32_t)t;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 
-    // Place the upper tree levels in shared memory while they fit.
+    // The levels up to the top (the first with at most kRelaxTopNodes nodes); the
+    // upper ones in shared memory while they fit.
+    int nl = 1;
+    while (nl < I.nlev && I.lvl_n[nl - 1] > kRelaxTopNodes) ++nl;
+    if (nl > kRelaxLevels) {  // (more islands than the indices allow; not reached)
+        if (threadIdx.x == 0) st->status = ST_BOUNDS;
+        return;
+    }
     Levels L;
     {
         int64_t used = 0;
-        int first_sm = I.nlev;
-        for (int lev = I.nlev - 1; lev >= 0; --lev) {
+        int first_sm = nl;
+        for (int lev = nl - 1; lev >= 0; --lev) {
             const int64_t b = (int64_t)I.lvl_n[lev] * (int64_t)sizeof(unsigned long long);
             if (used + b > smem_levels) break;
             used += b;
             first_sm = lev;
         }
         L.first_sm = first_sm;
-        L.nlev = I.nlev;
+        L.nlev = nl;
         // (static indices only: the descriptor stays in registers)
         int64_t off = 0;
 #pragma unroll
-        for (int lev = kMaxLevels - 1; lev >= 0; --lev) {
-            L.n[lev] = lev < I.nlev ? I.lvl_n[lev] : 0;
-            if (lev < I.nlev && lev >= first_sm) {
+        for (int lev = kRelaxLevels - 1; lev >= 0; --lev) {
+            L.n[lev] = lev < nl ? I.lvl_n[lev] : 0;
+            if (lev < nl && lev >= first_sm) {
                 L.p[lev] = sm_levels + off;
                 off += I.lvl_n[lev];
             } else {
-                L.p[lev] = lev < I.nlev ? I.tree + I.lvl_off[lev] : nullptr;
+                L.p[lev] = lev < nl ? I.tree + I.lvl_off[lev] : nullptr;
             }
         }
         for (int lev = first_sm; lev < L.nlev; ++lev)
