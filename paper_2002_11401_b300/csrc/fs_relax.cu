@@ -46,6 +46,9 @@ namespace {
 constexpr int kT = 256;  // threads per relax CTA
 constexpr int kNW = kT / 32;
 constexpr int kDirtyCap = kMaxPaddedDegree + 8;
+// Thread that folds each flip into the sequence hash, during the commit phase (off
+// warp 0's chain; it holds no update unless a row has kT - 34 entries).
+constexpr int kHashThread = kT - 2;
 // Levels the relax keeps: fewer than 2^31 islands need at most five (the fifth
 // has at most 64 nodes).
 constexpr int kRelaxLevels = 5;
@@ -667,15 +670,18 @@ __device__ int64_t recheck_scan(const Inst& I, const Levels& L, RecheckShared& R
 // Exact comparison of islands w and r when no other key reaches tau <= x(w) (the
 // caller has checked): the exact best of the two is the pick. Both get keys from
 // their exact values (lowered; their first-level nodes queued for the repair when
-// they held the old key). Warp-wide; returns the pick with its spin and row.
+// they held the old key). Warp-wide; returns the pick with its spin and row, and
+// the other one's new key in *kother.
 template <int PREC>
 __device__ int64_t pair_compare(const Inst& I, const Levels& L, Dirty& D, int64_t w, int64_t r,
                                 unsigned long long kw, unsigned long long kr, uint32_t step,
-                                int* sk, int64_t* a0, int64_t* a1) {
+                                int* sk, int64_t* a0, int64_t* a1,
+                                unsigned long long* kother) {
     const int lane = threadIdx.x & 31;
     double v = 0.0;
     int si = 0;
     int64_t r0 = 0, r1 = 0;
+    unsigned long long nk = 0ull;
     if (lane < 2) {
         const int64_t i = lane == 0 ? w : r;
         const unsigned long long old = lane == 0 ? kw : kr;
@@ -684,7 +690,7 @@ __device__ int64_t pair_compare(const Inst& I, const Levels& L, Dirty& D, int64_
         r0 = (int64_t)rc.rowq << 2;
         r1 = r0 + ((int64_t)rc.rowlenq << 2);
         v = exact_value<PREC>(I, i, step);
-        const unsigned long long nk = v > 0.0 ? key32_of(__double2float_ru(v), i) : 0ull;
+        nk = v > 0.0 ? key32_of(__double2float_ru(v), i) : 0ull;
         I.key32[i] = nk;
         I.rec[i].lo = v > 0.0 ? __double2float_rd(v) : -1.0f;
         if (nk < old && lp(L, 0)[i >> 5] == old) {
@@ -699,6 +705,7 @@ __device__ int64_t pair_compare(const Inst& I, const Levels& L, Dirty& D, int64_
     *sk = __shfl_sync(0xffffffffu, si, src);
     *a0 = __shfl_sync(0xffffffffu, r0, src);
     *a1 = __shfl_sync(0xffffffffu, r1, src);
+    *kother = __shfl_sync(0xffffffffu, nk, src ^ 1);
     __syncwarp();
     return src == 1 ? r : w;
 }
@@ -713,8 +720,10 @@ constexpr int64_t kPickMaxFlips = -6;  // flip budget of the step spent
 // key; takes w when its certified lower bound exceeds one and that key's upper
 // bound, else compares the contenders exactly. On return lane 0 holds the pick's
 // spin and row, `ru` the largest key other than the pick's when it was certified
-// from bounds (all ones otherwise), and `clean` whether no key changed on the way
-// (no exact comparison ran).
+// from bounds, or after an exact comparison of two the larger of the other one's
+// new key and the third key (the next pick's likeliest island; all ones after a
+// wider comparison), and `clean` whether no key changed on the way (no exact
+// comparison ran).
 template <int PREC>
 __device__ int64_t pick_warp(const Inst& I, const Levels& L, RecheckShared& R, Dirty& D,
                              InstState* st, uint32_t step, int* sk, int64_t* a0, int64_t* a1,
@@ -764,7 +773,10 @@ __device__ int64_t pick_warp(const Inst& I, const Levels& L, RecheckShared& R, D
             if (k3 < ((unsigned long long)__float_as_uint(tau) << 32)) {
                 *clean = false;
                 if (lane == 0) atomicAdd((unsigned long long*)&st->rechecks, 1ull);
-                return pair_compare<PREC>(I, L, D, w, r, kw, ru, step, sk, a0, a1);
+                unsigned long long ko;
+                const int64_t k = pair_compare<PREC>(I, L, D, w, r, kw, ru, step, sk, a0, a1, &ko);
+                *ru_out = ko > k3 ? ko : k3;
+                return k;
             }
         }
         int64_t k = -2;
@@ -859,12 +871,12 @@ __global__ void __launch_bounds__(kT, MINB)
 
     int64_t flips = 0;
     int32_t status = ST_OK;
-    uint64_t hash = threadIdx.x == 0 ? st->hash : 0ull;
+    uint64_t hash = threadIdx.x == kHashThread ? st->hash : 0ull;
     const int64_t flips_before = threadIdx.x == 0 ? st->n_flips : 0;
     const int64_t max_flips = I.max_flips;
     int par = 0;  // parity of the flip whose neighbour updates ran last
 
-    // Thread 0: flip island k, log it, fold it into the hash, publish its row.
+    // Thread 0: flip island k, log it, publish its row.
     auto do_flip = [&](int64_t k, int sk, int64_t a0, int64_t a1) {
         const int snew = -sk;
         I.s[k] = (int8_t)snew;
@@ -877,7 +889,6 @@ __global__ void __launch_bounds__(kT, MINB)
             I.log_step[q] = step;
             I.log_spin[q] = (uint32_t)k;
         }
-        hash = fnv_flip(hash, step, (uint32_t)k);
     };
 
     for (;;) {
@@ -980,14 +991,24 @@ __global__ void __launch_bounds__(kT, MINB)
         if (k < 0) break;
         ++flips;
         par ^= 1;
+        if (threadIdx.x == kHashThread) hash = fnv_flip(hash, step, (uint32_t)k);
         // every neighbour i of k: add 2 s_k(new) (P_ik, Q_ik), new key, tree update
         const int snew = sh_snew;
         const unsigned long long ru = sh_ru;
-        bool use_spec = k == pred && sh_clean != 0 && sh_spec_len < kT - 32;
+        // An exact comparison during the pick changes keys, bounds and kept values,
+        // never sums or spins; without thermal noise it writes nothing else the
+        // speculating warps read (with it, kept FP64 draws, which they may read while
+        // they are written), so their updates stay valid once each takes its island's
+        // current key as the old one.
+        const bool clean = sh_clean != 0;
+        bool use_spec = k == pred && (clean || I.sigma == 0.0) && sh_spec_len < kT - 32;
 #pragma unroll
         for (int w = 1; w < kNW; ++w) use_spec = use_spec && sh_spec_snew[w] == snew;
         if (use_spec) {
-            if (spec.i >= 0) commit_update<PREC>(I, L, D, P, par, spec, spec.i == k ? ~0ull : ru);
+            if (spec.i >= 0) {
+                if (!clean) spec.old = I.key32[spec.i];
+                commit_update<PREC>(I, L, D, P, par, spec, spec.i == k ? ~0ull : ru);
+            }
         } else {
             const int64_t e0 = sh_e0;
             const int len = (int)(sh_e1 - e0);
@@ -1016,11 +1037,11 @@ __global__ void __launch_bounds__(kT, MINB)
         if (threadIdx.x == 0 && ru != ~0ull && ru != 0ull) atomicMax(&P.best[par], ru);
         __syncthreads();
     }
+    if (threadIdx.x == kHashThread) st->hash = hash;
     __syncthreads();
     if (threadIdx.x == 0) {
         if (I.flips_per_step) I.flips_per_step[t] = flips;
         st->n_flips = flips_before + flips;
-        st->hash = hash;
         if (status != ST_OK) st->status = status;
         st->init = 0;
         st->t = t + 1;
