@@ -191,9 +191,11 @@ __device__ __forceinline__ void leaf_changed(const Inst& I, const Levels& L, Dir
                                              unsigned long long old, unsigned long long nk) {
     if (nk > old) {
         int64_t node = i;
-        for (int lev = 0; lev < L.nlev; ++lev) {
+#pragma unroll
+        for (int lev = 0; lev < kRelaxLevels; ++lev) {  // (compile-time level indices)
+            if (lev >= L.nlev) break;
             node >>= 5;
-            unsigned long long* a = lp(L, lev) + node;
+            unsigned long long* a = L.p[lev] + node;
             if (lev >= L.first_sm) {  // shared-memory instructions, not generic ones
                 const unsigned sa = (unsigned)__cvta_generic_to_shared(a);
                 unsigned long long cur;
@@ -256,14 +258,17 @@ __device__ void repair_warp(const Inst& I, const Levels& L, Dirty& D) {
     }
     int nn = min(nout, kDirtyCap);
     __syncwarp();
-    for (int lev = 1; lev < L.nlev && nn > 0; ++lev) {
+#pragma unroll
+    for (int lev = 1; lev < kRelaxLevels; ++lev) {  // (compile-time level indices)
+        if (lev >= L.nlev || nn <= 0) break;
         const int32_t* qin = D.up[lev & 1];
         qout = D.up[(lev + 1) & 1];
-        const int64_t nchild = ln(L, lev - 1);
+        const int64_t nchild = L.n[lev - 1];
         nout = 0;
-        unsigned long long* const here = lp(L, lev);
-        const unsigned long long* const below = lp(L, lev - 1);
-        unsigned long long* const above = lev + 1 < L.nlev ? lp(L, lev + 1) : nullptr;
+        unsigned long long* const here = L.p[lev];
+        const unsigned long long* const below = L.p[lev - 1];
+        unsigned long long* const above =
+            lev + 1 < kRelaxLevels && lev + 1 < L.nlev ? L.p[lev + 1 < kRelaxLevels ? lev + 1 : lev] : nullptr;
         for (int q = 0; q < nn; ++q) {
             const int64_t node = qin[q];
             const int64_t c = (node << 5) + lane;
