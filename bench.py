@@ -299,10 +299,11 @@ def main():
     fp32 = prec == B.FS_FP32_RECHECK
     # per flip and neighbour: the row entry (column, P and transposed Q; both
     # widths on the FP32 path), the neighbour's state read (exact sums, 32-bit sums,
-    # key, spin, angle class, 1/(b h_k) and 1/(c h_k) or h_k, row pointers for the
-    # next-pick prediction) and written back (sums, key, lower bound, exact value)
+    # key, spin, angle class, 1/(b h_k) and 1/(c h_k) in FP32 (8 B) or FP64 (16 B),
+    # row pointers for the next-pick prediction) and written back (sums, key, lower
+    # bound, exact value)
     per_nb = (4 + 4 + 4 + 8 + 8) + (16 + 8 + 8 + 1 + 2 + 8 + 16) + (16 + 8 + 8 + 8 + 4) \
-        if fp32 else (4 + 8 + 8) + (16 + 8 + 1 + 2 + 8 + 8 + 16) + (16 + 8 + 8 + 4)
+        if fp32 else (4 + 8 + 8) + (16 + 8 + 1 + 2 + 16 + 8 + 16) + (16 + 8 + 8 + 4)
     relax_bytes = flips_per_protocol * avg_deg * per_nb * args.steps
     relax_s = prof["relax_ms"] / 1000.0
     sweep_unit = sweep_bytes(n, nnz, fp32, bool(args.resweep), w["sigma_th"] > 0)

@@ -190,14 +190,16 @@ extern "C" fs_status fs_set_stream(fs_sim* sim, void* stream) {
 
 static bool bad_double(double v) { return !std::isfinite(v); }
 
-// Per-island scales of the FP32 evaluation: 1 / (b h_k) and 1 / (c h_k) in double,
-// each rounded once to FP32.
+// Per-island scales of the evaluations: 1 / (b h_k) and 1 / (c h_k) in double (the
+// FP64 astroid's), each rounded once more to FP32 (the FP32 one's).
 static void fill_rbc(fs_sim* sim) {
     sim->rbc32.resize((size_t)sim->n);
+    sim->rbc64.resize((size_t)sim->n);
     for (int64_t i = 0; i < sim->n; ++i) {
         const double h = sim->hk[(size_t)i];
-        sim->rbc32[(size_t)i] = make_float2((float)(1.0 / (sim->p.b * h)),
-                                            (float)(1.0 / (sim->p.c * h)));
+        const double rb = 1.0 / (sim->p.b * h), rc = 1.0 / (sim->p.c * h);
+        sim->rbc64[(size_t)i] = make_double2(rb, rc);
+        sim->rbc32[(size_t)i] = make_float2((float)rb, (float)rc);
     }
 }
 
@@ -346,13 +348,13 @@ fs_status fs_build_sim(fs_sim* sim) {
 
     // islands
     int8_t* s = nullptr;
-    double* hk64 = nullptr;
+    double2* rbc64 = nullptr;
     float2* rbc32 = nullptr;
     uint16_t* cls = nullptr;
     double2* c64 = nullptr;
     float2* c32 = nullptr;
     CK(palloc((void**)&s, n), "alloc");
-    CK(palloc((void**)&hk64, 8 * n), "alloc");
+    CK(palloc((void**)&rbc64, 16 * n), "alloc");
     CK(palloc((void**)&rbc32, 8 * n), "alloc");
     CK(palloc((void**)&cls, 2 * n), "alloc");
     CK(palloc((void**)&c64, 16 * ncls), "alloc");
@@ -365,7 +367,7 @@ fs_status fs_build_sim(fs_sim* sim) {
     CK(cudaMemcpyAsync(c64, cs64.data(), 16 * ncls, cudaMemcpyHostToDevice, st), "upload");
     CK(cudaMemcpyAsync(c32, cs32.data(), 8 * ncls, cudaMemcpyHostToDevice, st), "upload");
     I.s = s;
-    I.hk64 = hk64;
+    I.rbc64 = rbc64;
     I.rbc32 = rbc32;
     I.cls = cls;
     I.cs64 = c64;
@@ -452,8 +454,8 @@ fs_status fs_build_sim(fs_sim* sim) {
     sim->lanes = choose_lanes((double)nnzp / (double)n / 4.0);
 
     // coercive fields
-    CK(cudaMemcpyAsync(hk64, sim->hk.data(), 8 * n, cudaMemcpyHostToDevice, st), "upload");
     fill_rbc(sim);
+    CK(cudaMemcpyAsync(rbc64, sim->rbc64.data(), 16 * n, cudaMemcpyHostToDevice, st), "upload");
     CK(cudaMemcpyAsync(rbc32, sim->rbc32.data(), 8 * n, cudaMemcpyHostToDevice, st), "upload");
     CK(cudaMemcpyAsync(sim->d_inst, &I, sizeof(Inst), cudaMemcpyHostToDevice, st), "upload");
     tmp.release(st);
@@ -495,7 +497,7 @@ extern "C" fs_status fs_set_hk(fs_sim* sim, const double* hk, int64_t n) {
             return fail(sim, FS_ERR_INVALID, "hk values must be positive and finite");
     sim->hk.assign(hk, hk + n);
     fill_rbc(sim);
-    CK(cudaMemcpyAsync((void*)sim->inst.hk64, sim->hk.data(), 8 * n, cudaMemcpyHostToDevice,
+    CK(cudaMemcpyAsync((void*)sim->inst.rbc64, sim->rbc64.data(), 16 * n, cudaMemcpyHostToDevice,
                        sim->stream),
        "upload");
     CK(cudaMemcpyAsync((void*)sim->inst.rbc32, sim->rbc32.data(), 8 * n, cudaMemcpyHostToDevice,

@@ -76,8 +76,8 @@ struct Inst {
     const int* qt32;
     // islands
     int8_t* s;
-    const double* hk64;
-    const float2* rbc32;    // (1 / (b h_k), 1 / (c h_k)) per island, FP32
+    const double2* rbc64;   // (1 / (b h_k), 1 / (c h_k)) per island, FP64
+    const float2* rbc32;    // the same, FP32
     const uint16_t* cls;    // angle class
     const double2* cs64;    // (cos, sin) per class
     const float2* cs32;
@@ -302,13 +302,16 @@ struct Eval64 {
     bool flippable;
 };
 
+// rb: the island's (1 / (b h_k), 1 / (c h_k)) in FP64, so that the astroid's
+// arguments take a product where a quotient would cost a division (a long FP64
+// sequence on this GPU); each differs from the quotient by at most one rounding.
 __device__ __forceinline__ Eval64 eval64(const Inst& I, int s, long long dp, long long dq,
-                                         double hk, double2 ext, double tp, double tq) {
+                                         double2 rb, double2 ext, double tp, double tq) {
     Eval64 e;
     e.hpar = __dadd_rn(__dadd_rn(__dmul_rn((double)dp, I.inv64), ext.x), tp);
     e.hperp = __dadd_rn(__dadd_rn(__dmul_rn((double)dq, I.inv64), ext.y), tq);
-    const double x = __ddiv_rn(fabs(e.hpar), __dmul_rn(I.b, hk));
-    const double y = __ddiv_rn(fabs(e.hperp), __dmul_rn(I.c, hk));
+    const double x = __dmul_rn(fabs(e.hpar), rb.x);
+    const double y = __dmul_rn(fabs(e.hperp), rb.y);
     e.lhs = __dadd_rn(pow_pos(x, I.pexp), pow_pos(y, I.qexp));
     e.flippable = ((double)s * e.hpar < 0.0) && (e.lhs > 1.0);
     return e;

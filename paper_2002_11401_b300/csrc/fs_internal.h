@@ -40,6 +40,7 @@ struct fs_sim {
     fs_params p{};
     std::vector<double> hk;
     std::vector<float2> rbc32;
+    std::vector<double2> rbc64;
     bool built = false;
     bool fields_valid = false;
     // current external field and thermal step

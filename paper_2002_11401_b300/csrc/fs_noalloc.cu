@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kThreads)
         double tp = 0.0, tq = 0.0;
         if (I.sigma > 0.0) thermal64(I, i, step, &tp, &tq);
         const uint16_t ci = I.cls[i];
-        const Eval64 e = eval64(I, s[i], sums[wib][lane][0], sums[wib][lane][1], I.hk64[i],
+        const Eval64 e = eval64(I, s[i], sums[wib][lane][0], sums[wib][lane][1], I.rbc64[i],
                                 ext_proj(hx, hy, I.cs64[ci]), tp, tq);
         const double key = e.flippable ? e.lhs : 0.0;
         lhs_out[i] = key;

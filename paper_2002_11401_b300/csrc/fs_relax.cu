@@ -311,7 +311,7 @@ template <int PREC, bool KEEP>
 __device__ __forceinline__ unsigned long long key_of(const Inst& I, int64_t i, uint32_t step,
                                                      int si, uint16_t ci, longlong2 h64, int2 h32,
                                                      float2 rbc, float2 e32, float2 th,
-                                                     double hk, double2 e64, float* lo,
+                                                     double2 rb64, double2 e64, float* lo,
                                                      double* x64) {
     if constexpr (PREC == 1) {
         const float dp = __fmul_rn(__int2float_rn(h32.x), I.inv32);
@@ -322,7 +322,7 @@ __device__ __forceinline__ unsigned long long key_of(const Inst& I, int64_t i, u
             double tp = 0.0, tq = 0.0;
             if (I.sigma > 0.0) thermal64_at<KEEP>(I, i, step, &tp, &tq);
             const Eval64 f =
-                eval64(I, si, h64.x, h64.y, __ldg(&I.hk64[i]), __ldg(&I.ext64[ci]), tp, tq);
+                eval64(I, si, h64.x, h64.y, __ldg(&I.rbc64[i]), __ldg(&I.ext64[ci]), tp, tq);
             const double x = f.flippable ? f.lhs : 0.0;
             *x64 = x;
             *lo = x > 0.0 ? __double2float_rd(x) : -1.0f;
@@ -339,7 +339,7 @@ __device__ __forceinline__ unsigned long long key_of(const Inst& I, int64_t i, u
         if (e.possible) {
             double tp = 0.0, tq = 0.0;
             if (I.sigma > 0.0) thermal64_at<KEEP>(I, i, step, &tp, &tq);
-            const Eval64 f = eval64(I, si, h64.x, h64.y, hk, e64, tp, tq);
+            const Eval64 f = eval64(I, si, h64.x, h64.y, rb64, e64, tp, tq);
             if (f.flippable) x = f.lhs;
         }
         *x64 = x;
@@ -412,10 +412,10 @@ __device__ __forceinline__ Upd compute_update(const Inst& I, int64_t i, int snew
     if (I.sigma > 0.0) th = I.th32[i];
     u.r0 = (int64_t)r.rowq << 2;
     u.r1 = u.r0 + ((int64_t)r.rowlenq << 2);
-    double hk = 0.0;
+    double2 rb64 = make_double2(0.0, 0.0);
     double2 e64 = make_double2(0.0, 0.0);
     if constexpr (PREC == 0) {
-        hk = __ldg(&I.hk64[i]);
+        rb64 = __ldg(&I.rbc64[i]);
         e64 = __ldg(&I.ext64[ci]);
     }
     const float2 e32 = __ldg(&I.ext32[ci]);
@@ -431,7 +431,7 @@ __device__ __forceinline__ Upd compute_update(const Inst& I, int64_t i, int snew
     u.h = h;
     u.g = g;
     u.x = 0.0;
-    u.nk = key_of<PREC, KEEP>(I, i, step, si, ci, h, g, rbc, e32, th, hk, e64, &u.lo, &u.x);
+    u.nk = key_of<PREC, KEEP>(I, i, step, si, ci, h, g, rbc, e32, th, rb64, e64, &u.lo, &u.x);
     return u;
 }
 
@@ -463,12 +463,12 @@ __device__ __forceinline__ double exact_value(const Inst& I, int64_t i, uint32_t
         const longlong2 h = I.h64[i];
         const IslandRec r = rec_load(I, i);
         const int si = r.s;
-        const double hk = __ldg(&I.hk64[i]);
+        const double2 rb64 = __ldg(&I.rbc64[i]);
         const uint16_t ci = r.cls;
         if (kept >= 0.0) return kept;
         double tp = 0.0, tq = 0.0;
         if (I.sigma > 0.0) thermal64_kept(I, i, step, &tp, &tq);
-        const Eval64 e = eval64(I, si, h.x, h.y, hk, __ldg(&I.ext64[ci]), tp, tq);
+        const Eval64 e = eval64(I, si, h.x, h.y, rb64, __ldg(&I.ext64[ci]), tp, tq);
         const double v = e.flippable ? e.lhs : 0.0;
         I.key64[i] = v;
         return v;
@@ -1083,7 +1083,7 @@ __global__ void k_eval_all(const Inst* __restrict__ tab, double hx, double hy, u
         const longlong2 h = I.h64[i];
         double tp = 0.0, tq = 0.0;
         if (I.sigma > 0.0) thermal64(I, i, step, &tp, &tq);
-        const Eval64 e = eval64(I, si, h.x, h.y, I.hk64[i], ext, tp, tq);
+        const Eval64 e = eval64(I, si, h.x, h.y, I.rbc64[i], ext, tp, tq);
         hpar[i] = e.hpar;
         hperp[i] = e.hperp;
         lhs[i] = e.lhs;

@@ -54,7 +54,7 @@ struct Job {
     cudaGraphExec_t exec = nullptr;  // the request's whole protocol, one launch
 };
 
-// Device bytes of one request before it is built: per island ~148 B of state
+// Device bytes of one request before it is built: per island ~156 B of state
 // and, per neighbour pair, the CSR entry and both coefficient widths with their
 // transposed copies (40 B); the degree is the cutoff disc's area times the array's
 // island density, plus a margin for the rounding of the rows to multiples of 4.
@@ -68,7 +68,7 @@ size_t estimate_bytes(const fs_request& r) {
     const double n = islands_of(r);
     const double density = r.kind == FS_KAGOME ? 3.0 / (1.5 * std::sqrt(3.0)) : 2.0;
     const double deg = 1.05 * M_PI * rc * rc * density + 8.0;
-    return (size_t)(n * (deg * 40.0 + 148.0) + 16.0 * r.K + (1 << 20));
+    return (size_t)(n * (deg * 40.0 + 156.0) + 16.0 * r.K + (1 << 20));
 }
 
 // Admission order: a request that has waited longer than kAgeS goes first (oldest

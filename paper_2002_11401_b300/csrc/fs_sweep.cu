@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kSweepThreads, OCC)
             if (e.possible && !e.certain) {
                 // within its band of the threshold or of the sign change: FP64 now
                 if (!SUM64) h64 = I.h64[i];
-                const Eval64 f = eval64(I, si, h64.x, h64.y, I.hk64[i], I.ext64[ci], tp, tq);
+                const Eval64 f = eval64(I, si, h64.x, h64.y, I.rbc64[i], I.ext64[ci], tp, tq);
                 x = f.flippable ? f.lhs : 0.0;
                 node = x > 0.0 ? key32_of(__double2float_ru(x), i) : 0ull;
                 lo = x > 0.0 ? __double2float_rd(x) : -1.0f;
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(kSweepThreads, OCC)
             if (e.possible) {
                 double tp = 0.0, tq = 0.0;
                 if (I.sigma > 0.0) thermal64_kept(I, i, step, &tp, &tq);
-                const Eval64 f = eval64(I, si, h64.x, h64.y, I.hk64[i], I.ext64[ci], tp, tq);
+                const Eval64 f = eval64(I, si, h64.x, h64.y, I.rbc64[i], I.ext64[ci], tp, tq);
                 if (f.flippable) x = f.lhs;
             }
             I.key64[i] = x;

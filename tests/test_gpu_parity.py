@@ -92,6 +92,30 @@ def test_fields_match_oracle(B, oracle, prec, tol, kind, n, sigma):
         assert np.abs(lhs - olhs).max() <= (1e-11 if prec == FP64 else 1e-4) * olhs.max()
 
 
+@pytest.mark.parametrize("kind,n", [(I.PINWHEEL, 9), (I.KAGOME, 9)])
+def test_fp64_astroid_within_a_few_ulps(B, oracle, kind, n):
+    """Eq. 5 on the FS_FP64 path, taken on the library's own fields so that only the
+    astroid is compared: the oracle's libm pow against the kernels' x^(2/3), within
+    4e-15 relative (a dropped second-order term of its refinement would be ~3e-14)."""
+    w = small(kind, n, alpha=3e-3)
+    sim = lib_sim(w, precision=FP64)
+    S = oracle_sim(oracle, w)
+    checked = 0
+    for trial in range(6):
+        s = I.random_spins(S.n, 300 + trial)
+        hx, hy = 0.3 * math.cos(trial), 0.25 * math.sin(2 * trial + 1)
+        sim.set_spins(s)
+        sim.set_field(hx, hy, step=trial)
+        hp, hq = sim.fields()
+        lhs = sim.lhs()
+        for i in range(S.n):
+            o = oracle.astroid_lhs(hp[i], hq[i], S.hk[i], 1, 1, 3, 3)
+            if o > 0.0:
+                assert abs(lhs[i] - o) <= 4e-15 * o, (trial, i, lhs[i], o)
+                checked += 1
+    assert checked > 100
+
+
 # ---------------------------------------------------------------------------
 # Flip sequences (Sec. "Dynamics")
 # ---------------------------------------------------------------------------
