@@ -219,34 +219,41 @@ __device__ __forceinline__ void thermal64(const Inst& I, int64_t i, uint32_t ste
     *tq = __dmul_rn(I.sigma, z1);
 }
 
+// The kept draw of island i for `step`, when there is one. The draw is published
+// after its value (a block-scope fence between the two stores, the step number
+// written and read as a volatile, strong access, and a fence between reading it
+// and reading the value), so that a thread of the same block that sees the step
+// also sees the value written before it, even while another thread keeps a draw.
+__device__ __forceinline__ bool kept_draw(const Inst& I, int64_t i, uint32_t step, double* tp,
+                                          double* tq) {
+    if (*(volatile uint32_t*)&I.th_step[i] != step) return false;
+    __threadfence_block();
+    const double2 v = I.th64[i];
+    *tp = v.x;
+    *tq = v.y;
+    return true;
+}
+
 // thermal64 of island i, drawn once per island and step: the draw is kept with
-// its step number, and later evaluations of the same step reuse it. Callers
-// never evaluate one island from two threads at the same time.
+// its step number, and later evaluations of the same step reuse it. One island
+// is never kept by two threads at the same time; others may read it meanwhile.
 __device__ __forceinline__ void thermal64_kept(const Inst& I, int64_t i, uint32_t step, double* tp,
                                                double* tq) {
-    if (I.th_step[i] == step) {
-        const double2 v = I.th64[i];
-        *tp = v.x;
-        *tq = v.y;
-        return;
-    }
+    if (kept_draw(I, i, step, tp, tq)) return;
     thermal64(I, i, step, tp, tq);
     I.th64[i] = make_double2(*tp, *tq);
-    I.th_step[i] = step;
+    __threadfence_block();
+    *(volatile uint32_t*)&I.th_step[i] = step;
 }
 
 // thermal64 of island i at `step`, kept (KEEP) or only looked up among the kept
-// draws (otherwise drawn afresh without keeping it).
+// draws (otherwise drawn afresh without keeping it; the value is the same).
 template <bool KEEP>
 __device__ __forceinline__ void thermal64_at(const Inst& I, int64_t i, uint32_t step, double* tp,
                                              double* tq) {
     if constexpr (KEEP) {
         thermal64_kept(I, i, step, tp, tq);
-    } else if (I.th_step[i] == step) {
-        const double2 v = I.th64[i];
-        *tp = v.x;
-        *tq = v.y;
-    } else {
+    } else if (!kept_draw(I, i, step, tp, tq)) {
         thermal64(I, i, step, tp, tq);
     }
 }

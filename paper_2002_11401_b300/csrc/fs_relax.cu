@@ -1000,13 +1000,13 @@ __global__ void __launch_bounds__(kT, MINB)
         // every neighbour i of k: add 2 s_k(new) (P_ik, Q_ik), new key, tree update
         const int snew = sh_snew;
         const unsigned long long ru = sh_ru;
-        // An exact comparison during the pick changes keys, bounds and kept values,
-        // never sums or spins; without thermal noise it writes nothing else the
-        // speculating warps read (with it, kept FP64 draws, which they may read while
-        // they are written), so their updates stay valid once each takes its island's
-        // current key as the old one.
+        // An exact comparison during the pick changes keys, bounds, kept values and
+        // kept thermal draws (published so that a concurrent reader sees a whole draw
+        // or none, and a draw is the same value either way), never sums or spins, so
+        // the precomputed updates stay valid once each takes its island's current key
+        // as the old one.
         const bool clean = sh_clean != 0;
-        bool use_spec = k == pred && (clean || I.sigma == 0.0) && sh_spec_len < kT - 32;
+        bool use_spec = k == pred && sh_spec_len < kT - 32;
 #pragma unroll
         for (int w = 1; w < kNW; ++w) use_spec = use_spec && sh_spec_snew[w] == snew;
         if (use_spec) {
