@@ -496,7 +496,8 @@ __device__ void rebuild_path(const Inst& I, const Levels& L, int64_t w) {
 
 // Exact comparison of the islands whose key bound reaches tau, by warp 0 alone.
 // Returns the winner (its exact value is at least tau, so nothing outside the set
-// can beat it) with its spin and row in *sk, *a0, *a1 on every lane; -2 with R.tau
+// can beat it) with its spin and row in *sk, *a0, *a1 on every lane and the largest
+// new key among the other candidates in *next; -2 with R.tau
 // lowered to widen the set; -1 when none of them is flippable; -3 when the set
 // overflowed (nothing changed then). The candidates' keys become their exact
 // values rounded out; the first-level nodes that held a lowered key are queued for
@@ -505,7 +506,8 @@ __device__ void rebuild_path(const Inst& I, const Levels& L, int64_t w) {
 // for the next look at the root.
 template <int PREC>
 __device__ int64_t recheck_warp(const Inst& I, const Levels& L, RecheckShared& R, Dirty& D,
-                                float tau, uint32_t step, int* sk, int64_t* a0, int64_t* a1) {
+                                float tau, uint32_t step, int* sk, int64_t* a0, int64_t* a1,
+                                unsigned long long* next) {
     constexpr int kBatch = 4;  // frontier nodes whose children are loaded together
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -603,6 +605,11 @@ __device__ int64_t recheck_warp(const Inst& I, const Levels& L, RecheckShared& R
         *sk = __shfl_sync(0xffffffffu, bs, src);
         *a0 = __shfl_sync(0xffffffffu, b0, src);
         *a1 = __shfl_sync(0xffffffffu, b1, src);
+        // the largest new key among the other candidates: the next pick's likeliest
+        unsigned long long nx = 0ull;
+        for (int c = lane; c < nc; c += 32)
+            if (R.front[cur][c] != bi && R.new_key[c] > nx) nx = R.new_key[c];
+        *next = warp_max_key(nx);
         return bi;
     }
     if (bi >= 0) {
@@ -726,9 +733,9 @@ constexpr int64_t kPickMaxFlips = -6;  // flip budget of the step spent
 // bound, else compares the contenders exactly. On return lane 0 holds the pick's
 // spin and row, `ru` the largest key other than the pick's when it was certified
 // from bounds, or after an exact comparison of two the larger of the other one's
-// new key and the third key (the next pick's likeliest island; all ones after a
-// wider comparison), and `clean` whether no key changed on the way (no exact
-// comparison ran).
+// new key and the third key, or after a wider comparison the largest new key
+// among its other candidates (the next pick's likeliest island), and `clean`
+// whether no key changed on the way (no exact comparison ran).
 template <int PREC>
 __device__ int64_t pick_warp(const Inst& I, const Levels& L, RecheckShared& R, Dirty& D,
                              InstState* st, uint32_t step, int* sk, int64_t* a0, int64_t* a1,
@@ -785,10 +792,11 @@ __device__ int64_t pick_warp(const Inst& I, const Levels& L, RecheckShared& R, D
             }
         }
         int64_t k = -2;
+        unsigned long long nx = ~0ull;
         for (int rounds = 0; k == -2;) {
             if (++rounds > 64) return kPickBounds;
             *clean = false;
-            k = recheck_warp<PREC>(I, L, R, D, tau, step, sk, a0, a1);
+            k = recheck_warp<PREC>(I, L, R, D, tau, step, sk, a0, a1, &nx);
             if (lane == 0) atomicAdd((unsigned long long*)&st->rechecks, 1ull);
             if (k == -2) tau = R.tau;
         }
@@ -797,6 +805,7 @@ __device__ int64_t pick_warp(const Inst& I, const Levels& L, RecheckShared& R, D
             *tau_out = tau;
             return k;
         }
+        *ru_out = nx;
         return k;
     }
     return kPickBounds;
