@@ -59,13 +59,13 @@ def sweep_bytes(n: int, nnz: int, fp32: bool, resweep: bool, thermal: bool) -> i
 
 
 # DRAM bytes per launch (read + write) of the dominant kernels on this workload, from
-# one ncu capture of every launch of one protocol (profiles/traffic_pinwheel300.md),
+# one ncu capture of every launch of one protocol (summarised with the profiles),
 # with a hash of the kernel sources that were profiled: a changed kernel reports null.
 TRAFFIC = {
-    "k_relax": {"bytes_per_launch": 2.137e6, "sources": ("fs_relax.cu", "fs_common.cuh"),
-                "sha256_16": "edde4ca790c3d61a"},
-    "k_sweep": {"bytes_per_launch": 348.48e6, "sources": ("fs_sweep.cu", "fs_common.cuh"),
-                "sha256_16": "035e7e255877f294"},
+    "k_relax": {"bytes_per_launch": 2.132e6, "sources": ("fs_relax.cu", "fs_common.cuh"),
+                "sha256_16": "88f5cc816b3942dd"},
+    "k_sweep": {"bytes_per_launch": 348.24e6, "sources": ("fs_sweep.cu", "fs_common.cuh"),
+                "sha256_16": "b620db53096b4552"},
 }
 
 
