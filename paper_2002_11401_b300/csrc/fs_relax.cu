@@ -483,7 +483,7 @@ struct RecheckShared {
     float tau;
 };
 
-// Rebuilds every node on island w's path to the root from its children. Warp-wide.
+// Rebuilds every node on island w's path up to the top level from its children. Warp-wide.
 __device__ void rebuild_path(const Inst& I, const Levels& L, int64_t w) {
     int64_t node = w;
     for (int lev = 0; lev < L.nlev; ++lev) {
