@@ -21,7 +21,8 @@
  *     call returns. Device buffers passed to *_dev calls belong to the caller
  *     and must stay valid until the work queued on the simulation's stream ends.
  *   - The library owns every device allocation it makes for a simulation and
- *     frees it in fs_destroy.
+ *     frees it in fs_destroy; a buffer bound with fs_bind_workspace stays the
+ *     caller's.
  *   - Calls are synchronous on the simulation's stream unless named *_dev.
  *   - A fs_sim is not thread-safe; distinct fs_sim objects are independent.
  *   - Island order is the canonical order: ascending y, then ascending x, for
@@ -118,6 +119,34 @@ void fs_destroy(fs_sim* sim);
 
 /* CUDA stream (cudaStream_t) for all later work of `sim`; NULL = legacy default. */
 fs_status fs_set_stream(fs_sim* sim, void* stream);
+
+/* Device bytes fs_set_params(sim, p) would allocate: the simulation's state (the
+ * neighbour tensors of Eq. 3, the island arrays, the relax's records and keys, the
+ * max-tree) plus the build's temporaries, every allocation rounded up to 256
+ * bytes. Exact (fs_set_params checks its allocations against the same plan), for
+ * admission and for sizing a workspace. Runs the build's neighbour count on the
+ * simulation's stream (cell grid and degrees, with temporary pool memory freed
+ * before it returns) and changes nothing in `sim`. Not included: the per-call
+ * buffers of fs_run_protocol (16 B per field step, 8 B more with per-step flip
+ * counts, 8 B per logged flip), which come from the pool.
+ * Errors: FS_ERR_INVALID (NULL argument, a parameter out of range, a
+ * neighbourhood above the degree limit), FS_ERR_OOM, FS_ERR_CUDA. */
+fs_status fs_workspace_bytes(const fs_sim* sim, const fs_params* p, size_t* bytes);
+
+/* Carves the simulation's device state from the caller's buffer (memory a
+ * framework's allocator owns, say) instead of the library's stream-ordered pool.
+ * dev_ptr: device or managed memory, 256-byte aligned, `bytes` long; the state
+ * takes the buffer's bottom, the build's temporaries its top while fs_set_params
+ * runs (fs_workspace_bytes gives the need of a parameter set). The caller keeps
+ * the buffer alive and otherwise unused until fs_destroy or the next bind; the
+ * library never frees it. dev_ptr NULL returns to the pool. cuda_stream, when not
+ * NULL, becomes the simulation's stream (as fs_set_stream). Call before
+ * fs_set_params; a build that does not fit returns FS_ERR_OOM (after the work it
+ * queued has ended) and leaves the simulation without parameters, to be bound
+ * again. Per-call buffers still come from the pool.
+ * Errors: FS_ERR_INVALID (NULL sim; a misaligned or non-device pointer),
+ * FS_ERR_STATE (parameters already set). */
+fs_status fs_bind_workspace(fs_sim* sim, void* dev_ptr, size_t bytes, void* cuda_stream);
 
 /* Sets the parameters, draws h_k^(i) (Philox4x32-10 counter (i, r, instance, 0),
  * Box-Muller, redrawn while <= 0; Sec. "Imperfections and disorder") and builds

@@ -28,6 +28,7 @@ EXPORTS = (
     "fs_server_create", "fs_server_submit", "fs_server_poll", "fs_server_drain",
     "fs_server_now", "fs_server_destroy", "fs_server_last_error", "fs_set_spins_dev",
     "fs_set_profiling", "fs_get_profile", "fs_eval_argmax_static", "fs_autotune",
+    "fs_workspace_bytes", "fs_bind_workspace",
 )
 
 
@@ -119,6 +120,8 @@ def load():
             "fs_get_profile": ([P, P], i32),
             "fs_eval_argmax_static": ([P, P, dbl, dbl, u32, P, P, P], i32),
             "fs_autotune": ([P, P], i32),
+            "fs_workspace_bytes": ([P, P, P], i32),
+            "fs_bind_workspace": ([P, P, C.c_size_t, P], i32),
         }
         for name, (args, res) in sig.items():
             if not hasattr(lib, name):
@@ -196,6 +199,18 @@ class Sim:
 
     def set_params(self, params: fs_params):
         self._check(self._lib.fs_set_params(self._h, C.byref(params)))
+
+    def workspace_bytes(self, params: fs_params) -> int:
+        """Device bytes set_params(params) would allocate (state + build temporaries)."""
+        out = C.c_size_t(0)
+        self._check(self._lib.fs_workspace_bytes(self._h, C.byref(params), C.byref(out)))
+        return out.value
+
+    def bind_workspace(self, dev_ptr: int, nbytes: int, stream_ptr: int = 0):
+        """Carves the state from a caller-owned device buffer (0: the library's pool)."""
+        self._check(self._lib.fs_bind_workspace(self._h, C.c_void_p(dev_ptr or None),
+                                                 C.c_size_t(nbytes),
+                                                 C.c_void_p(stream_ptr or None)))
 
     def set_hk(self, hk):
         hk = np.ascontiguousarray(hk, dtype=np.float64)

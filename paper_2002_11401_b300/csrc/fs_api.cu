@@ -36,6 +36,7 @@ namespace fs {
 void Arena::release(cudaStream_t st) {
     for (void* p : blocks) cudaFreeAsync(p, st);
     blocks.clear();
+    if (ws) (top ? ws->hi : ws->lo) = 0;
     bytes = 0;
 }
 
@@ -43,6 +44,18 @@ cudaError_t Arena::alloc(void** out, size_t n, cudaStream_t st) {
     *out = nullptr;
     if (n == 0) n = 16;
     n = (n + 255) & ~(size_t)255;
+    if (ws) {  // carved from the caller's buffer (its base and size are 256-aligned)
+        if (ws->lo + ws->hi + n > ws->cap) return cudaErrorMemoryAllocation;
+        if (top) {
+            ws->hi += n;
+            *out = ws->base + (ws->cap - ws->hi);
+        } else {
+            *out = ws->base + ws->lo;
+            ws->lo += n;
+        }
+        bytes += (int64_t)n;
+        return cudaSuccess;
+    }
     void* p = nullptr;
     cudaError_t e = cudaMallocAsync(&p, n, st);
     if (e != cudaSuccess) return e;
@@ -75,7 +88,8 @@ static fs_status fail(fs_sim* s, fs_status code, const std::string& msg) {
 }
 
 static fs_status cfail(fs_sim* s, cudaError_t e, const char* where) {
-    return fail(s, FS_ERR_CUDA, std::string(where) + ": " + cuda_msg(e));
+    return fail(s, e == cudaErrorMemoryAllocation ? FS_ERR_OOM : FS_ERR_CUDA,
+                std::string(where) + ": " + cuda_msg(e));
 }
 
 #define CK(call, where)                                   \
@@ -203,42 +217,62 @@ static void fill_rbc(fs_sim* sim) {
     }
 }
 
-fs_status fs_build_sim(fs_sim* sim) {
-    cudaStream_t st = sim->stream;
+// Size of one Arena allocation of b bytes (as Arena::alloc rounds it).
+static size_t arena_round(size_t b) {
+    if (b == 0) b = 16;
+    return (b + 255) & ~(size_t)255;
+}
+
+// Nodes of the max-tree above the leaves: fan-out 32, every level up to the root.
+static int64_t tree_nodes(int64_t n) {
+    int64_t cnt = (n + 31) / 32, total = 0;
+    for (;;) {
+        total += cnt;
+        if (cnt == 1) return total;
+        cnt = (cnt + 31) / 32;
+    }
+}
+
+// Device bytes of one build: the simulation's state (kept until the next build or
+// fs_destroy) and the build's temporaries (released when it returns), every
+// allocation rounded as Arena::alloc rounds it. fs_build_sim checks its arenas
+// against this after allocating, so the two cannot drift apart.
+struct PlanBytes {
+    size_t state = 0, temps = 0;
+};
+
+static PlanBytes plan_bytes(int64_t n, size_t ncls, int64_t ncell, int64_t nnzp, bool fp32,
+                            bool thermal) {
+    PlanBytes b;
+    auto T = [&](int64_t x) { b.temps += arena_round((size_t)x); };
+    auto S = [&](int64_t x) { b.state += arena_round((size_t)x); };
+    const int64_t nc = (int64_t)ncls;
+    const int64_t scr = std::max(scan_scratch_elems(ncell + 1), scan_scratch_elems(n + 1)) + 8;
+    // count phase: positions, classes, cell grid, degrees, scan, rows
+    T(8 * n), T(8 * n), T(2 * n), T(16 * nc);
+    T(4 * n), T(4 * ncell), T(4 * (ncell + 1)), T(4 * n), T(8 * (ncell + 1)), T(8 * (ncell + 1));
+    T(8 * n), T(8 * scr), T((int64_t)sizeof(BuildStats)), T(8 * (n + 1));
+    // neighbour tensors (the 32-bit ones are scratch on the FP64 path)
+    S(8 * (n + 1)), S(4 * nnzp), S(16 * nnzp), S(8 * nnzp);
+    if (fp32)
+        S(8 * nnzp), S(4 * nnzp);
+    else
+        T(8 * nnzp), T(4 * nnzp);
+    // islands, classes, relax state
+    S(n), S(16 * n), S(8 * n), S(2 * n), S(16 * nc), S(8 * nc);
+    S(16 * n), S(8 * n), S((int64_t)sizeof(IslandRec) * n), S(8 * n), S(16 * nc), S(8 * nc);
+    if (thermal) S(8 * n), S(16 * n), S(4 * n);
+    const int64_t total = tree_nodes(n);
+    S(8 * total), S(4 * total);
+    S((int64_t)sizeof(InstState)), S((int64_t)sizeof(Inst)), S(16), S(8), S(16), S(16);
+    S(8 * 5 * n);
+    return b;
+}
+
+// The neighbour build's cell grid for cutoff rc: cells of at least rc, doubled
+// while there are more than 4 n + 4096 of them.
+static void grid_of(const fs_sim* sim, double rc, BuildWork& w) {
     const int64_t n = sim->n;
-    const fs_params& p = sim->p;
-    sim->mem.release(st);
-    sim->fields_valid = false;
-
-    // ---- temporaries of the build
-    Arena tmp;
-    auto talloc = [&](void** q, size_t b) { return tmp.alloc(q, b, st); };
-    double *dx = nullptr, *dy = nullptr;
-    uint16_t* dcls = nullptr;
-    double2* dcs = nullptr;
-    const size_t ncls = sim->cls_cos.size();
-    std::vector<double2> cs64(ncls);
-    for (size_t c = 0; c < ncls; ++c) cs64[c] = make_double2(sim->cls_cos[c], sim->cls_sin[c]);
-    CK(talloc((void**)&dx, 8 * n), "alloc");
-    CK(talloc((void**)&dy, 8 * n), "alloc");
-    CK(talloc((void**)&dcls, 2 * n), "alloc");
-    CK(talloc((void**)&dcs, 16 * ncls), "alloc");
-    CK(cudaMemcpyAsync(dx, sim->x.data(), 8 * n, cudaMemcpyHostToDevice, st), "upload");
-    CK(cudaMemcpyAsync(dy, sim->y.data(), 8 * n, cudaMemcpyHostToDevice, st), "upload");
-    CK(cudaMemcpyAsync(dcls, sim->cls.data(), 2 * n, cudaMemcpyHostToDevice, st), "upload");
-    CK(cudaMemcpyAsync(dcs, cs64.data(), 16 * ncls, cudaMemcpyHostToDevice, st), "upload");
-
-    BuildIn in;
-    in.n = n;
-    in.x = dx;
-    in.y = dy;
-    in.cls = dcls;
-    in.cs = dcs;
-    const double rc = p.cutoff * sim->a;
-    in.rc2 = rc * rc * (1.0 + 1e-9);
-    in.alpha = p.alpha;
-
-    BuildWork w;
     double xmin = sim->x[0], xmax = sim->x[0], ymin = sim->y[0], ymax = sim->y[0];
     for (int64_t i = 1; i < n; ++i) {
         xmin = std::min(xmin, sim->x[i]);
@@ -259,6 +293,41 @@ fs_status fs_build_sim(fs_sim* sim) {
     w.xmin = xmin;
     w.ymin = ymin;
     w.cell = cell;
+}
+
+// First phase of the build: positions and classes uploaded, the cell grid, every
+// island's padded degree and the row pointers (*rp_out), with temporaries from
+// `tmp` on `st`. Fills in, w and stats; returns the padded pair count in *nnzp.
+static fs_status count_pairs(fs_sim* sim, const fs_params& p, Arena& tmp, cudaStream_t st,
+                             BuildIn& in, BuildWork& w, int64_t** rp_out, BuildStats& stats,
+                             int64_t* nnzp) {
+    const int64_t n = sim->n;
+    auto talloc = [&](void** q, size_t b) { return tmp.alloc(q, b, st); };
+    double *dx = nullptr, *dy = nullptr;
+    uint16_t* dcls = nullptr;
+    double2* dcs = nullptr;
+    const size_t ncls = sim->cls_cos.size();
+    std::vector<double2> cs64(ncls);
+    for (size_t c = 0; c < ncls; ++c) cs64[c] = make_double2(sim->cls_cos[c], sim->cls_sin[c]);
+    CK(talloc((void**)&dx, 8 * n), "alloc");
+    CK(talloc((void**)&dy, 8 * n), "alloc");
+    CK(talloc((void**)&dcls, 2 * n), "alloc");
+    CK(talloc((void**)&dcs, 16 * ncls), "alloc");
+    CK(cudaMemcpyAsync(dx, sim->x.data(), 8 * n, cudaMemcpyHostToDevice, st), "upload");
+    CK(cudaMemcpyAsync(dy, sim->y.data(), 8 * n, cudaMemcpyHostToDevice, st), "upload");
+    CK(cudaMemcpyAsync(dcls, sim->cls.data(), 2 * n, cudaMemcpyHostToDevice, st), "upload");
+    CK(cudaMemcpyAsync(dcs, cs64.data(), 16 * ncls, cudaMemcpyHostToDevice, st), "upload");
+
+    in.n = n;
+    in.x = dx;
+    in.y = dy;
+    in.cls = dcls;
+    in.cs = dcs;
+    const double rc = p.cutoff * sim->a;
+    in.rc2 = rc * rc * (1.0 + 1e-9);
+    in.alpha = p.alpha;
+
+    grid_of(sim, rc, w);
     const int64_t ncell = w.gx * w.gy;
     CK(talloc((void**)&w.cell_of, 4 * n), "alloc");
     CK(talloc((void**)&w.cell_cnt, 4 * ncell), "alloc");
@@ -276,11 +345,45 @@ fs_status fs_build_sim(fs_sim* sim) {
     CK(build_cells(in, w, st), "cell grid");
     CK(build_degrees(in, w, st), "degrees");
     CK(build_rows(in, w, rp_tmp, st), "row scan");
-    BuildStats stats;
-    int64_t nnzp = 0;
+    *nnzp = 0;
     CK(cudaMemcpyAsync(&stats, w.stats, sizeof(stats), cudaMemcpyDeviceToHost, st), "stats");
-    CK(cudaMemcpyAsync(&nnzp, rp_tmp + n, 8, cudaMemcpyDeviceToHost, st), "stats");
+    CK(cudaMemcpyAsync(nnzp, rp_tmp + n, 8, cudaMemcpyDeviceToHost, st), "stats");
     CK(cudaStreamSynchronize(st), "build sync");
+    *rp_out = rp_tmp;
+    return FS_OK;
+}
+
+fs_status fs_build_sim(fs_sim* sim) {
+    cudaStream_t st = sim->stream;
+    const int64_t n = sim->n;
+    const fs_params& p = sim->p;
+    sim->mem.release(st);
+    sim->fields_valid = false;
+
+    // ---- temporaries of the build (the top of a bound workspace)
+    Arena tmp;
+    if (sim->ws.base) {
+        sim->ws.hi = 0;
+        tmp.ws = &sim->ws;
+        tmp.top = true;
+    }
+    auto talloc = [&](void** q, size_t b) { return tmp.alloc(q, b, st); };
+    const size_t ncls = sim->cls_cos.size();
+    std::vector<double2> cs64(ncls);
+    for (size_t c = 0; c < ncls; ++c) cs64[c] = make_double2(sim->cls_cos[c], sim->cls_sin[c]);
+    BuildIn in;
+    BuildWork w;
+    BuildStats stats;
+    int64_t* rp_tmp = nullptr;
+    int64_t nnzp = 0;
+    {
+        const fs_status r = count_pairs(sim, p, tmp, st, in, w, &rp_tmp, stats, &nnzp);
+        if (r != FS_OK) {
+            tmp.release(st);
+            return r;
+        }
+    }
+    const uint16_t* dcls = in.cls;
     if (stats.max_deg > kMaxPaddedDegree) {
         tmp.release(st);
         return fail(sim, FS_ERR_INVALID,
@@ -410,6 +513,14 @@ fs_status fs_build_sim(fs_sim* sim) {
     CK(palloc((void**)&sim->d_work, 16), "alloc");
     CK(palloc((void**)&sim->d_field, 16), "alloc");
     CK(palloc((void**)&sim->d_eval, 8 * 5 * n), "alloc");
+    {
+        const PlanBytes pb = plan_bytes(n, ncls, w.gx * w.gy, nnzp,
+                                        p.precision == FS_FP32_RECHECK, p.sigma_th > 0.0);
+        if ((size_t)sim->mem.bytes != pb.state || (size_t)tmp.bytes != pb.temps) {
+            tmp.release(st);
+            return fail(sim, FS_ERR_STATE, "internal: the build's device bytes differ from its plan");
+        }
+    }
     const int64_t ts[2] = {0, (n + 31) / 32};
     CK(cudaMemcpyAsync(sim->d_task_start, ts, 16, cudaMemcpyHostToDevice, st), "upload");
     CK(cudaMemcpyAsync(sim->d_tcnts, &sim->tcnt, 8, cudaMemcpyHostToDevice, st), "upload");
@@ -464,7 +575,7 @@ fs_status fs_build_sim(fs_sim* sim) {
     return FS_OK;
 }
 
-extern "C" fs_status fs_set_params(fs_sim* sim, const fs_params* p) {
+static fs_status check_params(fs_sim* sim, const fs_params* p) {
     if (!sim || !p) return fail(sim, FS_ERR_INVALID, "NULL argument");
     if (bad_double(p->alpha) || bad_double(p->hk) || bad_double(p->k_disorder) ||
         bad_double(p->b) || bad_double(p->c) || bad_double(p->beta) || bad_double(p->gamma) ||
@@ -476,10 +587,74 @@ extern "C" fs_status fs_set_params(fs_sim* sim, const fs_params* p) {
         return fail(sim, FS_ERR_INVALID, "parameter out of range");
     if (p->precision != FS_FP64 && p->precision != FS_FP32_RECHECK)
         return fail(sim, FS_ERR_INVALID, "unknown precision");
+    return FS_OK;
+}
+
+extern "C" fs_status fs_workspace_bytes(const fs_sim* csim, const fs_params* p, size_t* bytes) {
+    fs_sim* sim = const_cast<fs_sim*>(csim);  // (only its error message is written)
+    if (!bytes) return fail(sim, FS_ERR_INVALID, "NULL argument");
+    *bytes = 0;
+    fs_status r = check_params(sim, p);
+    if (r != FS_OK) return r;
+    // the build's neighbour count, with its temporaries from the pool
+    cudaStream_t st = sim->stream;
+    Arena tmp;
+    BuildIn in;
+    BuildWork w;
+    BuildStats stats;
+    int64_t* rp_tmp = nullptr;
+    int64_t nnzp = 0;
+    r = count_pairs(sim, *p, tmp, st, in, w, &rp_tmp, stats, &nnzp);
+    tmp.release(st);
+    if (r != FS_OK) return r;
+    if (stats.max_deg > kMaxPaddedDegree)
+        return fail(sim, FS_ERR_INVALID,
+                    "neighbourhood too large: " + std::to_string(stats.max_deg) +
+                        " neighbours (max " + std::to_string(kMaxPaddedDegree) +
+                        "); reduce the cutoff");
+    const PlanBytes pb = plan_bytes(sim->n, sim->cls_cos.size(), w.gx * w.gy, nnzp,
+                                    p->precision == FS_FP32_RECHECK, p->sigma_th > 0.0);
+    *bytes = pb.state + pb.temps;
+    return FS_OK;
+}
+
+extern "C" fs_status fs_bind_workspace(fs_sim* sim, void* dev_ptr, size_t bytes,
+                                       void* cuda_stream) {
+    if (!sim) return fail(nullptr, FS_ERR_INVALID, "sim is NULL");
+    if (sim->built) return fail(sim, FS_ERR_STATE, "bind the workspace before fs_set_params");
+    if (dev_ptr && ((uintptr_t)dev_ptr & 255u) != 0)
+        return fail(sim, FS_ERR_INVALID, "workspace must start on a 256-byte boundary");
+    if (dev_ptr) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, dev_ptr) != cudaSuccess ||
+            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();  // (clear the lookup's error)
+            return fail(sim, FS_ERR_INVALID, "workspace is not device memory");
+        }
+    }
+    if (cuda_stream) sim->stream = (cudaStream_t)cuda_stream;
+    sim->mem.release(sim->stream);  // (what a failed build left)
+    sim->ws = Workspace{};
+    sim->mem.ws = nullptr;
+    if (dev_ptr) {
+        sim->ws.base = (char*)dev_ptr;
+        sim->ws.cap = bytes & ~(size_t)255;
+        sim->mem.ws = &sim->ws;
+        sim->mem.top = false;
+    }
+    return FS_OK;
+}
+
+extern "C" fs_status fs_set_params(fs_sim* sim, const fs_params* p) {
+    const fs_status r = check_params(sim, p);
+    if (r != FS_OK) return r;
     sim->p = *p;
     draw_hk(sim->n, p->hk, p->k_disorder, p->seed, p->instance, sim->hk);
     sim->built = false;
-    return fs_build_sim(sim);
+    const fs_status b = fs_build_sim(sim);
+    // a failed build's queued work ends before the caller may reuse its buffer
+    if (b != FS_OK) cudaStreamSynchronize(sim->stream);
+    return b;
 }
 
 static fs_status need_built(fs_sim* sim) {

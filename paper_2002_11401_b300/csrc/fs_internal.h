@@ -12,10 +12,21 @@
 
 namespace fs {
 
-// Stream-ordered device allocations owned by one object.
+// A caller's device buffer that a simulation's allocations are carved from:
+// the state from the bottom (lo bytes used), a build's temporaries from the top
+// (hi bytes used).
+struct Workspace {
+    char* base = nullptr;
+    size_t cap = 0, lo = 0, hi = 0;
+};
+
+// Device allocations owned by one object: stream-ordered from the pool, or, bound
+// to a workspace (ws), carved from its bottom or its top end with nothing freed.
 struct Arena {
     std::vector<void*> blocks;
     int64_t bytes = 0;
+    Workspace* ws = nullptr;
+    bool top = false;
     cudaError_t alloc(void** out, size_t n, cudaStream_t st);
     void release(cudaStream_t st);
 };
@@ -48,7 +59,8 @@ struct fs_sim {
     uint32_t step = 0;
     // device
     cudaStream_t stream = nullptr;
-    fs::Arena mem;  // everything that lives as long as the parameters
+    fs::Workspace ws;  // caller's buffer (fs_bind_workspace), else unused
+    fs::Arena mem;     // everything that lives as long as the parameters
     fs::Arena run;  // per-call protocol buffers
     fs::Inst inst{};      // descriptor (host copy)
     fs::Inst inst_run{};  // descriptor of the queued call (host staging)

@@ -388,3 +388,65 @@ def test_fp32_thermal_draw_within_bound(B):
         err = np.maximum(np.abs(p32 - p64), np.abs(q32 - q64)) / r
         worst = max(worst, float(err.max()))
     assert worst < 32 * 2.0**-24 / 4, worst
+
+
+# ---------------------------------------------------------------------------
+# Caller-owned workspace (fs_workspace_bytes, fs_bind_workspace)
+# ---------------------------------------------------------------------------
+
+def _params_of(B, w, prec):
+    return B.make_params(alpha=w["alpha"], hk=w["hk"], k_disorder=w["k_disorder"], b=w["b"],
+                         c=w["c"], beta=w["beta"], gamma=w["gamma"], cutoff=w["cutoff"],
+                         sigma_th=w["sigma_th"], seed=w["seed"], precision=prec)
+
+
+@pytest.mark.parametrize("kind,n,sigma,prec", [(I.SQUARE, 16, 0.0, FP64),
+                                               (I.PINWHEEL, 12, 0.0, FP32),
+                                               (I.KAGOME, 10, 0.004, FP32),
+                                               (I.KAGOME, 10, 0.004, FP64)])
+def test_bound_workspace_of_the_stated_size_runs_identically(B, kind, n, sigma, prec):
+    """A simulation built inside a torch-owned buffer of exactly fs_workspace_bytes
+    bytes gives the same flips as one on the library's pool; one 256 bytes short
+    fails with FS_ERR_OOM and can be bound again."""
+    import torch
+    w = small(kind, n, sigma_th=sigma)
+    p = _params_of(B, w, prec)
+    hx, hy = I.ramp_protocol(120, 30.0, 0.3)
+    ref = lib_sim(w, precision=prec)
+    r0 = ref.run_protocol(hx, hy)
+    s0 = ref.spins()
+    state_bytes = ref.info().device_bytes
+    ref.close()
+
+    sim = B.Sim.geometry(kind, n, n)
+    need = sim.workspace_bytes(p)
+    assert need > state_bytes > 0
+    short = torch.empty(need - 256, dtype=torch.uint8, device="cuda")
+    sim.bind_workspace(short.data_ptr(), short.numel())
+    with pytest.raises(B.FsError) as e:
+        sim.set_params(p)
+    assert e.value.code == B.FS_ERR_OOM
+    buf = torch.empty(need, dtype=torch.uint8, device="cuda")
+    sim.bind_workspace(buf.data_ptr(), buf.numel(), torch.cuda.current_stream().cuda_stream)
+    sim.set_params(p)
+    assert sim.info().device_bytes == state_bytes
+    r1 = sim.run_protocol(hx, hy)
+    assert (r1["n_flips"], r1["hash"]) == (r0["n_flips"], r0["hash"])
+    np.testing.assert_array_equal(r1["log_spin"], r0["log_spin"])
+    np.testing.assert_array_equal(sim.spins(), s0)
+    # bound state is the caller's: binding again needs new parameters first
+    with pytest.raises(B.FsError) as e:
+        sim.bind_workspace(0, 0)
+    assert e.value.code == B.FS_ERR_STATE
+    sim.close()
+    del buf, short
+
+
+def test_workspace_must_be_device_memory(B):
+    host = np.zeros(1 << 16, dtype=np.uint8)
+    addr = (host.ctypes.data + 255) & ~255
+    sim = B.Sim.geometry(I.SQUARE, 4, 4)
+    with pytest.raises(B.FsError) as e:
+        sim.bind_workspace(addr, 1 << 15)
+    assert e.value.code == B.FS_ERR_INVALID
+    sim.close()

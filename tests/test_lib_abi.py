@@ -76,3 +76,26 @@ def test_bad_arguments_are_rejected(lib):
                              ctypes.byref(h), ctypes.byref(nf))
     assert st == B.FS_ERR_STATE
     assert b"parameters" in lib.fs_last_error(sim.handle)
+
+
+def test_workspace_calls_reject_bad_arguments_on_the_host(lib):
+    """fs_workspace_bytes and fs_bind_workspace check their arguments before any
+    device work: NULL handles and outputs, parameters out of range, a buffer that
+    does not start on a 256-byte boundary."""
+    from paper_2002_11401_b300 import binding as B
+    sim = B.Sim.geometry(I.SQUARE, 2, 2)
+    out = ctypes.c_size_t(7)
+    p = B.make_params(alpha=1e-3)
+    assert lib.fs_workspace_bytes(sim.handle, ctypes.byref(p), None) == B.FS_ERR_INVALID
+    assert lib.fs_workspace_bytes(sim.handle, None, ctypes.byref(out)) == B.FS_ERR_INVALID
+    bad = B.make_params(alpha=1e-3, cutoff=-1.0)
+    assert lib.fs_workspace_bytes(sim.handle, ctypes.byref(bad), ctypes.byref(out)) == \
+        B.FS_ERR_INVALID
+    assert out.value == 0
+    assert b"out of range" in lib.fs_last_error(sim.handle)
+    assert lib.fs_bind_workspace(None, None, 0, None) == B.FS_ERR_INVALID
+    assert lib.fs_bind_workspace(sim.handle, ctypes.c_void_p(0x1000 + 16), 1 << 20,
+                                 None) == B.FS_ERR_INVALID
+    assert b"256-byte" in lib.fs_last_error(sim.handle)
+    # NULL returns to the pool: always allowed before the parameters are set
+    assert lib.fs_bind_workspace(sim.handle, None, 0, None) == B.FS_OK
