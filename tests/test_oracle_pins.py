@@ -135,6 +135,26 @@ def test_generalised_astroid_exponents_as_printed(oracle):
     assert oracle.astroid_lhs(-0.1, -0.1, 0.2, 0.5, 1.0, 2.0, 4.0) == L
 
 
+def test_astroid_lhs_against_high_precision(oracle):
+    # Eq. (5) on random fields, coercive fields and the paper's four astroids, against
+    # a 60-digit evaluation (mpmath, an independent implementation of the powers):
+    # the oracle's FP64 value is within a few ulps of the exact one.
+    import mpmath
+    mpmath.mp.dps = 60
+    rng = np.random.default_rng(7)
+    shapes = [(1.0, 1.0, 3.0, 3.0), (0.28, 1.0, 4.8, 3.0), (0.42, 1.0, 1.7, 3.4),
+              (0.38, 1.0, 1.5, 3.2)]
+    for b, c, beta, gamma in shapes:
+        for _ in range(200):
+            hp, hq = rng.normal(0.0, 0.15, 2)
+            hk = float(rng.uniform(0.05, 0.3))
+            got = oracle.astroid_lhs(hp, hq, hk, b, c, beta, gamma)
+            B_, C_, K_ = mpmath.mpf(b), mpmath.mpf(c), mpmath.mpf(hk)
+            exact = (abs(mpmath.mpf(hp)) / (B_ * K_)) ** (2 / mpmath.mpf(gamma)) + \
+                (abs(mpmath.mpf(hq)) / (C_ * K_)) ** (2 / mpmath.mpf(beta))
+            assert abs(got - float(exact)) <= 8 * np.spacing(float(exact)), (b, hp, hq, hk)
+
+
 def test_antialignment_condition(oracle):
     # Eq. (6): a field outside the astroid switches only when h . m_i < 0.
     assert oracle.flippable(+1, -0.3, 2.0)
