@@ -377,6 +377,49 @@ def _brute_tables(x, y, th, hk, alpha, rc, b, c, beta, gamma, hex_, hey):
     return nxt
 
 
+def _pinwheel_reversal(oracle, angle_deg, cells=20, K=400, hmax=0.06):
+    # The paper's pinwheel reversal parameters (Sec. "Superferromagnetism in pinwheel
+    # ASI"): b = 0.28, c = 1, beta = 4.8, gamma = 3, alpha = 0.00033, h_k = 0.098,
+    # k_disorder = 0.05, neighbour distance 10; a linear loop -hmax -> +hmax at the
+    # given angle from +x. Returns, per field step, the fraction of each sublattice
+    # (islands at 45 and at 135 degrees) reversed since the first step's saturation.
+    x, y, th = oracle.geometry(I.PINWHEEL, cells, cells)
+    hk = oracle.draw_hk(len(x), 0.098, 0.05, 1)
+    S = oracle.Sim(x, y, th, hk, alpha=0.00033, b=0.28, c=1.0, beta=4.8, gamma=3.0,
+                   cutoff_abs=10.0)
+    h = -hmax + 2 * hmax * np.arange(K) / (K - 1)
+    a = math.radians(angle_deg)
+    r = S.run(np.ones(len(x), dtype=np.int8), h * math.cos(a), h * math.sin(a))
+    sub_a = np.isclose(np.degrees(th) % 180.0, 45.0)
+    s = np.ones(len(x), dtype=np.int8)
+    ls, lk = r["log_step"], r["log_spin"]
+    j, s0, rows = 0, None, []
+    for t in range(K):
+        while j < len(ls) and ls[j] == t:
+            s[lk[j]] *= -1
+            j += 1
+        if t == 0:
+            s0 = s.copy()
+        rows.append(((s[sub_a] != s0[sub_a]).mean(), (s[~sub_a] != s0[~sub_a]).mean()))
+    return np.array(rows)
+
+
+def test_pinwheel_reversal_angle_controls_avalanche_or_two_steps(oracle):
+    # The paper's key pinwheel result: a field equally aligned to both sublattices
+    # (theta = 0) reverses them in a single avalanche; one more aligned to one
+    # sublattice (theta = 30 degrees) reverses it completely before the other starts.
+    both = _pinwheel_reversal(oracle, 0.0)
+    assert both[-1].min() > 0.99
+    tot = both.mean(axis=1)  # (equal sublattice sizes)
+    t10, t90 = int(np.argmax(tot >= 0.1)), int(np.argmax(tot >= 0.9))
+    assert t90 - t10 <= 3, (t10, t90)
+    assert np.abs(both[:, 0] - both[:, 1]).max() < 0.3
+    two = _pinwheel_reversal(oracle, 30.0)
+    assert two[-1].min() > 0.99
+    assert ((two[:, 0] >= 0.99) & (two[:, 1] <= 0.01)).sum() >= 5  # A done, B not begun
+    assert not ((two[:, 1] >= 0.5) & (two[:, 0] <= 0.5)).any()     # never the other way
+
+
 def test_relax_matches_brute_force_state_table(oracle):
     # 2 x 2 closed square: 12 islands, all 4096 states enumerated.
     x, y, th = oracle.geometry(I.SQUARE, 2, 2)
