@@ -140,6 +140,22 @@ def _compare_runs(oracle, w, hx, hy, precs=(FP64, FP32), resweeps=(True,), **ove
     return ref, out
 
 
+@pytest.mark.parametrize("angle", [0.0, 30.0])
+def test_pinwheel_reversal_with_the_papers_parameters(B, oracle, angle):
+    """The paper's pinwheel reversal (asymmetric astroid b = 0.28, beta = 4.8,
+    alpha = 0.00033, h_k = 0.098, neighbour distance 10; a loop -0.06 -> +0.06 T):
+    every flip as the oracle's, both paths (the oracle's own pin checks the
+    avalanche at 0 degrees and the two steps at 30)."""
+    w = small(I.PINWHEEL, 20, alpha=0.00033, hk=0.098, k_disorder=0.05, cutoff=10.0, b=0.28,
+              c=1.0, beta=4.8, gamma=3.0, seed=1)
+    K = 400
+    h = -0.06 + 0.12 * np.arange(K) / (K - 1)
+    a = math.radians(angle)
+    ref, _ = _compare_runs(oracle, w, h * math.cos(a), h * math.sin(a))
+    # the first step saturates one sublattice (420 islands); then all 840 reverse
+    assert ref["n_flips"] == 420 + 840
+
+
 def test_square16_sequence(B, oracle):
     w = I.WORKLOADS["square16"]
     hx, hy = I.protocol_of(w["protocol"])
