@@ -247,7 +247,8 @@ fs_status fs_get_csr(const fs_sim* sim, int64_t* row_ptr, int32_t* col, double* 
  *
  * One field-and-margin sweep in the FS_FP64 arithmetic (exact 64-bit dipolar sums
  * over sim's neighbour tensors, external field (hx, hy), thermal draw of `step`,
- * Eq. 5 and 6) for the caller's spins, and the argmax of the relax rule.
+ * the same astroid and alignment test as fs_get_lhs) for the caller's spins, and
+ * the argmax of the relax rule.
  *   sim      built simulation (fs_set_params done); its spins are not used or
  *            changed; n = its island count, at most 2,097,152 (2^21)
  *   d_spins  device, n int8 in {-1,+1} (values are not checked)
@@ -263,9 +264,11 @@ fs_status fs_get_csr(const fs_sim* sim, int64_t* row_ptr, int32_t* col, double* 
  * array's address (once per device, with that device current); later calls only
  * queue a memset of the counters and one kernel. All calls share the array, so
  * calls whose work overlaps on the GPU race and give undefined results.
+ * The device current at the call must be the one that was current when the
+ * simulation's parameters were set (its buffers live there).
  * Returns FS_ERR_INVALID (NULL pointer or n above the limit), FS_ERR_STATE
- * (parameters not set) or FS_ERR_CUDA (lookup or launch failed); no message is
- * recorded for fs_last_error. */
+ * (parameters not set, or another device current) or FS_ERR_CUDA (lookup or
+ * launch failed); no message is recorded for fs_last_error. */
 fs_status fs_eval_argmax_static(const fs_sim* sim, const int8_t* d_spins, double hx, double hy,
                                 uint32_t step, double* d_lhs, int64_t* d_best, void* stream);
 
@@ -314,7 +317,8 @@ typedef struct {
 /* hbm_budget: bytes of device memory the server may hold for admitted requests. */
 fs_status fs_server_create(size_t hbm_budget, int32_t max_active, fs_server** out);
 fs_status fs_server_submit(fs_server* srv, const fs_request* req, uint64_t* ticket);
-/* FS_ERR_STATE while the request is not done; FS_OK with *out filled when done. */
+/* FS_ERR_STATE while the request is not done; FS_OK with *out filled when done. A
+ * result is handed out once: the ticket is then forgotten (FS_ERR_INVALID after). */
 fs_status fs_server_poll(fs_server* srv, uint64_t ticket, fs_result* out);
 /* Blocks until every submitted request is done. */
 fs_status fs_server_drain(fs_server* srv);

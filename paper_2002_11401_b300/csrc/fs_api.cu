@@ -65,10 +65,31 @@ cudaError_t Arena::alloc(void** out, size_t n, cudaStream_t st) {
     return cudaSuccess;
 }
 
-// Bound on |z32 - z64| / r of the FP32 and FP64 Box-Muller normals of one Philox
-// block, r = |z0| + |z1| >= the radius: a few ulp of ln u1, sqrt and sincospi,
-// taken as 32 u (tests/test_gpu_parity.py measures the largest ratio).
-const double kThermalRel = 32.0 * std::ldexp(1.0, -24);
+// Bound on |th32 - th64| / (|th_par| + |th_perp|) of the FP32 and FP64 thermal
+// draws of one Philox block (the sum is at least sigma times the Box-Muller
+// radius), from the maximum ulp errors the CUDA Math API documents for the FP32
+// functions (an error of k ulp against the correctly rounded value is within
+// k + 1/2 ulp, i.e. (2k + 1) u, of the exact one; u = 2^-24):
+//  - u1 (or 1 - u1, formed exactly in integers) rounded to FP32 twice: 2u;
+//  - ln u1: logf (1 ulp, 3u) plus 2u / ln 2 from u1's error, |ln u1| >= ln 2 when
+//    u1 < 1/2; log1pf(-(1 - u1)) (1 ulp, 3u) plus 2u / (1 - om) <= 4u from the
+//    argument's error, |ln(1 - om)| >= om: at most 7u;
+//  - the radius sqrt(-2 ln u1): half of that plus sqrtf's rounding (correctly
+//    rounded without fast-math): 4.5u;
+//  - cos and sin of the angle: sincospif (1 ulp, 3u relative) of the exactly split
+//    high part, the first-order correction's truncation (below 1e-13) and its
+//    product (|pi x_lo| < 4e-7), one subtraction: 4u of the value plus 1e-6 u;
+//  - the product with the radius (u), sigma rounded to FP32 (u) and the product
+//    with it (u); the FP64 draw's own error (log, sqrt, sincos: a few 1e-16).
+// 4.5u + 4u + 3u = 11.5u and change, taken as 12u.
+const double kThermalRel = 12.0 * std::ldexp(1.0, -24);
+
+// The smallest float at least v (v >= 0).
+float up_float(double v) {
+    float f = (float)v;
+    if ((double)f < v) f = std::nextafter(f, INFINITY);
+    return f;
+}
 
 int choose_lanes(double avg_groups) {
     if (avg_groups <= 4.5) return 4;
@@ -545,23 +566,41 @@ fs_status fs_build_sim(fs_sim* sim) {
     I.instance = p.instance;
     I.max_flips = p.max_flips_per_step > 0 ? p.max_flips_per_step : 16 * n;
     I.st = sim->d_state;
-    // FP32 error model, bounds on |FP32 evaluation - FS_FP64 evaluation|:
+    // FP32 error model, bounds on |FP32 evaluation - FS_FP64 evaluation| (u = 2^-24):
     //  - dh_abs: both fixed-point roundings over the longest row;
     //  - th_rel: the FP32 Box-Muller draw against the FP64 one, relative to the
-    //    draw's radius (a few ulp of ln, sqrt and sincospi; kThermalRel);
-    //  - dh_rel: four float roundings of the field pieces (u = 2^-24);
-    //  - div_rel: the FP32 rounding of 1 / (b h_k) and of the scaling, against the
-    //    FP64 division (two u, taken as three);
-    //  - pow_rel: powf (measured max 1.26 u on this GPU, taken as two); the bound
-    //    arithmetic itself rounds outward.
+    //    draw's radius (kThermalRel, from the documented ulp bounds);
+    //  - dh_rel: three roundings of the field pieces (int to float, the external
+    //    field to FP32, two sums: u |dp| + u |ext| + u |dp + ext| + u |h|, at most
+    //    3u (|dp| + |ext| + |th|) and change), widened by 2^-20 for the FP64 sums'
+    //    own roundings;
+    //  - div_rel: 1 / (b h_k) rounded to FP32 (u) and the FP32 product (u) against
+    //    the FP64 product with the FP64 reciprocal (2^-53), 2u + 2^-50;
+    //  - pow_rel_*: the power. For the exponent 2/3, x rcbrtf(x): rcbrtf's
+    //    documented 1 ulp (3u against the exact value) and the product's rounding,
+    //    (1 + 3u)(1 + u) - 1 < 4.01u; otherwise powf at the FP32-rounded exponent,
+    //    taken as 8 ulp (17u; no less than its documented maximum) plus the exponent's rounding
+    //    |p - pf| |ln x| (lnk_*, applied per argument in pow_err). Both include
+    //    2^-40 for the FP64 power's own error (pow: 2 ulp; the 2/3 power: 1.6 ulp).
+    //    The bound arithmetic itself rounds outward.
     const double u = std::ldexp(1.0, -24);
     const double quant = (double)stats.max_deg * (std::ldexp(1.0, -e32 - 1) +
                                                   std::ldexp(1.0, -e64 - 1));
-    I.dh_abs = (float)(quant * 1.5 + 1e-30);
-    I.th_rel = (float)kThermalRel;
-    I.dh_rel = (float)(4.0 * u);
-    I.div_rel = (float)(3.0 * u);
-    I.pow_rel = (float)(2.0 * u);
+    I.dh_abs = up_float(quant * 1.5 + 1e-30);
+    I.th_rel = up_float(kThermalRel);
+    I.dh_rel = up_float(3.0 * u * (1.0 + std::ldexp(1.0, -20)));
+    I.div_rel = up_float(2.0 * u + std::ldexp(1.0, -50));
+    I.cube_p = I.pexp == 2.0 / 3.0 ? 1 : 0;
+    I.cube_q = I.qexp == 2.0 / 3.0 ? 1 : 0;
+    const double rel_cube = 4.01 * u + std::ldexp(1.0, -40);
+    const double rel_powf = 17.0 * u + std::ldexp(1.0, -40);
+    const double ln2 = 0.69314718055994530942;
+    I.pow_rel_p = up_float(I.cube_p ? rel_cube : rel_powf);
+    I.pow_rel_q = up_float(I.cube_q ? rel_cube : rel_powf);
+    I.lnk_p = I.cube_p ? 0.0f
+                       : up_float(std::fabs(I.pexp - (double)I.pexpf) * ln2 * (1.0 + 1e-6));
+    I.lnk_q = I.cube_q ? 0.0f
+                       : up_float(std::fabs(I.qexp - (double)I.qexpf) * ln2 * (1.0 + 1e-6));
     sim->lanes = choose_lanes((double)nnzp / (double)n / 4.0);
 
     // coercive fields
@@ -571,6 +610,7 @@ fs_status fs_build_sim(fs_sim* sim) {
     CK(cudaMemcpyAsync(sim->d_inst, &I, sizeof(Inst), cudaMemcpyHostToDevice, st), "upload");
     tmp.release(st);
     CK(cudaStreamSynchronize(st), "build");
+    CK(cudaGetDevice(&sim->device), "device");
     sim->built = true;
     return FS_OK;
 }
@@ -1060,7 +1100,8 @@ extern "C" fs_status fs_get_info(const fs_sim* csim, fs_info* out) {
     out->e64 = sim->e64;
     out->e32 = sim->e32;
     out->device_bytes = sim->mem.bytes;
-    out->band_rel = sim->inst.pow_rel + sim->inst.div_rel + sim->inst.dh_rel;
+    out->band_rel = std::max(sim->inst.pow_rel_p, sim->inst.pow_rel_q) + sim->inst.div_rel +
+                    sim->inst.dh_rel;
     out->band_abs = sim->inst.dh_abs;
     // unpadded nnz: count non-self entries
     std::vector<int64_t> rp((size_t)sim->n + 1);

@@ -114,12 +114,15 @@ struct Inst {
     int32_t pad0;
     int64_t max_flips;
     // FP32 error model: |h32 - h64| <= dh_abs + th_rel * |h_th| + dh_rel * (|h_dip| +
-    // |h_ext| + |h_th|);
-    // div_rel bounds the relative error of |h| / (b h_k) against the FP64 division,
-    // pow_rel that of powf
-    float dh_abs, dh_rel, pow_rel, div_rel;
+    // |h_ext| + |h_th|); div_rel bounds the relative error of |h| / (b h_k) against
+    // the FP64 product |h| (1 / (b h_k)); the FP32 power of each astroid term is
+    // within pow_rel_* + lnk_* (|e| + 2) of x^p (e the binary exponent of x, p the
+    // FP64 exponent), see pow_err.
+    float dh_abs, dh_rel, div_rel;
     float th_rel;   // |th32 - th64| <= th_rel (|th_par| + |th_perp|)
-    float pad2;
+    float pow_rel_p, pow_rel_q;  // the FP32 power's own error (documented ulp bound)
+    float lnk_p, lnk_q;          // |p - (float)p| ln 2, rounded up (0 with the cube root)
+    int32_t cube_p, cube_q;      // exponent 2/3: x^(2/3) = x rcbrtf(x), no powf
     InstState* st;
 };
 
@@ -331,30 +334,56 @@ struct Eval32 {
     bool possible, certain;
 };
 
-__device__ __forceinline__ float pow_nonneg(float x, float p) {
-    return x > 0.0f ? powf(x, p) : 0.0f;
+// x^p in FP32 for x >= 0 (0 for x <= 0). With `cube` (p = 2/3, the Stoner-Wohlfarth
+// exponent) it is x rcbrtf(x): the exponent is exact and the error is that of rcbrtf
+// plus one rounding; otherwise powf at the FP32-rounded exponent.
+__device__ __forceinline__ float pow32(float x, float p, int cube) {
+    if (!(x > 0.0f)) return 0.0f;
+    return cube ? __fmul_rn(x, rcbrtf(x)) : powf(x, p);
 }
 
-// Bounds of one astroid term a^p, a = |h| / (b h_k), whose FP32 value t = powf(x, p)
+// Bound on the relative error of pow32(x) against x^p with the FP64 exponent p:
+// rel (the function's own error, from its documented maximum ulp error) plus the
+// exponent's rounding, x^pf / x^p = exp((pf - p) ln x) with |ln x| <= (|e| + 1) ln 2
+// for the binary exponent e of x (|e| + 2 leaves room for exp(t) - 1 <= t e^t; a
+// subnormal x counts as e = -150); the sum is widened by 2^-16 so that the bound
+// also covers 1 / (1 - r) - 1 where callers divide by 1 - r.
+__device__ __forceinline__ float pow_err(float x, float rel, float lnk) {
+    float r = rel;
+    if (lnk > 0.0f) {
+        const int bexp = (int)((__float_as_uint(x) >> 23) & 0xFFu);
+        const int e = bexp == 0 ? 150 : abs(bexp - 127);
+        r = __fadd_ru(r, __fmul_ru(lnk, (float)(e + 2)));
+    }
+    return __fmul_ru(r, 1.0f + 0x1.0p-16f);
+}
+
+// Bounds of one astroid term a^p, a = |h| / (b h_k), whose FP32 value t = pow32(x)
 // was taken at x; u bounds the relative error of x. For p <= 1 the concave power
 // gives (x(1+u))^p <= x^p (1 + p u) and (x(1-u))^p >= x^p (1 - p u / (1 - u)), and
 // 1 / (1 - u) <= 1 + 2u on u <= 1/4; for 1 < p <= 3, (1 + u)^(p-1) <= 2 on u <= 1/4
 // gives the factors 1 + 2 p u and 1 - p u. Outside u <= 1/4 the monotone bounds
-// are evaluated directly. `r` bounds the relative error of powf. Upper bounds are
-// formed with round-up and lower bounds with round-down arithmetic.
-__device__ __forceinline__ void term_bounds(float t, float x, float u, float p, float r,
-                                            float* hi, float* lo) {
+// are evaluated directly. The power's own error comes from pow_err at the argument
+// it was taken at. Upper bounds are formed with round-up and lower bounds with
+// round-down arithmetic.
+__device__ __forceinline__ void term_bounds(float t, float x, float u, float p, int cube,
+                                            float rel, float lnk, float* hi, float* lo) {
     if (u <= 0.25f && p <= 3.0f) {
+        const float r = pow_err(x, rel, lnk);
         const float pu = __fmul_ru(p, u);
         const float g_hi = p <= 1.0f ? pu : __fmul_ru(2.0f, pu);
         const float g_lo = p <= 1.0f ? __fmul_ru(pu, __fadd_ru(1.0f, __fmul_ru(2.0f, u))) : pu;
         *hi = __fmul_ru(__fmul_ru(t, __fadd_ru(1.0f, r)), __fadd_ru(1.0f, g_hi));
         *lo = __fmul_rd(__fmul_rd(t, __fsub_rd(1.0f, r)), fmaxf(__fsub_rd(1.0f, g_lo), 0.0f));
     } else {
-        *hi = __fmul_ru(pow_nonneg(__fmul_ru(x, __fadd_ru(1.0f, u)), p), __fadd_ru(1.0f, r));
-        *lo = u < 1.0f ? __fmul_rd(pow_nonneg(__fmul_rd(x, __fsub_rd(1.0f, u)), p),
-                                   __fsub_rd(1.0f, r))
-                       : 0.0f;
+        const float xh = __fmul_ru(x, __fadd_ru(1.0f, u));
+        *hi = __fmul_ru(pow32(xh, p, cube), __fadd_ru(1.0f, pow_err(xh, rel, lnk)));
+        if (u < 1.0f) {
+            const float xl = __fmul_rd(x, __fsub_rd(1.0f, u));
+            *lo = __fmul_rd(pow32(xl, p, cube), __fsub_rd(1.0f, pow_err(xl, rel, lnk)));
+        } else {
+            *lo = 0.0f;
+        }
     }
 }
 
@@ -384,26 +413,31 @@ __device__ __forceinline__ Eval32 eval32(const Inst& I, int s, float dp, float d
                                                                 fabsf(tq))));
     const float ap = fabsf(e.hpar), aq = fabsf(e.hperp);
     const float x = __fmul_rn(ap, rbc.x), y = __fmul_rn(aq, rbc.y);
-    const float tx = pow_nonneg(x, I.pexpf), ty = pow_nonneg(y, I.qexpf);
+    const float tx = pow32(x, I.pexpf, I.cube_p), ty = pow32(y, I.qexpf, I.cube_q);
     e.lhs = __fadd_rn(tx, ty);
-    // relative error of x and y: the field bound plus the scaling roundings
-    const float ux = ap > 0.0f ? __fadd_ru(__fmul_ru(dpar, rcp_up(ap)), I.div_rel) : 2.0f;
-    const float uy = aq > 0.0f ? __fadd_ru(__fmul_ru(dperp, rcp_up(aq)), I.div_rel) : 2.0f;
+    // relative error of x and y: the field bound (times 1 + 2^-22, which covers its
+    // product with the scaling's error) plus the scaling roundings
+    const float ux = ap > 0.0f ? __fadd_ru(__fmul_ru(__fmul_ru(dpar, rcp_up(ap)), 1.0f + 0x1.0p-22f),
+                                           I.div_rel)
+                               : 2.0f;
+    const float uy = aq > 0.0f ? __fadd_ru(__fmul_ru(__fmul_ru(dperp, rcp_up(aq)), 1.0f + 0x1.0p-22f),
+                                           I.div_rel)
+                               : 2.0f;
     float hx_, lx_, hy_, ly_;
     if (ap > 0.0f) {
-        term_bounds(tx, x, ux, I.pexpf, I.pow_rel, &hx_, &lx_);
+        term_bounds(tx, x, ux, I.pexpf, I.cube_p, I.pow_rel_p, I.lnk_p, &hx_, &lx_);
     } else {  // |h_par| <= dpar
-        hx_ = __fmul_ru(pow_nonneg(__fmul_ru(__fmul_ru(dpar, rbc.x), __fadd_ru(1.0f, I.div_rel)),
-                                   I.pexpf),
-                        __fadd_ru(1.0f, I.pow_rel));
+        const float xm = __fmul_ru(__fmul_ru(dpar, rbc.x), __fadd_ru(1.0f, I.div_rel));
+        hx_ = __fmul_ru(pow32(xm, I.pexpf, I.cube_p),
+                        __fadd_ru(1.0f, pow_err(xm, I.pow_rel_p, I.lnk_p)));
         lx_ = 0.0f;
     }
     if (aq > 0.0f) {
-        term_bounds(ty, y, uy, I.qexpf, I.pow_rel, &hy_, &ly_);
+        term_bounds(ty, y, uy, I.qexpf, I.cube_q, I.pow_rel_q, I.lnk_q, &hy_, &ly_);
     } else {
-        hy_ = __fmul_ru(pow_nonneg(__fmul_ru(__fmul_ru(dperp, rbc.y), __fadd_ru(1.0f, I.div_rel)),
-                                   I.qexpf),
-                        __fadd_ru(1.0f, I.pow_rel));
+        const float ym = __fmul_ru(__fmul_ru(dperp, rbc.y), __fadd_ru(1.0f, I.div_rel));
+        hy_ = __fmul_ru(pow32(ym, I.qexpf, I.cube_q),
+                        __fadd_ru(1.0f, pow_err(ym, I.pow_rel_q, I.lnk_q)));
         ly_ = 0.0f;
     }
     e.hi = __fadd_ru(hx_, hy_);

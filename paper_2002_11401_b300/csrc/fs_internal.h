@@ -53,6 +53,7 @@ struct fs_sim {
     std::vector<float2> rbc32;
     std::vector<double2> rbc64;
     bool built = false;
+    int device = -1;  // the CUDA device current when the parameters were set
     bool fields_valid = false;
     // current external field and thermal step
     double hx = 0.0, hy = 0.0;

@@ -148,6 +148,9 @@ extern "C" fs_status fs_eval_argmax_static(const fs_sim* sim, const int8_t* d_sp
     if (tree_bytes + cnt_bytes > kStaticScratchBytes) return FS_ERR_INVALID;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FS_ERR_CUDA;
+    // the simulation's buffers live on the device it was built on; the scratch
+    // address looked up below is that of the current device
+    if (dev != sim->device) return FS_ERR_STATE;
     void* base = nullptr;
     {
         std::lock_guard<std::mutex> g(g_mu);

@@ -889,6 +889,12 @@ __global__ void __launch_bounds__(kT, MINB)
     const int64_t flips_before = threadIdx.x == 0 ? st->n_flips : 0;
     const int64_t max_flips = I.max_flips;
     int par = 0;  // parity of the flip whose neighbour updates ran last
+    // Full-scan comparisons that demoted every contender without a flip, since the
+    // last flip. Each one lowers at least one key to zero, so a relax needs at most
+    // n of them in a row; the cap turns a failure of that argument into ST_BOUNDS
+    // instead of an endless loop.
+    int64_t demotions = 0;
+    const int64_t kMaxDemotions = I.n + 64;
 
     // Thread 0: flip island k, log it, publish its row.
     auto do_flip = [&](int64_t k, int sk, int64_t a0, int64_t a1) {
@@ -971,10 +977,11 @@ __global__ void __launch_bounds__(kT, MINB)
                 r = recheck_scan<PREC>(I, L, R, tau, step);
                 tau = R.tau;
             }
-            if (r == -1) {
+            if (r == -1 && ++demotions <= kMaxDemotions) {
                 __syncthreads();
                 continue;  // everything examined was demoted: look at the root again
             }
+            if (r == -1) r = -2;  // (the retries' cap: reported as a bounds failure)
             if (r == -2) {
                 k = kPickBounds;
             } else {
@@ -1004,6 +1011,7 @@ __global__ void __launch_bounds__(kT, MINB)
         }
         if (k < 0) break;
         ++flips;
+        demotions = 0;
         par ^= 1;
         if (threadIdx.x == kHashThread) hash = fnv_flip(hash, step, (uint32_t)k);
         // every neighbour i of k: add 2 s_k(new) (P_ik, Q_ik), new key, tree update

@@ -22,15 +22,23 @@ from .helpers import lib_sim, small
 pytestmark = pytest.mark.gpu
 
 
-def test_static_scratch_sweep_matches_allocating_entry_points():
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n_cells", [24, 110])
+def test_static_scratch_sweep_matches_allocating_entry_points(prec, n_cells):
+    """On a simulation of either precision (the entry point always evaluates in
+    the FS_FP64 arithmetic, which both keep) and on arrays with a three-level and a
+    four-level tree (kagome 24x24 = 1,775 and 110x110 = 36,739 islands). The call
+    leaves the simulation's own device memory as it was."""
     import torch
     from paper_2002_11401_b300 import build
     build.build()
     from paper_2002_11401_b300 import binding as B
     lib = B.load()
-    w = small(I.KAGOME, 24, sigma_th=0.004, alpha=3e-3, seed=21)
-    ref = lib_sim(w, precision=B.FS_FP64)
-    n = ref.n
+    w = small(I.KAGOME, n_cells, sigma_th=0.004, alpha=3e-3, seed=21)
+    sim = lib_sim(w, precision=prec)
+    ref = lib_sim(w, precision=B.FS_FP64)  # the allocating entry points' FP64 values
+    n = sim.n
+    bytes_before = sim.info().device_bytes
     stream = torch.cuda.Stream()
     d_lhs = torch.full((n,), -7.0, dtype=torch.float64, device="cuda")
     d_best = torch.full((1,), -9, dtype=torch.int64, device="cuda")
@@ -43,14 +51,15 @@ def test_static_scratch_sweep_matches_allocating_entry_points():
         hpar, _ = ref.fields()
         lhs = ref.lhs()
         expect = np.where((spins * hpar < 0) & (lhs > 1.0), lhs, 0.0)
-        probe = lib_sim(w, precision=B.FS_FP64)
+        probe = lib_sim(w, precision=prec)
         probe.set_spins(spins)
         probe.set_field(hx, hy, step=step)
         nflips, first = probe.relax(log_cap=1)
+        probe.close()
         # the allocation-free entry point
         d_spins = torch.from_numpy(spins).to("cuda")
         torch.cuda.synchronize()
-        st = lib.fs_eval_argmax_static(ref.handle, ctypes.c_void_p(d_spins.data_ptr()), hx, hy,
+        st = lib.fs_eval_argmax_static(sim.handle, ctypes.c_void_p(d_spins.data_ptr()), hx, hy,
                                        step, ctypes.c_void_p(d_lhs.data_ptr()),
                                        ctypes.c_void_p(d_best.data_ptr()),
                                        ctypes.c_void_p(stream.cuda_stream))
@@ -63,6 +72,9 @@ def test_static_scratch_sweep_matches_allocating_entry_points():
         assert nflips > 0
         assert best == int(first[0])
         assert best == int(np.argmax(expect))
+    assert sim.info().device_bytes == bytes_before
+    sim.close()
+    ref.close()
 
 
 def test_static_scratch_sweep_rejects_bad_calls():
