@@ -26,6 +26,9 @@ _lock = threading.Lock()
 _lib = None
 
 SQUARE, PINWHEEL, KAGOME = 0, 1, 2
+SQUARE_OPEN, PINWHEEL_DIAMOND, PINWHEEL_LUCKY_KNOT, ISING = 3, 4, 5, 6
+ASTROID, PARALLEL = 0, 1  # switching criteria
+SINUSOID, SAWTOOTH, ROTATION = 0, 1, 2  # input encoders
 MODE_INCREMENTAL, MODE_DEFINITION, MODE_LINEAR = 0, 1, 2
 OK, ERR_NOT_CONVERGED = 0, 4
 
@@ -83,6 +86,19 @@ def _load():
         lib.or_sim_fields.argtypes = [P, P, dbl, dbl, u32, P, P]
         lib.or_sim_run.argtypes = [P, P, P, P, i64, u32, P, P, i64, P, P, P, i64, C.c_int, P]
         lib.or_sim_run.restype = C.c_int
+        lib.or_sim_set_criterion.argtypes = [P, C.c_int]
+        lib.or_parallel_lhs.argtypes = [dbl, dbl]
+        lib.or_parallel_lhs.restype = dbl
+        lib.or_sim_lhs.argtypes = [P, i64, dbl, dbl]
+        lib.or_sim_lhs.restype = dbl
+        lib.or_sim_fields_ext.argtypes = [P, P, dbl, dbl, P, P, dbl, u32, P, P]
+        lib.or_sim_run_ext.argtypes = [P, P, P, P, P, P, P, i64, u32, P, P, i64, P, P, P, i64,
+                                       C.c_int, P]
+        lib.or_sim_run_ext.restype = C.c_int
+        lib.or_sample_grid.argtypes = [i64, P, P, i64, i32, i32, dbl, dbl, dbl, dbl, P, P, P, P]
+        lib.or_encode.argtypes = [C.c_int, i64, P, i32, dbl, dbl, dbl, P, P]
+        lib.or_encode.restype = i64
+        lib.or_correlation.argtypes = [i64, P, P, P, P, dbl, dbl, i32, P, P]
         lib.or_hash_init.restype = u64
         lib.or_hash_flip.argtypes = [u64, u32, u32]
         lib.or_hash_flip.restype = u64
@@ -167,6 +183,54 @@ def astroid_lhs(hpar, hperp, hk, b, c, beta, gamma) -> float:
     return float(_load().or_astroid_lhs(hpar, hperp, hk, b, c, beta, gamma))
 
 
+def parallel_lhs(hpar, hk) -> float:
+    """The parallel-only criterion's LHS, |h_par| / h_k (pinwheel section)."""
+    return float(_load().or_parallel_lhs(hpar, hk))
+
+
+def sample_grid(x, y, gw, gh, x0, y0, dx, dy, gx, gy):
+    """A spatial field h_ext(r) on a gw x gh grid (K steps of gh x gw vectors, arrays
+    of shape (K, gh, gw)) sampled at the island centres: (K, n) arrays per component."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    gx = np.ascontiguousarray(gx, dtype=np.float64)
+    gy = np.ascontiguousarray(gy, dtype=np.float64)
+    K = gx.shape[0]
+    n = len(x)
+    ox = np.empty((K, n))
+    oy = np.empty((K, n))
+    _load().or_sample_grid(n, _ptr(x), _ptr(y), K, gw, gh, x0, y0, dx, dy, _ptr(gx), _ptr(gy),
+                           _ptr(ox), _ptr(oy))
+    return ox, oy
+
+
+def encode(kind: int, inputs, period: int, h_lo: float, h_hi: float, angle_deg: float):
+    """Input encoder (Sec. "Simulation framework"): one period of a sinusoid, sawtooth
+    or rotation per input value, amplitude h_lo + (h_hi - h_lo) u."""
+    u = np.ascontiguousarray(inputs, dtype=np.float64)
+    m = len(u)
+    hx = np.empty(max(m * period, 1))
+    hy = np.empty(max(m * period, 1))
+    k = _load().or_encode(kind, m, _ptr(u), period, h_lo, h_hi, angle_deg, _ptr(hx), _ptr(hy))
+    if k < 0:
+        raise ValueError("bad encoder arguments")
+    return hx[:k].copy(), hy[:k].copy()
+
+
+def correlation(x, y, theta, s, rmax: float, width: float, nbins: int):
+    """Spin-spin correlation against separation (Sec. "Domain size in square ASI"):
+    per bin the number of pairs and the sum of their correlations."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    t = np.ascontiguousarray(theta, dtype=np.float64)
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    cnt = np.zeros(nbins, dtype=np.int64)
+    sm = np.zeros(nbins, dtype=np.int64)
+    _load().or_correlation(len(x), _ptr(x), _ptr(y), _ptr(t), _ptr(s), rmax, width, nbins,
+                           _ptr(cnt), _ptr(sm))
+    return cnt, sm
+
+
 def flippable(s: int, hpar: float, lhs: float) -> bool:
     """Eq. (5) > 1 and Eq. (6)."""
     return bool(_load().or_flippable(int(s), hpar, lhs))
@@ -205,7 +269,8 @@ class Sim:
     parameters (alpha, astroid b, c, beta, gamma, sigma_th, cutoff, seed)."""
 
     def __init__(self, x, y, theta, hk, *, alpha, b=1.0, c=1.0, beta=3.0, gamma=3.0,
-                 sigma_th=0.0, cutoff_abs, seed=0, instance=0, brute_neighbors=False):
+                 sigma_th=0.0, cutoff_abs, seed=0, instance=0, brute_neighbors=False,
+                 criterion=ASTROID):
         self._lib = _load()
         self.x = np.ascontiguousarray(x, dtype=np.float64)
         self.y = np.ascontiguousarray(y, dtype=np.float64)
@@ -219,6 +284,8 @@ class Sim:
                                           cutoff_abs, seed, instance, int(brute_neighbors))
         if not self._h:
             raise MemoryError("oracle: could not create the system")
+        self.criterion = criterion
+        self._lib.or_sim_set_criterion(self._h, int(criterion))
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -244,17 +311,33 @@ class Sim:
         self._lib.or_sim_dip_fields(self._h, _ptr(s), _ptr(hx), _ptr(hy))
         return hx, hy
 
-    def fields(self, s, hex_=0.0, hey=0.0, step=0):
-        """Eq. (2) in each island's frame: (h_par, h_perp)."""
+    def fields(self, s, hex_=0.0, hey=0.0, step=0, lx=None, ly=None, sigma=None):
+        """Eq. (2) in each island's frame: (h_par, h_perp); lx, ly: the per-island
+        external field (lab frame, added to the global one); sigma: the thermal
+        standard deviation of this step (default sigma_th)."""
         s = np.ascontiguousarray(s, dtype=np.int8)
         hp = np.empty(self.n)
         hq = np.empty(self.n)
-        self._lib.or_sim_fields(self._h, _ptr(s), hex_, hey, step, _ptr(hp), _ptr(hq))
+        lx = None if lx is None else np.ascontiguousarray(lx, dtype=np.float64)
+        ly = None if ly is None else np.ascontiguousarray(ly, dtype=np.float64)
+        sig = self.params["sigma_th"] if sigma is None else sigma
+        self._lib.or_sim_fields_ext(self._h, _ptr(s), hex_, hey,
+                                    _ptr(lx) if lx is not None else None,
+                                    _ptr(ly) if ly is not None else None, sig, step, _ptr(hp),
+                                    _ptr(hq))
         return hp, hq
 
+    def lhs(self, hp, hq):
+        """The LHS the switching rule ranks by (Eq. 5, or the parallel-only
+        criterion), per island, for fields in the islands' frames."""
+        return np.array([self._lib.or_sim_lhs(self._h, i, float(hp[i]), float(hq[i]))
+                         for i in range(self.n)])
+
     def run(self, s, hx, hy, *, step0=0, log_cap=None, mode=MODE_INCREMENTAL,
-            max_flips_per_step=0, hash_in=None):
+            max_flips_per_step=0, hash_in=None, lhx=None, lhy=None, sigma=None):
         """Field steps t = 0..K-1, each a relax to a fixed point (Sec. "Dynamics").
+        lhx, lhy: (K, n) per-island external fields added to the global (hx[t],
+        hy[t]); sigma: K per-step thermal standard deviations.
 
         Returns a dict with the final spins, the flip log (step, spin), flips per
         step, the sequence hash, the status and the near-tie counters."""
@@ -271,9 +354,19 @@ class Sim:
         h = C.c_uint64(hash_init() if hash_in is None else hash_in)
         nf = C.c_int64(0)
         ties = np.zeros(3, dtype=np.int64)
-        st = self._lib.or_sim_run(self._h, _ptr(s), _ptr(hx), _ptr(hy), K, step0, _ptr(ls),
-                                  _ptr(lk), log_cap, _ptr(fps), C.byref(h), C.byref(nf),
-                                  max_flips_per_step, mode, _ptr(ties))
+        lx = None if lhx is None else np.ascontiguousarray(lhx, dtype=np.float64)
+        ly = None if lhy is None else np.ascontiguousarray(lhy, dtype=np.float64)
+        sg = None if sigma is None else np.ascontiguousarray(sigma, dtype=np.float64)
+        if lx is not None:
+            assert lx.size == K * self.n and ly is not None and ly.size == K * self.n
+        if sg is not None:
+            assert sg.size == K
+        st = self._lib.or_sim_run_ext(self._h, _ptr(s), _ptr(hx), _ptr(hy),
+                                      _ptr(lx) if lx is not None else None,
+                                      _ptr(ly) if ly is not None else None,
+                                      _ptr(sg) if sg is not None else None, K, step0, _ptr(ls),
+                                      _ptr(lk), log_cap, _ptr(fps), C.byref(h), C.byref(nf),
+                                      max_flips_per_step, mode, _ptr(ties))
         m = min(nf.value, log_cap)
         return dict(status=st, spins=s, log_step=ls[:m].copy(), log_spin=lk[:m].copy(),
                     flips_per_step=fps[:K].copy(), hash=int(h.value), n_flips=int(nf.value),

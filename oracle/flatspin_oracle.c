@@ -31,12 +31,25 @@
  *   - random numbers come from Philox4x32-10 (Salmon, Moraes, Dror, Shaw,
  *     SC'11, "Parallel random numbers: as easy as 1, 2, 3") and Box-Muller.
  *
+ * Variants, with the readings they take where the paper gives only a figure or a
+ * name (all listed in the design notes): the open-edged square, the pinwheel
+ * "diamond" and "lucky-knot" edge forms and the ising array (Fig. "geometries");
+ * the parallel-only switching criterion the pinwheel section contrasts with
+ * Eq. (5); per-island and spatial external fields and the sinusoid, sawtooth and
+ * rotation input encoders (Sec. "External field", Sec. "Simulation framework");
+ * per-step thermal standard deviations (annealing) and the spin-spin correlation
+ * against separation (Sec. "Domain size in square ASI").
+ *
  * Parity pins (tests/test_oracle_*.py): the pair field against the closed-form
  * field of a point dipole; Eq. (5) against the Stoner-Wohlfarth astroid's closed
  * form; the relax against a brute-force state table and the energy invariant;
  * geometry counts against the paper's printed count (29x29 kagome = 2638) and
  * the 8-neighbour square neighbourhood of the performance section; Philox
- * against an independent third-party implementation.
+ * against an independent third-party implementation; the variants against the
+ * paper's 25 x 25 = 1250 pinwheel count, closed-form switching fields and switching
+ * times, uniform local and spatial fields against the global field, constant
+ * thermal series against sigma_th, and the correlation against closed-form pair
+ * counts and the sign of the Eq. (3) pair energy.
  */
 #include <math.h>
 #include <stdint.h>
@@ -150,7 +163,15 @@ void or_thermal(int64_t n, double sigma, uint64_t seed, uint32_t instance, uint3
 /* Geometry (Sec. "Geometries", Fig. "geometries")                           */
 /* ------------------------------------------------------------------------ */
 
-enum { OR_SQUARE = 0, OR_PINWHEEL = 1, OR_KAGOME = 2 };
+enum {
+    OR_SQUARE = 0,
+    OR_PINWHEEL = 1,
+    OR_KAGOME = 2,
+    OR_SQUARE_OPEN = 3,
+    OR_PINWHEEL_DIAMOND = 4,
+    OR_PINWHEEL_LUCKY_KNOT = 5,
+    OR_ISING = 6
+};
 
 typedef struct {
     int64_t X, Y; /* integer lattice coordinates (see or_geometry) */
@@ -169,6 +190,7 @@ static int site_cmp(const void* pa, const void* pb) {
 int64_t or_geometry_capacity(int kind, int32_t nx, int32_t ny) {
     if (nx <= 0 || ny <= 0) return 0;
     if (kind == OR_KAGOME) return 6 * (int64_t)nx * ny;
+    if (kind == OR_ISING) return (int64_t)nx * ny;
     return (int64_t)nx * (ny + 1) + (int64_t)ny * (nx + 1);
 }
 
@@ -181,6 +203,18 @@ int64_t or_geometry_capacity(int kind, int32_t nx, int32_t ny) {
  *
  * Pinwheel: the square's centres, each island turned 45 degrees about its
  * centre (45 and 135 degrees).
+ *
+ * The figure of the geometries names more edge forms without defining them; the
+ * readings here (stated in the design notes) are:
+ * - square, open edges: the closed square without the islands on its outer
+ *   boundary (horizontal islands at y = 0 and y = ny, vertical ones at x = 0 and
+ *   x = nx): 2 nx ny - nx - ny islands;
+ * - pinwheel "diamond": nx x ny unit cells of one horizontal island at
+ *   (x + 1/2, y) and one vertical at (x, y + 1/2), each turned 45 degrees:
+ *   2 nx ny islands (the pinwheel section's 25 x 25 array has 1250);
+ * - pinwheel "lucky-knot": the open-edged square's islands turned 45 degrees;
+ * - ising: one island at every lattice point (x, y), x < nx, y < ny, all along
+ *   x (0 degrees), a single sublattice.
  *
  * Kagome, nx x ny flat-top hexagons with edge length a: hexagon (c, r) centred
  * at (1.5 c, sqrt(3) r + (c odd ? sqrt(3)/2 : 0)); one island on the midpoint
@@ -197,9 +231,17 @@ int64_t or_geometry(int kind, int32_t nx, int32_t ny, double a, double* x, doubl
     if (!s) return -2;
     int64_t m = 0;
     double sx, sy;
-    if (kind == OR_SQUARE || kind == OR_PINWHEEL) {
-        const int rot = kind == OR_PINWHEEL ? 45 : 0;
-        for (int64_t yy = 0; yy <= ny; ++yy)
+    if (kind == OR_SQUARE || kind == OR_PINWHEEL || kind == OR_SQUARE_OPEN ||
+        kind == OR_PINWHEEL_DIAMOND || kind == OR_PINWHEEL_LUCKY_KNOT) {
+        const int rot = (kind == OR_PINWHEEL || kind == OR_PINWHEEL_DIAMOND ||
+                         kind == OR_PINWHEEL_LUCKY_KNOT) ? 45 : 0;
+        const int open = kind == OR_SQUARE_OPEN || kind == OR_PINWHEEL_LUCKY_KNOT;
+        const int cells = kind == OR_PINWHEEL_DIAMOND;
+        /* horizontal islands: rows y = 0..ny (closed), 1..ny-1 (open), 0..ny-1 (cells) */
+        const int64_t hy0 = open ? 1 : 0, hy1 = (open || cells) ? ny - 1 : ny;
+        /* vertical islands: columns x = 0..nx (closed), 1..nx-1 (open), 0..nx-1 (cells) */
+        const int64_t vx0 = open ? 1 : 0, vx1 = (open || cells) ? nx - 1 : nx;
+        for (int64_t yy = hy0; yy <= hy1; ++yy)
             for (int64_t xx = 0; xx < nx; ++xx) {
                 s[m].X = 2 * xx + 1;
                 s[m].Y = 2 * yy;
@@ -207,10 +249,20 @@ int64_t or_geometry(int kind, int32_t nx, int32_t ny, double a, double* x, doubl
                 ++m;
             }
         for (int64_t yy = 0; yy < ny; ++yy)
-            for (int64_t xx = 0; xx <= nx; ++xx) {
+            for (int64_t xx = vx0; xx <= vx1; ++xx) {
                 s[m].X = 2 * xx;
                 s[m].Y = 2 * yy + 1;
                 s[m].deg = 90 + rot;
+                ++m;
+            }
+        sx = 0.5;
+        sy = 0.5;
+    } else if (kind == OR_ISING) {
+        for (int64_t yy = 0; yy < ny; ++yy)
+            for (int64_t xx = 0; xx < nx; ++xx) {
+                s[m].X = 2 * xx;
+                s[m].Y = 2 * yy;
+                s[m].deg = 0;
                 ++m;
             }
         sx = 0.5;
@@ -249,7 +301,7 @@ int64_t or_geometry(int kind, int32_t nx, int32_t ny, double a, double* x, doubl
         theta[i] = ((double)s[i].deg * M_PI) / 180.0;
     }
     free(s);
-    return n;
+    return n > 0 ? n : -1;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -281,6 +333,13 @@ double or_astroid_lhs(double hpar, double hperp, double hk, double b, double c, 
 
 /* Eq. (5) > 1 and Eq. (6): h . m_i < 0, i.e. s_i h_par < 0. */
 int or_flippable(int s, double hpar, double lhs) { return ((double)s * hpar < 0.0) && (lhs > 1.0); }
+
+/* The simpler switching criterion the pinwheel section contrasts with Eq. (5):
+ * only the field component along the magnet counts. Read as: the island may switch
+ * when the component opposing its magnetisation exceeds its coercive field,
+ * -s h_par > h_k; its "left-hand side" is |h_par| / h_k, so that the same rule
+ * (LHS > 1 and Eq. (6)) and the same ranking (largest LHS first) apply. */
+double or_parallel_lhs(double hpar, double hk) { return fabs(hpar) / hk; }
 
 /* ------------------------------------------------------------------------ */
 /* Neighbourhoods (Sec. "Magnetic dipole-dipole interactions", cutoff)       */
@@ -376,6 +435,7 @@ typedef struct {
     double alpha, b, c, beta, gamma, sigma_th, cutoff_abs;
     uint64_t seed;
     uint32_t instance;
+    int criterion; /* 0: Eq. (5) and (6); 1: parallel component only (or_parallel_lhs) */
 } or_params;
 
 typedef struct {
@@ -448,6 +508,9 @@ or_sim* or_sim_create(int64_t n, const double* x, const double* y, const double*
     return s;
 }
 
+/* Switching criterion: 0 = Eq. (5) and (6) (the default), 1 = parallel only. */
+void or_sim_set_criterion(or_sim* s, int criterion) { s->p.criterion = criterion; }
+
 int64_t or_sim_n(const or_sim* s) { return s->n; }
 int64_t or_sim_nnz(const or_sim* s) { return s->nnz; }
 
@@ -498,22 +561,38 @@ static void project_total(const or_sim* S, int64_t i, double hdx, double hdy, do
 }
 
 /* Total field of every island in its own frame, for spin state s, external field
- * (hex, hey) and the thermal draw of field step `step`. */
-void or_sim_fields(const or_sim* S, const int8_t* s, double hex, double hey, uint32_t step,
-                   double* hpar, double* hperp) {
+ * (hex, hey) plus the per-island field (lx[i], ly[i]) when given (Sec. "External
+ * field": local or spatial form; lab frame, added to the global field), and the
+ * thermal draw of field step `step` with standard deviation sigma. */
+void or_sim_fields_ext(const or_sim* S, const int8_t* s, double hex, double hey, const double* lx,
+                       const double* ly, double sigma, uint32_t step, double* hpar,
+                       double* hperp) {
     const int64_t n = S->n;
     double* hdx = (double*)malloc(sizeof(double) * (size_t)n);
     double* hdy = (double*)malloc(sizeof(double) * (size_t)n);
     double* tp = (double*)calloc((size_t)n, sizeof(double));
     double* tq = (double*)calloc((size_t)n, sizeof(double));
     or_sim_dip_fields(S, s, hdx, hdy);
-    if (S->p.sigma_th > 0.0) or_thermal(n, S->p.sigma_th, S->p.seed, S->p.instance, step, tp, tq);
+    if (S->p.sigma_th > 0.0) or_thermal(n, sigma, S->p.seed, S->p.instance, step, tp, tq);
     for (int64_t i = 0; i < n; ++i)
-        project_total(S, i, hdx[i], hdy[i], hex, hey, tp[i], tq[i], &hpar[i], &hperp[i]);
+        project_total(S, i, hdx[i], hdy[i], lx ? hex + lx[i] : hex, ly ? hey + ly[i] : hey,
+                      tp[i], tq[i], &hpar[i], &hperp[i]);
     free(hdx);
     free(hdy);
     free(tp);
     free(tq);
+}
+
+/* As or_sim_fields_ext with the global field only and the system's sigma_th. */
+void or_sim_fields(const or_sim* S, const int8_t* s, double hex, double hey, uint32_t step,
+                   double* hpar, double* hperp) {
+    or_sim_fields_ext(S, s, hex, hey, NULL, NULL, S->p.sigma_th, step, hpar, hperp);
+}
+
+/* The LHS the switching rule ranks by, for the system's criterion. */
+double or_sim_lhs(const or_sim* S, int64_t i, double hpar, double hperp) {
+    if (S->p.criterion == 1) return or_parallel_lhs(hpar, S->hk[i]);
+    return or_astroid_lhs(hpar, hperp, S->hk[i], S->p.b, S->p.c, S->p.beta, S->p.gamma);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -608,6 +687,7 @@ typedef struct {
     const or_sim* S;
     const int8_t* s;
     double hex, hey;
+    const double *lx, *ly; /* this step's per-island external field, or NULL */
     const double *tp, *tq;
     double* hdx;
     double* hdy;
@@ -621,9 +701,10 @@ typedef struct {
 static void eval_island(relax_ctx* c, int64_t i) {
     const or_sim* S = c->S;
     double hpar, hperp;
-    project_total(S, i, c->hdx[i], c->hdy[i], c->hex, c->hey, c->tp ? c->tp[i] : 0.0,
+    project_total(S, i, c->hdx[i], c->hdy[i], c->lx ? c->hex + c->lx[i] : c->hex,
+                  c->ly ? c->hey + c->ly[i] : c->hey, c->tp ? c->tp[i] : 0.0,
                   c->tq ? c->tq[i] : 0.0, &hpar, &hperp);
-    const double L = or_astroid_lhs(hpar, hperp, S->hk[i], S->p.b, S->p.c, S->p.beta, S->p.gamma);
+    const double L = or_sim_lhs(S, i, hpar, hperp);
     c->hpar[i] = hpar;
     c->lhs[i] = L;
     const int fl = or_flippable(c->s[i], hpar, L);
@@ -634,16 +715,21 @@ static void eval_island(relax_ctx* c, int64_t i) {
     }
 }
 
-/* Runs K field steps. Step t uses the external field (hx[t], hy[t]) and the
- * thermal draw keyed by step index step0 + t. `s` holds the spins on entry and
+/* Runs K field steps. Step t uses the external field (hx[t], hy[t]), plus, when
+ * lhx/lhy are given, the per-island field (lhx[t n + i], lhy[t n + i]) (Sec.
+ * "External field": local, or spatial sampled at the island centres; lab frame),
+ * and the thermal draw keyed by step index step0 + t with standard deviation
+ * sig[t] when sig is given (a thermal protocol such as the annealing of Sec.
+ * "Domain size in square ASI"), else sigma_th. `s` holds the spins on entry and
  * receives the final state. The first log_cap flips are written to
  * log_step/log_spin (may be NULL); flips_per_step[K] may be NULL; *hash is
  * updated in place (start from or_hash_init()). max_flips_per_step <= 0 means
  * 16 * n. Returns OR_OK or OR_ERR_NOT_CONVERGED. */
-int or_sim_run(const or_sim* S, int8_t* s, const double* hx, const double* hy, int64_t K,
-               uint32_t step0, uint32_t* log_step, uint32_t* log_spin, int64_t log_cap,
-               int64_t* flips_per_step, uint64_t* hash, int64_t* n_flips,
-               int64_t max_flips_per_step, int mode, int64_t* ties) {
+int or_sim_run_ext(const or_sim* S, int8_t* s, const double* hx, const double* hy,
+                   const double* lhx, const double* lhy, const double* sig, int64_t K,
+                   uint32_t step0, uint32_t* log_step, uint32_t* log_spin, int64_t log_cap,
+                   int64_t* flips_per_step, uint64_t* hash, int64_t* n_flips,
+                   int64_t max_flips_per_step, int mode, int64_t* ties) {
     const int64_t n = S->n;
     int status = OR_OK;
     if (max_flips_per_step <= 0) max_flips_per_step = 16 * n;
@@ -678,7 +764,9 @@ int or_sim_run(const or_sim* S, int8_t* s, const double* hx, const double* hy, i
         const uint32_t step = step0 + (uint32_t)t;
         c.hex = hx[t];
         c.hey = hy[t];
-        if (tp) or_thermal(n, S->p.sigma_th, S->p.seed, S->p.instance, step, tp, tq);
+        c.lx = lhx ? lhx + t * n : NULL;
+        c.ly = lhy ? lhy + t * n : NULL;
+        if (tp) or_thermal(n, sig ? sig[t] : S->p.sigma_th, S->p.seed, S->p.instance, step, tp, tq);
         /* "At each simulation step, we calculate the total magnetic field". */
         or_sim_dip_fields(S, s, c.hdx, c.hdy);
         for (int64_t i = 0; i < n; ++i) eval_island(&c, i);
@@ -757,4 +845,116 @@ int or_sim_run(const or_sim* S, int8_t* s, const double* hx, const double* hy, i
     free(tp);
     free(tq);
     return status;
+}
+
+/* The global-field form of or_sim_run_ext. */
+int or_sim_run(const or_sim* S, int8_t* s, const double* hx, const double* hy, int64_t K,
+               uint32_t step0, uint32_t* log_step, uint32_t* log_spin, int64_t log_cap,
+               int64_t* flips_per_step, uint64_t* hash, int64_t* n_flips,
+               int64_t max_flips_per_step, int mode, int64_t* ties) {
+    return or_sim_run_ext(S, s, hx, hy, NULL, NULL, NULL, K, step0, log_step, log_spin, log_cap,
+                          flips_per_step, hash, n_flips, max_flips_per_step, mode, ties);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Spatial external field h_ext(r) (Sec. "External field")                   */
+/* ------------------------------------------------------------------------ */
+
+/* A spatial field given on a grid of gw x gh cells, cell (cx, cy) covering
+ * [x0 + cx dx, x0 + (cx + 1) dx) x [y0 + cy dy, y0 + (cy + 1) dy), K time steps of
+ * lab-frame vectors grid[t][cy][cx] (row-major), sampled at each island's centre:
+ * the island takes the value of the cell that contains it (a centre outside the
+ * grid takes the nearest edge cell). Writes out[t n + i]. */
+void or_sample_grid(int64_t n, const double* x, const double* y, int64_t K, int32_t gw,
+                    int32_t gh, double x0, double y0, double dx, double dy, const double* gx,
+                    const double* gy, double* outx, double* outy) {
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t cx = (int64_t)floor((x[i] - x0) / dx);
+        int64_t cy = (int64_t)floor((y[i] - y0) / dy);
+        if (cx < 0) cx = 0;
+        if (cx > gw - 1) cx = gw - 1;
+        if (cy < 0) cy = 0;
+        if (cy > gh - 1) cy = gh - 1;
+        for (int64_t t = 0; t < K; ++t) {
+            outx[t * n + i] = gx[(t * gh + cy) * gw + cx];
+            outy[t * n + i] = gy[(t * gh + cy) * gw + cx];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Input encoders (Sec. "Simulation framework": sinusoidal, sawtooth and      */
+/* rotational fields)                                                         */
+/* ------------------------------------------------------------------------ */
+
+/* Each input value u_k (k < m) becomes one period of `period` field values with
+ * amplitude A_k = h_lo + (h_hi - h_lo) u_k:
+ *   kind 0, sinusoid:  A_k sin(2 pi j / period) along the angle `angle_deg`;
+ *   kind 1, sawtooth:  A_k (2 j / (period - 1) - 1) along the angle, a linear rise
+ *                      from -A_k to +A_k;
+ *   kind 2, rotation:  magnitude A_k at the angle angle_deg + 360 j / period;
+ * for j = 0 .. period - 1, written to hx, hy[k period + j]. Angles in degrees,
+ * converted as (deg pi) / 180. Returns m period, or -1 on bad arguments. */
+int64_t or_encode(int kind, int64_t m, const double* u, int32_t period, double h_lo, double h_hi,
+                  double angle_deg, double* hx, double* hy) {
+    if (m < 0 || period < 1 || (kind == 1 && period < 2) || kind < 0 || kind > 2) return -1;
+    const double phi = (angle_deg * M_PI) / 180.0;
+    for (int64_t k = 0; k < m; ++k) {
+        const double A = h_lo + (h_hi - h_lo) * u[k];
+        for (int32_t j = 0; j < period; ++j) {
+            double h = 0.0, ang = phi;
+            if (kind == 0) {
+                h = A * sin((2.0 * M_PI * (double)j) / (double)period);
+            } else if (kind == 1) {
+                h = A * ((2.0 * (double)j) / (double)(period - 1) - 1.0);
+            } else {
+                h = A;
+                ang = ((angle_deg + (360.0 * (double)j) / (double)period) * M_PI) / 180.0;
+            }
+            hx[k * period + j] = h * cos(ang);
+            hy[k * period + j] = h * sin(ang);
+        }
+    }
+    return m * period;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Spin-spin correlation against separation (Sec. "Domain size in square ASI") */
+/* ------------------------------------------------------------------------ */
+
+/* The correlation of two spins is +1 when their dipolar interaction is at its
+ * minimum and -1 at its maximum. The pair energy of islands i, j is
+ * -alpha s_i s_j v_ij / r^3 with v_ij = 3 (mhat_i . rhat)(mhat_j . rhat) - mhat_i . mhat_j
+ * (Eq. 3), so the correlation is sign(s_i s_j v_ij). For every unordered pair
+ * i < j with |r_ij|^2 <= rmax^2 (1 + 1e-9) it goes to bin floor(|r_ij| / w + 1e-7)
+ * (the small offset keeps separations that are whole multiples of w, up to
+ * rounding, in the upper bin); pairs with |v_ij| <= 1e-9 (no preferred relative
+ * orientation) and bins >= nbins are left out. count[b] receives the pairs of bin
+ * b and sum[b] the sum of their correlations: the mean is sum / count. */
+void or_correlation(int64_t n, const double* x, const double* y, const double* theta,
+                    const int8_t* s, double rmax, double w, int32_t nbins, int64_t* count,
+                    int64_t* sum) {
+    for (int32_t b = 0; b < nbins; ++b) {
+        count[b] = 0;
+        sum[b] = 0;
+    }
+    const double r2max = rmax * rmax * (1.0 + 1e-9);
+    for (int64_t i = 0; i < n; ++i) {
+        const double mix = cos(theta[i]), miy = sin(theta[i]);
+        for (int64_t j = i + 1; j < n; ++j) {
+            const double rx = x[i] - x[j], ry = y[i] - y[j];
+            const double r2 = rx * rx + ry * ry;
+            if (r2 > r2max) continue;
+            const double r = sqrt(r2);
+            const int64_t b = (int64_t)floor(r / w + 1e-7);
+            if (b >= nbins) continue;
+            const double mjx = cos(theta[j]), mjy = sin(theta[j]);
+            const double ui = (mix * rx + miy * ry) / r, uj = (mjx * rx + mjy * ry) / r;
+            const double v = 3.0 * ui * uj - (mix * mjx + miy * mjy);
+            if (fabs(v) <= 1e-9) continue;
+            const int sv = v > 0.0 ? 1 : -1;
+            count[b] += 1;
+            sum[b] += (int64_t)s[i] * (int64_t)s[j] * sv;
+        }
+    }
 }
