@@ -53,7 +53,24 @@ typedef enum {
     FS_ERR_STATE = 8          /* call out of order (e.g. relax before params) */
 } fs_status;
 
-typedef enum { FS_SQUARE = 0, FS_PINWHEEL = 1, FS_KAGOME = 2 } fs_geom;
+/* Geometries (Sec. "Geometries", Fig. "geometries"); see fs_create_geometry. */
+typedef enum {
+    FS_SQUARE = 0,
+    FS_PINWHEEL = 1,
+    FS_KAGOME = 2,
+    FS_SQUARE_OPEN = 3,
+    FS_PINWHEEL_DIAMOND = 4,
+    FS_PINWHEEL_LUCKY_KNOT = 5,
+    FS_ISING = 6
+} fs_geom;
+
+/* Switching criterion. FS_CRITERION_ASTROID: Eq. 5 > 1 and Eq. 6 (Sec.
+ * "Switching"). FS_CRITERION_PARALLEL: the simpler criterion the pinwheel section
+ * contrasts with it (only the field component along the magnet counts): an island
+ * may switch when the component opposing its magnetisation exceeds its coercive
+ * field, -s h_par > h_k; its LHS, the ranked quantity, is |h_par| / h_k (b, c,
+ * beta and gamma are not used). */
+typedef enum { FS_CRITERION_ASTROID = 0, FS_CRITERION_PARALLEL = 1 } fs_criterion;
 
 /* Arithmetic of the relax loop.
  * FS_FP64: dipolar sums in 64-bit fixed point (exact integer sums of per-pair
@@ -77,6 +94,8 @@ typedef struct {
     uint32_t instance;  /* third Philox counter word (ensemble member) */
     int32_t precision;  /* fs_precision */
     int64_t max_flips_per_step; /* guard; <= 0 means 16 * n */
+    int32_t criterion;  /* fs_criterion (0: Eq. 5 and 6) */
+    int32_t reserved;   /* 0 */
 } fs_params;
 
 typedef struct fs_sim fs_sim;
@@ -101,11 +120,20 @@ const char* fs_last_error(const fs_sim* sim);
  * every flip, in order. */
 uint64_t fs_hash_init(void);
 
-/* Generated arrays (Sec. "Geometries"): nx x ny cells of spacing a.
- * Square: closed edges, islands at 0 and 90 degrees, 2 nx ny + nx + ny islands.
- * Pinwheel: the square's islands turned 45 degrees about their centres.
- * Kagome: nx x ny flat-top hexagons of edge a, islands at 0/60/120 degrees on
+/* Generated arrays (Sec. "Geometries", Fig. "geometries"): nx x ny cells of
+ * spacing a.
+ * FS_SQUARE: closed edges, islands at 0 and 90 degrees, 2 nx ny + nx + ny islands.
+ * FS_PINWHEEL: the square's islands turned 45 degrees about their centres.
+ * FS_KAGOME: nx x ny flat-top hexagons of edge a, islands at 0/60/120 degrees on
  *   the edge midpoints, 3 nx ny + 2 nx + 2 ny - 1 islands.
+ * The figure names further edge forms without defining them; these readings:
+ * FS_SQUARE_OPEN: open edges, the closed square without the islands on its outer
+ *   boundary, 2 nx ny - nx - ny islands (needs nx + ny > 2).
+ * FS_PINWHEEL_DIAMOND: nx x ny unit cells of one horizontal island at
+ *   (x + 1/2, y) and one vertical at (x, y + 1/2), turned 45 degrees: 2 nx ny
+ *   islands (the pinwheel section's 25 x 25 array has 1250).
+ * FS_PINWHEEL_LUCKY_KNOT: the open-edged square's islands turned 45 degrees.
+ * FS_ISING: one island at every lattice point (x, y), all at 0 degrees.
  * Angles are (deg * pi) / 180 in double. *out receives a new simulation. */
 fs_status fs_create_geometry(int32_t kind, int32_t nx, int32_t ny, double a, fs_sim** out);
 
@@ -238,6 +266,75 @@ fs_status fs_get_info(const fs_sim* sim, fs_info* out);
  * FP64-path coefficients P[nnz], Q[nnz] (fixed point converted back to double;
  * field at i per unit spin of j, in i's frame). Any output may be NULL. */
 fs_status fs_get_csr(const fs_sim* sim, int64_t* row_ptr, int32_t* col, double* P, double* Q);
+
+/* ---- External fields beyond the global one; thermal protocols ----------------
+ * Sec. "External field": besides the global field, a field set per island
+ * (local) or given as a spatial vector field, each a discrete time series. Both
+ * are lab-frame vectors added to the global field of the field step. Series are
+ * indexed by the field-step index, the one that keys the thermal draw (step0 + t
+ * in fs_run_protocol, `step` in fs_set_field); a call that reaches a step at or
+ * beyond a series' length fails with FS_ERR_INVALID. At most one local or spatial
+ * series is set at a time (setting one replaces the other); K = 0 clears it.
+ * Series are copied to device memory from the library's pool (not from a bound
+ * workspace) and freed by fs_destroy, by fs_set_params (new parameters drop every
+ * series) or by the next call. Batches accept members with series as long as
+ * they cover the protocol; the allocation-free entry point applies the global
+ * field only.
+ * Errors: FS_ERR_STATE (parameters not set), FS_ERR_INVALID (bad sizes, a
+ * non-finite value), FS_ERR_OOM, FS_ERR_CUDA. */
+
+/* Local field: hx[t*n + i], hy[t*n + i] at field step t for island i (canonical
+ * order), t < K; n must be the island count. Device bytes: 16 K n + 24 n. */
+fs_status fs_set_field_local(fs_sim* sim, const double* hx, const double* hy, int64_t K,
+                             int64_t n);
+
+/* Spatial field h_ext(r) on a grid of gw x gh cells, cell (cx, cy) covering
+ * [x0 + cx dx, x0 + (cx + 1) dx) x [y0 + cy dy, y0 + (cy + 1) dy): at field step
+ * t the cell holds (hx, hy)[(t gh + cy) gw + cx]. An island takes the value of the
+ * cell that contains its centre (an island outside the grid, the nearest edge
+ * cell's). Device bytes: 16 K gw gh + 28 n. */
+fs_status fs_set_field_spatial(fs_sim* sim, const double* hx, const double* hy, int64_t K,
+                               int32_t gw, int32_t gh, double x0, double y0, double dx,
+                               double dy);
+
+/* Thermal protocol (Sec. "Thermal field"; the annealing of Sec. "Domain size in
+ * square ASI" lowers sigma_th step by step): field step t draws its thermal field
+ * with standard deviation sigma[t] (>= 0) instead of sigma_th, t < K. The
+ * simulation's parameters must have sigma_th > 0 (which sets up the thermal
+ * buffers). Resets the FP64 draws kept from earlier calls. K = 0 clears it. */
+fs_status fs_set_sigma_series(fs_sim* sim, const double* sigma, int64_t K);
+
+/* ---- Input encoders (Sec. "Simulation framework") -----------------------------
+ * The encoder turns input values into a series of global external fields. Input
+ * u_k (k < m) becomes one period of `period` values, amplitude
+ * A_k = h_lo + (h_hi - h_lo) u_k, at j = 0 .. period - 1:
+ *   FS_ENCODE_SINUSOID: A_k sin(2 pi j / period) along angle_deg;
+ *   FS_ENCODE_SAWTOOTH: A_k (2 j / (period - 1) - 1) along angle_deg, a linear rise
+ *     from -A_k to +A_k (period >= 2);
+ *   FS_ENCODE_ROTATION: magnitude A_k at the angle angle_deg + 360 j / period.
+ * Writes hx, hy[k period + j] (host buffers of m period values; host arithmetic,
+ * no device work). Angles in degrees, (deg pi) / 180. FS_ERR_INVALID on bad
+ * arguments. */
+typedef enum { FS_ENCODE_SINUSOID = 0, FS_ENCODE_SAWTOOTH = 1, FS_ENCODE_ROTATION = 2 } fs_encoder;
+fs_status fs_encode(int32_t kind, const double* inputs, int64_t m, int32_t period, double h_lo,
+                    double h_hi, double angle_deg, double* hx, double* hy);
+
+/* ---- Spin-spin correlation (Sec. "Domain size in square ASI") -----------------
+ * The correlation of two spins is +1 when their dipolar interaction is at its
+ * minimum and -1 at its maximum: sign(s_i s_j v_ij), v_ij = 3 (mhat_i . rhat_ij)
+ * (mhat_j . rhat_ij) - mhat_i . mhat_j (the pair energy of Eq. 3 is
+ * -alpha s_i s_j v_ij / r^3). Over the current spins, every unordered pair with
+ * |r_ij|^2 <= rmax^2 (1 + 1e-9) falls into bin floor(|r_ij| / bin_width + 1e-7)
+ * (whole multiples of bin_width, up to rounding, go to the upper bin); pairs with
+ * |v_ij| <= 1e-9 and bins >= nbins are left out. Host outputs, nbins values each
+ * (1 <= nbins <= 2048): pair_count[b] pairs, corr_sum[b] the sum of their
+ * correlations (the mean correlation is corr_sum / pair_count). Positions in units
+ * of the array's spacing a as generated. Runs one GPU pass over a cell grid of
+ * cells rmax wide; synchronous on the simulation's stream.
+ * Errors: FS_ERR_STATE (parameters not set), FS_ERR_INVALID, FS_ERR_OOM,
+ * FS_ERR_CUDA. */
+fs_status fs_correlation(fs_sim* sim, double rmax, double bin_width, int32_t nbins,
+                         int64_t* pair_count, int64_t* corr_sum);
 
 /* ---- Allocation-free evaluation ----------------------------------------------
  * The paper has no counterpart; this is a service for callers that cannot

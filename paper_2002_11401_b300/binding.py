@@ -18,7 +18,10 @@ LIB_PATH = os.path.join(_HERE, "libflatspin_b300.so")
 FS_OK, FS_ERR_INVALID, FS_ERR_OOM, FS_ERR_CUDA = 0, 1, 2, 3
 FS_ERR_NOT_CONVERGED, FS_ERR_TIMEOUT, FS_ERR_BOUNDS, FS_ERR_STATE = 4, 5, 6, 8
 FS_SQUARE, FS_PINWHEEL, FS_KAGOME = 0, 1, 2
+FS_SQUARE_OPEN, FS_PINWHEEL_DIAMOND, FS_PINWHEEL_LUCKY_KNOT, FS_ISING = 3, 4, 5, 6
 FS_FP64, FS_FP32_RECHECK = 0, 1
+FS_CRITERION_ASTROID, FS_CRITERION_PARALLEL = 0, 1
+FS_ENCODE_SINUSOID, FS_ENCODE_SAWTOOTH, FS_ENCODE_ROTATION = 0, 1, 2
 
 EXPORTS = (
     "fs_last_error", "fs_hash_init", "fs_create_geometry", "fs_create_custom", "fs_destroy",
@@ -28,7 +31,8 @@ EXPORTS = (
     "fs_server_create", "fs_server_submit", "fs_server_poll", "fs_server_drain",
     "fs_server_now", "fs_server_destroy", "fs_server_last_error", "fs_set_spins_dev",
     "fs_set_profiling", "fs_get_profile", "fs_eval_argmax_static", "fs_autotune",
-    "fs_workspace_bytes", "fs_bind_workspace",
+    "fs_workspace_bytes", "fs_bind_workspace", "fs_set_field_local", "fs_set_field_spatial",
+    "fs_set_sigma_series", "fs_encode", "fs_correlation",
 )
 
 
@@ -43,7 +47,8 @@ class fs_params(C.Structure):
                 ("b", C.c_double), ("c", C.c_double), ("beta", C.c_double),
                 ("gamma", C.c_double), ("cutoff", C.c_double), ("sigma_th", C.c_double),
                 ("seed", C.c_uint64), ("instance", C.c_uint32), ("precision", C.c_int32),
-                ("max_flips_per_step", C.c_int64)]
+                ("max_flips_per_step", C.c_int64), ("criterion", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class fs_info(C.Structure):
@@ -122,6 +127,11 @@ def load():
             "fs_autotune": ([P, P], i32),
             "fs_workspace_bytes": ([P, P, P], i32),
             "fs_bind_workspace": ([P, P, C.c_size_t, P], i32),
+            "fs_set_field_local": ([P, P, P, i64, i64], i32),
+            "fs_set_field_spatial": ([P, P, P, i64, i32, i32, dbl, dbl, dbl, dbl], i32),
+            "fs_set_sigma_series": ([P, P, i64], i32),
+            "fs_encode": ([i32, P, i64, i32, dbl, dbl, dbl, P, P], i32),
+            "fs_correlation": ([P, dbl, dbl, i32, P, P], i32),
         }
         for name, (args, res) in sig.items():
             if not hasattr(lib, name):
@@ -143,9 +153,9 @@ def hash_init() -> int:
 
 def make_params(alpha, hk=0.2, k_disorder=0.05, b=1.0, c=1.0, beta=3.0, gamma=3.0, cutoff=3.0,
                 sigma_th=0.0, seed=0, instance=0, precision=FS_FP64,
-                max_flips_per_step=0) -> fs_params:
+                max_flips_per_step=0, criterion=0) -> fs_params:
     return fs_params(alpha, hk, k_disorder, b, c, beta, gamma, cutoff, sigma_th, seed, instance,
-                     precision, max_flips_per_step)
+                     precision, max_flips_per_step, criterion, 0)
 
 
 class Sim:
@@ -311,6 +321,34 @@ class Sim:
         self._check(self._lib.fs_get_info(self._h, C.byref(out)))
         return out
 
+    def set_field_local(self, hx, hy):
+        """Local external field series: (K, n) arrays per component (K = 0 clears)."""
+        hx = np.ascontiguousarray(hx, dtype=np.float64)
+        hy = np.ascontiguousarray(hy, dtype=np.float64)
+        K = hx.shape[0] if hx.ndim == 2 else 0
+        self._check(self._lib.fs_set_field_local(self._h, _p(hx) if K else None,
+                                                 _p(hy) if K else None, K, self.n))
+
+    def set_field_spatial(self, gx, gy, x0, y0, dx, dy):
+        """Spatial external field series: (K, gh, gw) arrays per component."""
+        gx = np.ascontiguousarray(gx, dtype=np.float64)
+        gy = np.ascontiguousarray(gy, dtype=np.float64)
+        K, gh, gw = gx.shape
+        self._check(self._lib.fs_set_field_spatial(self._h, _p(gx), _p(gy), K, gw, gh, x0, y0,
+                                                   dx, dy))
+
+    def set_sigma_series(self, sigma):
+        """Thermal standard deviation per field step (empty clears)."""
+        sg = np.ascontiguousarray(sigma, dtype=np.float64)
+        self._check(self._lib.fs_set_sigma_series(self._h, _p(sg) if len(sg) else None, len(sg)))
+
+    def correlation(self, rmax: float, width: float, nbins: int):
+        """Spin-spin correlation against separation: (pairs, sums) per bin."""
+        cnt = np.zeros(nbins, dtype=np.int64)
+        sm = np.zeros(nbins, dtype=np.int64)
+        self._check(self._lib.fs_correlation(self._h, rmax, width, nbins, _p(cnt), _p(sm)))
+        return cnt, sm
+
     def csr(self):
         inf = self.info()
         rp = np.empty(self.n + 1, dtype=np.int64)
@@ -319,6 +357,20 @@ class Sim:
         Q = np.empty(max(inf.nnz, 1))
         self._check(self._lib.fs_get_csr(self._h, _p(rp), _p(col), _p(P), _p(Q)))
         return rp, col[:inf.nnz], P[:inf.nnz], Q[:inf.nnz]
+
+
+def encode(kind: int, inputs, period: int, h_lo: float, h_hi: float, angle_deg: float):
+    """Input encoder (``fs_encode``): one period of a sinusoid, sawtooth or rotation
+    per input value; returns the (hx, hy) field series."""
+    lib = load()
+    u = np.ascontiguousarray(inputs, dtype=np.float64)
+    m = len(u)
+    hx = np.empty(max(m * period, 1))
+    hy = np.empty(max(m * period, 1))
+    st = lib.fs_encode(kind, _p(u), m, period, h_lo, h_hi, angle_deg, _p(hx), _p(hy))
+    if st != FS_OK:
+        raise FsError(st, "bad encoder arguments")
+    return hx[:m * period].copy(), hy[:m * period].copy()
 
 
 def batch_run_protocol(sims, hx, hy, *, resweep: bool = True, with_counts: bool = False):

@@ -162,7 +162,8 @@ extern "C" fs_status fs_create_geometry(int32_t kind, int32_t nx, int32_t ny, do
                                         fs_sim** out) {
     if (!out) return fail(nullptr, FS_ERR_INVALID, "out is NULL");
     *out = nullptr;
-    if (kind < 0 || kind > 2) return fail(nullptr, FS_ERR_INVALID, "unknown geometry kind");
+    if (kind < FS_SQUARE || kind > FS_ISING)
+        return fail(nullptr, FS_ERR_INVALID, "unknown geometry kind");
     if (nx <= 0 || ny <= 0 || nx > 100000 || ny > 100000 || !(a > 0.0))
         return fail(nullptr, FS_ERR_INVALID, "bad geometry size or spacing");
     Geometry g;
@@ -208,6 +209,8 @@ extern "C" void fs_destroy(fs_sim* sim) {
     cudaStreamSynchronize(sim->stream);
     for (cudaEvent_t e : sim->ev_pool) cudaEventDestroy(e);
     sim->run.release(sim->stream);
+    sim->ext_mem.release(sim->stream);
+    sim->sig_mem.release(sim->stream);
     sim->mem.release(sim->stream);
     cudaStreamSynchronize(sim->stream);
     delete sim;
@@ -230,9 +233,11 @@ static bool bad_double(double v) { return !std::isfinite(v); }
 static void fill_rbc(fs_sim* sim) {
     sim->rbc32.resize((size_t)sim->n);
     sim->rbc64.resize((size_t)sim->n);
+    // (the parallel-only criterion compares |h_par| with h_k itself: b = 1)
+    const double b = sim->p.criterion == FS_CRITERION_PARALLEL ? 1.0 : sim->p.b;
     for (int64_t i = 0; i < sim->n; ++i) {
         const double h = sim->hk[(size_t)i];
-        const double rb = 1.0 / (sim->p.b * h), rc = 1.0 / (sim->p.c * h);
+        const double rb = 1.0 / (b * h), rc = 1.0 / (sim->p.c * h);
         sim->rbc64[(size_t)i] = make_double2(rb, rc);
         sim->rbc32[(size_t)i] = make_float2((float)rb, (float)rc);
     }
@@ -548,11 +553,14 @@ fs_status fs_build_sim(fs_sim* sim) {
     const int32_t wk = 0;
     CK(cudaMemcpyAsync(sim->d_work, &wk, 4, cudaMemcpyHostToDevice, st), "upload");
 
-    // parameters
-    I.b = p.b;
+    // parameters; the parallel-only criterion is the astroid's first term with
+    // b = 1 and the exponent 1, without the second
+    const bool parallel = p.criterion == FS_CRITERION_PARALLEL;
+    I.perp = parallel ? 0 : 1;
+    I.b = parallel ? 1.0 : p.b;
     I.c = p.c;
-    I.pexp = 2.0 / p.gamma;
-    I.qexp = 2.0 / p.beta;
+    I.pexp = parallel ? 1.0 : 2.0 / p.gamma;
+    I.qexp = parallel ? 1.0 : 2.0 / p.beta;
     I.sigma = p.sigma_th;
     I.bf = (float)p.b;
     I.cf = (float)p.c;
@@ -590,17 +598,23 @@ fs_status fs_build_sim(fs_sim* sim) {
     I.th_rel = up_float(kThermalRel);
     I.dh_rel = up_float(3.0 * u * (1.0 + std::ldexp(1.0, -20)));
     I.div_rel = up_float(2.0 * u + std::ldexp(1.0, -50));
-    I.cube_p = I.pexp == 2.0 / 3.0 ? 1 : 0;
-    I.cube_q = I.qexp == 2.0 / 3.0 ? 1 : 0;
-    const double rel_cube = 4.01 * u + std::ldexp(1.0, -40);
-    const double rel_powf = 17.0 * u + std::ldexp(1.0, -40);
+    auto pmode = [](double e) { return e == 2.0 / 3.0 ? kPowCube : e == 1.0 ? kPowOne : kPowF; };
+    I.pmode_p = pmode(I.pexp);
+    I.pmode_q = pmode(I.qexp);
+    auto prel = [&](int32_t m) {
+        return up_float(m == kPowCube ? 4.01 * u + std::ldexp(1.0, -40)
+                                      : m == kPowOne ? std::ldexp(1.0, -40)
+                                                     : 17.0 * u + std::ldexp(1.0, -40));
+    };
     const double ln2 = 0.69314718055994530942;
-    I.pow_rel_p = up_float(I.cube_p ? rel_cube : rel_powf);
-    I.pow_rel_q = up_float(I.cube_q ? rel_cube : rel_powf);
-    I.lnk_p = I.cube_p ? 0.0f
-                       : up_float(std::fabs(I.pexp - (double)I.pexpf) * ln2 * (1.0 + 1e-6));
-    I.lnk_q = I.cube_q ? 0.0f
-                       : up_float(std::fabs(I.qexp - (double)I.qexpf) * ln2 * (1.0 + 1e-6));
+    I.pow_rel_p = prel(I.pmode_p);
+    I.pow_rel_q = prel(I.pmode_q);
+    I.lnk_p = I.pmode_p != kPowF
+                  ? 0.0f
+                  : up_float(std::fabs(I.pexp - (double)I.pexpf) * ln2 * (1.0 + 1e-6));
+    I.lnk_q = I.pmode_q != kPowF
+                  ? 0.0f
+                  : up_float(std::fabs(I.qexp - (double)I.qexpf) * ln2 * (1.0 + 1e-6));
     sim->lanes = choose_lanes((double)nnzp / (double)n / 4.0);
 
     // coercive fields
@@ -627,6 +641,8 @@ static fs_status check_params(fs_sim* sim, const fs_params* p) {
         return fail(sim, FS_ERR_INVALID, "parameter out of range");
     if (p->precision != FS_FP64 && p->precision != FS_FP32_RECHECK)
         return fail(sim, FS_ERR_INVALID, "unknown precision");
+    if (p->criterion != FS_CRITERION_ASTROID && p->criterion != FS_CRITERION_PARALLEL)
+        return fail(sim, FS_ERR_INVALID, "unknown switching criterion");
     return FS_OK;
 }
 
@@ -691,6 +707,9 @@ extern "C" fs_status fs_set_params(fs_sim* sim, const fs_params* p) {
     sim->p = *p;
     draw_hk(sim->n, p->hk, p->k_disorder, p->seed, p->instance, sim->hk);
     sim->built = false;
+    // (new parameters drop any local, spatial or thermal series)
+    sim->ext_mem.release(sim->stream);
+    sim->sig_mem.release(sim->stream);
     const fs_status b = fs_build_sim(sim);
     // a failed build's queued work ends before the caller may reuse its buffer
     if (b != FS_OK) cudaStreamSynchronize(sim->stream);
@@ -855,9 +874,22 @@ struct RunBufs {
     int64_t* fps = nullptr;
 };
 
+// A protocol's field steps step0 .. step0 + K - 1 must lie inside the simulation's
+// local, spatial and thermal series, when it has them.
+static fs_status check_series(fs_sim* sim, uint64_t step0, int64_t K) {
+    const uint64_t end = step0 + (uint64_t)std::max<int64_t>(K, 1);
+    if (sim->inst.exti64 && end > (uint64_t)sim->inst.ext_K)
+        return fail(sim, FS_ERR_INVALID, "field step beyond the local or spatial field series");
+    if (sim->inst.sig && end > (uint64_t)sim->inst.sig_K)
+        return fail(sim, FS_ERR_INVALID, "field step beyond the thermal series");
+    return FS_OK;
+}
+
 static fs_status run_device(fs_sim* sim, const double* d_hx, const double* d_hy, int64_t K,
                             uint32_t step0, int32_t resweep, uint32_t* d_ls, uint32_t* d_lk,
                             int64_t log_cap, int64_t* d_fps, uint64_t hash0) {
+    const fs_status rs = check_series(sim, step0, K);
+    if (rs != FS_OK) return rs;
     cudaStream_t st = sim->stream;
     Inst I = sim->inst;
     I.phx = d_hx;
@@ -1044,6 +1076,8 @@ static fs_status eval_into(fs_sim* sim, double* hpar, double* hperp, double* lhs
     fs_status r = need_built(sim);
     if (r != FS_OK) return r;
     if (n != sim->n) return fail(sim, FS_ERR_INVALID, "outputs must hold n values");
+    r = check_series(sim, sim->step, 1);
+    if (r != FS_OK) return r;
     r = refresh_fields(sim);
     if (r != FS_OK) return r;
     cudaStream_t st = sim->stream;
@@ -1188,6 +1222,8 @@ extern "C" fs_status fs_get_profile(fs_sim* sim, fs_profile* out) {
 // keeps the fastest. Every choice gives bit-identical results (integer sums).
 extern "C" fs_status fs_autotune(fs_sim* sim, int32_t* lanes_out) {
     fs_status r = need_built(sim);
+    if (r != FS_OK) return r;
+    r = check_series(sim, sim->step, 1);
     if (r != FS_OK) return r;
     r = refresh_fields(sim);
     if (r != FS_OK) return r;

@@ -168,6 +168,12 @@ extern "C" fs_status fs_batch_run_protocol(fs_sim* const* sims, int32_t n, const
             lead->err = "batch members must share one precision";
             return FS_ERR_INVALID;
         }
+        const Inst& M = sims[i]->inst;
+        if ((M.exti64 && K > M.ext_K) || (M.sig && K > M.sig_K)) {
+            lead->err = "batch member " + std::to_string(i) +
+                        ": its local, spatial or thermal series is shorter than the protocol";
+            return FS_ERR_INVALID;
+        }
         v[(size_t)i] = sims[i];
     }
     // graphs cannot be captured on the legacy default stream: run the batch on a

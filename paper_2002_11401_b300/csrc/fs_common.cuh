@@ -121,10 +121,33 @@ struct Inst {
     float dh_abs, dh_rel, div_rel;
     float th_rel;   // |th32 - th64| <= th_rel (|th_par| + |th_perp|)
     float pow_rel_p, pow_rel_q;  // the FP32 power's own error (documented ulp bound)
-    float lnk_p, lnk_q;          // |p - (float)p| ln 2, rounded up (0 with the cube root)
-    int32_t cube_p, cube_q;      // exponent 2/3: x^(2/3) = x rcbrtf(x), no powf
+    float lnk_p, lnk_q;          // |p - (float)p| ln 2, rounded up (0 unless powf)
+    int32_t pmode_p, pmode_q;    // power: kPowF, kPowCube (x rcbrtf(x)) or kPowOne (x)
+    int32_t perp;                // 1: Eq. 5 has its perpendicular term; 0: the parallel-only criterion
+    int32_t pad3;
+    // External field of each island beyond the global one (Sec. "External field"):
+    // a local series lx[step n + i] or a spatial one gx[step G + gcell[i]] (lab frame),
+    // step < ext_K; the sweep writes the step's projected total into exti64/exti32,
+    // which the relax reads in place of the per-class table. NULL: global field only.
+    const double* lx;
+    const double* ly;
+    const double* gx;
+    const double* gy;
+    const int32_t* gcell;
+    int64_t ext_K, grid_G;
+    double2* exti64;
+    float2* exti32;
+    // Thermal standard deviation per field step (a thermal protocol, e.g. annealing):
+    // sig[step], step < sig_K; NULL: sigma.
+    const double* sig;
+    int64_t sig_K;
     InstState* st;
 };
+
+// Powers of the astroid terms.
+constexpr int32_t kPowF = 0;     // powf at the FP32-rounded exponent
+constexpr int32_t kPowCube = 1;  // exponent 2/3: x rcbrtf(x)
+constexpr int32_t kPowOne = 2;   // exponent 1: x itself
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and Box-Muller
@@ -212,14 +235,20 @@ __device__ __forceinline__ void box_muller32(const uint32_t w[4], float* z0, flo
 
 // Thermal field (par, perp) of island i at thermal step `step`: counter
 // (i, step, instance, 1).
+// Thermal standard deviation of field step `step`.
+__device__ __forceinline__ double sigma_at(const Inst& I, uint32_t step) {
+    return I.sig ? I.sig[step] : I.sigma;
+}
+
 __device__ __forceinline__ void thermal64(const Inst& I, int64_t i, uint32_t step, double* tp,
                                           double* tq) {
     uint32_t c[4] = {(uint32_t)i, step, I.instance, 1u};
     philox10(c, I.seed);
     double z0, z1;
     box_muller64(c, &z0, &z1);
-    *tp = __dmul_rn(I.sigma, z0);
-    *tq = __dmul_rn(I.sigma, z1);
+    const double sg = sigma_at(I, step);
+    *tp = __dmul_rn(sg, z0);
+    *tq = __dmul_rn(sg, z1);
 }
 
 // The kept draw of island i for `step`, when there is one. The draw is published
@@ -266,7 +295,8 @@ __device__ __forceinline__ float2 thermal32(const Inst& I, int64_t i, uint32_t s
     philox10(c, I.seed);
     float z0, z1;
     box_muller32(c, &z0, &z1);
-    return make_float2(__fmul_rn(I.sigmaf, z0), __fmul_rn(I.sigmaf, z1));
+    const float sg = I.sig ? __double2float_rn(I.sig[step]) : I.sigmaf;
+    return make_float2(__fmul_rn(sg, z0), __fmul_rn(sg, z1));
 }
 
 // ---------------------------------------------------------------------------
@@ -279,6 +309,32 @@ __device__ __forceinline__ float2 thermal32(const Inst& I, int64_t i, uint32_t s
 __device__ __forceinline__ double2 ext_proj(double hx, double hy, double2 cs) {
     return make_double2(__dadd_rn(__dmul_rn(hx, cs.x), __dmul_rn(hy, cs.y)),
                         __dadd_rn(__dmul_rn(-hx, cs.y), __dmul_rn(hy, cs.x)));
+}
+
+// The external field of island i (class ci) projected on its frame at the current
+// field step: the per-island values the sweep wrote when a local or spatial field
+// is set, else the per-class table of the global field.
+__device__ __forceinline__ double2 ext64_at(const Inst& I, int64_t i, uint16_t ci) {
+    return I.exti64 ? __ldg(&I.exti64[i]) : __ldg(&I.ext64[ci]);
+}
+__device__ __forceinline__ float2 ext32_at(const Inst& I, int64_t i, uint16_t ci) {
+    return I.exti32 ? __ldg(&I.exti32[i]) : __ldg(&I.ext32[ci]);
+}
+
+// The lab-frame external field of island i at field step `step`: the global
+// (hx, hy) plus its local or spatial part (the sum in this order, as the reference
+// evaluation takes it).
+__device__ __forceinline__ double2 ext_lab(const Inst& I, int64_t i, uint32_t step, double hx,
+                                           double hy) {
+    if (I.lx) {
+        const int64_t q = (int64_t)step * I.n + i;
+        return make_double2(__dadd_rn(hx, I.lx[q]), __dadd_rn(hy, I.ly[q]));
+    }
+    if (I.gx) {
+        const int64_t q = (int64_t)step * I.grid_G + I.gcell[i];
+        return make_double2(__dadd_rn(hx, I.gx[q]), __dadd_rn(hy, I.gy[q]));
+    }
+    return make_double2(hx, hy);
 }
 
 // x^(2/3) for x > 0 as x r, r = x^(-1/3). The seed r0 is the FP32 reciprocal cube
@@ -303,6 +359,7 @@ __device__ __forceinline__ double pow23(double x) {
 __device__ __forceinline__ double pow_pos(double x, double p) {
     if (x <= 0.0) return 0.0;
     if (p == 2.0 / 3.0) return pow23(x);
+    if (p == 1.0) return x;
     return pow(x, p);
 }
 
@@ -322,7 +379,8 @@ __device__ __forceinline__ Eval64 eval64(const Inst& I, int s, long long dp, lon
     e.hperp = __dadd_rn(__dadd_rn(__dmul_rn((double)dq, I.inv64), ext.y), tq);
     const double x = __dmul_rn(fabs(e.hpar), rb.x);
     const double y = __dmul_rn(fabs(e.hperp), rb.y);
-    e.lhs = __dadd_rn(pow_pos(x, I.pexp), pow_pos(y, I.qexp));
+    // (the parallel-only criterion: |h_par| / h_k alone, exponent 1, no second term)
+    e.lhs = I.perp ? __dadd_rn(pow_pos(x, I.pexp), pow_pos(y, I.qexp)) : pow_pos(x, I.pexp);
     e.flippable = ((double)s * e.hpar < 0.0) && (e.lhs > 1.0);
     return e;
 }
@@ -334,12 +392,14 @@ struct Eval32 {
     bool possible, certain;
 };
 
-// x^p in FP32 for x >= 0 (0 for x <= 0). With `cube` (p = 2/3, the Stoner-Wohlfarth
-// exponent) it is x rcbrtf(x): the exponent is exact and the error is that of rcbrtf
-// plus one rounding; otherwise powf at the FP32-rounded exponent.
-__device__ __forceinline__ float pow32(float x, float p, int cube) {
+// x^p in FP32 for x >= 0 (0 for x <= 0). kPowCube (p = 2/3, the Stoner-Wohlfarth
+// exponent): x rcbrtf(x), the exponent exact and the error that of rcbrtf plus one
+// rounding; kPowOne (p = 1): x, exact; otherwise powf at the FP32-rounded exponent.
+__device__ __forceinline__ float pow32(float x, float p, int mode) {
     if (!(x > 0.0f)) return 0.0f;
-    return cube ? __fmul_rn(x, rcbrtf(x)) : powf(x, p);
+    if (mode == kPowCube) return __fmul_rn(x, rcbrtf(x));
+    if (mode == kPowOne) return x;
+    return powf(x, p);
 }
 
 // Bound on the relative error of pow32(x) against x^p with the FP64 exponent p:
@@ -366,7 +426,7 @@ __device__ __forceinline__ float pow_err(float x, float rel, float lnk) {
 // are evaluated directly. The power's own error comes from pow_err at the argument
 // it was taken at. Upper bounds are formed with round-up and lower bounds with
 // round-down arithmetic.
-__device__ __forceinline__ void term_bounds(float t, float x, float u, float p, int cube,
+__device__ __forceinline__ void term_bounds(float t, float x, float u, float p, int mode,
                                             float rel, float lnk, float* hi, float* lo) {
     if (u <= 0.25f && p <= 3.0f) {
         const float r = pow_err(x, rel, lnk);
@@ -377,10 +437,10 @@ __device__ __forceinline__ void term_bounds(float t, float x, float u, float p, 
         *lo = __fmul_rd(__fmul_rd(t, __fsub_rd(1.0f, r)), fmaxf(__fsub_rd(1.0f, g_lo), 0.0f));
     } else {
         const float xh = __fmul_ru(x, __fadd_ru(1.0f, u));
-        *hi = __fmul_ru(pow32(xh, p, cube), __fadd_ru(1.0f, pow_err(xh, rel, lnk)));
+        *hi = __fmul_ru(pow32(xh, p, mode), __fadd_ru(1.0f, pow_err(xh, rel, lnk)));
         if (u < 1.0f) {
             const float xl = __fmul_rd(x, __fsub_rd(1.0f, u));
-            *lo = __fmul_rd(pow32(xl, p, cube), __fsub_rd(1.0f, pow_err(xl, rel, lnk)));
+            *lo = __fmul_rd(pow32(xl, p, mode), __fsub_rd(1.0f, pow_err(xl, rel, lnk)));
         } else {
             *lo = 0.0f;
         }
@@ -413,7 +473,8 @@ __device__ __forceinline__ Eval32 eval32(const Inst& I, int s, float dp, float d
                                                                 fabsf(tq))));
     const float ap = fabsf(e.hpar), aq = fabsf(e.hperp);
     const float x = __fmul_rn(ap, rbc.x), y = __fmul_rn(aq, rbc.y);
-    const float tx = pow32(x, I.pexpf, I.cube_p), ty = pow32(y, I.qexpf, I.cube_q);
+    const float tx = pow32(x, I.pexpf, I.pmode_p);
+    const float ty = I.perp ? pow32(y, I.qexpf, I.pmode_q) : 0.0f;
     e.lhs = __fadd_rn(tx, ty);
     // relative error of x and y: the field bound (times 1 + 2^-22, which covers its
     // product with the scaling's error) plus the scaling roundings
@@ -425,18 +486,21 @@ __device__ __forceinline__ Eval32 eval32(const Inst& I, int s, float dp, float d
                                : 2.0f;
     float hx_, lx_, hy_, ly_;
     if (ap > 0.0f) {
-        term_bounds(tx, x, ux, I.pexpf, I.cube_p, I.pow_rel_p, I.lnk_p, &hx_, &lx_);
+        term_bounds(tx, x, ux, I.pexpf, I.pmode_p, I.pow_rel_p, I.lnk_p, &hx_, &lx_);
     } else {  // |h_par| <= dpar
         const float xm = __fmul_ru(__fmul_ru(dpar, rbc.x), __fadd_ru(1.0f, I.div_rel));
-        hx_ = __fmul_ru(pow32(xm, I.pexpf, I.cube_p),
+        hx_ = __fmul_ru(pow32(xm, I.pexpf, I.pmode_p),
                         __fadd_ru(1.0f, pow_err(xm, I.pow_rel_p, I.lnk_p)));
         lx_ = 0.0f;
     }
-    if (aq > 0.0f) {
-        term_bounds(ty, y, uy, I.qexpf, I.cube_q, I.pow_rel_q, I.lnk_q, &hy_, &ly_);
+    if (!I.perp) {
+        hy_ = 0.0f;
+        ly_ = 0.0f;
+    } else if (aq > 0.0f) {
+        term_bounds(ty, y, uy, I.qexpf, I.pmode_q, I.pow_rel_q, I.lnk_q, &hy_, &ly_);
     } else {
         const float ym = __fmul_ru(__fmul_ru(dperp, rbc.y), __fadd_ru(1.0f, I.div_rel));
-        hy_ = __fmul_ru(pow32(ym, I.qexpf, I.cube_q),
+        hy_ = __fmul_ru(pow32(ym, I.qexpf, I.pmode_q),
                         __fadd_ru(1.0f, pow_err(ym, I.pow_rel_q, I.lnk_q)));
         ly_ = 0.0f;
     }

@@ -27,20 +27,43 @@ struct Site {
 // (1.5 c, sqrt(3) r + (c odd) sqrt(3)/2); islands on the six edge midpoints, along
 // the edges; integer coordinates in units of (a/4, a sqrt(3)/4); shared edges
 // appear once.
+// Edge forms of the square lattice (the figure of the geometries names them; these
+// are the readings): open edges drop the closed square's boundary islands
+// (horizontal rows y = 0 and y = ny, vertical columns x = 0 and x = nx); the
+// pinwheel "diamond" keeps one horizontal and one vertical island per unit cell
+// (rows y < ny, columns x < nx: 2 nx ny islands); "lucky-knot" is the open square
+// turned 45 degrees. Ising: one island at every lattice point, all at 0 degrees.
 // Order: ascending Y, then ascending X (ascending y, then x).
 bool make_geometry(int kind, int32_t nx, int32_t ny, double a, Geometry& g) {
     if (nx <= 0 || ny <= 0 || !(a > 0.0)) return false;
     std::vector<Site> s;
     double ux, uy;
-    if (kind == 0 || kind == 1) {
-        const int rot = kind == 1 ? 45 : 0;
+    if (kind == 0 || kind == 1 || (kind >= 3 && kind <= 5)) {
+        const int rot = (kind == 1 || kind == 4 || kind == 5) ? 45 : 0;
+        // rows of horizontal islands [h_lo, h_hi] and columns of vertical ones [v_lo, v_hi]
+        int64_t h_lo = 0, h_hi = ny, v_lo = 0, v_hi = nx;
+        if (kind == 3 || kind == 5) {
+            h_lo = 1;
+            h_hi = ny - 1;
+            v_lo = 1;
+            v_hi = nx - 1;
+        } else if (kind == 4) {
+            h_hi = ny - 1;
+            v_hi = nx - 1;
+        }
         s.reserve((size_t)nx * (ny + 1) + (size_t)ny * (nx + 1));
-        for (int64_t y = 0; y <= ny; ++y)
+        for (int64_t y = h_lo; y <= h_hi; ++y)
             for (int64_t x = 0; x < nx; ++x) s.push_back({2 * x + 1, 2 * y, rot});
         for (int64_t y = 0; y < ny; ++y)
-            for (int64_t x = 0; x <= nx; ++x) s.push_back({2 * x, 2 * y + 1, 90 + rot});
+            for (int64_t x = v_lo; x <= v_hi; ++x) s.push_back({2 * x, 2 * y + 1, 90 + rot});
         ux = 0.5;
         uy = 0.5;
+    } else if (kind == 6) {
+        s.reserve((size_t)nx * ny);
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) s.push_back({x, y, 0});
+        ux = 1.0;
+        uy = 1.0;
     } else if (kind == 2) {
         // midpoint of edge k (direction 30 + 60k degrees) and the island's angle
         const int ox[6] = {3, 0, -3, -3, 0, 3};
@@ -63,6 +86,7 @@ bool make_geometry(int kind, int32_t nx, int32_t ny, double a, Geometry& g) {
                         [](const Site& p, const Site& q) { return p.X == q.X && p.Y == q.Y; }),
             s.end());
     const size_t n = s.size();
+    if (n == 0) return false;
     g.x.resize(n);
     g.y.resize(n);
     g.theta.resize(n);

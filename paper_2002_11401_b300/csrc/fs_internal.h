@@ -63,6 +63,8 @@ struct fs_sim {
     fs::Workspace ws;  // caller's buffer (fs_bind_workspace), else unused
     fs::Arena mem;     // everything that lives as long as the parameters
     fs::Arena run;  // per-call protocol buffers
+    fs::Arena ext_mem;  // local or spatial external-field series and per-island projections
+    fs::Arena sig_mem;  // thermal standard deviation series
     fs::Inst inst{};      // descriptor (host copy)
     fs::Inst inst_run{};  // descriptor of the queued call (host staging)
     fs::InstState state_host{};

@@ -322,7 +322,7 @@ __device__ __forceinline__ unsigned long long key_of(const Inst& I, int64_t i, u
             double tp = 0.0, tq = 0.0;
             if (I.sigma > 0.0) thermal64_at<KEEP>(I, i, step, &tp, &tq);
             const Eval64 f =
-                eval64(I, si, h64.x, h64.y, __ldg(&I.rbc64[i]), __ldg(&I.ext64[ci]), tp, tq);
+                eval64(I, si, h64.x, h64.y, __ldg(&I.rbc64[i]), ext64_at(I, i, ci), tp, tq);
             const double x = f.flippable ? f.lhs : 0.0;
             *x64 = x;
             *lo = x > 0.0 ? __double2float_rd(x) : -1.0f;
@@ -416,9 +416,9 @@ __device__ __forceinline__ Upd compute_update(const Inst& I, int64_t i, int snew
     double2 e64 = make_double2(0.0, 0.0);
     if constexpr (PREC == 0) {
         rb64 = __ldg(&I.rbc64[i]);
-        e64 = __ldg(&I.ext64[ci]);
+        e64 = ext64_at(I, i, ci);
     }
-    const float2 e32 = __ldg(&I.ext32[ci]);
+    const float2 e32 = ext32_at(I, i, ci);
     const unsigned long long up = 2ull * (unsigned long long)dp;
     const unsigned long long uq = 2ull * (unsigned long long)dq;
     h.x = (long long)(snew > 0 ? (unsigned long long)h.x + up : (unsigned long long)h.x - up);
@@ -468,7 +468,7 @@ __device__ __forceinline__ double exact_value(const Inst& I, int64_t i, uint32_t
         if (kept >= 0.0) return kept;
         double tp = 0.0, tq = 0.0;
         if (I.sigma > 0.0) thermal64_kept(I, i, step, &tp, &tq);
-        const Eval64 e = eval64(I, si, h.x, h.y, rb64, __ldg(&I.ext64[ci]), tp, tq);
+        const Eval64 e = eval64(I, si, h.x, h.y, rb64, ext64_at(I, i, ci), tp, tq);
         const double v = e.flippable ? e.lhs : 0.0;
         I.key64[i] = v;
         return v;
@@ -1083,7 +1083,8 @@ __global__ void k_eval_all(const Inst* __restrict__ tab, double hx, double hy, u
     const IslandRec r = rec_load(I, i);
     const int si = r.s;
     const uint16_t ci = r.cls;
-    const double2 ext = ext_proj(hx, hy, I.cs64[ci]);
+    const double2 lab = ext_lab(I, i, step, hx, hy);
+    const double2 ext = ext_proj(lab.x, lab.y, I.cs64[ci]);
     if (I.prec == 1) {
         const int2 h = r.h32;
         const float2 th = I.sigma > 0.0 ? thermal32(I, i, step) : make_float2(0.0f, 0.0f);

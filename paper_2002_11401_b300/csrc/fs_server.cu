@@ -59,14 +59,28 @@ struct Job {
 // transposed copies (40 B); the degree is the cutoff disc's area times the array's
 // island density, plus a margin for the rounding of the rows to multiples of 4.
 double islands_of(const fs_request& r) {
-    return r.kind == FS_KAGOME ? 3.0 * r.nx * r.ny + 2.0 * r.nx + 2.0 * r.ny
-                               : 2.0 * r.nx * r.ny + r.nx + r.ny;
+    const double x = r.nx, y = r.ny;
+    switch (r.kind) {
+        case FS_KAGOME:
+            return 3.0 * x * y + 2.0 * x + 2.0 * y;
+        case FS_ISING:
+            return x * y;
+        case FS_PINWHEEL_DIAMOND:
+            return 2.0 * x * y;
+        case FS_SQUARE_OPEN:
+        case FS_PINWHEEL_LUCKY_KNOT:
+            return 2.0 * x * y - x - y;
+        default:
+            return 2.0 * x * y + x + y;
+    }
 }
 
 size_t estimate_bytes(const fs_request& r) {
     const double rc = r.params.cutoff;
     const double n = islands_of(r);
-    const double density = r.kind == FS_KAGOME ? 3.0 / (1.5 * std::sqrt(3.0)) : 2.0;
+    const double density = r.kind == FS_KAGOME ? 3.0 / (1.5 * std::sqrt(3.0))
+                           : r.kind == FS_ISING ? 1.0
+                                                : 2.0;
     const double deg = 1.05 * M_PI * rc * rc * density + 8.0;
     return (size_t)(n * (deg * 40.0 + 156.0) + 16.0 * r.K + (1 << 20));
 }

@@ -170,7 +170,18 @@ __global__ void __launch_bounds__(kSweepThreads, OCC)
         const uint16_t ci = I.cls[i];
         const float2 rbc = I.rbc32[i];
         const int64_t ra = __ldg(&I.rp[i]), rb = __ldg(&I.rp[i + 1]);
-        const float2 e32 = I.ext32[ci];
+        // the external field on the island's frame: the class table of the global
+        // field, or with a local or spatial field the island's own projection,
+        // kept for the relax
+        double2 e64 = I.ext64[ci];
+        float2 e32 = I.ext32[ci];
+        if (I.exti64) {
+            const double2 lab = ext_lab(I, i, step, I.phx[t], I.phy[t]);
+            e64 = ext_proj(lab.x, lab.y, I.cs64[ci]);
+            e32 = make_float2(__double2float_rn(e64.x), __double2float_rn(e64.y));
+            I.exti64[i] = e64;
+            I.exti32[i] = e32;
+        }
         float2 th = make_float2(0.0f, 0.0f);
         if (I.sigma > 0.0) {
             th = thermal32(I, i, step);
@@ -198,7 +209,7 @@ __global__ void __launch_bounds__(kSweepThreads, OCC)
             if (e.possible && !e.certain) {
                 // within its band of the threshold or of the sign change: FP64 now
                 if (!SUM64) h64 = I.h64[i];
-                const Eval64 f = eval64(I, si, h64.x, h64.y, I.rbc64[i], I.ext64[ci], tp, tq);
+                const Eval64 f = eval64(I, si, h64.x, h64.y, I.rbc64[i], e64, tp, tq);
                 x = f.flippable ? f.lhs : 0.0;
                 node = x > 0.0 ? key32_of(__double2float_ru(x), i) : 0ull;
                 lo = x > 0.0 ? __double2float_rd(x) : -1.0f;
@@ -215,7 +226,7 @@ __global__ void __launch_bounds__(kSweepThreads, OCC)
             if (e.possible) {
                 double tp = 0.0, tq = 0.0;
                 if (I.sigma > 0.0) thermal64_kept(I, i, step, &tp, &tq);
-                const Eval64 f = eval64(I, si, h64.x, h64.y, I.rbc64[i], I.ext64[ci], tp, tq);
+                const Eval64 f = eval64(I, si, h64.x, h64.y, I.rbc64[i], e64, tp, tq);
                 if (f.flippable) x = f.lhs;
             }
             I.key64[i] = x;

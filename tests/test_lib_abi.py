@@ -49,7 +49,7 @@ def test_hash_init_is_fnv_offset_basis(lib):
 
 
 @pytest.mark.parametrize("kind,n", [(I.SQUARE, 16), (I.PINWHEEL, 9), (I.KAGOME, 29),
-                                    (I.KAGOME, 7)])
+                                    (I.KAGOME, 7), (3, 8), (4, 25), (5, 6), (6, 11)])
 def test_geometry_matches_oracle_bitwise(lib, oracle, kind, n):
     from paper_2002_11401_b300 import binding as B
     sim = B.Sim.geometry(kind, n, n + 1)
@@ -99,3 +99,37 @@ def test_workspace_calls_reject_bad_arguments_on_the_host(lib):
     assert b"256-byte" in lib.fs_last_error(sim.handle)
     # NULL returns to the pool: always allowed before the parameters are set
     assert lib.fs_bind_workspace(sim.handle, None, 0, None) == B.FS_OK
+
+
+@pytest.mark.parametrize("kind,period,angle", [(0, 8, 0.0), (0, 13, 70.0), (1, 5, 30.0),
+                                               (1, 40, 200.0), (2, 12, 15.0), (2, 7, -40.0)])
+def test_encoders_match_oracle(lib, oracle, kind, period, angle):
+    """fs_encode is host arithmetic: the same values as the oracle's encoder, to the
+    last bit or one rounding apart."""
+    from paper_2002_11401_b300 import binding as B
+    u = np.array([0.0, 0.3, 1.0, 0.77])
+    hx, hy = B.encode(kind, u, period, 0.05, 0.3, angle)
+    ox, oy = oracle.encode(kind, u, period, 0.05, 0.3, angle)
+    np.testing.assert_allclose(hx, ox, rtol=2e-16, atol=1e-17)
+    np.testing.assert_allclose(hy, oy, rtol=2e-16, atol=1e-17)
+    with pytest.raises(B.FsError):
+        B.encode(1, u, 1, 0.0, 0.1, 0.0)  # a sawtooth needs two values per period
+    with pytest.raises(B.FsError):
+        B.encode(5, u, 4, 0.0, 0.1, 0.0)
+
+
+def test_series_and_correlation_need_parameters(lib):
+    from paper_2002_11401_b300 import binding as B
+    sim = B.Sim.geometry(I.SQUARE, 3, 3)
+    with pytest.raises(B.FsError) as e:
+        sim.set_field_local(np.zeros((2, sim.n)), np.zeros((2, sim.n)))
+    assert e.value.code == B.FS_ERR_STATE
+    with pytest.raises(B.FsError) as e:
+        sim.set_sigma_series([0.1, 0.2])
+    assert e.value.code == B.FS_ERR_STATE
+    with pytest.raises(B.FsError) as e:
+        sim.correlation(3.0, 0.5, 8)
+    assert e.value.code == B.FS_ERR_STATE
+    p = B.make_params(alpha=1e-3, criterion=3)
+    assert lib.fs_workspace_bytes(sim.handle, ctypes.byref(p), ctypes.byref(ctypes.c_size_t())) \
+        == B.FS_ERR_INVALID
