@@ -148,6 +148,24 @@ void fs_destroy(fs_sim* sim);
 /* CUDA stream (cudaStream_t) for all later work of `sim`; NULL = legacy default. */
 fs_status fs_set_stream(fs_sim* sim, void* stream);
 
+/* How a relax (Sec. "Dynamics") runs on the device; every mode flips the same
+ * islands in the same order.
+ * FS_RELAX_SINGLE: one flip at a time, by one CTA: the flippable island with the
+ *   largest LHS, then its neighbours' updates.
+ * FS_RELAX_MULTI: rounds of several flips: the islands with the largest LHS, in
+ *   order, as long as each is the one the single-flip order takes next: its exact
+ *   value beats everything outside the round, it lies more than twice the cutoff
+ *   from every earlier island of the round (so that no flip of the round changes
+ *   its field or a neighbour shared with it), and no earlier flip's neighbour got a
+ *   value that beats it. Faster on large arrays, where many of the largest values
+ *   lie far apart. A field step whose rounds stay below 8 flips for 4 rounds in a
+ *   row (a chain of flips that each make a neighbour the largest) is finished by
+ *   the single-flip chain.
+ * FS_RELAX_AUTO (default): multi-flip rounds from 262,144 islands on.
+ * Batches always use single flips. Errors: FS_ERR_INVALID. */
+typedef enum { FS_RELAX_AUTO = 0, FS_RELAX_SINGLE = 1, FS_RELAX_MULTI = 2 } fs_relax_mode;
+fs_status fs_set_relax_mode(fs_sim* sim, int32_t mode);
+
 /* Device bytes fs_set_params(sim, p) would allocate: the simulation's state (the
  * neighbour tensors of Eq. 3, the island arrays, the relax's records and keys, the
  * max-tree) plus the build's temporaries, every allocation rounded up to 256
@@ -235,6 +253,8 @@ typedef struct {
     int64_t sweep_launches, relax_launches;
     int64_t rechecks;           /* FP64 recheck rounds of the FP32 path so far */
     int64_t fallbacks;          /* rechecks that overflowed into a full scan */
+    int64_t rounds;             /* multi-flip relax: rounds that flipped so far */
+    int64_t idle_rounds;        /* multi-flip relax: candidate passes that flipped nothing */
 } fs_profile;
 fs_status fs_set_profiling(fs_sim* sim, int32_t on);
 fs_status fs_get_profile(fs_sim* sim, fs_profile* out);

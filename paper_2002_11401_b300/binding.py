@@ -22,6 +22,7 @@ FS_SQUARE_OPEN, FS_PINWHEEL_DIAMOND, FS_PINWHEEL_LUCKY_KNOT, FS_ISING = 3, 4, 5,
 FS_FP64, FS_FP32_RECHECK = 0, 1
 FS_CRITERION_ASTROID, FS_CRITERION_PARALLEL = 0, 1
 FS_ENCODE_SINUSOID, FS_ENCODE_SAWTOOTH, FS_ENCODE_ROTATION = 0, 1, 2
+FS_RELAX_AUTO, FS_RELAX_SINGLE, FS_RELAX_MULTI = 0, 1, 2
 
 EXPORTS = (
     "fs_last_error", "fs_hash_init", "fs_create_geometry", "fs_create_custom", "fs_destroy",
@@ -32,7 +33,7 @@ EXPORTS = (
     "fs_server_now", "fs_server_destroy", "fs_server_last_error", "fs_set_spins_dev",
     "fs_set_profiling", "fs_get_profile", "fs_eval_argmax_static", "fs_autotune",
     "fs_workspace_bytes", "fs_bind_workspace", "fs_set_field_local", "fs_set_field_spatial",
-    "fs_set_sigma_series", "fs_encode", "fs_correlation",
+    "fs_set_sigma_series", "fs_encode", "fs_correlation", "fs_set_relax_mode",
 )
 
 
@@ -60,7 +61,8 @@ class fs_info(C.Structure):
 class fs_profile(C.Structure):
     _fields_ = [("sweep_ms", C.c_double), ("relax_ms", C.c_double),
                 ("sweep_launches", C.c_int64), ("relax_launches", C.c_int64),
-                ("rechecks", C.c_int64), ("fallbacks", C.c_int64)]
+                ("rechecks", C.c_int64), ("fallbacks", C.c_int64), ("rounds", C.c_int64),
+                ("idle_rounds", C.c_int64)]
 
 
 class fs_request(C.Structure):
@@ -132,6 +134,7 @@ def load():
             "fs_set_sigma_series": ([P, P, i64], i32),
             "fs_encode": ([i32, P, i64, i32, dbl, dbl, dbl, P, P], i32),
             "fs_correlation": ([P, dbl, dbl, i32, P, P], i32),
+            "fs_set_relax_mode": ([P, i32], i32),
         }
         for name, (args, res) in sig.items():
             if not hasattr(lib, name):
@@ -320,6 +323,10 @@ class Sim:
         out = fs_info()
         self._check(self._lib.fs_get_info(self._h, C.byref(out)))
         return out
+
+    def set_relax_mode(self, mode: int):
+        """FS_RELAX_AUTO, FS_RELAX_SINGLE or FS_RELAX_MULTI."""
+        self._check(self._lib.fs_set_relax_mode(self._h, mode))
 
     def set_field_local(self, hx, hy):
         """Local external field series: (K, n) arrays per component (K = 0 clears)."""

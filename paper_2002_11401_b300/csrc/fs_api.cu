@@ -216,6 +216,14 @@ extern "C" void fs_destroy(fs_sim* sim) {
     delete sim;
 }
 
+extern "C" fs_status fs_set_relax_mode(fs_sim* sim, int32_t mode) {
+    if (!sim) return fail(nullptr, FS_ERR_INVALID, "sim is NULL");
+    if (mode != FS_RELAX_AUTO && mode != FS_RELAX_SINGLE && mode != FS_RELAX_MULTI)
+        return fail(sim, FS_ERR_INVALID, "unknown relax mode");
+    sim->relax_mode = mode;
+    return FS_OK;
+}
+
 extern "C" fs_status fs_set_stream(fs_sim* sim, void* stream) {
     if (!sim) return fail(nullptr, FS_ERR_INVALID, "sim is NULL");
     sim->stream = (cudaStream_t)stream;
@@ -287,6 +295,7 @@ static PlanBytes plan_bytes(int64_t n, size_t ncls, int64_t ncell, int64_t nnzp,
     // islands, classes, relax state
     S(n), S(16 * n), S(8 * n), S(2 * n), S(16 * nc), S(8 * nc);
     S(16 * n), S(8 * n), S((int64_t)sizeof(IslandRec) * n), S(8 * n), S(16 * nc), S(8 * nc);
+    S(16 * n);  // island centres
     if (thermal) S(8 * n), S(16 * n), S(4 * n);
     const int64_t total = tree_nodes(n);
     S(8 * total), S(4 * total);
@@ -509,6 +518,28 @@ fs_status fs_build_sim(fs_sim* sim) {
     CK(palloc((void**)&I.ext64, 16 * ncls), "alloc");
     CK(palloc((void**)&I.ext32, 8 * ncls), "alloc");
     I.nclass = (int32_t)ncls;
+    {
+        double2* pos = nullptr;
+        CK(palloc((void**)&pos, 16 * n), "alloc");
+        std::vector<double2> hp((size_t)n);
+        for (int64_t i = 0; i < n; ++i)
+            hp[(size_t)i] = make_double2(sim->x[(size_t)i], sim->y[(size_t)i]);
+        CK(cudaMemcpyAsync(pos, hp.data(), 16 * n, cudaMemcpyHostToDevice, st), "upload");
+        CK(cudaStreamSynchronize(st), "upload");  // (the host copy goes out of scope)
+        I.pos = pos;
+        const double rc = 2.0 * p.cutoff * sim->a;
+        I.rconf2 = rc * rc * (1.0 + 1e-6);
+        // the same test on FP32 centres: each coordinate is within ext 2^-24 of its
+        // double (ext: the largest magnitude), a difference within 3 ext 2^-24 more
+        // (its own rounding included), so a squared distance below (rc + d)^2 with
+        // d = 2 sqrt(2) 3 ext 2^-24 plus the FP32 sum's roundings covers every pair
+        // within rc in double; widened further to be safe
+        double ext = 1.0;
+        for (int64_t i = 0; i < n; ++i)
+            ext = std::max(ext, std::max(std::fabs(sim->x[(size_t)i]), std::fabs(sim->y[(size_t)i])));
+        const double d = 10.0 * ext * std::ldexp(1.0, -24);
+        I.rconf2f = up_float((rc + d) * (rc + d) * (1.0 + 1e-5) + 1e-6);
+    }
     if (p.sigma_th > 0.0) {
         CK(palloc((void**)&I.th32, 8 * n), "alloc");
         CK(palloc((void**)&I.th64, 16 * n), "alloc");
@@ -826,6 +857,14 @@ cudaError_t collect_profile(fs_sim* sim) {
 // Queues K field steps of one simulation: per step the external-field table,
 // the sweep and the relax. With profiling on, events bracket the sweep and the
 // relax of every step.
+// Whether the simulation's relaxes run as multi-flip rounds: by choice, or (auto)
+// for arrays large enough that many of the largest keys lie far apart.
+bool relax_multi(const fs_sim* sim) {
+    if (sim->relax_mode == FS_RELAX_MULTI) return true;
+    if (sim->relax_mode == FS_RELAX_SINGLE) return false;
+    return sim->n >= kMultiAutoIslands;
+}
+
 cudaError_t enqueue_steps(fs_sim* sim, int64_t K, int resweep, cudaStream_t st) {
     SweepLaunch S;
     S.tab = sim->d_inst;
@@ -843,6 +882,8 @@ cudaError_t enqueue_steps(fs_sim* sim, int64_t K, int resweep, cudaStream_t st) 
     R.n_work = 1;
     R.prec = sim->p.precision;
     R.smem_levels = relax_smem_levels(sim->n);
+    R.multi = relax_multi(sim) ? 1 : 0;
+    if (R.multi) R.smem_multi = relax_multi_smem(sim->n);
     cudaError_t e;
     if (sim->profiling && sim->ev_used + 3 * (size_t)K > 30000 &&
         (e = collect_profile(sim)) != cudaSuccess)
@@ -924,6 +965,8 @@ static fs_status finish_run(fs_sim* sim, InstState* out) {
     *out = sim->state_host;
     sim->rechecks += out->rechecks;
     sim->fallbacks += out->fallbacks;
+    sim->rounds += out->rounds;
+    sim->idle_rounds += out->idle;
     if (out->status == ST_NOT_CONVERGED)
         return fail(sim, FS_ERR_NOT_CONVERGED, "a relax exceeded max_flips_per_step");
     if (out->status == ST_BOUNDS)
@@ -1214,6 +1257,8 @@ extern "C" fs_status fs_get_profile(fs_sim* sim, fs_profile* out) {
     out->relax_launches = sim->prof_relaxes;
     out->rechecks = sim->rechecks;
     out->fallbacks = sim->fallbacks;
+    out->rounds = sim->rounds;
+    out->idle_rounds = sim->idle_rounds;
     return FS_OK;
 }
 

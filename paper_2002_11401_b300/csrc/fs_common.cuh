@@ -39,6 +39,11 @@ struct InstState {
     uint32_t pad;
     int64_t rechecks;   // FP64 recheck rounds (FP32 path)
     int64_t fallbacks;  // full-scan rechecks (candidate overflow)
+    int64_t rounds;     // multi-flip relax: rounds that flipped, and iterations without a flip
+    int64_t idle;
+    int32_t handoff;    // 1: the multi-flip relax left the rest of step t to the single-flip one
+    int32_t pad2;
+    int64_t step_flips; // flips of step t before the hand-off
 };
 
 // Read-only descriptor of one simulation (one entry of a batch table).
@@ -141,6 +146,13 @@ struct Inst {
     // sig[step], step < sig_K; NULL: sigma.
     const double* sig;
     int64_t sig_K;
+    // Island centres (the multi-flip relax's independence test) and the square of
+    // the distance below which two islands may share a neighbour: (2 cutoff)^2,
+    // widened by 1e-6 beyond the inclusive cutoff.
+    const double2* pos;
+    double rconf2;
+    float rconf2f;  // the same, for FP32 centres: widened by their rounding
+    int32_t pad4;
     InstState* st;
 };
 

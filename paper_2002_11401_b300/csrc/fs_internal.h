@@ -31,6 +31,11 @@ struct Arena {
     void release(cudaStream_t st);
 };
 
+// Arrays of at least this many islands relax in multi-flip rounds unless the
+// simulation chooses otherwise (fs_set_relax_mode).
+constexpr int64_t kMultiAutoIslands = 262144;
+bool relax_multi(const fs_sim* sim);
+
 int choose_lanes(double avg_groups);
 int relax_smem_levels(int64_t n);  // bytes of upper tree levels kept in shared memory
 int relax_smem_max();              // largest dynamic shared memory of any relax launch
@@ -81,7 +86,9 @@ struct fs_sim {
     int32_t e64 = 0, e32 = 0;
     int lanes = 16;
     int sweep_occ = 4;  // resident sweep CTAs per SM (4 or 5), set by the autotuner
+    int relax_mode = 0; // FS_RELAX_AUTO, FS_RELAX_SINGLE or FS_RELAX_MULTI
     int64_t rechecks = 0, fallbacks = 0;
+    int64_t rounds = 0, idle_rounds = 0;  // multi-flip relax
     cudaGraphExec_t graph_exec = nullptr;
     // profiling: CUDA events around each sweep and relax launch
     bool profiling = false;

@@ -38,6 +38,7 @@
 
 #include "fs_common.cuh"
 #include "fs_kernels.h"
+#include "fs_update.cuh"
 
 namespace fs {
 
@@ -76,15 +77,6 @@ __device__ __forceinline__ int64_t ln(const Levels& L, int lev) {
 #pragma unroll
     for (int q = 1; q < kRelaxLevels; ++q) r = lev == q ? L.n[q] : r;
     return r;
-}
-
-// Warp maximum of 64-bit keys (every lane gets it): the largest upper half, then
-// among those the largest lower half.
-__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v) {
-    const unsigned hi = (unsigned)(v >> 32), lo = (unsigned)v;
-    const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
-    const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
-    return ((unsigned long long)mh << 32) | ml;
 }
 
 // Node `node` of level `lev` from its 32 children (leaves when lev == 0).
@@ -302,52 +294,6 @@ __device__ void rebuild_tree(const Inst& I, const Levels& L) {
     }
 }
 
-// Key of island i from its current state (already loaded): returns the new key
-// and writes lo and the exact value x (the FS_FP64 LHS when flippable, 0 when
-// not; on the FP32 path -1 when only the FP32 bounds were taken). KEEP: an FP64
-// thermal draw taken here is kept for later evaluations; without it the kept
-// draws are only read (for evaluations ahead of the pick, which store nothing).
-template <int PREC, bool KEEP>
-__device__ __forceinline__ unsigned long long key_of(const Inst& I, int64_t i, uint32_t step,
-                                                     int si, uint16_t ci, longlong2 h64, int2 h32,
-                                                     float2 rbc, float2 e32, float2 th,
-                                                     double2 rb64, double2 e64, float* lo,
-                                                     double* x64) {
-    if constexpr (PREC == 1) {
-        const float dp = __fmul_rn(__int2float_rn(h32.x), I.inv32);
-        const float dq = __fmul_rn(__int2float_rn(h32.y), I.inv32);
-        const Eval32 e = eval32(I, si, dp, dq, rbc, e32, th.x, th.y);
-        if (e.possible && !e.certain) {
-            // within its band of the threshold or of the sign change: FP64 now
-            double tp = 0.0, tq = 0.0;
-            if (I.sigma > 0.0) thermal64_at<KEEP>(I, i, step, &tp, &tq);
-            const Eval64 f =
-                eval64(I, si, h64.x, h64.y, __ldg(&I.rbc64[i]), ext64_at(I, i, ci), tp, tq);
-            const double x = f.flippable ? f.lhs : 0.0;
-            *x64 = x;
-            *lo = x > 0.0 ? __double2float_rd(x) : -1.0f;
-            return x > 0.0 ? key32_of(__double2float_ru(x), i) : 0ull;
-        }
-        *x64 = e.possible ? -1.0 : 0.0;
-        *lo = e.certain ? e.lo : -1.0f;
-        return e.possible ? key32_of(e.hi, i) : 0ull;
-    } else {
-        const float dp = __fmul_rn(__ll2float_rn(h64.x), I.inv64f);
-        const float dq = __fmul_rn(__ll2float_rn(h64.y), I.inv64f);
-        const Eval32 e = eval32(I, si, dp, dq, rbc, e32, th.x, th.y);
-        double x = 0.0;
-        if (e.possible) {
-            double tp = 0.0, tq = 0.0;
-            if (I.sigma > 0.0) thermal64_at<KEEP>(I, i, step, &tp, &tq);
-            const Eval64 f = eval64(I, si, h64.x, h64.y, rb64, e64, tp, tq);
-            if (f.flippable) x = f.lhs;
-        }
-        *x64 = x;
-        *lo = x > 0.0 ? __double2float_rd(x) : -1.0f;
-        return x > 0.0 ? key32_of(__double2float_ru(x), i) : 0ull;
-    }
-}
-
 // Asks L2 for bytes [p, p + n) ahead of their use (TMA bulk prefetch: p 16-byte
 // aligned, n a multiple of 16; no completion to wait for).
 __device__ __forceinline__ void bulk_prefetch_l2(const void* p, uint32_t n) {
@@ -375,66 +321,6 @@ __device__ __forceinline__ void predict_candidate(const Inst& I, Prediction& P, 
     if (*(volatile unsigned long long*)&P.best[par] < kj) atomicMax(&P.best[par], kj);
 }
 
-// One neighbour update: island i's field changes by 2 s_new (dp, dq) (exact 64-bit
-// sums; dp32, dq32 the 32-bit ones) and its key is re-evaluated. Computing it
-// (loads and arithmetic) is kept apart from its effects (stores, tree, prediction)
-// so that it can be computed ahead of the pick and committed once the pick is
-// known; both ways run the same code.
-struct Upd {
-    int64_t i;  // -1: none
-    longlong2 h;
-    int2 g;
-    unsigned long long old, nk;
-    float lo;
-    double x;
-    int64_t r0, r1;  // island i's row, for the prediction
-    int s;           // island i's spin (written back with the sums)
-};
-
-// Every load is issued before any result is needed so that they overlap. `own`:
-// island i's spin when given (nonzero), else read from memory.
-template <int PREC, bool KEEP>
-__device__ __forceinline__ Upd compute_update(const Inst& I, int64_t i, int snew, long long dp,
-                                              long long dq, int dp32, int dq32, uint32_t step,
-                                              int own = 0) {
-    Upd u;
-    u.i = i;
-    longlong2 h = I.h64[i];
-    const IslandRec r = rec_load(I, i);
-    int2 g = make_int2(0, 0);
-    if constexpr (PREC == 1) g = r.h32;
-    u.old = I.key32[i];
-    const int si = own != 0 ? own : r.s;
-    u.s = si;
-    const uint16_t ci = r.cls;
-    const float2 rbc = r.rbc;
-    float2 th = make_float2(0.0f, 0.0f);
-    if (I.sigma > 0.0) th = I.th32[i];
-    u.r0 = (int64_t)r.rowq << 2;
-    u.r1 = u.r0 + ((int64_t)r.rowlenq << 2);
-    double2 rb64 = make_double2(0.0, 0.0);
-    double2 e64 = make_double2(0.0, 0.0);
-    if constexpr (PREC == 0) {
-        rb64 = __ldg(&I.rbc64[i]);
-        e64 = ext64_at(I, i, ci);
-    }
-    const float2 e32 = ext32_at(I, i, ci);
-    const unsigned long long up = 2ull * (unsigned long long)dp;
-    const unsigned long long uq = 2ull * (unsigned long long)dq;
-    h.x = (long long)(snew > 0 ? (unsigned long long)h.x + up : (unsigned long long)h.x - up);
-    h.y = (long long)(snew > 0 ? (unsigned long long)h.y + uq : (unsigned long long)h.y - uq);
-    if constexpr (PREC == 1) {
-        const unsigned vp = 2u * (unsigned)dp32, vq = 2u * (unsigned)dq32;
-        g.x = (int)(snew > 0 ? (unsigned)g.x + vp : (unsigned)g.x - vp);
-        g.y = (int)(snew > 0 ? (unsigned)g.y + vq : (unsigned)g.y - vq);
-    }
-    u.h = h;
-    u.g = g;
-    u.x = 0.0;
-    u.nk = key_of<PREC, KEEP>(I, i, step, si, ci, h, g, rbc, e32, th, rb64, e64, &u.lo, &u.x);
-    return u;
-}
-
 // The update's effects: new sums, key, bounds and kept value; the tree told; and,
 // when the new key exceeds `pf_above` (the largest key the flip did not touch),
 // the island enters the prediction of the next pick.
@@ -448,31 +334,6 @@ __device__ __forceinline__ void commit_update(const Inst& I, const Levels& L, Di
     I.key32[u.i] = u.nk;
     leaf_changed(I, L, D, u.i, u.old, u.nk);
     if (u.nk > pf_above) predict_candidate<PREC>(I, P, par, u.nk, u.r0, u.r1);
-}
-
-// Exact FP64 value of island i (0 when not flippable): the value kept with its
-// key when its current fields were evaluated in FP64, else (FP32 path) a fresh
-// FP64 evaluation of its exact sums, which is then kept. The island's state is
-// loaded before the kept value is looked at, so that a miss costs no extra trip.
-template <int PREC>
-__device__ __forceinline__ double exact_value(const Inst& I, int64_t i, uint32_t step) {
-    const double kept = I.key64[i];
-    if constexpr (PREC == 0) {
-        return kept;
-    } else {
-        const longlong2 h = I.h64[i];
-        const IslandRec r = rec_load(I, i);
-        const int si = r.s;
-        const double2 rb64 = __ldg(&I.rbc64[i]);
-        const uint16_t ci = r.cls;
-        if (kept >= 0.0) return kept;
-        double tp = 0.0, tq = 0.0;
-        if (I.sigma > 0.0) thermal64_kept(I, i, step, &tp, &tq);
-        const Eval64 e = eval64(I, si, h.x, h.y, rb64, ext64_at(I, i, ci), tp, tq);
-        const double v = e.flippable ? e.lhs : 0.0;
-        I.key64[i] = v;
-        return v;
-    }
 }
 
 struct RecheckShared {
@@ -819,7 +680,7 @@ __device__ int64_t pick_warp(const Inst& I, const Levels& L, RecheckShared& R, D
 template <int PREC, int MINB>
 __global__ void __launch_bounds__(kT, MINB)
     k_relax(const Inst* __restrict__ tab, const int32_t* __restrict__ work, int n_work,
-            int smem_levels) {
+            int smem_levels, int cont) {
     extern __shared__ unsigned long long sm_levels[];
     __shared__ int64_t sh_k;
     __shared__ Prediction P;
@@ -835,8 +696,12 @@ __global__ void __launch_bounds__(kT, MINB)
 
     const Inst& I = tab[work[blockIdx.x]];
     InstState* st = I.st;
+    // cont: launched after the multi-flip relax of the same step, which either
+    // finished it (nothing to do) or handed the rest over (continue from its flips)
+    if (cont && st->handoff == 0) return;
     const int64_t t = st->t;
     if (st->status != ST_OK || t >= I.K) return;
+    const int64_t prior = cont ? st->step_flips : 0;  // the step's flips before the hand-off
     const uint32_t step = I.step0 + (uint32_t)t;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 
@@ -929,7 +794,7 @@ __global__ void __launch_bounds__(kT, MINB)
                 pick_warp<PREC>(I, L, R, D, st, step, &sk, &a0, &a1, &ru, &tau, &clean);
             if (lane == 0) {
                 if (k >= 0) {
-                    if (flips < max_flips)
+                    if (prior + flips < max_flips)
                         do_flip(k, sk, a0, a1);
                     else
                         k = kPickMaxFlips;
@@ -986,7 +851,7 @@ __global__ void __launch_bounds__(kT, MINB)
                 k = kPickBounds;
             } else {
                 if (threadIdx.x == 0) {
-                    if (flips < max_flips) {
+                    if (prior + flips < max_flips) {
                         const IslandRec rr = rec_load(I, r);
                         const int64_t ra = (int64_t)rr.rowq << 2;
                         do_flip(r, rr.s, ra, ra + ((int64_t)rr.rowlenq << 2));
@@ -1062,8 +927,9 @@ __global__ void __launch_bounds__(kT, MINB)
     if (threadIdx.x == kHashThread) st->hash = hash;
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (I.flips_per_step) I.flips_per_step[t] = flips;
+        if (I.flips_per_step) I.flips_per_step[t] = prior + flips;
         st->n_flips = flips_before + flips;
+        st->handoff = 0;
         if (status != ST_OK) st->status = status;
         st->init = 0;
         st->t = t + 1;
@@ -1148,19 +1014,27 @@ cudaError_t prepare_relax(int prec, int smem) {
 
 cudaError_t launch_relax(const RelaxLaunch& L, cudaStream_t st) {
     if (L.n_work == 0) return cudaSuccess;
+    // multi-flip rounds first; the single-flip kernel then takes over a step they
+    // handed off (and returns at once otherwise)
+    if (L.multi) {
+        const cudaError_t e = launch_relax_multi(L, st);
+        if (e != cudaSuccess) return e;
+    }
+    const int cont = L.multi ? 1 : 0;
     const cudaError_t e = prepare_relax(L.prec, L.smem_levels);
     if (e != cudaSuccess) return e;
     const unsigned g = (unsigned)L.n_work;
+    const int sm = L.smem_levels;
     if (L.prec == 1) {
         if (L.min_blocks == 2)
-            k_relax<1, 2><<<g, kT, L.smem_levels, st>>>(L.tab, L.work, L.n_work, L.smem_levels);
+            k_relax<1, 2><<<g, kT, sm, st>>>(L.tab, L.work, L.n_work, sm, cont);
         else
-            k_relax<1, 1><<<g, kT, L.smem_levels, st>>>(L.tab, L.work, L.n_work, L.smem_levels);
+            k_relax<1, 1><<<g, kT, sm, st>>>(L.tab, L.work, L.n_work, sm, cont);
     } else {
         if (L.min_blocks == 2)
-            k_relax<0, 2><<<g, kT, L.smem_levels, st>>>(L.tab, L.work, L.n_work, L.smem_levels);
+            k_relax<0, 2><<<g, kT, sm, st>>>(L.tab, L.work, L.n_work, sm, cont);
         else
-            k_relax<0, 1><<<g, kT, L.smem_levels, st>>>(L.tab, L.work, L.n_work, L.smem_levels);
+            k_relax<0, 1><<<g, kT, sm, st>>>(L.tab, L.work, L.n_work, sm, cont);
     }
     return cudaGetLastError();
 }

@@ -88,7 +88,10 @@ def run_single(name, precision, steps, resweep, cells=0):
             "sweep_frac_of_peak": sb / (sw_ms / 1e3) / 1e9 / peak if sw_ms > 0 else None,
             "peak_gbs": peak, "peak_kind": kind,
             "relax_share": prof["relax_ms"] / (dt * 1e3), "rechecks": prof["rechecks"],
-            "device_bytes": info.device_bytes}
+            "multi_rounds": prof["rounds"], "multi_idle_rounds": prof["idle_rounds"],
+            "relax_us_per_launch": prof["relax_ms"] * 1e3 / max(prof["relax_launches"], 1),
+            "device_bytes": info.device_bytes,
+            "flips_per_step_head": r["flips_per_step"][:16].tolist()}
 
 
 def run_ensemble(members, sample):

@@ -99,14 +99,28 @@ def test_pinwheel300_full_protocol_invariants_and_fields(B, oracle):
     assert max(np.abs(p32 - op).max(), np.abs(q32 - oq).max()) <= 1e-5 * scale
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_kagome1000_full_protocol_matches_oracle(B, prec):
+@pytest.mark.parametrize("prec,mode", [(0, 0), (1, 0), (1, 1)])
+def test_kagome1000_full_protocol_matches_oracle(B, prec, mode):
     # the whole 720-step rotation with thermal noise (3.0M islands, 3,146,771 flips):
-    # flips per step and the sequence hash as the oracle ran it
+    # flips per step and the sequence hash as the oracle ran it; the default relax
+    # (multi-flip rounds at this size) and the single-flip chain
     g = gold("kagome1000_full")
     w = I.WORKLOADS["kagome1000"]
     hx, hy = I.protocol_of(w["protocol"])
     sim = lib_sim(w, precision=prec)
+    sim.set_relax_mode(mode)
+    got = sim.run_protocol(hx, hy, log_cap=0)
+    assert got["status"] == 0
+    _check_against(g, got)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pinwheel300_full_protocol_multi_flip(B, prec):
+    g = gold("pinwheel300_full")
+    w = I.WORKLOADS["pinwheel300"]
+    hx, hy = I.protocol_of(w["protocol"])
+    sim = lib_sim(w, precision=prec)
+    sim.set_relax_mode(B.FS_RELAX_MULTI)
     got = sim.run_protocol(hx, hy, log_cap=0)
     assert got["status"] == 0
     _check_against(g, got)
