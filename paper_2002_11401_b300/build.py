@@ -21,6 +21,11 @@ LIB = os.path.join(HERE, "libflatspin_b300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I" + os.path.join(ROOT, "include")]
+# Per-file flags. The multi-flip relax runs one cluster of CTAs on several SMs that
+# read island state other CTAs of the same launch rewrite: its global loads bypass
+# the (per-SM, not coherent) L1 cache by default; read-only data keeps the
+# non-coherent cache path through __ldg.
+FILE_FLAGS = {"fs_relax_multi.cu": ["-Xptxas", "-dlcm=cg"]}
 
 
 def _nvcc() -> str:
@@ -45,7 +50,8 @@ def _compile(src: str, verbose: bool) -> str:
     if (os.path.exists(obj) and os.path.getmtime(obj) >= os.path.getmtime(src)
             and os.path.getmtime(obj) >= _headers_mtime()):
         return obj
-    cmd = [_nvcc(), *FLAGS, *ARCH, "-c", src, "-o", obj]
+    cmd = [_nvcc(), *FLAGS, *FILE_FLAGS.get(os.path.basename(src), []), *ARCH, "-c", src, "-o",
+           obj]
     if verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -25,9 +25,18 @@
 //
 // The max-tree over the keys is kept as an upper bound: keys that grow are pushed
 // up with atomic maxima, keys that shrink leave their ancestors stale, and the
-// candidate descent rebuilds every node it expands from its children. One CTA per
-// simulation and field step, like the single-flip relax.
+// candidate descent rebuilds every node it expands from its children.
+//
+// One thread-block cluster of NC CTAs per simulation and field step. The leader
+// (rank 0) holds the round's state and the upper tree levels in its shared memory,
+// chooses the threshold, descends the upper levels, sorts and tests the candidates
+// and finds the prefix; all CTAs together expand the lowest level into candidate
+// islands, evaluate their exact values, flip the picks and flip back the rest
+// (the others reach the leader's shared memory as distributed shared memory).
+// Cluster barriers separate the phases; every decision that steers the control
+// flow is read from the leader after a barrier, so all CTAs take the same path.
 #include <cuda_runtime.h>
+#include <cooperative_groups.h>
 #include <stdint.h>
 
 #include <atomic>
@@ -71,8 +80,19 @@ struct MultiShared {
     unsigned long long sel;
     int32_t sel_rem;
     int32_t lsh;                             // levels lsh.. are in shared memory
-    unsigned long long* lp[kMaxLevels];      // base of each tree level
+    unsigned long long* lp[kMaxLevels];      // base of each tree level (as this CTA sees it)
+    // the leader's decisions for the whole cluster
+    unsigned long long tkey;                 // this round's threshold
+    int32_t cmd;                             // what the round does next (kCmd*)
+    int32_t f0;                              // buffer of the level-0 nodes to expand
+    int32_t nl;                              // candidate islands found
+    int32_t stop;                            // 1: the relax of this launch ends after the round
 };
+
+constexpr int32_t kCmdExpand = 0;  // expand the level-0 nodes in front[f0]
+constexpr int32_t kCmdCommit = 1;  // the picks are ready (q in S.q)
+constexpr int32_t kCmdRetry = 2;   // nothing to flip yet: the leader starts again
+constexpr int32_t kCmdStop = 3;    // the relax of this launch is over
 
 // Tree levels: the upper ones (from lsh up) are copied into shared memory for the
 // whole launch (the next sweep rebuilds the tree in global memory), the lower ones
@@ -153,43 +173,48 @@ __device__ unsigned long long select_threshold(const Inst& I, int lev, int M, Mu
     return S.sel;
 }
 
-// A key that grew is pushed up every level with atomic maxima: reductions that do
-// not wait for the old value on the global levels, and on the shared ones an atomic
-// only while the node is still smaller (most keys stop below the top nodes).
+// A key that grew is pushed up with atomic maxima, on every level below the root
+// (the descent always expands the root's children, so the root is never read and
+// every key needs no atomic on its one node): reductions that do not wait for the
+// old value on the global levels; on the levels in shared memory (the one-CTA
+// launch) the old value the atomic returns stops the push at the first node that
+// already held the key (its ancestors hold it too once the phase's pushes are done).
 __device__ __forceinline__ void push_up(const MultiShared& S, int nlev, int64_t i,
                                         unsigned long long nk) {
+    const int top = nlev > 1 ? nlev - 1 : 1;  // levels 0 .. top - 1
     int64_t node = i;
-    for (int lev = 0; lev < nlev; ++lev) {
+    for (int lev = 0; lev < top; ++lev) {
         node >>= 5;
         unsigned long long* a = S.lp[lev] + node;
         if (lev < S.lsh) {
             atomicMax(a, nk);
-        } else {
-            if (*(volatile unsigned long long*)a >= nk) break;
-            atomicMax(a, nk);
+        } else if (atomicMax(a, nk) >= nk) {
+            break;
         }
     }
 }
 
-// Collects every leaf whose key reaches tkey (>= 1) into S.front[result], from the
-// root down, rebuilding each expanded node from its children; returns the buffer
-// index, or -1 when more than kCandCap nodes or leaves reach tkey. CTA-wide.
-__device__ int descend(const Inst& I, unsigned long long tkey, MultiShared& S) {
+// The leader descends from the root to the level-0 nodes (the parents of the
+// keys) whose value reaches tkey (>= 1), rebuilding each expanded node from its
+// children; the nodes go to S.front[result] (S.nf[result] of them). Returns the
+// buffer, or -1 when more than kCandCap nodes of a level reach tkey. With a single
+// level the root is the one level-0 node. CTA-wide.
+__device__ int descend_upper(const Inst& I, unsigned long long tkey, MultiShared& S) {
     constexpr int kB = 4;  // frontier nodes whose children a warp loads together
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int r = I.nlev - 1;
-    if (tid == 0) {
+    if (tid == 0) {  // (the root's value is not kept: its children are always expanded)
         S.front[0][0] = 0;
-        S.nf[0] = lvl_load(S, r, 0) >= tkey ? 1 : 0;
+        S.nf[0] = 1;
     }
     __syncthreads();
     int cur = 0;
-    for (int lev = r; lev >= 0; --lev) {
+    for (int lev = r; lev >= 1; --lev) {
         const int nf = S.nf[cur];
         if (tid == 0) S.nf[cur ^ 1] = 0;
         __syncthreads();
-        const int64_t lim = lev > 0 ? (int64_t)I.lvl_n[lev - 1] : I.n;
+        const int64_t lim = I.lvl_n[lev - 1];
         for (int f0 = wid * kB; f0 < nf; f0 += kMW * kB) {
             int64_t node[kB];
             unsigned long long v[kB];
@@ -197,16 +222,15 @@ __device__ int descend(const Inst& I, unsigned long long tkey, MultiShared& S) {
             for (int u = 0; u < kB; ++u) {  // every load in flight together
                 node[u] = f0 + u < nf ? (int64_t)S.front[cur][f0 + u] : -1;
                 const int64_t c = (node[u] << 5) + lane;
-                v[u] = 0ull;
-                if (node[u] >= 0 && c < lim) v[u] = lev > 0 ? lvl_load(S, lev - 1, c) : __ldcg(&I.key32[c]);
+                v[u] = node[u] >= 0 && c < lim ? lvl_load(S, lev - 1, c) : 0ull;
             }
 #pragma unroll
             for (int u = 0; u < kB; ++u) {
                 if (node[u] < 0) break;
                 const int64_t c = (node[u] << 5) + lane;
                 // (a node is never below its children: pushes raise every ancestor,
-                // repairs set a node to its children's maximum; so the maximum can be
-                // stored without reading the node first)
+                // repairs set a node to its children's maximum; so the maximum can
+                // be stored without reading the node first)
                 const unsigned long long m = warp_max_key(v[u]);
                 if (lane == 0) S.lp[lev][node[u]] = m;
                 const bool hit = v[u] != 0ull && v[u] >= tkey;
@@ -223,6 +247,44 @@ __device__ int descend(const Inst& I, unsigned long long tkey, MultiShared& S) {
         cur ^= 1;
     }
     return cur;
+}
+
+// Every CTA of the cluster: the level-0 nodes L->front[L->f0] expanded into the
+// keys that reach L->tkey, appended to L->ci (L->nl counts them, past kCandCap
+// too); each node is rebuilt from its keys. Warps of all CTAs share the nodes.
+template <int NC>
+__device__ void expand_leaves(const Inst& I, MultiShared* L, const MultiShared& S, int rank) {
+    constexpr int kB = 8;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int gw = rank * kMW + wid;
+    const int f0 = L->f0;
+    const int nf = L->nf[f0];
+    const unsigned long long tkey = L->tkey;
+    for (int fb = gw * kB; fb < nf; fb += NC * kMW * kB) {
+        int64_t node[kB];
+        unsigned long long v[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            node[u] = fb + u < nf ? (int64_t)L->front[f0][fb + u] : -1;
+            const int64_t c = (node[u] << 5) + lane;
+            v[u] = node[u] >= 0 && c < I.n ? __ldcg(&I.key32[c]) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            if (node[u] < 0) break;
+            const int64_t c = (node[u] << 5) + lane;
+            const unsigned long long m = warp_max_key(v[u]);
+            if (lane == 0) S.lp[0][node[u]] = m;
+            const bool hit = v[u] != 0ull && v[u] >= tkey;
+            const unsigned msk = __ballot_sync(0xffffffffu, hit);
+            int base = 0;
+            if (lane == 0 && msk) base = atomicAdd(&L->nl, __popc(msk));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            const int pos = base + __popc(msk & lt);
+            if (hit && pos < kCandCap) L->ci[pos] = (int32_t)c;
+        }
+    }
 }
 
 // Sorts S.cv / S.ci[0 .. n) into "before" order: up to kRankMax entries by rank
@@ -389,21 +451,40 @@ __device__ void scan_best(const Inst& I, uint32_t step, MultiShared& S) {
     __syncthreads();
 }
 
-template <int PREC>
+template <int PREC, int NC>
 __global__ void __launch_bounds__(kMT, 1)
     k_relax_multi(const Inst* __restrict__ tab, const int32_t* __restrict__ work, int n_work,
                   int smem_levels) {
+    namespace cg = cooperative_groups;
     __shared__ MultiShared S;
     extern __shared__ unsigned long long sm_levels[];
-    const Inst& I = tab[work[blockIdx.x]];
+    int rank = 0;
+    MultiShared* L = &S;  // the leader's state, as this CTA reaches it
+    unsigned long long* lead_levels = sm_levels;
+    if constexpr (NC > 1) {
+        cg::cluster_group cl = cg::this_cluster();
+        rank = (int)cl.block_rank();
+        if (rank != 0) {
+            L = cl.map_shared_rank(&S, 0);
+            lead_levels = cl.map_shared_rank(sm_levels, 0);
+        }
+    }
+    auto csync = [&]() {
+        if constexpr (NC > 1)
+            cg::this_cluster().sync();
+        else
+            __syncthreads();
+    };
+    const bool leader = rank == 0;
+    const Inst& I = tab[work[blockIdx.x / NC]];
     InstState* st = I.st;
     const int64_t t = st->t;
-    if (st->status != ST_OK || t >= I.K) return;
+    if (st->status != ST_OK || t >= I.K) return;  // (the same for every CTA)
     const uint32_t step = I.step0 + (uint32_t)t;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 
-    // the upper tree levels that fit smem_levels bytes, from the top down, in
-    // shared memory (the host sizes the launch by the same rule)
+    // the upper tree levels that fit smem_levels bytes, from the top down, in the
+    // leader's shared memory (the host sizes the launch by the same rule)
     if (tid == 0) {
         int64_t used = 0;
         int lsh = I.nlev;
@@ -419,7 +500,7 @@ __global__ void __launch_bounds__(kMT, 1)
             if (lev >= I.nlev) {
                 S.lp[lev] = nullptr;
             } else if (lev >= lsh) {
-                S.lp[lev] = sm_levels + off;
+                S.lp[lev] = lead_levels + off;
                 off += I.lvl_n[lev];
             } else {
                 S.lp[lev] = I.tree + I.lvl_off[lev];
@@ -427,179 +508,241 @@ __global__ void __launch_bounds__(kMT, 1)
         }
     }
     __syncthreads();
-    for (int lev = S.lsh; lev < I.nlev; ++lev)
-        for (int q = tid; q < I.lvl_n[lev]; q += kMT)
-            S.lp[lev][q] = __ldcg(&I.tree[I.lvl_off[lev] + q]);
-    __syncthreads();
+    if (leader)
+        for (int lev = S.lsh; lev < I.nlev; ++lev)
+            for (int q = tid; q < I.lvl_n[lev]; q += kMT)
+                S.lp[lev][q] = __ldcg(&I.tree[I.lvl_off[lev] + q]);
+    csync();
 
     int lsel = 0;
     while (lsel < I.nlev - 1 && I.lvl_n[lsel] > kSelMax) ++lsel;
 
+    // the leader's round state (the same in every leader thread)
     int64_t flips = 0;
     int32_t status = ST_OK;
-    uint64_t hash = tid == kHashT ? st->hash : 0ull;
+    uint64_t hash = leader && tid == kHashT ? st->hash : 0ull;
     const int64_t flips_before = st->n_flips;
     const int64_t max_flips = I.max_flips;
     const int m0 = max(1, min(kM0, I.lvl_n[lsel] / 8));  // rank of the threshold node
     int M = m0;
     int idle = 0;
-    unsigned long long carry = 0ull;  // a threshold from the previous round's candidates
     int64_t rounds = 0, idle_total = 0;
     int low = 0;
     bool handoff = false;
+    bool need_scan = false;
+    bool was_carried = false, was_forced = false;
+    unsigned long long carry = 0ull;   // a threshold from the previous round's candidates
     unsigned long long forced = 0ull;  // a threshold set by the previous iteration
 
     for (;;) {
-        if (++idle > kMaxIdle) {
-            status = ST_BOUNDS;
-            break;
+        // ---- A (leader): the threshold and the level-0 nodes that reach it --------
+        if (leader) {
+            int32_t cmd = kCmdExpand;
+            if (++idle > kMaxIdle) {
+                status = ST_BOUNDS;
+                cmd = kCmdStop;
+            } else if (need_scan) {  // a candidate set too large for any threshold
+                need_scan = false;
+                M = m0;
+                scan_best<PREC>(I, step, S);
+                if (S.nc == 0) {
+                    cmd = kCmdStop;
+                } else {
+                    const int64_t allowed = max_flips - flips;
+                    if (allowed <= 0) {
+                        status = ST_NOT_CONVERGED;
+                        cmd = kCmdStop;
+                    } else {
+                        if (tid == 0) {
+                            S.q = 1;
+                            S.cs[0] = rec_load(I, S.ci[0]).s;
+                        }
+                        cmd = kCmdCommit;
+                    }
+                }
+            } else {
+                ++idle_total;
+                unsigned long long tkey = 1ull;
+                was_forced = forced != 0ull;
+                was_carried = !was_forced && carry != 0ull;
+                if (was_forced) {
+                    tkey = forced;
+                    forced = 0ull;
+                } else if (was_carried) {
+                    tkey = carry;
+                    carry = 0ull;
+                } else {
+                    const unsigned long long sel = select_threshold(I, lsel, M, S);
+                    // lowered by 2^-18 (relative) so that the node's own island, whose
+                    // exact value lies within its key's band, counts as reaching it
+                    const float hi = __uint_as_float((uint32_t)(sel >> 32));
+                    const float lo = __fmul_rd(hi, 1.0f - 0x1.0p-18f);
+                    tkey = sel ? ((unsigned long long)__float_as_uint(lo) << 32) : 1ull;
+                    if (tkey == 0ull) tkey = 1ull;
+                }
+                const int buf = descend_upper(I, tkey, S);
+                if (buf < 0) {  // too many nodes reach it: a higher threshold, or a scan
+                    if (!was_carried) {
+                        if (M > 1 && !was_forced)
+                            M >>= 1;
+                        else
+                            need_scan = true;
+                    }
+                    cmd = kCmdRetry;
+                } else if (S.nf[buf] == 0) {
+                    if (tkey == 1ull) {
+                        cmd = kCmdStop;  // no key above zero: the relax is done
+                    } else {
+                        M = m0;  // the threshold came from stale nodes, repaired on the way
+                        cmd = kCmdRetry;
+                    }
+                } else if (tid == 0) {
+                    S.f0 = buf;
+                    S.tkey = tkey;
+                    S.nl = 0;
+                }
+            }
+            if (tid == 0) S.cmd = cmd;
         }
-        ++idle_total;
-        // ---- candidates: every leaf whose key reaches the threshold ----------------
-        unsigned long long tkey = 1ull;
-        const bool was_forced = forced != 0ull;
-        const bool was_carried = !was_forced && carry != 0ull;
-        if (was_forced) {
-            tkey = forced;
-            forced = 0ull;
-        } else if (was_carried) {
-            tkey = carry;
-            carry = 0ull;
-        } else {
-            const unsigned long long sel = select_threshold(I, lsel, M, S);
-            // lowered by 2^-18 (relative) so that the node's own island, whose exact
-            // value lies within its key's band, counts as reaching it
-            const float hi = __uint_as_float((uint32_t)(sel >> 32));
-            const float lo = __fmul_rd(hi, 1.0f - 0x1.0p-18f);
-            tkey = sel ? ((unsigned long long)__float_as_uint(lo) << 32) : 1ull;
-            if (tkey == 0ull) tkey = 1ull;
-        }
-        int buf = descend(I, tkey, S);
-        if (buf < 0) {  // too many reach it: a higher threshold, or a full scan
-            if (was_carried) continue;  // (select one instead)
-            if (M > 1 && !was_forced) {
-                M >>= 1;
+        csync();
+        int32_t cmd = L->cmd;
+        if (cmd == kCmdStop) break;
+        if (cmd == kCmdRetry) continue;
+        if (cmd == kCmdExpand) {
+            // ---- B (all): the candidate islands ------------------------------------
+            expand_leaves<NC>(I, L, S, rank);
+            csync();
+            const int nl = L->nl;
+            if (nl > kCandCap) {
+                if (leader && !was_carried) {
+                    if (M > 1 && !was_forced)
+                        M >>= 1;
+                    else
+                        need_scan = true;
+                }
                 continue;
             }
-            M = m0;
-            scan_best<PREC>(I, step, S);
-            if (S.nc == 0) break;
-            if (tid == 0) {
-                S.q = 1;
-                S.p = 1;
-                S.cs[0] = rec_load(I, S.ci[0]).s;
-            }
-            __syncthreads();
-        } else {
-            const int nc0 = S.nf[buf];
-            if (tid == 0) S.nc = nc0;
-            if (nc0 == 0) {
-                if (tkey == 1ull) break;  // no key above zero: the relax is done
-                M = m0;  // the threshold came from stale nodes, repaired on the way down
+            if (nl == 0) {
+                if (L->tkey == 1ull) break;  // (cannot happen: its parent reached it)
+                if (leader) M = m0;
                 continue;
             }
-            // exact values (islands found not flippable are demoted), in "before" order
+            // ---- C (all): exact values; islands found not flippable are demoted ----
             int n2 = 1;
-            while (n2 < nc0) n2 <<= 1;
-            for (int c = tid; c < n2; c += kMT) {
-                if (c < nc0) {
-                    const int32_t i = S.front[buf][c];
+            while (n2 < nl) n2 <<= 1;
+            for (int c = rank * kMT + tid; c < n2; c += NC * kMT) {
+                if (c < nl) {
+                    const int32_t i = L->ci[c];
                     const double v = exact_value<PREC>(I, i, step);
                     if (v > 0.0) {
                         if constexpr (PREC == 1) I.key32[i] = key32_of(__double2float_ru(v), i);
-                        S.cv[c] = (unsigned long long)__double_as_longlong(v);
+                        L->cv[c] = (unsigned long long)__double_as_longlong(v);
                     } else {
                         I.key32[i] = 0ull;
-                        S.cv[c] = 0ull;
+                        L->cv[c] = 0ull;
                     }
-                    S.ci[c] = i;
                 } else {
-                    S.cv[c] = 0ull;
-                    S.ci[c] = 0x7fffffff;
+                    L->cv[c] = 0ull;
+                    L->ci[c] = 0x7fffffff;
                 }
             }
-            __syncthreads();
-            sort_candidates(S, nc0, n2);
-            // (a) a pick must beat every island below the threshold: (v, i) no later
-            // than (tau, tau_index) in "before" order
-            const double tau = (double)__uint_as_float((uint32_t)(tkey >> 32));
-            const uint32_t tau_i = key32_idx(tkey);
-            const unsigned long long tb = (unsigned long long)__double_as_longlong(tau);
-            if (tid == 0) {
-                S.eligible = 0;
-                S.conflict_at = kPickCap;
-            }
-            __syncthreads();
-            for (int c = tid; c < min(nc0, kPickCap); c += kMT) {
-                const unsigned long long v = S.cv[c];
-                const bool ok = v != 0ull && (v > tb || (v == tb && (uint32_t)S.ci[c] <= tau_i));
-                if (ok) atomicMax(&S.eligible, c + 1);  // eligibility is a prefix of the order
-            }
-            __syncthreads();
-            int q = S.eligible;
-            if (q == 0) {
-                if (S.cv[0] == 0ull) {  // none of them is flippable (all demoted): select again
-                    M = m0;
-                    continue;
+            csync();
+            // ---- D (leader): order, threshold test, independence ---------------------
+            if (leader) {
+                if (tid == 0) S.nc = nl;
+                sort_candidates(S, nl, n2);
+                // (a) a pick must beat every island below the threshold: (v, i) no
+                // later than (tau, tau_index) in "before" order
+                const unsigned long long tkey = S.tkey;
+                const double tau = (double)__uint_as_float((uint32_t)(tkey >> 32));
+                const uint32_t tau_i = key32_idx(tkey);
+                const unsigned long long tb = (unsigned long long)__double_as_longlong(tau);
+                if (tid == 0) {
+                    S.eligible = 0;
+                    S.conflict_at = kPickCap;
                 }
-                // every candidate lies below the threshold: the next iteration takes
-                // the best one's value (rounded down) as the threshold, so that every
-                // island that could beat it is a candidate and the best one is eligible
-                const float v0 = __double2float_rd(__longlong_as_double((long long)S.cv[0]));
-                const unsigned long long tk = (unsigned long long)__float_as_uint(v0) << 32;
-                forced = tk > 0ull ? tk : 1ull;
                 __syncthreads();
-                continue;
-            }
-            // (b) picks more than twice the cutoff apart: the prefix before the first
-            // candidate that lies near an earlier one
-            for (int c = tid; c < q; c += kMT) {
-                const double2 pc = __ldg(&I.pos[S.ci[c]]);
-                S.cpos[c] = make_float2(__double2float_rn(pc.x), __double2float_rn(pc.y));
-            }
-            __syncthreads();
-            // pair (c, j), j < c: warp per row c, lanes over j; in FP32 against a
-            // radius widened by the rounding of the centres (I.rconf2f)
-            for (int c = 1 + wid; c < q; c += kMW) {
-                if (c >= S.conflict_at) break;
-                const float2 a = S.cpos[c];
-                bool hit = false;
-                for (int j = lane; j < c; j += 32) {
-                    const float dx = __fsub_rn(a.x, S.cpos[j].x), dy = __fsub_rn(a.y, S.cpos[j].y);
-                    hit = hit || __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) <= I.rconf2f;
+                for (int c = tid; c < min(nl, kPickCap); c += kMT) {
+                    const unsigned long long v = S.cv[c];
+                    const bool ok = v != 0ull && (v > tb || (v == tb && (uint32_t)S.ci[c] <= tau_i));
+                    if (ok) atomicMax(&S.eligible, c + 1);  // eligibility is a prefix of the order
                 }
-                if (__any_sync(0xffffffffu, hit)) {
-                    if (lane == 0) atomicMin(&S.conflict_at, c);
-                    break;
+                __syncthreads();
+                int q = S.eligible;
+                int32_t c2 = kCmdCommit;
+                if (q == 0) {
+                    if (S.cv[0] == 0ull) {  // none of them is flippable (all demoted)
+                        M = m0;
+                    } else {
+                        // every candidate lies below the threshold: the next iteration
+                        // takes the best one's value (rounded down) as the threshold, so
+                        // that every island that could beat it is a candidate
+                        const float v0 =
+                            __double2float_rd(__longlong_as_double((long long)S.cv[0]));
+                        const unsigned long long tk = (unsigned long long)__float_as_uint(v0) << 32;
+                        forced = tk > 0ull ? tk : 1ull;
+                    }
+                    c2 = kCmdRetry;
+                } else {
+                    // (b) picks more than twice the cutoff apart
+                    for (int c = tid; c < q; c += kMT) {
+                        const double2 pc = __ldg(&I.pos[S.ci[c]]);
+                        S.cpos[c] = make_float2(__double2float_rn(pc.x), __double2float_rn(pc.y));
+                    }
+                    __syncthreads();
+                    // pair (c, j), j < c: warp per row c, lanes over j; in FP32 against a
+                    // radius widened by the rounding of the centres (I.rconf2f)
+                    for (int c = 1 + wid; c < q; c += kMW) {
+                        if (c >= S.conflict_at) break;
+                        const float2 a = S.cpos[c];
+                        bool hit = false;
+                        for (int j = lane; j < c; j += 32) {
+                            const float dx = __fsub_rn(a.x, S.cpos[j].x);
+                            const float dy = __fsub_rn(a.y, S.cpos[j].y);
+                            hit = hit || __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) <= I.rconf2f;
+                        }
+                        if (__any_sync(0xffffffffu, hit)) {
+                            if (lane == 0) atomicMin(&S.conflict_at, c);
+                            break;
+                        }
+                    }
+                    __syncthreads();
+                    q = min(q, S.conflict_at);
+                    // the step's flip budget
+                    const int64_t allowed = max_flips - flips;
+                    if (allowed <= 0) {
+                        status = ST_NOT_CONVERGED;
+                        c2 = kCmdStop;
+                    } else if (q > allowed) {
+                        q = (int)allowed;
+                    }
+                    for (int c = tid; c < q; c += kMT) S.cs[c] = rec_load(I, S.ci[c]).s;
+                    if (tid == 0) S.q = q;
                 }
+                if (tid == 0) S.cmd = c2;
             }
-            __syncthreads();
-            q = min(q, S.conflict_at);
-            if (tid == 0) S.q = q;
-            for (int c = tid; c < q; c += kMT) S.cs[c] = rec_load(I, S.ci[c]).s;
-            __syncthreads();
+            csync();
+            cmd = L->cmd;
+            if (cmd == kCmdStop) break;
+            if (cmd == kCmdRetry) continue;
         }
+        // ---- E (all): flip the picks together (disjoint neighbourhoods) --------------
         {
-            int q = S.q;
-            // the step's flip budget
-            const int64_t allowed = max_flips - flips;
-            if (allowed <= 0) {
-                status = ST_NOT_CONVERGED;
-                break;
-            }
-            if (q > allowed) q = (int)allowed;
-            // ---- flip the picks together (disjoint neighbourhoods) -----------------
-            for (int j = wid; j < q; j += kMW) {
+            const int q = L->q;
+            for (int j = rank + NC * wid; j < q; j += NC * kMW) {
                 unsigned long long xv;
                 int32_t xi;
-                flip_warp<PREC>(I, S, S.ci[j], -S.cs[j], step, &xv, &xi);
+                flip_warp<PREC>(I, S, L->ci[j], -L->cs[j], step, &xv, &xi);
                 if (lane == 0) {
-                    S.xv[j] = xv;
-                    S.xi[j] = xi;
+                    L->xv[j] = xv;
+                    L->xi[j] = xi;
                 }
             }
-            __syncthreads();
-            // ---- (c): the longest prefix no earlier pick's neighbour overtakes -------
+        }
+        csync();
+        // ---- F (leader): the longest prefix no earlier pick's neighbour overtakes ----
+        if (leader) {
+            const int q = S.q;
             // warp 0, 32 picks at a time: the best of the earlier picks' neighbour
             // values (an exclusive prefix maximum), carried between chunks
             if (wid == 0) {
@@ -610,9 +753,8 @@ __global__ void __launch_bounds__(kMT, 1)
                     const int j = j0 + lane;
                     unsigned long long xv = j < q ? S.xv[j] : 0ull;
                     int32_t xi = j < q ? S.xi[j] : 0x7fffffff;
-                    // inclusive prefix maximum in "before" order
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
+                    for (int o = 1; o < 32; o <<= 1) {  // inclusive prefix maximum
                         const unsigned long long ov = __shfl_up_sync(0xffffffffu, xv, o);
                         const int32_t oi = __shfl_up_sync(0xffffffffu, xi, o);
                         if (lane >= o && ov && (!xv || before(ov, oi, xv, xi))) {
@@ -620,7 +762,6 @@ __global__ void __launch_bounds__(kMT, 1)
                             xi = oi;
                         }
                     }
-                    // exclusive: the lane before's inclusive value, or the carry
                     unsigned long long ev = __shfl_up_sync(0xffffffffu, xv, 1);
                     int32_t ei = __shfl_up_sync(0xffffffffu, xi, 1);
                     if (lane == 0) {
@@ -637,7 +778,6 @@ __global__ void __launch_bounds__(kMT, 1)
                         p = j0 + __ffs(fm) - 1;
                         break;
                     }
-                    // carry the chunk's inclusive maximum (lane 31's, or the carry)
                     const unsigned long long lv = __shfl_sync(0xffffffffu, xv, 31);
                     const int32_t li = __shfl_sync(0xffffffffu, xi, 31);
                     if (lv && (!cv_ || before(lv, li, cv_, ci_))) {
@@ -649,13 +789,7 @@ __global__ void __launch_bounds__(kMT, 1)
             }
             __syncthreads();
             const int p = S.p;
-            // ---- flip the rest back ---------------------------------------------------
-            for (int j = p + wid; j < q; j += kMW) {
-                unsigned long long xv;
-                int32_t xi;
-                flip_warp<PREC>(I, S, S.ci[j], S.cs[j], step, &xv, &xi);
-            }
-            // ---- log and hash, in the order of the picks --------------------------------
+            // log and hash, in the order of the picks
             for (int j = tid; j < p; j += kMT) {
                 const int64_t qq = flips_before + flips + j;
                 if (I.log_spin && qq < I.log_cap) {
@@ -685,10 +819,23 @@ __global__ void __launch_bounds__(kMT, 1)
                     carry = (unsigned long long)__float_as_uint(f) << 32;
                 }
             }
-            __syncthreads();
-            if (handoff) break;
+            if (tid == 0) S.stop = handoff ? 1 : 0;
         }
+        csync();
+        // ---- G (all): flip the rest back ---------------------------------------------
+        {
+            const int q = L->q, p = L->p;
+            for (int j = p + rank + NC * wid; j < q; j += NC * kMW) {
+                unsigned long long xv;
+                int32_t xi;
+                flip_warp<PREC>(I, S, L->ci[j], L->cs[j], step, &xv, &xi);
+            }
+        }
+        csync();
+        if (L->stop) break;
     }
+    csync();  // (no CTA leaves while another may still reach the leader's memory)
+    if (!leader) return;
     if (tid == kHashT) st->hash = hash;
     if (handoff && status == ST_OK) {
         // the single-flip relax reads the whole tree from global memory: the levels
@@ -732,30 +879,82 @@ int relax_multi_smem(int64_t n) {
     return (int)used;
 }
 
+namespace {
+
+constexpr int kNC = 8;  // CTAs of a multi-flip relax cluster
+
+template <int PREC, int NC>
+cudaError_t launch_multi(const RelaxLaunch& L, int smem, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(L.n_work * NC));
+    cfg.blockDim = dim3(kMT);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = NC;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_relax_multi<PREC, NC>, L.tab, L.work, L.n_work, smem);
+}
+
+template <int PREC, int NC>
+cudaError_t set_multi_smem(int smem) {
+    return cudaFuncSetAttribute(k_relax_multi<PREC, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem);
+}
+
+// Whether a cluster of kNC CTAs with this much dynamic shared memory fits the GPU.
+template <int PREC>
+bool cluster_fits(int smem) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kNC);
+    cfg.blockDim = dim3(kMT);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kNC;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&clusters, k_relax_multi<PREC, kNC>, &cfg);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return clusters >= 1;
+}
+
+}  // namespace
+
 cudaError_t launch_relax_multi(const RelaxLaunch& L, cudaStream_t st) {
     if (L.n_work == 0) return cudaSuccess;
+    // per precision: the dynamic shared memory set so far, and whether the cluster
+    // of that size fits (checked once per size, before any launch is captured)
     static std::atomic<int> set_bytes[2] = {{-1}, {-1}};
+    static std::atomic<int> use_cluster[2] = {{0}, {0}};
     static std::mutex mu;
     const int k = L.prec == 1 ? 1 : 0;
     const int smem = L.smem_multi;
     if (set_bytes[k].load() < smem) {
         std::lock_guard<std::mutex> g(mu);
         if (set_bytes[k].load() < smem) {
-            const cudaError_t e =
-                L.prec == 1 ? cudaFuncSetAttribute(k_relax_multi<1>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
-                            : cudaFuncSetAttribute(k_relax_multi<0>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            cudaError_t e = k ? set_multi_smem<1, 1>(smem) : set_multi_smem<0, 1>(smem);
+            if (e == cudaSuccess) e = k ? set_multi_smem<1, kNC>(smem) : set_multi_smem<0, kNC>(smem);
             if (e != cudaSuccess) return e;
+            use_cluster[k].store((k ? cluster_fits<1>(0) : cluster_fits<0>(0)) ? 1 : 0);
             set_bytes[k].store(smem);
         }
     }
-    const unsigned g = (unsigned)L.n_work;
-    if (L.prec == 1)
-        k_relax_multi<1><<<g, kMT, smem, st>>>(L.tab, L.work, L.n_work, smem);
-    else
-        k_relax_multi<0><<<g, kMT, smem, st>>>(L.tab, L.work, L.n_work, smem);
-    return cudaGetLastError();
+    // A cluster keeps the whole tree in global memory (every CTA pushes keys into
+    // it); the one-CTA launch keeps the upper levels in its shared memory.
+    if (use_cluster[k].load())
+        return k ? launch_multi<1, kNC>(L, 0, st) : launch_multi<0, kNC>(L, 0, st);
+    return k ? launch_multi<1, 1>(L, smem, st) : launch_multi<0, 1>(L, smem, st);
 }
 
 }  // namespace fs
