@@ -21,11 +21,8 @@ LIB = os.path.join(HERE, "libflatspin_b300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I" + os.path.join(ROOT, "include")]
-# Per-file flags. The multi-flip relax runs one cluster of CTAs on several SMs that
-# read island state other CTAs of the same launch rewrite: its global loads bypass
-# the (per-SM, not coherent) L1 cache by default; read-only data keeps the
-# non-coherent cache path through __ldg.
-FILE_FLAGS = {"fs_relax_multi.cu": ["-Xptxas", "-dlcm=cg"]}
+# Per-file flags (none at present).
+FILE_FLAGS: dict = {}
 
 
 def _nvcc() -> str:

@@ -883,7 +883,6 @@ cudaError_t enqueue_steps(fs_sim* sim, int64_t K, int resweep, cudaStream_t st) 
     R.prec = sim->p.precision;
     R.smem_levels = relax_smem_levels(sim->n);
     R.multi = relax_multi(sim) ? 1 : 0;
-    if (R.multi) R.smem_multi = relax_multi_smem(sim->n);
     cudaError_t e;
     if (sim->profiling && sim->ev_used + 3 * (size_t)K > 30000 &&
         (e = collect_profile(sim)) != cudaSuccess)

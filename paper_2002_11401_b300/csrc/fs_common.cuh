@@ -325,12 +325,13 @@ __device__ __forceinline__ double2 ext_proj(double hx, double hy, double2 cs) {
 
 // The external field of island i (class ci) projected on its frame at the current
 // field step: the per-island values the sweep wrote when a local or spatial field
-// is set, else the per-class table of the global field.
+// is set, else the per-class table of the global field (read with plain loads: a
+// kernel may point the descriptor's table at a copy in its shared memory).
 __device__ __forceinline__ double2 ext64_at(const Inst& I, int64_t i, uint16_t ci) {
-    return I.exti64 ? __ldg(&I.exti64[i]) : __ldg(&I.ext64[ci]);
+    return I.exti64 ? __ldg(&I.exti64[i]) : I.ext64[ci];
 }
 __device__ __forceinline__ float2 ext32_at(const Inst& I, int64_t i, uint16_t ci) {
-    return I.exti32 ? __ldg(&I.exti32[i]) : __ldg(&I.ext32[ci]);
+    return I.exti32 ? __ldg(&I.exti32[i]) : I.ext32[ci];
 }
 
 // The lab-frame external field of island i at field step `step`: the global

@@ -33,14 +33,12 @@ struct RelaxLaunch {
     int min_blocks = 1;   // 2: the build for two resident CTAs per SM (shared GPU)
     int multi = 0;        // 1: multi-flip rounds (fs_relax_multi.cu) first, then the
                           // single-flip kernel for what they hand off
-    int smem_multi = 0;   // dynamic shared memory of the multi-flip launch
 };
 
 cudaError_t launch_ext_table(const SweepLaunch& L, cudaStream_t st);
 cudaError_t launch_sweep(const SweepLaunch& L, cudaStream_t st);
 cudaError_t launch_relax(const RelaxLaunch& L, cudaStream_t st);
 cudaError_t launch_relax_multi(const RelaxLaunch& L, cudaStream_t st);
-int relax_multi_smem(int64_t n);  // dynamic shared memory of a multi-flip relax launch
 cudaError_t prepare_relax(int prec, int smem);
 // out5 = [h_par | h_perp | lhs | lo | hi], 5 n doubles
 cudaError_t launch_eval_all(const Inst* tab, int64_t n, double hx, double hy, uint32_t step,

@@ -24,24 +24,27 @@
 // sequence, the flips per field step and the hash equal the single-flip relax's.
 //
 // The max-tree over the keys is kept as an upper bound: keys that grow are pushed
-// up with atomic maxima, keys that shrink leave their ancestors stale, and the
-// candidate descent rebuilds every node it expands from its children.
+// up with atomic maxima, keys that shrink leave their ancestors stale, and every
+// node the candidate search expands is rebuilt from its children.
 //
-// One thread-block cluster of NC CTAs per simulation and field step. The leader
-// (rank 0) holds the round's state and the upper tree levels in its shared memory,
-// chooses the threshold, descends the upper levels, sorts and tests the candidates
-// and finds the prefix; all CTAs together expand the lowest level into candidate
-// islands, evaluate their exact values, flip the picks and flip back the rest
-// (the others reach the leader's shared memory as distributed shared memory).
-// Cluster barriers separate the phases; every decision that steers the control
-// flow is read from the leader after a barrier, so all CTAs take the same path.
+// One thread-block cluster of NC CTAs per simulation and field step. A round is
+// two cluster-wide phases, each between two cluster barriers:
+//   expand: all CTAs expand the frontier the leader chose into the candidate
+//           islands and evaluate each one exactly (value, spin, row, centre);
+//   commit: all CTAs flip the picks, one warp a pick.
+// The leader (rank 0) holds the round's state in its shared memory and does the
+// serial work alone between the phases: after an expand it orders and tests the
+// candidates and chooses the picks; after a commit it finds the prefix, flips the
+// rest back, and chooses the next threshold and frontier from one level of the tree
+// (loaded whole). The other CTAs reach the leader's shared memory as distributed
+// shared memory; every decision that steers the control flow is read from the
+// leader after a barrier, so all CTAs take the same path.
 #include <cuda_runtime.h>
 #include <cooperative_groups.h>
 #include <stdint.h>
 
 #include <atomic>
 #include <mutex>
-#include <vector>
 
 #include "fs_common.cuh"
 #include "fs_kernels.h"
@@ -55,7 +58,7 @@ constexpr int kMT = 512;          // threads of a multi-flip relax CTA
 constexpr int kMW = kMT / 32;
 constexpr int kCandCap = 1024;    // candidate islands per round
 constexpr int kPickCap = 256;     // picks tested per round
-constexpr int kSelMax = 8192;     // threshold chosen on the lowest level with at most this many nodes
+constexpr int kSelMax = 8192;     // thresholds are chosen on the lowest level with at most this many nodes
 constexpr int kSelPer = kSelMax / kMT;
 constexpr int kM0 = 256;          // rank of the threshold node
 constexpr int kHashT = kMT - 1;   // thread that folds the flips into the sequence hash
@@ -65,59 +68,93 @@ constexpr int kCarry = 160;       // candidates carried below a round's last fli
 // fewer than kPMin flips (a chain of flips that each make a neighbour the largest).
 constexpr int kPMin = 8;
 constexpr int kLowRounds = 4;
+constexpr int kClsSh = 32;        // angle classes whose external field is read from shared memory
+constexpr int kRankMax = 256;     // candidates sorted by rank (more: a bitonic network)
+constexpr int kHashQ = 2 * kPickCap;  // flips waiting to be folded into the sequence hash
 
-struct MultiShared {
-    unsigned long long cv[kCandCap];  // candidates' exact values (double bits; 0 = none)
-    int32_t ci[kCandCap];             // candidates' islands
-    int32_t front[2][kCandCap];       // descent frontier
-    float2 cpos[kPickCap];            // the first candidates' centres (FP32)
-    unsigned long long xv[kPickCap];  // per pick: the best new value among its neighbours
-    int32_t xi[kPickCap];             //   and its island
-    int32_t cs[kPickCap];             // the picks' spins before the round
-    int32_t hist[256];
-    int32_t nf[2];
-    int32_t nc, q, p, overflow, conflict_at, eligible;
-    unsigned long long sel;
-    int32_t sel_rem;
-    int32_t lsh;                             // levels lsh.. are in shared memory
-    unsigned long long* lp[kMaxLevels];      // base of each tree level (as this CTA sees it)
-    // the leader's decisions for the whole cluster
-    unsigned long long tkey;                 // this round's threshold
-    int32_t cmd;                             // what the round does next (kCmd*)
-    int32_t f0;                              // buffer of the level-0 nodes to expand
-    int32_t nl;                              // candidate islands found
-    int32_t stop;                            // 1: the relax of this launch ends after the round
+// One candidate island as its exact evaluation found it.
+struct __align__(16) Cand {
+    unsigned long long v;  // exact value (double bits; 0 = not flippable)
+    int32_t i;
+    uint32_t rowq;         // its neighbour row (first entry / 4, entries / 4)
+    float2 pos;            // centre (FP32)
+    uint16_t rowlenq;
+    int16_t s;             // spin
+    int32_t pad;
 };
 
-constexpr int32_t kCmdExpand = 0;  // expand the level-0 nodes in front[f0]
-constexpr int32_t kCmdCommit = 1;  // the picks are ready (q in S.q)
-constexpr int32_t kCmdRetry = 2;   // nothing to flip yet: the leader starts again
-constexpr int32_t kCmdStop = 3;    // the relax of this launch is over
+// One pick of a round: the island, its spin before the round and its row.
+struct __align__(16) Pick {
+    int32_t i;
+    uint32_t rowq;
+    uint16_t rowlenq;
+    int16_t s;
+    int32_t eager;  // 1: flipped (stored) at once, to be flipped back if after the prefix
+};
 
-// Tree levels: the upper ones (from lsh up) are copied into shared memory for the
-// whole launch (the next sweep rebuilds the tree in global memory), the lower ones
-// stay in global memory and are read through L2.
-__device__ __forceinline__ unsigned long long lvl_load(const MultiShared& S, int lev,
-                                                       int64_t idx) {
-    return lev >= S.lsh ? S.lp[lev][idx] : __ldcg(S.lp[lev] + idx);
-}
+struct MultiShared {
+    Cand cand[kCandCap];              // candidates in the order found
+    unsigned long long sv[kCandCap];  // candidates in "before" order: value,
+    int32_t si[kCandCap];             //   island,
+    int16_t so[kCandCap];             //   and slot in cand
+    float2 sp[kPickCap];              // the first candidates' centres, in that order
+    int32_t front[2][kCandCap];       // frontier of the tree search
+    int32_t loc[kCandCap];            // the candidate islands this CTA found
+    Pick pk[kPickCap];                // the round's picks
+    unsigned long long xv[kPickCap];  // per pick: the best new value among its neighbours
+    int32_t xi[kPickCap];             //   and its island
+    int32_t hist[256];
+    int32_t hq[kHashQ];               // flips not yet in the hash, in order (leader)
+    int32_t hq_n;
+    double2 ext64[kClsSh];            // the step's external field per angle class
+    float2 ext32[kClsSh];
+    Inst inst;                        // this CTA's copy of the simulation's descriptor
+    unsigned long long* lp[kMaxLevels];  // base of each tree level (global memory)
+    int32_t nf[2];
+    int32_t nloc, lbase;              // this CTA's candidates; their first slot
+    int32_t nl;                       // candidate islands found (leader; past kCandCap too)
+    int32_t nc, nz, q, p, conflict_at, eligible;
+    unsigned long long sel;
+    int32_t sel_rem;
+    // the leader's decisions for the whole cluster
+    unsigned long long tkey;          // this round's threshold
+    int32_t cmd;                      // what the cluster does next (kCmd*)
+    int32_t f_lev;                    // level of the frontier nodes to expand (0 or 1)
+    int32_t f_buf;                    // their buffer in front
+};
+
+// Dynamic shared memory of a CTA: its state, then every warp's staging slots.
+constexpr int kStageOff = (int)((sizeof(MultiShared) + 15) & ~(size_t)15);
+
+constexpr int32_t kCmdExpand = 0;   // expand the frontier into candidates
+constexpr int32_t kCmdCompute = 1;  // compute the picks' flips (q in S.q)
+constexpr int32_t kCmdStore = 4;    // store the staged flips of the prefix (p in S.p)
+constexpr int32_t kCmdStop = 2;     // the relax of this launch is over
 
 __device__ __forceinline__ bool before(unsigned long long va, int32_t ia, unsigned long long vb,
                                        int32_t ib) {
     return va > vb || (va == vb && ia < ib);
 }
 
-// The M-th largest key among the nodes of level `lev` (all nodes, stale ones too),
-// by a radix selection over the 64-bit values, eight bits a pass. CTA-wide.
-__device__ unsigned long long select_threshold(const Inst& I, int lev, int M, MultiShared& S) {
+// Appends the lanes' hits (island or node `c` where `hit`) to list[*cnt ...) (the
+// count runs on past cap; entries past it are dropped). Warp-wide.
+__device__ __forceinline__ void warp_append(bool hit, int32_t c, int32_t* list, int32_t* cnt,
+                                            int cap) {
+    const int lane = threadIdx.x & 31;
+    const unsigned msk = __ballot_sync(0xffffffffu, hit);
+    int base = 0;
+    if (lane == 0 && msk) base = atomicAdd(cnt, __popc(msk));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const int pos = base + __popc(msk & ((1u << lane) - 1u));
+    if (hit && pos < cap) list[pos] = c;
+}
+
+// The M-th largest of the values v[u] (node tid + u kMT, cnt nodes; all of them,
+// stale ones too), by a radix selection over the 64-bit values, eight bits a pass.
+// CTA-wide.
+__device__ unsigned long long select_threshold(const unsigned long long (&v)[kSelPer], int cnt,
+                                               int M, MultiShared& S) {
     const int tid = threadIdx.x, lane = tid & 31;
-    const int cnt = I.lvl_n[lev];
-    unsigned long long v[kSelPer];
-#pragma unroll
-    for (int u = 0; u < kSelPer; ++u) {
-        const int c = tid + u * kMT;
-        v[u] = c < cnt ? lvl_load(S, lev, c) : 0ull;
-    }
     if (M > cnt) M = cnt;
     if (tid == 0) {
         S.sel = 0ull;
@@ -173,252 +210,225 @@ __device__ unsigned long long select_threshold(const Inst& I, int lev, int M, Mu
     return S.sel;
 }
 
-// A key that grew is pushed up with atomic maxima, on every level below the root
-// (the descent always expands the root's children, so the root is never read and
-// every key needs no atomic on its one node): reductions that do not wait for the
-// old value on the global levels; on the levels in shared memory (the one-CTA
-// launch) the old value the atomic returns stops the push at the first node that
-// already held the key (its ancestors hold it too once the phase's pushes are done).
-__device__ __forceinline__ void push_up(const MultiShared& S, int nlev, int64_t i,
+// A key that grew is pushed up with atomic maxima (reductions that do not wait for
+// the old value) on every level below the root: the search never reads the root,
+// and the single-flip relax that may take over reads only levels below it.
+__device__ __forceinline__ void push_up(unsigned long long* const* lp, int nlev, int64_t i,
                                         unsigned long long nk) {
     const int top = nlev > 1 ? nlev - 1 : 1;  // levels 0 .. top - 1
     int64_t node = i;
     for (int lev = 0; lev < top; ++lev) {
         node >>= 5;
-        unsigned long long* a = S.lp[lev] + node;
-        if (lev < S.lsh) {
-            atomicMax(a, nk);
-        } else if (atomicMax(a, nk) >= nk) {
-            break;
-        }
+        atomicMax(lp[lev] + node, nk);
     }
 }
 
-// The leader descends from the root to the level-0 nodes (the parents of the
-// keys) whose value reaches tkey (>= 1), rebuilding each expanded node from its
-// children; the nodes go to S.front[result] (S.nf[result] of them). Returns the
-// buffer, or -1 when more than kCandCap nodes of a level reach tkey. With a single
-// level the root is the one level-0 node. CTA-wide.
-__device__ int descend_upper(const Inst& I, unsigned long long tkey, MultiShared& S) {
-    constexpr int kB = 4;  // frontier nodes whose children a warp loads together
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    const int r = I.nlev - 1;
-    if (tid == 0) {  // (the root's value is not kept: its children are always expanded)
-        S.front[0][0] = 0;
-        S.nf[0] = 1;
-    }
-    __syncthreads();
-    int cur = 0;
-    for (int lev = r; lev >= 1; --lev) {
-        const int nf = S.nf[cur];
-        if (tid == 0) S.nf[cur ^ 1] = 0;
-        __syncthreads();
-        const int64_t lim = I.lvl_n[lev - 1];
-        for (int f0 = wid * kB; f0 < nf; f0 += kMW * kB) {
-            int64_t node[kB];
-            unsigned long long v[kB];
-#pragma unroll
-            for (int u = 0; u < kB; ++u) {  // every load in flight together
-                node[u] = f0 + u < nf ? (int64_t)S.front[cur][f0 + u] : -1;
-                const int64_t c = (node[u] << 5) + lane;
-                v[u] = node[u] >= 0 && c < lim ? lvl_load(S, lev - 1, c) : 0ull;
-            }
-#pragma unroll
-            for (int u = 0; u < kB; ++u) {
-                if (node[u] < 0) break;
-                const int64_t c = (node[u] << 5) + lane;
-                // (a node is never below its children: pushes raise every ancestor,
-                // repairs set a node to its children's maximum; so the maximum can
-                // be stored without reading the node first)
-                const unsigned long long m = warp_max_key(v[u]);
-                if (lane == 0) S.lp[lev][node[u]] = m;
-                const bool hit = v[u] != 0ull && v[u] >= tkey;
-                const unsigned msk = __ballot_sync(0xffffffffu, hit);
-                int base = 0;
-                if (lane == 0 && msk) base = atomicAdd(&S.nf[cur ^ 1], __popc(msk));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                const int pos = base + __popc(msk & lt);
-                if (hit && pos < kCandCap) S.front[cur ^ 1][pos] = (int32_t)c;
-            }
-        }
-        __syncthreads();
-        if (S.nf[cur ^ 1] > kCandCap) return -1;
-        cur ^= 1;
-    }
-    return cur;
-}
+// What one neighbour update writes: the island's exact sums, the changing half of
+// its record and its keys, and whether its key grew (then it is pushed up the tree).
+struct __align__(16) Stage {
+    longlong2 h;
+    unsigned long long nk;
+    double x;
+    int2 g;
+    int32_t i;  // -1: none
+    float lo;
+    int32_t s;
+    int32_t push;
+};
 
-// Every CTA of the cluster: the level-0 nodes L->front[L->f0] expanded into the
-// keys that reach L->tkey, appended to L->ci (L->nl counts them, past kCandCap
-// too); each node is rebuilt from its keys. Warps of all CTAs share the nodes.
-template <int NC>
-__device__ void expand_leaves(const Inst& I, MultiShared* L, const MultiShared& S, int rank) {
-    constexpr int kB = 8;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    const int gw = rank * kMW + wid;
-    const int f0 = L->f0;
-    const int nf = L->nf[f0];
-    const unsigned long long tkey = L->tkey;
-    for (int fb = gw * kB; fb < nf; fb += NC * kMW * kB) {
-        int64_t node[kB];
-        unsigned long long v[kB];
-#pragma unroll
-        for (int u = 0; u < kB; ++u) {
-            node[u] = fb + u < nf ? (int64_t)L->front[f0][fb + u] : -1;
-            const int64_t c = (node[u] << 5) + lane;
-            v[u] = node[u] >= 0 && c < I.n ? __ldcg(&I.key32[c]) : 0ull;
-        }
-#pragma unroll
-        for (int u = 0; u < kB; ++u) {
-            if (node[u] < 0) break;
-            const int64_t c = (node[u] << 5) + lane;
-            const unsigned long long m = warp_max_key(v[u]);
-            if (lane == 0) S.lp[0][node[u]] = m;
-            const bool hit = v[u] != 0ull && v[u] >= tkey;
-            const unsigned msk = __ballot_sync(0xffffffffu, hit);
-            int base = 0;
-            if (lane == 0 && msk) base = atomicAdd(&L->nl, __popc(msk));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            const int pos = base + __popc(msk & lt);
-            if (hit && pos < kCandCap) L->ci[pos] = (int32_t)c;
-        }
-    }
-}
+constexpr int kSlots = 3;                 // slots a lane takes per pass
+constexpr int kStageSlots = 32 * kSlots;  // a warp's staging slots (one pass)
 
-// Sorts S.cv / S.ci[0 .. n) into "before" order: up to kRankMax entries by rank
-// (every entry counts those that go before it; keys are distinct), more by a
-// bitonic network over the next power of two (padding entries sort last).
-constexpr int kRankMax = 256;
-__device__ void sort_candidates(MultiShared& S, int n, int n2) {
-    if (n <= kRankMax) {
-        unsigned long long v[kRankMax / kMT + 1];
-        int32_t ix[kRankMax / kMT + 1], rk[kRankMax / kMT + 1];
-        int m = 0;
-        for (int t = threadIdx.x; t < n; t += kMT, ++m) {
-            v[m] = S.cv[t];
-            ix[m] = S.ci[t];
-            int r = 0;
-            for (int u = 0; u < n; ++u) r += before(S.cv[u], S.ci[u], v[m], ix[m]) ? 1 : 0;
-            rk[m] = r;
-        }
-        __syncthreads();
-        for (int u = 0; u < m; ++u) {
-            S.cv[rk[u]] = v[u];
-            S.ci[rk[u]] = ix[u];
-        }
-        __syncthreads();
-        return;
-    }
-    for (int k = 2; k <= n2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int t = threadIdx.x; t < n2; t += kMT) {
-                const int o = t ^ j;
-                if (o > t) {
-                    const bool up = (t & k) == 0;
-                    const unsigned long long va = S.cv[t], vb = S.cv[o];
-                    const int32_t ia = S.ci[t], ib = S.ci[o];
-                    const bool swap = up ? before(vb, ib, va, ia) : before(va, ia, vb, ib);
-                    if (swap) {
-                        S.cv[t] = vb;
-                        S.cv[o] = va;
-                        S.ci[t] = ib;
-                        S.ci[o] = ia;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
-
-// Flips island k to spin snew (its neighbours' exact sums change by 2 snew times
-// their coefficients) with every new value stored; warp-wide. Returns, on every
-// lane, the best new value among the neighbours (FS_FP64: exact; FP32 path: the
-// upper bound of the key) and its island.
+// One pass over the slots e0, e0 + 32, ... (e0 = first + lane) of the flip of
+// island k (row [.., r1)) to spin snew: each neighbour's exact sums change by
+// 2 snew times their coefficients and its key is evaluated again; k's own update
+// (its field unchanged, its spin flipped) takes the slot r1, just past the row; the
+// row's padding (self-entries of zero weight) is skipped. Every load of the pass
+// is in flight before any result is used; nothing is stored.
 template <int PREC>
-__device__ void flip_warp(const Inst& I, const MultiShared& S, int64_t k, int snew, uint32_t step,
-                          unsigned long long* xv, int32_t* xi) {
-    const int lane = threadIdx.x & 31;
-    const IslandRec rk = rec_load(I, k);
-    const int64_t r0 = (int64_t)rk.rowq << 2, r1 = r0 + ((int64_t)rk.rowlenq << 2);
-    unsigned long long bv = 0ull;
-    int32_t bi = 0x7fffffff;
-    // two entries a lane at a time: both updates are computed (loads in flight
-    // together) before either is stored
-    // k's own update (its field unchanged, its spin flipped) takes the slot of the
-    // row's last entry when that is padding (a self-entry of zero weight, which
-    // gives exactly that update), else it follows the row
-    const bool own_in_row = r1 > r0 && __ldg(&I.col[r1 - 1]) == (int32_t)k;
-    for (int64_t e0 = r0 + lane; e0 < r1; e0 += 64) {
-        Upd u[2];
+__device__ __forceinline__ void pass_compute(const Inst& I, int64_t k, int snew, int64_t e0,
+                                             int64_t r1, uint32_t step, Stage (&t)[kSlots]) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t e = e0 + 32 * h;
-            u[h].i = -1;
-            if (e < r1) {
-                const int32_t i = __ldg(&I.col[e]);
-                const long long dp = __ldg(&I.pq64[e].x), dq = __ldg(&I.qt64[e]);
-                int dp32 = 0, dq32 = 0;
-                if constexpr (PREC == 1) {
-                    dp32 = __ldg(&I.pq32[e].x);
-                    dq32 = __ldg(&I.qt32[e]);
-                }
-                if (i != (int32_t)k)
-                    u[h] = compute_update<PREC, true>(I, i, snew, dp, dq, dp32, dq32, step);
-                else if (e == r1 - 1)
-                    u[h] = compute_update<PREC, true>(I, k, snew, 0, 0, 0, 0, step, snew);
+    for (int h = 0; h < kSlots; ++h) {
+        const int64_t e = e0 + 32 * h;
+        Upd u;
+        u.i = -1;
+        if (e < r1) {
+            const int32_t i = __ldg(&I.col[e]);
+            const long long dp = __ldg(&I.pq64[e].x), dq = __ldg(&I.qt64[e]);
+            int dp32 = 0, dq32 = 0;
+            if constexpr (PREC == 1) {
+                dp32 = __ldg(&I.pq32[e].x);
+                dq32 = __ldg(&I.qt32[e]);
             }
+            if (i != (int32_t)k) u = compute_update<PREC, true>(I, i, snew, dp, dq, dp32, dq32, step);
+        } else if (e == r1) {
+            u = compute_update<PREC, true>(I, k, snew, 0, 0, 0, 0, step, snew);
         }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (u[h].i < 0) continue;
-            const int64_t i = u[h].i;
-            if (i == k) I.s[k] = (int8_t)snew;
-            I.h64[i] = u[h].h;
-            rec_store_dyn(I, i, u[h].g, u[h].lo, u[h].s);
-            I.key64[i] = u[h].x;
-            I.key32[i] = u[h].nk;
-            if (u[h].nk > u[h].old) push_up(S, I.nlev, i, u[h].nk);
-            unsigned long long val = 0ull;
-            if constexpr (PREC == 0) {
-                val = u[h].x > 0.0 ? (unsigned long long)__double_as_longlong(u[h].x) : 0ull;
-            } else {
-                val = u[h].nk ? (unsigned long long)__double_as_longlong((double)key32_hi(u[h].nk))
-                              : 0ull;
-            }
-            if (i != k && val && before(val, (int32_t)i, bv, bi)) {
-                bv = val;
-                bi = (int32_t)i;
-            }
-        }
+        t[h].i = (int32_t)u.i;
+        t[h].h = u.h;
+        t[h].nk = u.nk;
+        t[h].x = u.x;
+        t[h].g = u.g;
+        t[h].lo = u.lo;
+        t[h].s = u.s;
+        t[h].push = u.nk > u.old ? 1 : 0;
     }
-    if (!own_in_row && lane == 0) {  // k itself: its field is unchanged, its spin is not
-        I.s[k] = (int8_t)snew;
-        const Upd u = compute_update<PREC, true>(I, k, snew, 0, 0, 0, 0, step, snew);
-        I.h64[k] = u.h;
-        rec_store_dyn(I, k, u.g, u.lo, u.s);
-        I.key64[k] = u.x;
-        I.key32[k] = u.nk;
-        if (u.nk > u.old) push_up(S, I.nlev, k, u.nk);
+}
+
+// Stores one update (t.i == k: the flipped island itself, whose spin goes too).
+__device__ __forceinline__ void stage_commit(const Inst& I, unsigned long long* const* lp,
+                                             int64_t k, int snew, const Stage& t) {
+    const int64_t i = t.i;
+    if (i == k) I.s[k] = (int8_t)snew;
+    I.h64[i] = t.h;
+    rec_store_dyn(I, i, t.g, t.lo, t.s);
+    I.key64[i] = t.x;
+    I.key32[i] = t.nk;
+    if (t.push) push_up(lp, I.nlev, i, t.nk);
+}
+
+// The best new value among a pick's neighbours, (*bv, *bi) so far: FS_FP64 the
+// exact value, the FP32 path the upper bound of the key.
+template <int PREC>
+__device__ __forceinline__ void stage_best(const Stage& t, int64_t k, unsigned long long* bv,
+                                           int32_t* bi) {
+    if (t.i < 0 || t.i == k) return;
+    unsigned long long val = 0ull;
+    if constexpr (PREC == 0) {
+        val = t.x > 0.0 ? (unsigned long long)__double_as_longlong(t.x) : 0ull;
+    } else {
+        val = t.nk ? (unsigned long long)__double_as_longlong((double)key32_hi(t.nk)) : 0ull;
     }
+    if (val && before(val, t.i, *bv, *bi)) {
+        *bv = val;
+        *bi = t.i;
+    }
+}
+
+__device__ __forceinline__ void warp_best(unsigned long long* bv, int32_t* bi) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int32_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov && before(ov, oi, bv, bi)) {
-            bv = ov;
-            bi = oi;
+        const unsigned long long ov = __shfl_xor_sync(0xffffffffu, *bv, o);
+        const int32_t oi = __shfl_xor_sync(0xffffffffu, *bi, o);
+        if (ov && before(ov, oi, *bv, *bi)) {
+            *bv = ov;
+            *bi = oi;
         }
     }
+}
+
+// Flips island k (row [r0, r1)) to spin snew with every update stored, pass by
+// pass. Warp-wide; returns, on every lane, the best new value among the neighbours
+// and its island.
+template <int PREC>
+__device__ void flip_warp(const Inst& I, unsigned long long* const* lp, int64_t k, int snew,
+                          int64_t r0, int64_t r1, uint32_t step, unsigned long long* xv,
+                          int32_t* xi) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long bv = 0ull;
+    int32_t bi = 0x7fffffff;
+    for (int64_t e0 = r0 + lane; e0 <= r1; e0 += kStageSlots) {
+        Stage t[kSlots];
+        pass_compute<PREC>(I, k, snew, e0, r1, step, t);
+#pragma unroll
+        for (int h = 0; h < kSlots; ++h) {
+            if (t[h].i < 0) continue;
+            stage_commit(I, lp, k, snew, t[h]);
+            stage_best<PREC>(t[h], k, &bv, &bi);
+        }
+    }
+    warp_best(&bv, &bi);
     *xv = bv;
     *xi = bi;
 }
 
+// The flip of island k (row [r0, r1), which with k's own slot fits one pass)
+// computed into the warp's staging slots stg[0 .. kStageSlots), nothing stored;
+// returns the best new neighbour value as flip_warp does. Warp-wide.
+template <int PREC>
+__device__ void compute_pick(const Inst& I, int64_t k, int snew, int64_t r0, int64_t r1,
+                             uint32_t step, Stage* stg, unsigned long long* xv, int32_t* xi) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long bv = 0ull;
+    int32_t bi = 0x7fffffff;
+    Stage t[kSlots];
+    pass_compute<PREC>(I, k, snew, r0 + lane, r1, step, t);
+#pragma unroll
+    for (int h = 0; h < kSlots; ++h) {
+        stg[lane + 32 * h] = t[h];
+        stage_best<PREC>(t[h], k, &bv, &bi);
+    }
+    warp_best(&bv, &bi);
+    *xv = bv;
+    *xi = bi;
+}
+
+// Stores the flip compute_pick staged. Warp-wide.
+__device__ void store_pick(const Inst& I, unsigned long long* const* lp, int64_t k, int snew,
+                           const Stage* stg) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = 0; h < kSlots; ++h) {
+        const Stage t = stg[lane + 32 * h];
+        if (t.i >= 0) stage_commit(I, lp, k, snew, t);
+    }
+}
+
+// The exact FS_FP64 value of candidate island i, with what a round needs of it
+// (spin, row, centre). An island found not flippable gets key 0 (no candidate until
+// a flip raises it again); on the FP32 path a flippable one gets the key of its
+// exact value (an upper bound no higher than the one it had). The FP32 path
+// evaluates the exact sums in FP64 unless its current fields already were
+// (key64 >= 0); the step's thermal draw is the kept one, or drawn and kept (no
+// other thread evaluates island i meanwhile). Every load is issued up front.
+template <int PREC>
+__device__ __forceinline__ Cand eval_cand(const Inst& I, int64_t i, uint32_t step) {
+    const IslandRec r = rec_load(I, i);
+    const double2 pc = __ldg(&I.pos[i]);
+    const double kept = I.key64[i];
+    double v = kept;
+    if constexpr (PREC == 1) {
+        const longlong2 h = I.h64[i];
+        const double2 rb64 = __ldg(&I.rbc64[i]);
+        const bool th = I.sigma > 0.0;
+        uint32_t ts = 0u;
+        double2 tv = make_double2(0.0, 0.0);
+        if (th) {
+            ts = I.th_step[i];
+            tv = I.th64[i];
+        }
+        if (kept < 0.0) {
+            if (th && ts != step) {
+                thermal64(I, i, step, &tv.x, &tv.y);
+                I.th64[i] = tv;
+                __threadfence_block();
+                *(volatile uint32_t*)&I.th_step[i] = step;
+            }
+            const Eval64 e = eval64(I, r.s, h.x, h.y, rb64, ext64_at(I, i, r.cls), tv.x, tv.y);
+            v = e.flippable ? e.lhs : 0.0;
+            I.key64[i] = v;
+        }
+    }
+    if (v > 0.0) {
+        if constexpr (PREC == 1) I.key32[i] = key32_of(__double2float_ru(v), i);
+    } else {
+        I.key32[i] = 0ull;
+    }
+    Cand c;
+    c.v = v > 0.0 ? (unsigned long long)__double_as_longlong(v) : 0ull;
+    c.i = (int32_t)i;
+    c.rowq = r.rowq;
+    c.pos = make_float2(__double2float_rn(pc.x), __double2float_rn(pc.y));
+    c.rowlenq = r.rowlenq;
+    c.s = (int16_t)r.s;
+    c.pad = 0;
+    return c;
+}
+
 // The exact best flippable island of the whole array by a full scan (every key
 // above zero evaluated exactly), for rounds whose candidate set cannot be held;
-// S.ci[0] / S.cv[0] receive it (S.nc = 0 when none). CTA-wide.
+// S.si[0] / S.sv[0] receive it (S.nc = 0 when none). CTA-wide.
 template <int PREC>
 __device__ void scan_best(const Inst& I, uint32_t step, MultiShared& S) {
     const int tid = threadIdx.x;
@@ -437,37 +447,582 @@ __device__ void scan_best(const Inst& I, uint32_t step, MultiShared& S) {
             bi = (int32_t)i;
         }
     }
-    S.cv[tid] = bv;
-    S.ci[tid] = bi;
+    S.sv[tid] = bv;
+    S.si[tid] = bi;
     __syncthreads();
     for (int w = kMT / 2; w > 0; w >>= 1) {
-        if (tid < w && S.cv[tid + w] && before(S.cv[tid + w], S.ci[tid + w], S.cv[tid], S.ci[tid])) {
-            S.cv[tid] = S.cv[tid + w];
-            S.ci[tid] = S.ci[tid + w];
+        if (tid < w && S.sv[tid + w] && before(S.sv[tid + w], S.si[tid + w], S.sv[tid], S.si[tid])) {
+            S.sv[tid] = S.sv[tid + w];
+            S.si[tid] = S.si[tid + w];
         }
         __syncthreads();
     }
-    if (tid == 0) S.nc = S.cv[0] ? 1 : 0;
+    if (tid == 0) S.nc = S.sv[0] ? 1 : 0;
     __syncthreads();
+}
+
+// S.cand[0 .. n) into "before" order in S.sv / S.si / S.so: up to kRankMax entries
+// by rank (each entry counts those that go before it; islands are distinct), more
+// by a bitonic network over the next power of two (padding entries sort last).
+// CTA-wide.
+__device__ void sort_candidates(MultiShared& S, int n) {
+    const int tid = threadIdx.x;
+    if (n <= kRankMax) {
+        if (tid < n) {
+            const unsigned long long v = S.cand[tid].v;
+            const int32_t ix = S.cand[tid].i;
+            int r = 0;
+            int u = 0;
+            for (; u + 8 <= n; u += 8) {  // (eight loads in flight)
+                unsigned long long w[8];
+                int32_t wi[8];
+#pragma unroll
+                for (int z = 0; z < 8; ++z) {
+                    w[z] = S.cand[u + z].v;
+                    wi[z] = S.cand[u + z].i;
+                }
+#pragma unroll
+                for (int z = 0; z < 8; ++z) r += before(w[z], wi[z], v, ix) ? 1 : 0;
+            }
+            for (; u < n; ++u) r += before(S.cand[u].v, S.cand[u].i, v, ix) ? 1 : 0;
+            S.sv[r] = v;
+            S.si[r] = ix;
+            S.so[r] = (int16_t)tid;
+        }
+        __syncthreads();
+        return;
+    }
+    int n2 = 1;
+    while (n2 < n) n2 <<= 1;
+    for (int t = tid; t < n2; t += kMT) {
+        const bool real = t < n;
+        S.sv[t] = real ? S.cand[t].v : 0ull;
+        S.si[t] = real ? S.cand[t].i : 0x7fffffff;
+        S.so[t] = real ? (int16_t)t : (int16_t)-1;
+    }
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = tid; t < n2; t += kMT) {
+                const int o = t ^ j;
+                if (o > t) {
+                    const bool up = (t & k) == 0;
+                    const unsigned long long va = S.sv[t], vb = S.sv[o];
+                    const int32_t ia = S.si[t], ib = S.si[o];
+                    const bool swap = up ? before(vb, ib, va, ia) : before(va, ia, vb, ib);
+                    if (swap) {
+                        S.sv[t] = vb;
+                        S.sv[o] = va;
+                        S.si[t] = ib;
+                        S.si[o] = ia;
+                        const int16_t so = S.so[t];
+                        S.so[t] = S.so[o];
+                        S.so[o] = so;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+constexpr int32_t kCmdPlan = 3;  // (the leader's own step: choose the next threshold)
+
+// The leader's round state (the same in every leader thread; the hash on kHashT).
+struct Lead {
+    int64_t flips, rounds, idle_total, max_flips, flips_before;
+    uint64_t hash;
+    unsigned long long carry;   // a threshold from the previous round's candidates
+    unsigned long long forced;  // a threshold set by the previous iteration
+    int32_t status;
+    int M, m0, idle, low, lsel;
+    bool need_scan, was_carried, was_forced, handoff;
+};
+
+// The leader: the next threshold and the frontier of tree nodes that reach it (on
+// level 1, or level 0 for a one-level selection), or, for a candidate set too large
+// at every threshold, the one best island by a full scan. The threshold is chosen
+// on level lsel, loaded whole (its M-th largest node, unless the previous round
+// carried one or forced one). Returns the cluster's next command. Leader CTA-wide.
+template <int PREC>
+__device__ int32_t plan(const Inst& I, MultiShared& S, Lead& G, uint32_t step) {
+    constexpr int kB = 4;  // frontier nodes whose children a warp loads together
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    for (;;) {
+        if (++G.idle > kMaxIdle) {
+            G.status = ST_BOUNDS;
+            return kCmdStop;
+        }
+        if (G.need_scan) {  // a candidate set too large for any threshold
+            G.need_scan = false;
+            G.M = G.m0;
+            scan_best<PREC>(I, step, S);
+            if (S.nc == 0) return kCmdStop;
+            if (G.max_flips - G.flips <= 0) {
+                G.status = ST_NOT_CONVERGED;
+                return kCmdStop;
+            }
+            if (tid == 0) {
+                const IslandRec r = rec_load(I, S.si[0]);
+                Pick pk;
+                pk.i = S.si[0];
+                pk.rowq = r.rowq;
+                pk.rowlenq = r.rowlenq;
+                pk.s = (int16_t)r.s;
+                pk.eager = 0;
+                S.pk[0] = pk;
+                S.q = 1;
+                S.nz = 1;
+            }
+            __syncthreads();
+            return kCmdCompute;
+        }
+        ++G.idle_total;
+        const int lsel = G.lsel;
+        const int cnt = I.lvl_n[lsel];
+        unsigned long long v[kSelPer];
+#pragma unroll
+        for (int u = 0; u < kSelPer; ++u) {
+            const int c = tid + u * kMT;
+            v[u] = c < cnt ? __ldcg(S.lp[lsel] + c) : 0ull;
+        }
+        unsigned long long tkey = 1ull;
+        G.was_forced = G.forced != 0ull;
+        G.was_carried = !G.was_forced && G.carry != 0ull;
+        if (G.was_forced) {
+            tkey = G.forced;
+            G.forced = 0ull;
+        } else if (G.was_carried) {
+            tkey = G.carry;
+            G.carry = 0ull;
+        } else {
+            const unsigned long long sel = select_threshold(v, cnt, G.M, S);
+            // lowered by 2^-18 (relative) so that the node's own island, whose exact
+            // value lies within its key's band, counts as reaching it
+            const float hi = __uint_as_float((uint32_t)(sel >> 32));
+            const float lo = __fmul_rd(hi, 1.0f - 0x1.0p-18f);
+            tkey = sel ? ((unsigned long long)__float_as_uint(lo) << 32) : 1ull;
+            if (tkey == 0ull) tkey = 1ull;
+        }
+        // the nodes of level lsel that reach it
+        if (tid == 0) S.nf[0] = 0;
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kSelPer; ++u) {
+            const int c = tid + u * kMT;
+            warp_append(c < cnt && v[u] != 0ull && v[u] >= tkey, c, S.front[0], &S.nf[0], kCandCap);
+        }
+        __syncthreads();
+        int cur = 0;
+        bool over = S.nf[0] > kCandCap;
+        // down to level 1, every expanded node rebuilt from its children (a node is
+        // never below its children: pushes raise every ancestor, rebuilds set a node
+        // to its children's maximum; so it is stored without being read first)
+        for (int lev = lsel; lev >= 2 && !over; --lev) {
+            const int nf = S.nf[cur];
+            if (tid == 0) S.nf[cur ^ 1] = 0;
+            __syncthreads();
+            const int64_t lim = I.lvl_n[lev - 1];
+            for (int f0 = wid * kB; f0 < nf; f0 += kMW * kB) {
+                int64_t node[kB];
+                unsigned long long w[kB];
+#pragma unroll
+                for (int u = 0; u < kB; ++u) {
+                    node[u] = f0 + u < nf ? (int64_t)S.front[cur][f0 + u] : -1;
+                    const int64_t c = (node[u] << 5) + lane;
+                    w[u] = node[u] >= 0 && c < lim ? __ldcg(S.lp[lev - 1] + c) : 0ull;
+                }
+#pragma unroll
+                for (int u = 0; u < kB; ++u) {
+                    if (node[u] < 0) break;
+                    const int64_t c = (node[u] << 5) + lane;
+                    const unsigned long long m = warp_max_key(w[u]);
+                    if (lane == 0) S.lp[lev][node[u]] = m;
+                    warp_append(w[u] != 0ull && w[u] >= tkey, (int32_t)c, S.front[cur ^ 1],
+                                &S.nf[cur ^ 1], kCandCap);
+                }
+            }
+            __syncthreads();
+            over = S.nf[cur ^ 1] > kCandCap;
+            cur ^= 1;
+        }
+        if (over) {  // too many nodes reach it: a higher threshold, or a scan
+            if (!G.was_carried) {
+                if (G.M > 1 && !G.was_forced)
+                    G.M >>= 1;
+                else
+                    G.need_scan = true;
+            }
+            continue;
+        }
+        if (S.nf[cur] == 0) {
+            if (tkey == 1ull) return kCmdStop;  // no key above zero: the relax is done
+            G.M = G.m0;  // the threshold came from stale nodes, rebuilt on the way
+            continue;
+        }
+        if (tid == 0) {
+            S.f_lev = lsel >= 1 ? 1 : 0;
+            S.f_buf = cur;
+            S.tkey = tkey;
+            S.nl = 0;
+        }
+        __syncthreads();
+        return kCmdExpand;
+    }
+}
+
+// The leader after an expansion: the candidates in order, the eligible prefix (a),
+// the cut at the first pick too close to an earlier one (b) and the step's flip
+// budget give the picks. Returns the cluster's next command (kCmdPlan when there
+// is nothing to flip at this threshold). Leader CTA-wide.
+__device__ int32_t decide(const Inst& I, MultiShared& S, Lead& G) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nl = S.nl;
+    if (nl > kCandCap) {  // too many candidates: a higher threshold, or a scan
+        if (!G.was_carried) {
+            if (G.M > 1 && !G.was_forced)
+                G.M >>= 1;
+            else
+                G.need_scan = true;
+        }
+        return kCmdPlan;
+    }
+    if (nl == 0) {
+        if (S.tkey == 1ull) return kCmdStop;  // no key above zero
+        G.M = G.m0;  // stale nodes, rebuilt by the expansion
+        return kCmdPlan;
+    }
+    sort_candidates(S, nl);
+    // (a) a pick must beat every island below the threshold: (v, i) no later than
+    // (tau, tau_index) in "before" order; eligibility is a prefix of the order
+    const unsigned long long tkey = S.tkey;
+    const double tau = (double)__uint_as_float((uint32_t)(tkey >> 32));
+    const uint32_t tau_i = key32_idx(tkey);
+    const unsigned long long tb = (unsigned long long)__double_as_longlong(tau);
+    if (tid == 0) {
+        S.eligible = 0;
+        S.nz = 0;
+        S.conflict_at = kPickCap;
+    }
+    __syncthreads();
+    for (int c = tid; c < nl; c += kMT) {
+        const unsigned long long v = S.sv[c];
+        if (c < kPickCap) S.sp[c] = S.cand[S.so[c]].pos;
+        if (v != 0ull) atomicMax(&S.nz, c + 1);  // (flippable ones are a prefix too)
+        const bool ok =
+            c < kPickCap && v != 0ull && (v > tb || (v == tb && (uint32_t)S.si[c] <= tau_i));
+        if (ok) atomicMax(&S.eligible, c + 1);
+    }
+    __syncthreads();
+    int q = S.eligible;
+    if (q == 0) {
+        if (S.sv[0] != 0ull) {
+            // every candidate lies below the threshold: the next iteration takes the
+            // best one's value (rounded down) as the threshold, so that every island
+            // that could beat it is a candidate
+            const float v0 = __double2float_rd(__longlong_as_double((long long)S.sv[0]));
+            const unsigned long long tk = (unsigned long long)__float_as_uint(v0) << 32;
+            G.forced = tk > 0ull ? tk : 1ull;
+        } else {
+            G.M = G.m0;  // none of them is flippable (all demoted)
+        }
+        return kCmdPlan;
+    }
+    // (b) picks more than twice the cutoff apart: pair (c, j), j < c, a warp per row
+    // c, lanes over j; in FP32 against a radius widened by the rounding of the centres
+    for (int c = 1 + wid; c < q; c += kMW) {
+        if (c >= __shfl_sync(0xffffffffu, S.conflict_at, 0)) break;
+        const float2 a = S.sp[c];
+        bool hit = false;
+        for (int j = lane; j < c; j += 32) {
+            const float2 b = S.sp[j];
+            const float dx = __fsub_rn(a.x, b.x);
+            const float dy = __fsub_rn(a.y, b.y);
+            hit = hit || __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) <= I.rconf2f;
+        }
+        if (__any_sync(0xffffffffu, hit)) {
+            if (lane == 0) atomicMin(&S.conflict_at, c);
+            break;
+        }
+    }
+    __syncthreads();
+    q = min(q, S.conflict_at);
+    // the step's flip budget
+    const int64_t allowed = G.max_flips - G.flips;
+    if (allowed <= 0) {
+        G.status = ST_NOT_CONVERGED;
+        return kCmdStop;
+    }
+    if (q > allowed) q = (int)allowed;
+    for (int c = tid; c < q; c += kMT) {
+        const Cand& cd = S.cand[S.so[c]];
+        Pick pk;
+        pk.i = cd.i;
+        pk.rowq = cd.rowq;
+        pk.rowlenq = cd.rowlenq;
+        pk.s = cd.s;
+        pk.eager = 0;
+        S.pk[c] = pk;
+    }
+    if (tid == 0) {
+        S.q = q;
+        S.nc = nl;
+    }
+    __syncthreads();
+    return kCmdCompute;
+}
+
+// The hash thread folds the first n queued flips into the sequence hash, in order.
+__device__ __forceinline__ void hash_queue(const MultiShared& S, Lead& G, uint32_t step, int n) {
+    for (int j = 0; j < n; ++j) G.hash = fnv_flip(G.hash, step, (uint32_t)S.hq[j]);
+}
+
+// The leader after the picks are computed: the longest prefix of the picks that no
+// earlier pick's neighbour overtakes (c); the eager picks after it flipped back (a
+// warp a pick); the prefix logged and queued for the hash in order; the threshold
+// carried to the next round. Returns kCmdStore. Leader CTA-wide.
+template <int PREC>
+__device__ int32_t prefix_step(const Inst& I, MultiShared& S, Lead& G, uint32_t step) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int q = S.q;
+    // warp 0, 32 picks at a time: the best of the earlier picks' neighbour values
+    // (an exclusive prefix maximum), carried between chunks
+    if (wid == 0) {
+        unsigned long long cv_ = 0ull;  // carried maximum
+        int32_t ci_ = 0x7fffffff;
+        int p = q;
+        for (int j0 = 0; j0 < q; j0 += 32) {
+            const int j = j0 + lane;
+            unsigned long long xv = j < q ? S.xv[j] : 0ull;
+            int32_t xi = j < q ? S.xi[j] : 0x7fffffff;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {  // inclusive prefix maximum
+                const unsigned long long ov = __shfl_up_sync(0xffffffffu, xv, o);
+                const int32_t oi = __shfl_up_sync(0xffffffffu, xi, o);
+                if (lane >= o && ov && (!xv || before(ov, oi, xv, xi))) {
+                    xv = ov;
+                    xi = oi;
+                }
+            }
+            unsigned long long ev = __shfl_up_sync(0xffffffffu, xv, 1);
+            int32_t ei = __shfl_up_sync(0xffffffffu, xi, 1);
+            if (lane == 0) {
+                ev = 0ull;
+                ei = 0x7fffffff;
+            }
+            if (cv_ && (!ev || before(cv_, ci_, ev, ei))) {
+                ev = cv_;
+                ei = ci_;
+            }
+            const bool fail = j < q && j > 0 && ev && !before(S.sv[j], S.si[j], ev, ei);
+            const unsigned fm = __ballot_sync(0xffffffffu, fail);
+            if (fm) {
+                p = j0 + __ffs(fm) - 1;
+                break;
+            }
+            const unsigned long long lv = __shfl_sync(0xffffffffu, xv, 31);
+            const int32_t li = __shfl_sync(0xffffffffu, xi, 31);
+            if (lv && (!cv_ || before(lv, li, cv_, ci_))) {
+                cv_ = lv;
+                ci_ = li;
+            }
+        }
+        if (lane == 0) S.p = p;
+    }
+    __syncthreads();
+    const int p = S.p;
+    // the eager ones among the rest flipped back (the staged ones are dropped)
+    for (int j = p + wid; j < q; j += kMW) {
+        const Pick pk = S.pk[j];
+        if (!pk.eager) continue;
+        const int64_t r0 = (int64_t)pk.rowq << 2;
+        unsigned long long xv;
+        int32_t xi;
+        flip_warp<PREC>(I, S.lp, pk.i, pk.s, r0, r0 + ((int64_t)pk.rowlenq << 2), step, &xv, &xi);
+    }
+    // log and hash, in the order of the picks
+    for (int j = tid; j < p; j += kMT) {
+        const int64_t qq = G.flips_before + G.flips + j;
+        if (I.log_spin && qq < I.log_cap) {
+            I.log_step[qq] = step;
+            I.log_spin[qq] = (uint32_t)S.si[j];
+        }
+    }
+    // the flips join the hash queue (folded in by the hash thread during the next
+    // expansion, or here when the queue is full)
+    const int hn = S.hq_n;  // (rewritten below only after a barrier)
+    int h0 = hn;
+    if (hn + p > kHashQ) {
+        if (tid == kHashT) hash_queue(S, G, step, hn);
+        __syncthreads();
+        h0 = 0;
+    }
+    for (int j = tid; j < p; j += kMT) S.hq[h0 + j] = S.si[j];
+    G.flips += p;
+    G.idle = 0;
+    --G.idle_total;
+    ++G.rounds;
+    G.M = G.m0;
+    G.low = p < kPMin ? G.low + 1 : 0;
+    if (G.low >= kLowRounds) G.handoff = true;
+    // the next round's threshold: the value kCarry places below this round's last
+    // flip among its flippable candidates (most of them are still unflipped), so
+    // that the next candidate set is about that large
+    {
+        const int r = min(S.nz - 1, p + kCarry);
+        const unsigned long long vr = r > p ? S.sv[r] : 0ull;
+        G.carry = 0ull;
+        if (vr) {
+            const float f = __fmul_rd(__double2float_rd(__longlong_as_double((long long)vr)),
+                                      1.0f - 0x1.0p-18f);
+            G.carry = (unsigned long long)__float_as_uint(f) << 32;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) S.hq_n = h0 + p;
+    return kCmdStore;
+}
+
+// Every CTA of the cluster: the frontier nodes L->front[L->f_buf] expanded into the
+// keys that reach L->tkey (level-1 nodes first into their level-0 children that
+// reach it), each expanded node rebuilt from its children; the candidate islands
+// this CTA found are then evaluated exactly into the leader's list (L->nl counts
+// them, past kCandCap too). Warps of all CTAs share the nodes.
+template <int PREC, int NC>
+__device__ void expand_eval(const Inst& I, MultiShared* L, MultiShared& S, Lead& G, int rank,
+                            uint32_t step) {
+    constexpr int kB = 8;
+    constexpr int kW = NC * kMW - 1;  // warps that expand (the leader's last one hashes)
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int gw = rank == 0 ? wid : rank * kMW + wid - 1;
+    const bool hasher = rank == 0 && wid == kMW - 1;
+    if (tid == 0) S.nloc = 0;
+    __syncthreads();
+    if (hasher) {  // meanwhile: the queued flips into the hash
+        if (tid == kHashT) {
+            hash_queue(S, G, step, S.hq_n);
+            S.hq_n = 0;
+        }
+    } else {
+        const int f_lev = L->f_lev, buf = L->f_buf;
+        const int nf = L->nf[buf];
+        const unsigned long long tkey = L->tkey;
+        if (f_lev == 0) {
+            for (int fb = gw * kB; fb < nf; fb += kW * kB) {
+                int64_t node[kB];
+                unsigned long long v[kB];
+#pragma unroll
+                for (int u = 0; u < kB; ++u) {
+                    node[u] = fb + u < nf ? (int64_t)L->front[buf][fb + u] : -1;
+                    const int64_t c = (node[u] << 5) + lane;
+                    v[u] = node[u] >= 0 && c < I.n ? __ldcg(&I.key32[c]) : 0ull;
+                }
+#pragma unroll
+                for (int u = 0; u < kB; ++u) {
+                    if (node[u] < 0) break;
+                    const int64_t c = (node[u] << 5) + lane;
+                    const unsigned long long m = warp_max_key(v[u]);
+                    if (lane == 0) S.lp[0][node[u]] = m;
+                    warp_append(v[u] != 0ull && v[u] >= tkey, (int32_t)c, S.loc, &S.nloc,
+                                kCandCap);
+                }
+            }
+        } else {
+            const int64_t n0 = I.lvl_n[0];
+            for (int f = gw; f < nf; f += kW) {
+                const int64_t node1 = L->front[buf][f];
+                const int64_t c1 = (node1 << 5) + lane;
+                const unsigned long long w = c1 < n0 ? __ldcg(S.lp[0] + c1) : 0ull;
+                const unsigned long long m1 = warp_max_key(w);
+                if (lane == 0) S.lp[1][node1] = m1;
+                unsigned hm = __ballot_sync(0xffffffffu, w != 0ull && w >= tkey);
+                while (hm) {  // the children that reach it, kB at a time
+                    int64_t node[kB];
+                    unsigned long long v[kB];
+#pragma unroll
+                    for (int u = 0; u < kB; ++u) {
+                        node[u] = -1;
+                        if (hm) {
+                            node[u] = (node1 << 5) + (__ffs(hm) - 1);
+                            hm &= hm - 1u;
+                        }
+                        const int64_t c = (node[u] << 5) + lane;
+                        v[u] = node[u] >= 0 && c < I.n ? __ldcg(&I.key32[c]) : 0ull;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kB; ++u) {
+                        if (node[u] < 0) break;
+                        const int64_t c = (node[u] << 5) + lane;
+                        const unsigned long long m = warp_max_key(v[u]);
+                        if (lane == 0) S.lp[0][node[u]] = m;
+                        warp_append(v[u] != 0ull && v[u] >= tkey, (int32_t)c, S.loc, &S.nloc,
+                                    kCandCap);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // one block of slots in the leader's list for this CTA's candidates
+    const int nloc = S.nloc;
+    if (tid == 0) S.lbase = nloc ? atomicAdd(&L->nl, nloc) : 0;
+    __syncthreads();
+    const int base = S.lbase;
+    const int lim = min(nloc, kCandCap - base);  // (an overflowing set is dropped by the leader)
+    const int nthr = rank == 0 ? kMT - 32 : kMT;
+    if (!hasher)
+        for (int k = tid; k < lim; k += nthr) L->cand[base + k] = eval_cand<PREC>(I, S.loc[k], step);
+}
+
+// Every CTA of the cluster: the round's picks (their neighbourhoods are disjoint), a
+// warp a pick. A warp's first pick whose row fits one pass is computed into the
+// warp's staging slots, to be stored once the prefix is known (returns true, with
+// the pick's index, island and new spin); any other pick is flipped at once and
+// marked eager. Each pick's best new neighbour value goes to the leader.
+template <int PREC, int NC>
+__device__ bool compute_picks(const Inst& I, MultiShared* L, const MultiShared& S, Stage* stg,
+                              int rank, uint32_t step, int* held_j, int64_t* held_k,
+                              int* held_s) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int q = L->q;
+    bool held = false;
+    for (int j = rank + NC * wid; j < q; j += NC * kMW) {
+        const Pick pk = L->pk[j];
+        const int64_t r0 = (int64_t)pk.rowq << 2, r1 = r0 + ((int64_t)pk.rowlenq << 2);
+        unsigned long long xv;
+        int32_t xi;
+        if (!held && r1 - r0 < kStageSlots) {
+            compute_pick<PREC>(I, pk.i, -pk.s, r0, r1, step, stg, &xv, &xi);
+            held = true;
+            *held_j = j;
+            *held_k = pk.i;
+            *held_s = -pk.s;
+        } else {
+            flip_warp<PREC>(I, S.lp, pk.i, -pk.s, r0, r1, step, &xv, &xi);
+            if (lane == 0) L->pk[j].eager = 1;
+        }
+        if (lane == 0) {
+            L->xv[j] = xv;
+            L->xi[j] = xi;
+        }
+    }
+    return held;
 }
 
 template <int PREC, int NC>
 __global__ void __launch_bounds__(kMT, 1)
-    k_relax_multi(const Inst* __restrict__ tab, const int32_t* __restrict__ work, int n_work,
-                  int smem_levels) {
+    k_relax_multi(const Inst* __restrict__ tab, const int32_t* __restrict__ work, int n_work) {
     namespace cg = cooperative_groups;
-    __shared__ MultiShared S;
-    extern __shared__ unsigned long long sm_levels[];
+    extern __shared__ __align__(16) unsigned char multi_smem[];
+    MultiShared& S = *reinterpret_cast<MultiShared*>(multi_smem);
+    Stage* const stg = reinterpret_cast<Stage*>(multi_smem + kStageOff) +
+                       (threadIdx.x >> 5) * kStageSlots;  // this warp's staging slots
     int rank = 0;
     MultiShared* L = &S;  // the leader's state, as this CTA reaches it
-    unsigned long long* lead_levels = sm_levels;
     if constexpr (NC > 1) {
         cg::cluster_group cl = cg::this_cluster();
         rank = (int)cl.block_rank();
-        if (rank != 0) {
-            L = cl.map_shared_rank(&S, 0);
-            lead_levels = cl.map_shared_rank(sm_levels, 0);
-        }
+        if (rank != 0) L = cl.map_shared_rank(&S, 0);
     }
     auto csync = [&]() {
         if constexpr (NC > 1)
@@ -476,410 +1031,106 @@ __global__ void __launch_bounds__(kMT, 1)
             __syncthreads();
     };
     const bool leader = rank == 0;
-    const Inst& I = tab[work[blockIdx.x / NC]];
+    const int tid = threadIdx.x;
+
+    // this CTA's copy of the descriptor, read from shared memory from here on; with
+    // a global external field, the step's per-class table is copied too
+    {
+        const unsigned long long* src =
+            reinterpret_cast<const unsigned long long*>(&tab[work[blockIdx.x / NC]]);
+        unsigned long long* dst = reinterpret_cast<unsigned long long*>(&S.inst);
+        for (int w = tid; w < (int)(sizeof(Inst) / 8); w += kMT) dst[w] = src[w];
+    }
+    __syncthreads();
+    const Inst& I = S.inst;
     InstState* st = I.st;
     const int64_t t = st->t;
     if (st->status != ST_OK || t >= I.K) return;  // (the same for every CTA)
     const uint32_t step = I.step0 + (uint32_t)t;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-
-    // the upper tree levels that fit smem_levels bytes, from the top down, in the
-    // leader's shared memory (the host sizes the launch by the same rule)
+    const bool cls_sh = I.exti64 == nullptr && I.nclass <= kClsSh;
+    if (cls_sh)
+        for (int c = tid; c < I.nclass; c += kMT) {
+            S.ext64[c] = I.ext64[c];
+            S.ext32[c] = I.ext32[c];
+        }
+    __syncthreads();
     if (tid == 0) {
-        int64_t used = 0;
-        int lsh = I.nlev;
-        for (int lev = I.nlev - 1; lev >= 0; --lev) {
-            const int64_t b = 8 * (int64_t)I.lvl_n[lev];
-            if (used + b > smem_levels) break;
-            used += b;
-            lsh = lev;
+        if (cls_sh) {
+            S.inst.ext64 = S.ext64;
+            S.inst.ext32 = S.ext32;
         }
-        S.lsh = lsh;
-        int64_t off = 0;
-        for (int lev = kMaxLevels - 1; lev >= 0; --lev) {
-            if (lev >= I.nlev) {
-                S.lp[lev] = nullptr;
-            } else if (lev >= lsh) {
-                S.lp[lev] = lead_levels + off;
-                off += I.lvl_n[lev];
-            } else {
-                S.lp[lev] = I.tree + I.lvl_off[lev];
-            }
-        }
+        for (int lev = 0; lev < kMaxLevels; ++lev)
+            S.lp[lev] = lev < I.nlev ? I.tree + I.lvl_off[lev] : nullptr;
+        S.hq_n = 0;
     }
     __syncthreads();
-    if (leader)
-        for (int lev = S.lsh; lev < I.nlev; ++lev)
-            for (int q = tid; q < I.lvl_n[lev]; q += kMT)
-                S.lp[lev][q] = __ldcg(&I.tree[I.lvl_off[lev] + q]);
-    csync();
 
-    int lsel = 0;
-    while (lsel < I.nlev - 1 && I.lvl_n[lsel] > kSelMax) ++lsel;
+    Lead G;
+    G.lsel = 0;
+    while (G.lsel < I.nlev - 1 && I.lvl_n[G.lsel] > kSelMax) ++G.lsel;
+    G.flips = 0;
+    G.rounds = 0;
+    G.idle_total = 0;
+    G.max_flips = I.max_flips;
+    G.flips_before = st->n_flips;
+    G.hash = leader && tid == kHashT ? st->hash : 0ull;
+    G.carry = 0ull;
+    G.forced = 0ull;
+    G.status = ST_OK;
+    G.m0 = max(1, min(kM0, I.lvl_n[G.lsel] / 8));  // rank of the threshold node
+    G.M = G.m0;
+    G.idle = 0;
+    G.low = 0;
+    G.need_scan = G.was_carried = G.was_forced = G.handoff = false;
 
-    // the leader's round state (the same in every leader thread)
-    int64_t flips = 0;
-    int32_t status = ST_OK;
-    uint64_t hash = leader && tid == kHashT ? st->hash : 0ull;
-    const int64_t flips_before = st->n_flips;
-    const int64_t max_flips = I.max_flips;
-    const int m0 = max(1, min(kM0, I.lvl_n[lsel] / 8));  // rank of the threshold node
-    int M = m0;
-    int idle = 0;
-    int64_t rounds = 0, idle_total = 0;
-    int low = 0;
-    bool handoff = false;
-    bool need_scan = false;
-    bool was_carried = false, was_forced = false;
-    unsigned long long carry = 0ull;   // a threshold from the previous round's candidates
-    unsigned long long forced = 0ull;  // a threshold set by the previous iteration
-
+    int32_t cmd = kCmdPlan;  // (the leader's next step)
+    bool held = false;       // this warp holds a staged pick:
+    int held_j = 0, held_s = 0;  // its index and new spin,
+    int64_t held_k = 0;      // its island
     for (;;) {
-        // ---- A (leader): the threshold and the level-0 nodes that reach it --------
         if (leader) {
-            int32_t cmd = kCmdExpand;
-            if (++idle > kMaxIdle) {
-                status = ST_BOUNDS;
-                cmd = kCmdStop;
-            } else if (need_scan) {  // a candidate set too large for any threshold
-                need_scan = false;
-                M = m0;
-                scan_best<PREC>(I, step, S);
-                if (S.nc == 0) {
-                    cmd = kCmdStop;
-                } else {
-                    const int64_t allowed = max_flips - flips;
-                    if (allowed <= 0) {
-                        status = ST_NOT_CONVERGED;
-                        cmd = kCmdStop;
-                    } else {
-                        if (tid == 0) {
-                            S.q = 1;
-                            S.cs[0] = rec_load(I, S.ci[0]).s;
-                        }
-                        cmd = kCmdCommit;
-                    }
-                }
-            } else {
-                ++idle_total;
-                unsigned long long tkey = 1ull;
-                was_forced = forced != 0ull;
-                was_carried = !was_forced && carry != 0ull;
-                if (was_forced) {
-                    tkey = forced;
-                    forced = 0ull;
-                } else if (was_carried) {
-                    tkey = carry;
-                    carry = 0ull;
-                } else {
-                    const unsigned long long sel = select_threshold(I, lsel, M, S);
-                    // lowered by 2^-18 (relative) so that the node's own island, whose
-                    // exact value lies within its key's band, counts as reaching it
-                    const float hi = __uint_as_float((uint32_t)(sel >> 32));
-                    const float lo = __fmul_rd(hi, 1.0f - 0x1.0p-18f);
-                    tkey = sel ? ((unsigned long long)__float_as_uint(lo) << 32) : 1ull;
-                    if (tkey == 0ull) tkey = 1ull;
-                }
-                const int buf = descend_upper(I, tkey, S);
-                if (buf < 0) {  // too many nodes reach it: a higher threshold, or a scan
-                    if (!was_carried) {
-                        if (M > 1 && !was_forced)
-                            M >>= 1;
-                        else
-                            need_scan = true;
-                    }
-                    cmd = kCmdRetry;
-                } else if (S.nf[buf] == 0) {
-                    if (tkey == 1ull) {
-                        cmd = kCmdStop;  // no key above zero: the relax is done
-                    } else {
-                        M = m0;  // the threshold came from stale nodes, repaired on the way
-                        cmd = kCmdRetry;
-                    }
-                } else if (tid == 0) {
-                    S.f0 = buf;
-                    S.tkey = tkey;
-                    S.nl = 0;
-                }
-            }
+            if (cmd == kCmdPlan) cmd = plan<PREC>(I, S, G, step);
             if (tid == 0) S.cmd = cmd;
         }
-        csync();
-        int32_t cmd = L->cmd;
+        csync();  // the leader's command is out
+        cmd = L->cmd;
         if (cmd == kCmdStop) break;
-        if (cmd == kCmdRetry) continue;
         if (cmd == kCmdExpand) {
-            // ---- B (all): the candidate islands ------------------------------------
-            expand_leaves<NC>(I, L, S, rank);
-            csync();
-            const int nl = L->nl;
-            if (nl > kCandCap) {
-                if (leader && !was_carried) {
-                    if (M > 1 && !was_forced)
-                        M >>= 1;
-                    else
-                        need_scan = true;
-                }
-                continue;
-            }
-            if (nl == 0) {
-                if (L->tkey == 1ull) break;  // (cannot happen: its parent reached it)
-                if (leader) M = m0;
-                continue;
-            }
-            // ---- C (all): exact values; islands found not flippable are demoted ----
-            int n2 = 1;
-            while (n2 < nl) n2 <<= 1;
-            for (int c = rank * kMT + tid; c < n2; c += NC * kMT) {
-                if (c < nl) {
-                    const int32_t i = L->ci[c];
-                    const double v = exact_value<PREC>(I, i, step);
-                    if (v > 0.0) {
-                        if constexpr (PREC == 1) I.key32[i] = key32_of(__double2float_ru(v), i);
-                        L->cv[c] = (unsigned long long)__double_as_longlong(v);
-                    } else {
-                        I.key32[i] = 0ull;
-                        L->cv[c] = 0ull;
-                    }
-                } else {
-                    L->cv[c] = 0ull;
-                    L->ci[c] = 0x7fffffff;
-                }
-            }
-            csync();
-            // ---- D (leader): order, threshold test, independence ---------------------
-            if (leader) {
-                if (tid == 0) S.nc = nl;
-                sort_candidates(S, nl, n2);
-                // (a) a pick must beat every island below the threshold: (v, i) no
-                // later than (tau, tau_index) in "before" order
-                const unsigned long long tkey = S.tkey;
-                const double tau = (double)__uint_as_float((uint32_t)(tkey >> 32));
-                const uint32_t tau_i = key32_idx(tkey);
-                const unsigned long long tb = (unsigned long long)__double_as_longlong(tau);
-                if (tid == 0) {
-                    S.eligible = 0;
-                    S.conflict_at = kPickCap;
-                }
-                __syncthreads();
-                for (int c = tid; c < min(nl, kPickCap); c += kMT) {
-                    const unsigned long long v = S.cv[c];
-                    const bool ok = v != 0ull && (v > tb || (v == tb && (uint32_t)S.ci[c] <= tau_i));
-                    if (ok) atomicMax(&S.eligible, c + 1);  // eligibility is a prefix of the order
-                }
-                __syncthreads();
-                int q = S.eligible;
-                int32_t c2 = kCmdCommit;
-                if (q == 0) {
-                    if (S.cv[0] == 0ull) {  // none of them is flippable (all demoted)
-                        M = m0;
-                    } else {
-                        // every candidate lies below the threshold: the next iteration
-                        // takes the best one's value (rounded down) as the threshold, so
-                        // that every island that could beat it is a candidate
-                        const float v0 =
-                            __double2float_rd(__longlong_as_double((long long)S.cv[0]));
-                        const unsigned long long tk = (unsigned long long)__float_as_uint(v0) << 32;
-                        forced = tk > 0ull ? tk : 1ull;
-                    }
-                    c2 = kCmdRetry;
-                } else {
-                    // (b) picks more than twice the cutoff apart
-                    for (int c = tid; c < q; c += kMT) {
-                        const double2 pc = __ldg(&I.pos[S.ci[c]]);
-                        S.cpos[c] = make_float2(__double2float_rn(pc.x), __double2float_rn(pc.y));
-                    }
-                    __syncthreads();
-                    // pair (c, j), j < c: warp per row c, lanes over j; in FP32 against a
-                    // radius widened by the rounding of the centres (I.rconf2f)
-                    for (int c = 1 + wid; c < q; c += kMW) {
-                        if (c >= S.conflict_at) break;
-                        const float2 a = S.cpos[c];
-                        bool hit = false;
-                        for (int j = lane; j < c; j += 32) {
-                            const float dx = __fsub_rn(a.x, S.cpos[j].x);
-                            const float dy = __fsub_rn(a.y, S.cpos[j].y);
-                            hit = hit || __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) <= I.rconf2f;
-                        }
-                        if (__any_sync(0xffffffffu, hit)) {
-                            if (lane == 0) atomicMin(&S.conflict_at, c);
-                            break;
-                        }
-                    }
-                    __syncthreads();
-                    q = min(q, S.conflict_at);
-                    // the step's flip budget
-                    const int64_t allowed = max_flips - flips;
-                    if (allowed <= 0) {
-                        status = ST_NOT_CONVERGED;
-                        c2 = kCmdStop;
-                    } else if (q > allowed) {
-                        q = (int)allowed;
-                    }
-                    for (int c = tid; c < q; c += kMT) S.cs[c] = rec_load(I, S.ci[c]).s;
-                    if (tid == 0) S.q = q;
-                }
-                if (tid == 0) S.cmd = c2;
-            }
-            csync();
-            cmd = L->cmd;
-            if (cmd == kCmdStop) break;
-            if (cmd == kCmdRetry) continue;
+            expand_eval<PREC, NC>(I, L, S, G, rank, step);
+            csync();  // the candidates are in
+            if (leader) cmd = decide(I, S, G);
+        } else if (cmd == kCmdCompute) {
+            held = compute_picks<PREC, NC>(I, L, S, stg, rank, step, &held_j, &held_k, &held_s);
+            csync();  // the picks are computed
+            if (leader) cmd = prefix_step<PREC>(I, S, G, step);
+        } else {  // kCmdStore
+            if (held && held_j < L->p) store_pick(I, S.lp, held_k, held_s, stg);
+            held = false;
+            csync();  // the prefix is stored
+            if (leader) cmd = G.handoff ? kCmdStop : kCmdPlan;
         }
-        // ---- E (all): flip the picks together (disjoint neighbourhoods) --------------
-        {
-            const int q = L->q;
-            for (int j = rank + NC * wid; j < q; j += NC * kMW) {
-                unsigned long long xv;
-                int32_t xi;
-                flip_warp<PREC>(I, S, L->ci[j], -L->cs[j], step, &xv, &xi);
-                if (lane == 0) {
-                    L->xv[j] = xv;
-                    L->xi[j] = xi;
-                }
-            }
-        }
-        csync();
-        // ---- F (leader): the longest prefix no earlier pick's neighbour overtakes ----
-        if (leader) {
-            const int q = S.q;
-            // warp 0, 32 picks at a time: the best of the earlier picks' neighbour
-            // values (an exclusive prefix maximum), carried between chunks
-            if (wid == 0) {
-                unsigned long long cv_ = 0ull;  // carried maximum
-                int32_t ci_ = 0x7fffffff;
-                int p = q;
-                for (int j0 = 0; j0 < q; j0 += 32) {
-                    const int j = j0 + lane;
-                    unsigned long long xv = j < q ? S.xv[j] : 0ull;
-                    int32_t xi = j < q ? S.xi[j] : 0x7fffffff;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {  // inclusive prefix maximum
-                        const unsigned long long ov = __shfl_up_sync(0xffffffffu, xv, o);
-                        const int32_t oi = __shfl_up_sync(0xffffffffu, xi, o);
-                        if (lane >= o && ov && (!xv || before(ov, oi, xv, xi))) {
-                            xv = ov;
-                            xi = oi;
-                        }
-                    }
-                    unsigned long long ev = __shfl_up_sync(0xffffffffu, xv, 1);
-                    int32_t ei = __shfl_up_sync(0xffffffffu, xi, 1);
-                    if (lane == 0) {
-                        ev = 0ull;
-                        ei = 0x7fffffff;
-                    }
-                    if (cv_ && (!ev || before(cv_, ci_, ev, ei))) {
-                        ev = cv_;
-                        ei = ci_;
-                    }
-                    const bool fail = j < q && j > 0 && ev && !before(S.cv[j], S.ci[j], ev, ei);
-                    const unsigned fm = __ballot_sync(0xffffffffu, fail);
-                    if (fm) {
-                        p = j0 + __ffs(fm) - 1;
-                        break;
-                    }
-                    const unsigned long long lv = __shfl_sync(0xffffffffu, xv, 31);
-                    const int32_t li = __shfl_sync(0xffffffffu, xi, 31);
-                    if (lv && (!cv_ || before(lv, li, cv_, ci_))) {
-                        cv_ = lv;
-                        ci_ = li;
-                    }
-                }
-                if (lane == 0) S.p = p;
-            }
-            __syncthreads();
-            const int p = S.p;
-            // log and hash, in the order of the picks
-            for (int j = tid; j < p; j += kMT) {
-                const int64_t qq = flips_before + flips + j;
-                if (I.log_spin && qq < I.log_cap) {
-                    I.log_step[qq] = step;
-                    I.log_spin[qq] = (uint32_t)S.ci[j];
-                }
-            }
-            if (tid == kHashT)
-                for (int j = 0; j < p; ++j) hash = fnv_flip(hash, step, (uint32_t)S.ci[j]);
-            flips += p;
-            idle = 0;
-            --idle_total;
-            ++rounds;
-            M = m0;
-            low = p < kPMin ? low + 1 : 0;
-            if (low >= kLowRounds) handoff = true;
-            // the next round's threshold: the value kCarry places below this round's
-            // last flip among its candidates (most of them are still unflipped), so
-            // that the next candidate set is about that large
-            {
-                const int nc = S.nc;
-                const int r = min(nc - 1, p + kCarry);
-                const unsigned long long vr = r > p ? S.cv[r] : 0ull;
-                if (vr) {
-                    const float f = __fmul_rd(__double2float_rd(__longlong_as_double((long long)vr)),
-                                              1.0f - 0x1.0p-18f);
-                    carry = (unsigned long long)__float_as_uint(f) << 32;
-                }
-            }
-            if (tid == 0) S.stop = handoff ? 1 : 0;
-        }
-        csync();
-        // ---- G (all): flip the rest back ---------------------------------------------
-        {
-            const int q = L->q, p = L->p;
-            for (int j = p + rank + NC * wid; j < q; j += NC * kMW) {
-                unsigned long long xv;
-                int32_t xi;
-                flip_warp<PREC>(I, S, L->ci[j], L->cs[j], step, &xv, &xi);
-            }
-        }
-        csync();
-        if (L->stop) break;
     }
     csync();  // (no CTA leaves while another may still reach the leader's memory)
     if (!leader) return;
-    if (tid == kHashT) st->hash = hash;
-    if (handoff && status == ST_OK) {
-        // the single-flip relax reads the whole tree from global memory: the levels
-        // kept here (raised by this launch's pushes) go back there
-        for (int lev = S.lsh; lev < I.nlev; ++lev)
-            for (int q = tid; q < I.lvl_n[lev]; q += kMT) I.tree[I.lvl_off[lev] + q] = S.lp[lev][q];
+    if (tid == kHashT) {
+        hash_queue(S, G, step, S.hq_n);
+        st->hash = G.hash;
     }
-    __syncthreads();
     if (tid == 0) {
-        st->rounds += rounds;
-        st->idle += idle_total;
-        st->n_flips = flips_before + flips;
-        if (status != ST_OK) st->status = status;
-        if (handoff && status == ST_OK) {  // the single-flip relax finishes step t
+        st->rounds += G.rounds;
+        st->idle += G.idle_total;
+        st->n_flips = G.flips_before + G.flips;
+        if (G.status != ST_OK) st->status = G.status;
+        if (G.handoff && G.status == ST_OK) {  // the single-flip relax finishes step t
             st->handoff = 1;
-            st->step_flips = flips;
+            st->step_flips = G.flips;
         } else {
-            if (I.flips_per_step) I.flips_per_step[t] = flips;
+            if (I.flips_per_step) I.flips_per_step[t] = G.flips;
             st->init = 0;
             st->t = t + 1;
         }
     }
 }
-
-}  // namespace
-
-// Dynamic shared memory of a multi-flip relax CTA: the tree levels above the keys
-// that fit 128 KiB, counted from the top down (the kernel places them the same way).
-int relax_multi_smem(int64_t n) {
-    const int64_t cap = 128 * 1024;
-    std::vector<int64_t> lv;
-    for (int64_t cnt = (n + 31) / 32;; cnt = (cnt + 31) / 32) {
-        lv.push_back(cnt);
-        if (cnt == 1) break;
-    }
-    int64_t used = 0;
-    for (size_t q = lv.size(); q-- > 0;) {
-        if (used + 8 * lv[q] > cap) break;
-        used += 8 * lv[q];
-    }
-    return (int)used;
-}
-
-namespace {
 
 constexpr int kNC = 8;  // CTAs of a multi-flip relax cluster
 
@@ -897,7 +1148,7 @@ cudaError_t launch_multi(const RelaxLaunch& L, int smem, cudaStream_t st) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_relax_multi<PREC, NC>, L.tab, L.work, L.n_work, smem);
+    return cudaLaunchKernelEx(&cfg, k_relax_multi<PREC, NC>, L.tab, L.work, L.n_work);
 }
 
 template <int PREC, int NC>
@@ -933,27 +1184,25 @@ bool cluster_fits(int smem) {
 
 cudaError_t launch_relax_multi(const RelaxLaunch& L, cudaStream_t st) {
     if (L.n_work == 0) return cudaSuccess;
-    // per precision: the dynamic shared memory set so far, and whether the cluster
-    // of that size fits (checked once per size, before any launch is captured)
-    static std::atomic<int> set_bytes[2] = {{-1}, {-1}};
+    // per precision: whether the attributes are set, and whether a cluster fits
+    // (checked once, before any launch is captured)
+    static std::atomic<int> ready[2] = {{0}, {0}};
     static std::atomic<int> use_cluster[2] = {{0}, {0}};
     static std::mutex mu;
     const int k = L.prec == 1 ? 1 : 0;
-    const int smem = L.smem_multi;
-    if (set_bytes[k].load() < smem) {
+    const int smem = kStageOff + kMW * kStageSlots * (int)sizeof(Stage);
+    if (!ready[k].load()) {
         std::lock_guard<std::mutex> g(mu);
-        if (set_bytes[k].load() < smem) {
+        if (!ready[k].load()) {
             cudaError_t e = k ? set_multi_smem<1, 1>(smem) : set_multi_smem<0, 1>(smem);
             if (e == cudaSuccess) e = k ? set_multi_smem<1, kNC>(smem) : set_multi_smem<0, kNC>(smem);
             if (e != cudaSuccess) return e;
-            use_cluster[k].store((k ? cluster_fits<1>(0) : cluster_fits<0>(0)) ? 1 : 0);
-            set_bytes[k].store(smem);
+            use_cluster[k].store((k ? cluster_fits<1>(smem) : cluster_fits<0>(smem)) ? 1 : 0);
+            ready[k].store(1);
         }
     }
-    // A cluster keeps the whole tree in global memory (every CTA pushes keys into
-    // it); the one-CTA launch keeps the upper levels in its shared memory.
     if (use_cluster[k].load())
-        return k ? launch_multi<1, kNC>(L, 0, st) : launch_multi<0, kNC>(L, 0, st);
+        return k ? launch_multi<1, kNC>(L, smem, st) : launch_multi<0, kNC>(L, smem, st);
     return k ? launch_multi<1, 1>(L, smem, st) : launch_multi<0, 1>(L, smem, st);
 }
 
