@@ -113,7 +113,7 @@ struct MultiShared {
     int32_t nf[2];
     int32_t nloc, lbase;              // this CTA's candidates; their first slot
     int32_t nl;                       // candidate islands found (leader; past kCandCap too)
-    int32_t nc, nz, q, p, conflict_at, eligible;
+    int32_t nc, nz, q, p, conflict_at;
     unsigned long long sel;
     int32_t sel_rem;
     // the leader's decisions for the whole cluster
@@ -241,13 +241,14 @@ constexpr int kStageSlots = 32 * kSlots;  // a warp's staging slots (one pass)
 
 // One pass over the slots e0, e0 + 32, ... (e0 = first + lane) of the flip of
 // island k (row [.., r1)) to spin snew: each neighbour's exact sums change by
-// 2 snew times their coefficients and its key is evaluated again; k's own update
-// (its field unchanged, its spin flipped) takes the slot r1, just past the row; the
-// row's padding (self-entries of zero weight) is skipped. Every load of the pass
-// is in flight before any result is used; nothing is stored.
+// 2 snew times their coefficients and its key is evaluated again; with `own`, k's
+// own update (its field unchanged, its spin snew) takes the slot r1, just past the
+// row; the row's padding (self-entries of zero weight) is skipped. Every load of
+// the pass is in flight before any result is used; nothing is stored.
 template <int PREC>
 __device__ __forceinline__ void pass_compute(const Inst& I, int64_t k, int snew, int64_t e0,
-                                             int64_t r1, uint32_t step, Stage (&t)[kSlots]) {
+                                             int64_t r1, bool own, uint32_t step,
+                                             Stage (&t)[kSlots]) {
 #pragma unroll
     for (int h = 0; h < kSlots; ++h) {
         const int64_t e = e0 + 32 * h;
@@ -262,7 +263,7 @@ __device__ __forceinline__ void pass_compute(const Inst& I, int64_t k, int snew,
                 dq32 = __ldg(&I.qt32[e]);
             }
             if (i != (int32_t)k) u = compute_update<PREC, true>(I, i, snew, dp, dq, dp32, dq32, step);
-        } else if (e == r1) {
+        } else if (own && e == r1) {
             u = compute_update<PREC, true>(I, k, snew, 0, 0, 0, 0, step, snew);
         }
         t[h].i = (int32_t)u.i;
@@ -286,6 +287,18 @@ __device__ __forceinline__ void stage_commit(const Inst& I, unsigned long long* 
     I.key64[i] = t.x;
     I.key32[i] = t.nk;
     if (t.push) push_up(lp, I.nlev, i, t.nk);
+}
+
+// The own update of a pick flipped forward: island k keeps its field and its spin
+// now points along h_par, so by Eq. 6 it is not flippable (its evaluation always
+// gives key 0, exact value 0 and no lower bound); the 32-bit sums in its record
+// stay as they are, so only the record's lower bound and spin are written.
+__device__ __forceinline__ void own_flipped(const Inst& I, int64_t k, int snew) {
+    I.s[k] = (int8_t)snew;
+    *reinterpret_cast<int2*>(reinterpret_cast<int*>(I.rec + k) + 2) =
+        make_int2(__float_as_int(-1.0f), snew);
+    I.key64[k] = 0.0;
+    I.key32[k] = 0ull;
 }
 
 // The best new value among a pick's neighbours, (*bv, *bi) so far: FS_FP64 the
@@ -319,18 +332,21 @@ __device__ __forceinline__ void warp_best(unsigned long long* bv, int32_t* bi) {
 }
 
 // Flips island k (row [r0, r1)) to spin snew with every update stored, pass by
-// pass. Warp-wide; returns, on every lane, the best new value among the neighbours
-// and its island.
+// pass; `forward`: a flip of the round (k's own update is own_flipped), else a flip
+// back (k's own update evaluated like a neighbour's). Warp-wide; returns, on every
+// lane, the best new value among the neighbours and its island.
 template <int PREC>
 __device__ void flip_warp(const Inst& I, unsigned long long* const* lp, int64_t k, int snew,
-                          int64_t r0, int64_t r1, uint32_t step, unsigned long long* xv,
-                          int32_t* xi) {
+                          int64_t r0, int64_t r1, bool forward, uint32_t step,
+                          unsigned long long* xv, int32_t* xi) {
     const int lane = threadIdx.x & 31;
     unsigned long long bv = 0ull;
     int32_t bi = 0x7fffffff;
-    for (int64_t e0 = r0 + lane; e0 <= r1; e0 += kStageSlots) {
+    if (forward && lane == 0) own_flipped(I, k, snew);
+    const int64_t last = forward ? r1 - 1 : r1;  // the last slot
+    for (int64_t e0 = r0 + lane; e0 <= last; e0 += kStageSlots) {
         Stage t[kSlots];
-        pass_compute<PREC>(I, k, snew, e0, r1, step, t);
+        pass_compute<PREC>(I, k, snew, e0, r1, !forward, step, t);
 #pragma unroll
         for (int h = 0; h < kSlots; ++h) {
             if (t[h].i < 0) continue;
@@ -343,9 +359,9 @@ __device__ void flip_warp(const Inst& I, unsigned long long* const* lp, int64_t 
     *xi = bi;
 }
 
-// The flip of island k (row [r0, r1), which with k's own slot fits one pass)
-// computed into the warp's staging slots stg[0 .. kStageSlots), nothing stored;
-// returns the best new neighbour value as flip_warp does. Warp-wide.
+// The forward flip of island k (row [r0, r1) of at most kStageSlots entries): the
+// neighbours' updates computed into the warp's staging slots stg[0 .. kStageSlots),
+// nothing stored; returns the best new neighbour value as flip_warp does. Warp-wide.
 template <int PREC>
 __device__ void compute_pick(const Inst& I, int64_t k, int snew, int64_t r0, int64_t r1,
                              uint32_t step, Stage* stg, unsigned long long* xv, int32_t* xi) {
@@ -353,7 +369,7 @@ __device__ void compute_pick(const Inst& I, int64_t k, int snew, int64_t r0, int
     unsigned long long bv = 0ull;
     int32_t bi = 0x7fffffff;
     Stage t[kSlots];
-    pass_compute<PREC>(I, k, snew, r0 + lane, r1, step, t);
+    pass_compute<PREC>(I, k, snew, r0 + lane, r1, false, step, t);
 #pragma unroll
     for (int h = 0; h < kSlots; ++h) {
         stg[lane + 32 * h] = t[h];
@@ -364,10 +380,11 @@ __device__ void compute_pick(const Inst& I, int64_t k, int snew, int64_t r0, int
     *xi = bi;
 }
 
-// Stores the flip compute_pick staged. Warp-wide.
+// Stores the flip compute_pick staged, and k's own update. Warp-wide.
 __device__ void store_pick(const Inst& I, unsigned long long* const* lp, int64_t k, int snew,
                            const Stage* stg) {
     const int lane = threadIdx.x & 31;
+    if (lane == 0) own_flipped(I, k, snew);
 #pragma unroll
     for (int h = 0; h < kSlots; ++h) {
         const Stage t = stg[lane + 32 * h];
@@ -699,22 +716,20 @@ __device__ int32_t decide(const Inst& I, MultiShared& S, Lead& G) {
     const double tau = (double)__uint_as_float((uint32_t)(tkey >> 32));
     const uint32_t tau_i = key32_idx(tkey);
     const unsigned long long tb = (unsigned long long)__double_as_longlong(tau);
-    if (tid == 0) {
-        S.eligible = 0;
-        S.nz = 0;
-        S.conflict_at = kPickCap;
-    }
-    __syncthreads();
-    for (int c = tid; c < nl; c += kMT) {
-        const unsigned long long v = S.sv[c];
-        if (c < kPickCap) S.sp[c] = S.cand[S.so[c]].pos;
-        if (v != 0ull) atomicMax(&S.nz, c + 1);  // (flippable ones are a prefix too)
+    if (tid == 0) S.conflict_at = kPickCap;
+    // flippable candidates and eligible ones are prefixes of the order: their counts
+    // are their lengths
+    int nz = 0, q = 0;
+    for (int c0 = 0; c0 < nl; c0 += kMT) {  // (uniform: nl <= kCandCap)
+        const int c = c0 + tid;
+        const unsigned long long v = c < nl ? S.sv[c] : 0ull;
+        if (c < kPickCap && c < nl) S.sp[c] = S.cand[S.so[c]].pos;
         const bool ok =
             c < kPickCap && v != 0ull && (v > tb || (v == tb && (uint32_t)S.si[c] <= tau_i));
-        if (ok) atomicMax(&S.eligible, c + 1);
+        nz += __syncthreads_count(v != 0ull);
+        q += __syncthreads_count(ok);
     }
-    __syncthreads();
-    int q = S.eligible;
+    if (tid == 0) S.nz = nz;
     if (q == 0) {
         if (S.sv[0] != 0ull) {
             // every candidate lies below the threshold: the next iteration takes the
@@ -838,7 +853,8 @@ __device__ int32_t prefix_step(const Inst& I, MultiShared& S, Lead& G, uint32_t 
         const int64_t r0 = (int64_t)pk.rowq << 2;
         unsigned long long xv;
         int32_t xi;
-        flip_warp<PREC>(I, S.lp, pk.i, pk.s, r0, r0 + ((int64_t)pk.rowlenq << 2), step, &xv, &xi);
+        flip_warp<PREC>(I, S.lp, pk.i, pk.s, r0, r0 + ((int64_t)pk.rowlenq << 2), false, step, &xv,
+                        &xi);
     }
     // log and hash, in the order of the picks
     for (int j = tid; j < p; j += kMT) {
@@ -848,8 +864,8 @@ __device__ int32_t prefix_step(const Inst& I, MultiShared& S, Lead& G, uint32_t 
             I.log_spin[qq] = (uint32_t)S.si[j];
         }
     }
-    // the flips join the hash queue (folded in by the hash thread during the next
-    // expansion, or here when the queue is full)
+    // the flips join the hash queue (folded in by the hash thread while the next
+    // picks are computed, or here when the queue is full)
     const int hn = S.hq_n;  // (rewritten below only after a barrier)
     int h0 = hn;
     if (hn + p > kHashQ) {
@@ -889,21 +905,15 @@ __device__ int32_t prefix_step(const Inst& I, MultiShared& S, Lead& G, uint32_t 
 // this CTA found are then evaluated exactly into the leader's list (L->nl counts
 // them, past kCandCap too). Warps of all CTAs share the nodes.
 template <int PREC, int NC>
-__device__ void expand_eval(const Inst& I, MultiShared* L, MultiShared& S, Lead& G, int rank,
+__device__ void expand_eval(const Inst& I, MultiShared* L, MultiShared& S, int rank,
                             uint32_t step) {
     constexpr int kB = 8;
-    constexpr int kW = NC * kMW - 1;  // warps that expand (the leader's last one hashes)
+    constexpr int kW = NC * kMW;  // warps that expand
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int gw = rank == 0 ? wid : rank * kMW + wid - 1;
-    const bool hasher = rank == 0 && wid == kMW - 1;
+    const int gw = rank * kMW + wid;
     if (tid == 0) S.nloc = 0;
     __syncthreads();
-    if (hasher) {  // meanwhile: the queued flips into the hash
-        if (tid == kHashT) {
-            hash_queue(S, G, step, S.hq_n);
-            S.hq_n = 0;
-        }
-    } else {
+    {
         const int f_lev = L->f_lev, buf = L->f_buf;
         const int nf = L->nf[buf];
         const unsigned long long tkey = L->tkey;
@@ -969,9 +979,7 @@ __device__ void expand_eval(const Inst& I, MultiShared* L, MultiShared& S, Lead&
     __syncthreads();
     const int base = S.lbase;
     const int lim = min(nloc, kCandCap - base);  // (an overflowing set is dropped by the leader)
-    const int nthr = rank == 0 ? kMT - 32 : kMT;
-    if (!hasher)
-        for (int k = tid; k < lim; k += nthr) L->cand[base + k] = eval_cand<PREC>(I, S.loc[k], step);
+    for (int k = tid; k < lim; k += kMT) L->cand[base + k] = eval_cand<PREC>(I, S.loc[k], step);
 }
 
 // Every CTA of the cluster: the round's picks (their neighbourhoods are disjoint), a
@@ -980,7 +988,7 @@ __device__ void expand_eval(const Inst& I, MultiShared* L, MultiShared& S, Lead&
 // the pick's index, island and new spin); any other pick is flipped at once and
 // marked eager. Each pick's best new neighbour value goes to the leader.
 template <int PREC, int NC>
-__device__ bool compute_picks(const Inst& I, MultiShared* L, const MultiShared& S, Stage* stg,
+__device__ bool compute_picks(const Inst& I, MultiShared* L, MultiShared& S, Lead& G, Stage* stg,
                               int rank, uint32_t step, int* held_j, int64_t* held_k,
                               int* held_s) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -991,20 +999,26 @@ __device__ bool compute_picks(const Inst& I, MultiShared* L, const MultiShared& 
         const int64_t r0 = (int64_t)pk.rowq << 2, r1 = r0 + ((int64_t)pk.rowlenq << 2);
         unsigned long long xv;
         int32_t xi;
-        if (!held && r1 - r0 < kStageSlots) {
+        if (!held && r1 - r0 <= kStageSlots) {
             compute_pick<PREC>(I, pk.i, -pk.s, r0, r1, step, stg, &xv, &xi);
             held = true;
             *held_j = j;
             *held_k = pk.i;
             *held_s = -pk.s;
         } else {
-            flip_warp<PREC>(I, S.lp, pk.i, -pk.s, r0, r1, step, &xv, &xi);
+            flip_warp<PREC>(I, S.lp, pk.i, -pk.s, r0, r1, true, step, &xv, &xi);
             if (lane == 0) L->pk[j].eager = 1;
         }
         if (lane == 0) {
             L->xv[j] = xv;
             L->xi[j] = xi;
         }
+    }
+    // the leader's hash thread (its warp has no pick for q <= 120): the queued flips
+    // of the earlier rounds into the hash
+    if (rank == 0 && threadIdx.x == kHashT) {
+        hash_queue(S, G, step, S.hq_n);
+        S.hq_n = 0;
     }
     return held;
 }
@@ -1096,11 +1110,11 @@ __global__ void __launch_bounds__(kMT, 1)
         cmd = L->cmd;
         if (cmd == kCmdStop) break;
         if (cmd == kCmdExpand) {
-            expand_eval<PREC, NC>(I, L, S, G, rank, step);
+            expand_eval<PREC, NC>(I, L, S, rank, step);
             csync();  // the candidates are in
             if (leader) cmd = decide(I, S, G);
         } else if (cmd == kCmdCompute) {
-            held = compute_picks<PREC, NC>(I, L, S, stg, rank, step, &held_j, &held_k, &held_s);
+            held = compute_picks<PREC, NC>(I, L, S, G, stg, rank, step, &held_j, &held_k, &held_s);
             csync();  // the picks are computed
             if (leader) cmd = prefix_step<PREC>(I, S, G, step);
         } else {  // kCmdStore
