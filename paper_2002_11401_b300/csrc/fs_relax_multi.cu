@@ -57,7 +57,7 @@ namespace {
 constexpr int kMT = 512;          // threads of a multi-flip relax CTA
 constexpr int kMW = kMT / 32;
 constexpr int kCandCap = 1024;    // candidate islands per round
-constexpr int kPickCap = 256;     // picks tested per round
+constexpr int kPickCap = 128;     // picks tested per round (one a warp of a cluster of 8)
 constexpr int kSelMax = 8192;     // thresholds are chosen on the lowest level with at most this many nodes
 constexpr int kSelPer = kSelMax / kMT;
 constexpr int kM0 = 256;          // rank of the threshold node
@@ -114,8 +114,8 @@ struct MultiShared {
     int32_t nloc, lbase;              // this CTA's candidates; their first slot
     int32_t nl;                       // candidate islands found (leader; past kCandCap too)
     int32_t nc, nz, q, p, conflict_at;
-    unsigned long long sel;
-    int32_t sel_rem;
+    int32_t sel_n, sel_d, sel_r;      // threshold selection: values, digit, rank left
+    unsigned dmin[4], dmax[4];        //   digit range of each pass
     // the leader's decisions for the whole cluster
     unsigned long long tkey;          // this round's threshold
     int32_t cmd;                      // what the cluster does next (kCmd*)
@@ -149,65 +149,98 @@ __device__ __forceinline__ void warp_append(bool hit, int32_t c, int32_t* list, 
     if (hit && pos < cap) list[pos] = c;
 }
 
-// The M-th largest of the values v[u] (node tid + u kMT, cnt nodes; all of them,
-// stale ones too), by a radix selection over the 64-bit values, eight bits a pass.
+// The upper half (the FP32 bound) of the M-th largest nonzero value v[u] (node
+// tid + u kMT, cnt nodes; stale ones too), by a radix selection over those 32 bits,
+// eight a pass; a pass in which every value still in the running has the same digit
+// takes that digit without a histogram. Returns 0 when no value is nonzero.
 // CTA-wide.
-__device__ unsigned long long select_threshold(const unsigned long long (&v)[kSelPer], int cnt,
-                                               int M, MultiShared& S) {
+__device__ uint32_t select_threshold(const unsigned long long (&v)[kSelPer], int cnt, int M,
+                                     MultiShared& S) {
     const int tid = threadIdx.x, lane = tid & 31;
-    if (M > cnt) M = cnt;
-    if (tid == 0) {
-        S.sel = 0ull;
-        S.sel_rem = M;
+    uint32_t h[kSelPer];
+    int nn = 0;
+#pragma unroll
+    for (int u = 0; u < kSelPer; ++u) {
+        h[u] = tid + u * kMT < cnt ? (uint32_t)(v[u] >> 32) : 0u;
+        nn += h[u] != 0u ? 1 : 0;
     }
-    unsigned long long mask = 0ull;
-    for (int pass = 0; pass < 8; ++pass) {
-        const int shift = 56 - 8 * pass;
-        for (int b = tid; b < 256; b += kMT) S.hist[b] = 0;
-        __syncthreads();
-        const unsigned long long pre = S.sel;
+    if (tid == 0) {
+        S.sel_n = 0;
+        for (int q = 0; q < 4; ++q) {
+            S.dmin[q] = 255u;
+            S.dmax[q] = 0u;
+        }
+    }
+    __syncthreads();
+    nn = __reduce_add_sync(0xffffffffu, nn);
+    if (lane == 0 && nn) atomicAdd(&S.sel_n, nn);
+    __syncthreads();
+    const int total = S.sel_n;
+    if (total == 0) return 0u;
+    int rem = min(M, total);  // the rank still to find among the values in the running
+    uint32_t pre = 0u, mask = 0u;
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 24 - 8 * pass;
+        unsigned dmin = 255u, dmax = 0u;
 #pragma unroll
         for (int u = 0; u < kSelPer; ++u)
-            if (tid + u * kMT < cnt && (v[u] & mask) == pre)
-                atomicAdd(&S.hist[(int)((v[u] >> shift) & 255ull)], 1);
+            if (h[u] != 0u && (h[u] & mask) == pre) {
+                const unsigned d = (h[u] >> shift) & 255u;
+                dmin = min(dmin, d);
+                dmax = max(dmax, d);
+            }
+        dmin = __reduce_min_sync(0xffffffffu, dmin);
+        dmax = __reduce_max_sync(0xffffffffu, dmax);
+        if (lane == 0) {
+            atomicMin(&S.dmin[pass], dmin);
+            atomicMax(&S.dmax[pass], dmax);
+        }
+        for (int q = tid; q < 256; q += kMT) S.hist[q] = 0;
         __syncthreads();
-        if (tid < 32) {
-            // lane l holds digits 255 - 8l .. 248 - 8l (descending)
-            int h[8], sum = 0;
+        const unsigned gmin = S.dmin[pass], gmax = S.dmax[pass];
+        if (gmin == gmax) {
+            pre |= gmin << shift;
+        } else {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                h[u] = S.hist[255 - 8 * lane - u];
-                sum += h[u];
-            }
-            int incl = sum;  // inclusive prefix over lanes (from the top digit down)
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            const int excl = incl - sum;
-            const int rem = S.sel_rem;
-            const bool here = excl < rem && rem <= incl;
-            const unsigned who = __ballot_sync(0xffffffffu, here);
-            if (here) {
-                int acc = excl, d = 0;
+            for (int u = 0; u < kSelPer; ++u)
+                if (h[u] != 0u && (h[u] & mask) == pre) atomicAdd(&S.hist[(h[u] >> shift) & 255u], 1);
+            __syncthreads();
+            if (tid < 32) {
+                // lane l holds digits 255 - 8l .. 248 - 8l (descending)
+                int hh[8], sum = 0;
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    if (acc + h[u] >= rem) {
-                        d = 255 - 8 * lane - u;
-                        break;
-                    }
-                    acc += h[u];
+                    hh[u] = S.hist[255 - 8 * lane - u];
+                    sum += hh[u];
                 }
-                S.sel = pre | ((unsigned long long)d << shift);
-                S.sel_rem = rem - acc;
+                int incl = sum;  // inclusive prefix over lanes (from the top digit down)
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int excl = incl - sum;
+                if (excl < rem && rem <= incl) {  // (one lane: rem <= the values in the running)
+                    int acc = excl, d = 0;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        if (acc + hh[u] >= rem) {
+                            d = 255 - 8 * lane - u;
+                            break;
+                        }
+                        acc += hh[u];
+                    }
+                    S.sel_d = d;
+                    S.sel_r = rem - acc;
+                }
             }
-            if (who == 0u && lane == 0) S.sel_rem = 0;  // (fewer values than M: keep the prefix)
+            __syncthreads();
+            pre |= (uint32_t)S.sel_d << shift;
+            rem = S.sel_r;
         }
-        mask |= 255ull << shift;
-        __syncthreads();
+        mask |= 255u << shift;
     }
-    return S.sel;
+    return pre;
 }
 
 // A key that grew is pushed up with atomic maxima (reductions that do not wait for
@@ -613,21 +646,37 @@ __device__ int32_t plan(const Inst& I, MultiShared& S, Lead& G, uint32_t step) {
             tkey = G.carry;
             G.carry = 0ull;
         } else {
-            const unsigned long long sel = select_threshold(v, cnt, G.M, S);
+            const uint32_t sel = select_threshold(v, cnt, G.M, S);
             // lowered by 2^-18 (relative) so that the node's own island, whose exact
             // value lies within its key's band, counts as reaching it
-            const float hi = __uint_as_float((uint32_t)(sel >> 32));
-            const float lo = __fmul_rd(hi, 1.0f - 0x1.0p-18f);
+            const float lo = __fmul_rd(__uint_as_float(sel), 1.0f - 0x1.0p-18f);
             tkey = sel ? ((unsigned long long)__float_as_uint(lo) << 32) : 1ull;
             if (tkey == 0ull) tkey = 1ull;
         }
         // the nodes of level lsel that reach it
         if (tid == 0) S.nf[0] = 0;
         __syncthreads();
+        {  // (each thread's hits as a mask; one reservation a warp)
+            unsigned hm = 0u;
 #pragma unroll
-        for (int u = 0; u < kSelPer; ++u) {
-            const int c = tid + u * kMT;
-            warp_append(c < cnt && v[u] != 0ull && v[u] >= tkey, c, S.front[0], &S.nf[0], kCandCap);
+            for (int u = 0; u < kSelPer; ++u)
+                if (tid + u * kMT < cnt && v[u] != 0ull && v[u] >= tkey) hm |= 1u << u;
+            const int nh = __popc(hm);
+            int incl = nh;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            int base = 0;
+            if (lane == 31 && incl) base = atomicAdd(&S.nf[0], incl);
+            int pos = __shfl_sync(0xffffffffu, base, 31) + incl - nh;
+#pragma unroll
+            for (int u = 0; u < kSelPer; ++u)
+                if ((hm >> u) & 1u) {
+                    if (pos < kCandCap) S.front[0][pos] = tid + u * kMT;
+                    ++pos;
+                }
         }
         __syncthreads();
         int cur = 0;
