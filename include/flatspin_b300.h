@@ -158,7 +158,7 @@ fs_status fs_set_stream(fs_sim* sim, void* stream);
  *   from every earlier island of the round (so that no flip of the round changes
  *   its field or a neighbour shared with it), and no earlier flip's neighbour got a
  *   value that beats it. Faster on large arrays, where many of the largest values
- *   lie far apart. A field step whose rounds stay below 8 flips for 4 rounds in a
+ *   lie far apart. A field step whose rounds stay below 4 flips for 4 rounds in a
  *   row (a chain of flips that each make a neighbour the largest) is finished by
  *   the single-flip chain.
  * FS_RELAX_AUTO (default): multi-flip rounds from 262,144 islands on.
@@ -255,6 +255,8 @@ typedef struct {
     int64_t fallbacks;          /* rechecks that overflowed into a full scan */
     int64_t rounds;             /* multi-flip relax: rounds that flipped so far */
     int64_t idle_rounds;        /* multi-flip relax: candidate passes that flipped nothing */
+    int64_t round_flips;        /* multi-flip relax: flips made in its rounds */
+    int64_t handoffs;           /* multi-flip relax: field steps handed to the single-flip one */
 } fs_profile;
 fs_status fs_set_profiling(fs_sim* sim, int32_t on);
 fs_status fs_get_profile(fs_sim* sim, fs_profile* out);

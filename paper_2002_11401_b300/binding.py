@@ -62,7 +62,7 @@ class fs_profile(C.Structure):
     _fields_ = [("sweep_ms", C.c_double), ("relax_ms", C.c_double),
                 ("sweep_launches", C.c_int64), ("relax_launches", C.c_int64),
                 ("rechecks", C.c_int64), ("fallbacks", C.c_int64), ("rounds", C.c_int64),
-                ("idle_rounds", C.c_int64)]
+                ("idle_rounds", C.c_int64), ("round_flips", C.c_int64), ("handoffs", C.c_int64)]
 
 
 class fs_request(C.Structure):

@@ -966,6 +966,8 @@ static fs_status finish_run(fs_sim* sim, InstState* out) {
     sim->fallbacks += out->fallbacks;
     sim->rounds += out->rounds;
     sim->idle_rounds += out->idle;
+    sim->round_flips += out->round_flips;
+    sim->handoffs += out->handoffs;
     if (out->status == ST_NOT_CONVERGED)
         return fail(sim, FS_ERR_NOT_CONVERGED, "a relax exceeded max_flips_per_step");
     if (out->status == ST_BOUNDS)
@@ -1258,6 +1260,8 @@ extern "C" fs_status fs_get_profile(fs_sim* sim, fs_profile* out) {
     out->fallbacks = sim->fallbacks;
     out->rounds = sim->rounds;
     out->idle_rounds = sim->idle_rounds;
+    out->round_flips = sim->round_flips;
+    out->handoffs = sim->handoffs;
     return FS_OK;
 }
 

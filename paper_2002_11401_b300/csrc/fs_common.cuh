@@ -44,6 +44,8 @@ struct InstState {
     int32_t handoff;    // 1: the multi-flip relax left the rest of step t to the single-flip one
     int32_t pad2;
     int64_t step_flips; // flips of step t before the hand-off
+    int64_t round_flips;  // multi-flip relax: flips made in its rounds,
+    int64_t handoffs;     //   and field steps it handed to the single-flip relax
 };
 
 // Read-only descriptor of one simulation (one entry of a batch table).

@@ -89,6 +89,7 @@ struct fs_sim {
     int relax_mode = 0; // FS_RELAX_AUTO, FS_RELAX_SINGLE or FS_RELAX_MULTI
     int64_t rechecks = 0, fallbacks = 0;
     int64_t rounds = 0, idle_rounds = 0;  // multi-flip relax
+    int64_t round_flips = 0, handoffs = 0;
     cudaGraphExec_t graph_exec = nullptr;
     // profiling: CUDA events around each sweep and relax launch
     bool profiling = false;

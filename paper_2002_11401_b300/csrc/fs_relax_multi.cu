@@ -66,7 +66,7 @@ constexpr int kMaxIdle = 1024;    // consecutive iterations without a flip befor
 constexpr int kCarry = 160;       // candidates carried below a round's last flip
 // A step is handed to the single-flip relax after kLowRounds consecutive rounds of
 // fewer than kPMin flips (a chain of flips that each make a neighbour the largest).
-constexpr int kPMin = 8;
+constexpr int kPMin = 4;
 constexpr int kLowRounds = 4;
 constexpr int kClsSh = 32;        // angle classes whose external field is read from shared memory
 constexpr int kRankMax = 256;     // candidates sorted by rank (more: a bitonic network)
@@ -104,6 +104,8 @@ struct MultiShared {
     unsigned long long xv[kPickCap];  // per pick: the best new value among its neighbours
     int32_t xi[kPickCap];             //   and its island
     int32_t hist[256];
+    unsigned long long wv[kMW];       // per warp: a prefix maximum and its island
+    int32_t wi[kMW];
     int32_t hq[kHashQ];               // flips not yet in the hash, in order (leader)
     int32_t hq_n;
     double2 ext64[kClsSh];            // the step's external field per angle class
@@ -518,26 +520,34 @@ __device__ void scan_best(const Inst& I, uint32_t step, MultiShared& S) {
 __device__ void sort_candidates(MultiShared& S, int n) {
     const int tid = threadIdx.x;
     if (n <= kRankMax) {
-        if (tid < n) {
-            const unsigned long long v = S.cand[tid].v;
-            const int32_t ix = S.cand[tid].i;
-            int r = 0;
-            int u = 0;
-            for (; u + 8 <= n; u += 8) {  // (eight loads in flight)
+        // sub consecutive threads count for one entry, each over every sub-th other
+        const int sub = n <= kMT / 4 ? 4 : 2;  // (kRankMax <= kMT / 2)
+        const int e = tid / sub, part = tid % sub;
+        int r = 0;
+        unsigned long long v = 0ull;
+        int32_t ix = 0;
+        if (e < n) {
+            v = S.cand[e].v;
+            ix = S.cand[e].i;
+            int u = part;
+            for (; u + 7 * sub < n; u += 8 * sub) {  // (eight loads in flight)
                 unsigned long long w[8];
                 int32_t wi[8];
 #pragma unroll
                 for (int z = 0; z < 8; ++z) {
-                    w[z] = S.cand[u + z].v;
-                    wi[z] = S.cand[u + z].i;
+                    w[z] = S.cand[u + z * sub].v;
+                    wi[z] = S.cand[u + z * sub].i;
                 }
 #pragma unroll
                 for (int z = 0; z < 8; ++z) r += before(w[z], wi[z], v, ix) ? 1 : 0;
             }
-            for (; u < n; ++u) r += before(S.cand[u].v, S.cand[u].i, v, ix) ? 1 : 0;
+            for (; u < n; u += sub) r += before(S.cand[u].v, S.cand[u].i, v, ix) ? 1 : 0;
+        }
+        for (int o = 1; o < sub; o <<= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+        if (e < n && part == 0) {
             S.sv[r] = v;
             S.si[r] = ix;
-            S.so[r] = (int16_t)tid;
+            S.so[r] = (int16_t)e;
         }
         __syncthreads();
         return;
@@ -742,7 +752,7 @@ __device__ int32_t plan(const Inst& I, MultiShared& S, Lead& G, uint32_t step) {
 // budget give the picks. Returns the cluster's next command (kCmdPlan when there
 // is nothing to flip at this threshold). Leader CTA-wide.
 __device__ int32_t decide(const Inst& I, MultiShared& S, Lead& G) {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tid = threadIdx.x;
     const int nl = S.nl;
     if (nl > kCandCap) {  // too many candidates: a higher threshold, or a scan
         if (!G.was_carried) {
@@ -792,22 +802,29 @@ __device__ int32_t decide(const Inst& I, MultiShared& S, Lead& G) {
         }
         return kCmdPlan;
     }
-    // (b) picks more than twice the cutoff apart: pair (c, j), j < c, a warp per row
-    // c, lanes over j; in FP32 against a radius widened by the rounding of the centres
-    for (int c = 1 + wid; c < q; c += kMW) {
-        if (c >= __shfl_sync(0xffffffffu, S.conflict_at, 0)) break;
-        const float2 a = S.sp[c];
+    // (b) picks more than twice the cutoff apart: thread c tests pick c against every
+    // j < c, in FP32 against a radius widened by the rounding of the centres
+    if (tid >= 1 && tid < q) {  // (q <= kPickCap <= kMT)
+        const float2 a = S.sp[tid];
+        const float r2 = I.rconf2f;
         bool hit = false;
-        for (int j = lane; j < c; j += 32) {
+        int j = 0;
+        for (; j + 4 <= tid; j += 4) {
+#pragma unroll
+            for (int z = 0; z < 4; ++z) {
+                const float2 b = S.sp[j + z];
+                const float dx = __fsub_rn(a.x, b.x);
+                const float dy = __fsub_rn(a.y, b.y);
+                hit |= __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) <= r2;
+            }
+        }
+        for (; j < tid; ++j) {
             const float2 b = S.sp[j];
             const float dx = __fsub_rn(a.x, b.x);
             const float dy = __fsub_rn(a.y, b.y);
-            hit = hit || __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) <= I.rconf2f;
+            hit |= __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) <= r2;
         }
-        if (__any_sync(0xffffffffu, hit)) {
-            if (lane == 0) atomicMin(&S.conflict_at, c);
-            break;
-        }
+        if (hit) atomicMin(&S.conflict_at, tid);
     }
     __syncthreads();
     q = min(q, S.conflict_at);
@@ -849,49 +866,42 @@ template <int PREC>
 __device__ int32_t prefix_step(const Inst& I, MultiShared& S, Lead& G, uint32_t step) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int q = S.q;
-    // warp 0, 32 picks at a time: the best of the earlier picks' neighbour values
-    // (an exclusive prefix maximum), carried between chunks
-    if (wid == 0) {
-        unsigned long long cv_ = 0ull;  // carried maximum
-        int32_t ci_ = 0x7fffffff;
-        int p = q;
-        for (int j0 = 0; j0 < q; j0 += 32) {
-            const int j = j0 + lane;
-            unsigned long long xv = j < q ? S.xv[j] : 0ull;
-            int32_t xi = j < q ? S.xi[j] : 0x7fffffff;
+    // the best of the earlier picks' neighbour values, an exclusive prefix maximum
+    // over the picks in order (thread j: pick j; within warps, then across them)
+    if (tid == 0) S.p = q;
+    {
+        const int j = tid;  // (q <= kPickCap <= kMT)
+        unsigned long long xv = j < q ? S.xv[j] : 0ull;
+        int32_t xi = j < q ? S.xi[j] : 0x7fffffff;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {  // inclusive prefix maximum
-                const unsigned long long ov = __shfl_up_sync(0xffffffffu, xv, o);
-                const int32_t oi = __shfl_up_sync(0xffffffffu, xi, o);
-                if (lane >= o && ov && (!xv || before(ov, oi, xv, xi))) {
-                    xv = ov;
-                    xi = oi;
-                }
-            }
-            unsigned long long ev = __shfl_up_sync(0xffffffffu, xv, 1);
-            int32_t ei = __shfl_up_sync(0xffffffffu, xi, 1);
-            if (lane == 0) {
-                ev = 0ull;
-                ei = 0x7fffffff;
-            }
-            if (cv_ && (!ev || before(cv_, ci_, ev, ei))) {
-                ev = cv_;
-                ei = ci_;
-            }
-            const bool fail = j < q && j > 0 && ev && !before(S.sv[j], S.si[j], ev, ei);
-            const unsigned fm = __ballot_sync(0xffffffffu, fail);
-            if (fm) {
-                p = j0 + __ffs(fm) - 1;
-                break;
-            }
-            const unsigned long long lv = __shfl_sync(0xffffffffu, xv, 31);
-            const int32_t li = __shfl_sync(0xffffffffu, xi, 31);
-            if (lv && (!cv_ || before(lv, li, cv_, ci_))) {
-                cv_ = lv;
-                ci_ = li;
+        for (int o = 1; o < 32; o <<= 1) {  // inclusive prefix maximum within the warp
+            const unsigned long long ov = __shfl_up_sync(0xffffffffu, xv, o);
+            const int32_t oi = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o && ov && (!xv || before(ov, oi, xv, xi))) {
+                xv = ov;
+                xi = oi;
             }
         }
-        if (lane == 0) S.p = p;
+        if (lane == 31) {
+            S.wv[wid] = xv;
+            S.wi[wid] = xi;
+        }
+        unsigned long long ev = __shfl_up_sync(0xffffffffu, xv, 1);
+        int32_t ei = __shfl_up_sync(0xffffffffu, xi, 1);
+        if (lane == 0) {
+            ev = 0ull;
+            ei = 0x7fffffff;
+        }
+        __syncthreads();
+        for (int w = 0; w < wid && w * 32 < q; ++w) {  // the earlier warps' maxima
+            const unsigned long long wv = S.wv[w];
+            const int32_t wi = S.wi[w];
+            if (wv && (!ev || before(wv, wi, ev, ei))) {
+                ev = wv;
+                ei = wi;
+            }
+        }
+        if (j < q && j > 0 && ev && !before(S.sv[j], S.si[j], ev, ei)) atomicMin(&S.p, j);
     }
     __syncthreads();
     const int p = S.p;
@@ -1182,11 +1192,13 @@ __global__ void __launch_bounds__(kMT, 1)
     if (tid == 0) {
         st->rounds += G.rounds;
         st->idle += G.idle_total;
+        st->round_flips += G.flips;
         st->n_flips = G.flips_before + G.flips;
         if (G.status != ST_OK) st->status = G.status;
         if (G.handoff && G.status == ST_OK) {  // the single-flip relax finishes step t
             st->handoff = 1;
             st->step_flips = G.flips;
+            ++st->handoffs;
         } else {
             if (I.flips_per_step) I.flips_per_step[t] = G.flips;
             st->init = 0;

@@ -89,6 +89,7 @@ def run_single(name, precision, steps, resweep, cells=0):
             "peak_gbs": peak, "peak_kind": kind,
             "relax_share": prof["relax_ms"] / (dt * 1e3), "rechecks": prof["rechecks"],
             "multi_rounds": prof["rounds"], "multi_idle_rounds": prof["idle_rounds"],
+            "multi_round_flips": prof["round_flips"], "multi_handoffs": prof["handoffs"],
             "relax_us_per_launch": prof["relax_ms"] * 1e3 / max(prof["relax_launches"], 1),
             "device_bytes": info.device_bytes,
             "flips_per_step_head": r["flips_per_step"][:16].tolist()}
