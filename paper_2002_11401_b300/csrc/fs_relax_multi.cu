@@ -123,6 +123,8 @@ struct MultiShared {
     int32_t cmd;                      // what the cluster does next (kCmd*)
     int32_t f_lev;                    // level of the frontier nodes to expand (0 or 1)
     int32_t f_buf;                    // their buffer in front
+    int32_t next;                     // the command that follows the stores (kCmdPlan: the
+                                      //   leader chooses it after them)
 };
 
 // Dynamic shared memory of a CTA: its state, then every warp's staging slots.
@@ -312,16 +314,22 @@ __device__ __forceinline__ void pass_compute(const Inst& I, int64_t k, int snew,
     }
 }
 
-// Stores one update (t.i == k: the flipped island itself, whose spin goes too).
-__device__ __forceinline__ void stage_commit(const Inst& I, unsigned long long* const* lp,
-                                             int64_t k, int snew, const Stage& t) {
+// Stores one update (t.i == k: the flipped island itself, whose spin goes too), the
+// tree aside.
+__device__ __forceinline__ void stage_store(const Inst& I, int64_t k, int snew, const Stage& t) {
     const int64_t i = t.i;
     if (i == k) I.s[k] = (int8_t)snew;
     I.h64[i] = t.h;
     rec_store_dyn(I, i, t.g, t.lo, t.s);
     I.key64[i] = t.x;
     I.key32[i] = t.nk;
-    if (t.push) push_up(lp, I.nlev, i, t.nk);
+}
+
+// Stores one update and pushes its key up the tree when it grew.
+__device__ __forceinline__ void stage_commit(const Inst& I, unsigned long long* const* lp,
+                                             int64_t k, int snew, const Stage& t) {
+    stage_store(I, k, snew, t);
+    if (t.push) push_up(lp, I.nlev, t.i, t.nk);
 }
 
 // The own update of a pick flipped forward: island k keeps its field and its spin
@@ -395,11 +403,13 @@ __device__ void flip_warp(const Inst& I, unsigned long long* const* lp, int64_t 
 }
 
 // The forward flip of island k (row [r0, r1) of at most kStageSlots entries): the
-// neighbours' updates computed into the warp's staging slots stg[0 .. kStageSlots),
-// nothing stored; returns the best new neighbour value as flip_warp does. Warp-wide.
+// neighbours' updates computed into the warp's staging slots stg[0 .. kStageSlots)
+// and the keys that grow pushed up the tree, nothing else stored; returns the best
+// new neighbour value as flip_warp does. Warp-wide.
 template <int PREC>
-__device__ void compute_pick(const Inst& I, int64_t k, int snew, int64_t r0, int64_t r1,
-                             uint32_t step, Stage* stg, unsigned long long* xv, int32_t* xi) {
+__device__ void compute_pick(const Inst& I, unsigned long long* const* lp, int64_t k, int snew,
+                             int64_t r0, int64_t r1, uint32_t step, Stage* stg,
+                             unsigned long long* xv, int32_t* xi) {
     const int lane = threadIdx.x & 31;
     unsigned long long bv = 0ull;
     int32_t bi = 0x7fffffff;
@@ -408,6 +418,10 @@ __device__ void compute_pick(const Inst& I, int64_t k, int snew, int64_t r0, int
 #pragma unroll
     for (int h = 0; h < kSlots; ++h) {
         stg[lane + 32 * h] = t[h];
+        // (the keys that grow go up the tree now: a pick that is not stored leaves
+        // the tree an upper bound still, and the next threshold can be chosen before
+        // the stores)
+        if (t[h].i >= 0 && t[h].push) push_up(lp, I.nlev, t[h].i, t[h].nk);
         stage_best<PREC>(t[h], k, &bv, &bi);
     }
     warp_best(&bv, &bi);
@@ -415,15 +429,15 @@ __device__ void compute_pick(const Inst& I, int64_t k, int snew, int64_t r0, int
     *xi = bi;
 }
 
-// Stores the flip compute_pick staged, and k's own update. Warp-wide.
-__device__ void store_pick(const Inst& I, unsigned long long* const* lp, int64_t k, int snew,
-                           const Stage* stg) {
+// Stores the flip compute_pick staged (its keys are up the tree already), and k's
+// own update. Warp-wide.
+__device__ void store_pick(const Inst& I, int64_t k, int snew, const Stage* stg) {
     const int lane = threadIdx.x & 31;
     if (lane == 0) own_flipped(I, k, snew);
 #pragma unroll
     for (int h = 0; h < kSlots; ++h) {
         const Stage t = stg[lane + 32 * h];
-        if (t.i >= 0) stage_commit(I, lp, k, snew, t);
+        if (t.i >= 0) stage_store(I, k, snew, t);
     }
 }
 
@@ -603,9 +617,11 @@ struct Lead {
 // level 1, or level 0 for a one-level selection), or, for a candidate set too large
 // at every threshold, the one best island by a full scan. The threshold is chosen
 // on level lsel, loaded whole (its M-th largest node, unless the previous round
-// carried one or forced one). Returns the cluster's next command. Leader CTA-wide.
+// carried one or forced one). `early`: the round's stores are still to come (the
+// tree holds their keys already); a scan then waits for them (returns kCmdPlan).
+// Returns the cluster's next command. Leader CTA-wide.
 template <int PREC>
-__device__ int32_t plan(const Inst& I, MultiShared& S, Lead& G, uint32_t step) {
+__device__ int32_t plan(const Inst& I, MultiShared& S, Lead& G, uint32_t step, bool early) {
     constexpr int kB = 4;  // frontier nodes whose children a warp loads together
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
     for (;;) {
@@ -613,6 +629,7 @@ __device__ int32_t plan(const Inst& I, MultiShared& S, Lead& G, uint32_t step) {
             G.status = ST_BOUNDS;
             return kCmdStop;
         }
+        if (G.need_scan && early) return kCmdPlan;  // (a scan reads the stored keys)
         if (G.need_scan) {  // a candidate set too large for any threshold
             G.need_scan = false;
             G.M = G.m0;
@@ -861,7 +878,8 @@ __device__ __forceinline__ void hash_queue(const MultiShared& S, Lead& G, uint32
 // The leader after the picks are computed: the longest prefix of the picks that no
 // earlier pick's neighbour overtakes (c); the eager picks after it flipped back (a
 // warp a pick); the prefix logged and queued for the hash in order; the threshold
-// carried to the next round. Returns kCmdStore. Leader CTA-wide.
+// carried to the next round, and the next round planned (S.next: what follows the
+// stores). Returns kCmdStore. Leader CTA-wide.
 template <int PREC>
 __device__ int32_t prefix_step(const Inst& I, MultiShared& S, Lead& G, uint32_t step) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -955,6 +973,9 @@ __device__ int32_t prefix_step(const Inst& I, MultiShared& S, Lead& G, uint32_t 
     }
     __syncthreads();
     if (tid == 0) S.hq_n = h0 + p;
+    // the next threshold and frontier now (the tree holds the round's keys)
+    const int32_t next = G.handoff ? kCmdStop : plan<PREC>(I, S, G, step, true);
+    if (tid == 0) S.next = next;
     return kCmdStore;
 }
 
@@ -1059,7 +1080,7 @@ __device__ bool compute_picks(const Inst& I, MultiShared* L, MultiShared& S, Lea
         unsigned long long xv;
         int32_t xi;
         if (!held && r1 - r0 <= kStageSlots) {
-            compute_pick<PREC>(I, pk.i, -pk.s, r0, r1, step, stg, &xv, &xi);
+            compute_pick<PREC>(I, S.lp, pk.i, -pk.s, r0, r1, step, stg, &xv, &xi);
             held = true;
             *held_j = j;
             *held_k = pk.i;
@@ -1157,16 +1178,22 @@ __global__ void __launch_bounds__(kMT, 1)
     G.need_scan = G.was_carried = G.was_forced = G.handoff = false;
 
     int32_t cmd = kCmdPlan;  // (the leader's next step)
+    bool known = false;      // every CTA has the next command already (S.next)
     bool held = false;       // this warp holds a staged pick:
     int held_j = 0, held_s = 0;  // its index and new spin,
     int64_t held_k = 0;      // its island
     for (;;) {
-        if (leader) {
-            if (cmd == kCmdPlan) cmd = plan<PREC>(I, S, G, step);
-            if (tid == 0) S.cmd = cmd;
+        if (known) {
+            csync();  // the stores are in
+            known = false;
+        } else {
+            if (leader) {
+                if (cmd == kCmdPlan) cmd = plan<PREC>(I, S, G, step, false);
+                if (tid == 0) S.cmd = cmd;
+            }
+            csync();  // the leader's command is out
+            cmd = L->cmd;
         }
-        csync();  // the leader's command is out
-        cmd = L->cmd;
         if (cmd == kCmdStop) break;
         if (cmd == kCmdExpand) {
             expand_eval<PREC, NC>(I, L, S, rank, step);
@@ -1177,10 +1204,14 @@ __global__ void __launch_bounds__(kMT, 1)
             csync();  // the picks are computed
             if (leader) cmd = prefix_step<PREC>(I, S, G, step);
         } else {  // kCmdStore
-            if (held && held_j < L->p) store_pick(I, S.lp, held_k, held_s, stg);
+            if (held && held_j < L->p) store_pick(I, held_k, held_s, stg);
             held = false;
-            csync();  // the prefix is stored
-            if (leader) cmd = G.handoff ? kCmdStop : kCmdPlan;
+            cmd = L->next;
+            if (cmd == kCmdPlan) {
+                csync();  // the prefix is stored (before the leader plans)
+            } else {
+                known = true;  // (planned already: one barrier, then on)
+            }
         }
     }
     csync();  // (no CTA leaves while another may still reach the leader's memory)
