@@ -273,7 +273,7 @@ struct __align__(16) Stage {
     int32_t push;
 };
 
-constexpr int kSlots = 3;                 // slots a lane takes per pass
+constexpr int kSlots = 2;                 // slots a lane takes per pass (rows of up to 64 staged)
 constexpr int kStageSlots = 32 * kSlots;  // a warp's staging slots (one pass)
 
 // One pass over the slots e0, e0 + 32, ... (e0 = first + lane) of the flip of
