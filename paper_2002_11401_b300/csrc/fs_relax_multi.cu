@@ -58,9 +58,9 @@ constexpr int kMT = 512;          // threads of a multi-flip relax CTA
 constexpr int kMW = kMT / 32;
 constexpr int kCandCap = 1024;    // candidate islands per round
 constexpr int kPickCap = 128;     // picks tested per round (one a warp of a cluster of 8)
-constexpr int kSelMax = 8192;     // thresholds are chosen on the lowest level with at most this many nodes
+constexpr int kSelMax = 4096;     // thresholds are chosen on the lowest level with at most this many nodes
 constexpr int kSelPer = kSelMax / kMT;
-constexpr int kM0 = 256;          // rank of the threshold node
+constexpr int kM0 = 512;          // rank of the threshold node
 constexpr int kHashT = kMT - 1;   // thread that folds the flips into the sequence hash
 constexpr int kMaxIdle = 1024;    // consecutive iterations without a flip before ST_BOUNDS
 constexpr int kCarry = 160;       // candidates carried below a round's last flip
