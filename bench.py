@@ -114,8 +114,15 @@ def flip_layout_bytes(degree: float, fp32: bool) -> float:
 # launch by its units, with a hash of the kernel sources that were profiled: a
 # changed kernel reports null.
 TRAFFIC = {
-    "k_sweep": {"per": "neighbour pair", "bytes_per_unit": None,
-                "sources": ("fs_sweep.cu", "fs_common.cuh"), "sha256_16": ""},
+    # DRAM bytes (read + write) per unit from one small-case ncu capture of the kernel
+    # (profiles/), valid while the listed sources are unchanged (sha256 prefix): the sweep
+    # capture is of its 8-lanes-a-row build on kagome 300x300, the multi-flip one of field
+    # step 5 of that rotation; both are scaled to a full launch by their units
+    "k_sweep": {"per": "neighbour pair", "bytes_per_unit": 13.39,
+                "sources": ("fs_sweep.cu",), "sha256_16": "6f2859ae689aa7d3"},
+    "k_relax_multi": {"per": "flip", "bytes_per_unit": 11837.0,
+                      "sources": ("fs_relax_multi.cu", "fs_update.cuh", "fs_common.cuh"),
+                      "sha256_16": "e922795e1f0fc41e"},
     "k_relax": {"per": "flip", "bytes_per_unit": None,
                 "sources": ("fs_relax.cu", "fs_common.cuh"), "sha256_16": ""},
 }
@@ -579,7 +586,7 @@ def main():
     relax_kernel = "k_relax_multi" if n >= 262144 else "k_relax"  # the library's automatic choice
     roof_relax = {"kernel": relax_kernel, "bound": "hbm", "achieved": relax_ach, "peak": peak,
                   "unit": "GB/s", "frac": relax_ach / peak,
-                  "traffic": traffic_of("k_relax", flips_per_launch),
+                  "traffic": traffic_of(relax_kernel, flips_per_launch),
                   "peak_kind": peak_kind,
                   "avg_launch_ms": prof["relax_ms"] / relax_launches,
                   "share_of_step": prof["relax_ms"] / ms if ms > 0 else None,
