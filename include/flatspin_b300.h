@@ -409,8 +409,10 @@ fs_status fs_batch_run_protocol(fs_sim* const* sims, int32_t n, const double* hx
  * stream of its own with its whole protocol queued, so requests that arrive while
  * others run start as soon as they are built and all of them overlap on the
  * device. Admission order: a request waiting longer than 10 s first (oldest
- * first), else the least estimated work (islands x field steps). Results equal
- * those of running each request alone. */
+ * first), else the least estimated work (islands x field steps). Every request
+ * relaxes with the single-flip chain (FS_RELAX_SINGLE: one CTA, one SM), which
+ * makes the most flips per SM on a shared device. Results equal those of running
+ * each request alone. */
 typedef struct fs_server fs_server;
 
 typedef struct {

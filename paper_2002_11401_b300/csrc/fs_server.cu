@@ -173,6 +173,9 @@ void builder_loop(fs_server* S, int which) {
         fs_status st = fs_create_geometry(j->req.kind, j->req.nx, j->req.ny, j->req.a, &sim);
         if (st == FS_OK) {
             fs_set_stream(sim, bst);
+            // one CTA per request: a shared device does the most flips per SM this way
+            // (a multi-flip cluster holds 8 SMs and waits for them to empty)
+            fs_set_relax_mode(sim, FS_RELAX_SINGLE);
             st = fs_set_params(sim, &j->req.params);
         }
         if (st == FS_OK) {
