@@ -95,6 +95,23 @@ def run_single(name, precision, steps, resweep, cells=0):
             "flips_per_step_head": r["flips_per_step"][:16].tolist()}
 
 
+def step_barrier(fps, slots=2 * 148):
+    """What the batch's per-step barrier costs, with a member's relax time taken as its
+    flips in the step: fps [members, K]. With the barrier every step lasts as long as
+    its largest member's relax, or the step's flips spread over the resident relax CTAs
+    (`slots`), whichever is longer; without it (each member advancing on its own) the
+    protocol lasts as long as the longest member chain, or all flips over the slots."""
+    fps = np.asarray(fps, dtype=np.float64)
+    per_step = np.maximum(fps.max(axis=0), fps.sum(axis=0) / slots)
+    with_barrier = float(per_step.sum())
+    without = float(max(fps.sum(axis=1).max(), fps.sum() / slots))
+    return {"flip_steps_with_barrier": with_barrier, "flip_steps_without": without,
+            "bound_on_gain": with_barrier / without if without > 0 else None,
+            "largest_member_is_the_slowest_in_steps": int(
+                (fps.argmax(axis=0) == fps.sum(axis=1).argmax()).sum()),
+            "steps": int(fps.shape[1]), "slots": slots}
+
+
 def run_ensemble(members, sample):
     mem, proto = I.ensemble_workload()
     mem = mem[:members]
@@ -106,10 +123,12 @@ def run_ensemble(members, sample):
         sims = [make_sim(m, prec) for m in mem]
         out["islands"] = int(sum(s.n for s in sims))
         t0 = time.perf_counter()
-        res = B.batch_run_protocol(sims, hx, hy)
+        res = B.batch_run_protocol(sims, hx, hy, with_counts=tag == "fp32")
         dt = time.perf_counter() - t0
         flips = int(res["n_flips"].sum())
         hashes[tag] = res["hash"].copy()
+        if tag == "fp32":
+            out["step_barrier"] = step_barrier(res["flips_per_step"])
         out[f"batched_{tag}_s"] = dt
         out[f"batched_{tag}_flips_per_s"] = flips / dt
         out["flips"] = flips
