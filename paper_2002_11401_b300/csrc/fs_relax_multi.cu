@@ -1238,7 +1238,7 @@ __global__ void __launch_bounds__(kMT, 1)
     }
 }
 
-constexpr int kNC = 8;  // CTAs of a multi-flip relax cluster
+constexpr int kNC = 16;  // CTAs of a multi-flip relax cluster (a non-portable size)
 
 template <int PREC, int NC>
 cudaError_t launch_multi(const RelaxLaunch& L, int smem, cudaStream_t st) {
@@ -1259,6 +1259,11 @@ cudaError_t launch_multi(const RelaxLaunch& L, int smem, cudaStream_t st) {
 
 template <int PREC, int NC>
 cudaError_t set_multi_smem(int smem) {
+    if (NC > 8) {  // (more than the portable 8 CTAs a cluster)
+        const cudaError_t e = cudaFuncSetAttribute(
+            k_relax_multi<PREC, NC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
     return cudaFuncSetAttribute(k_relax_multi<PREC, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 smem);
 }
