@@ -57,7 +57,7 @@ namespace {
 constexpr int kMT = 512;          // threads of a multi-flip relax CTA
 constexpr int kMW = kMT / 32;
 constexpr int kCandCap = 1024;    // candidate islands per round
-constexpr int kPickCap = 128;     // picks tested per round (one a warp of a cluster of 8)
+constexpr int kPickCap = 256;     // picks tested per round (one a warp of a cluster of 16)
 constexpr int kSelMax = 4096;     // thresholds are chosen on the lowest level with at most this many nodes
 constexpr int kSelPer = kSelMax / kMT;
 constexpr int kM0 = 512;          // rank of the threshold node
@@ -1094,7 +1094,8 @@ __device__ bool compute_picks(const Inst& I, MultiShared* L, MultiShared& S, Lea
             L->xi[j] = xi;
         }
     }
-    // the leader's hash thread (its warp has no pick for q <= 120): the queued flips
+    // the leader's hash thread (its warp's first pick, NC (kMW - 1), lies past most
+    // rounds' picks): the queued flips
     // of the earlier rounds into the hash
     if (rank == 0 && threadIdx.x == kHashT) {
         hash_queue(S, G, step, S.hq_n);
