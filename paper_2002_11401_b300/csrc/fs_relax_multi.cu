@@ -1095,8 +1095,7 @@ __device__ bool compute_picks(const Inst& I, MultiShared* L, MultiShared& S, Lea
         }
     }
     // the leader's hash thread (its warp's first pick, NC (kMW - 1), lies past most
-    // rounds' picks): the queued flips
-    // of the earlier rounds into the hash
+    // rounds' picks): the queued flips of the earlier rounds into the hash
     if (rank == 0 && threadIdx.x == kHashT) {
         hash_queue(S, G, step, S.hq_n);
         S.hq_n = 0;
