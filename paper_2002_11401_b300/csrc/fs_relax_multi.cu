@@ -619,9 +619,13 @@ struct Lead {
 // on level lsel, loaded whole (its M-th largest node, unless the previous round
 // carried one or forced one). `early`: the round's stores are still to come (the
 // tree holds their keys already); a scan then waits for them (returns kCmdPlan).
+// `pre`: the level's values as this thread loaded them (node tid + u kMT), when
+// `have_pre`.
 // Returns the cluster's next command. Leader CTA-wide.
 template <int PREC>
-__device__ int32_t plan(const Inst& I, MultiShared& S, Lead& G, uint32_t step, bool early) {
+__device__ __forceinline__ int32_t plan(const Inst& I, MultiShared& S, Lead& G, uint32_t step,
+                                        bool early, const unsigned long long (&pre)[kSelPer],
+                                        bool have_pre) {
     constexpr int kB = 4;  // frontier nodes whose children a warp loads together
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
     for (;;) {
@@ -661,8 +665,9 @@ __device__ int32_t plan(const Inst& I, MultiShared& S, Lead& G, uint32_t step, b
 #pragma unroll
         for (int u = 0; u < kSelPer; ++u) {
             const int c = tid + u * kMT;
-            v[u] = c < cnt ? __ldcg(S.lp[lsel] + c) : 0ull;
+            v[u] = have_pre ? pre[u] : (c < cnt ? __ldcg(S.lp[lsel] + c) : 0ull);
         }
+        have_pre = false;  // (a retry reads the level again: it rebuilt nodes)
         unsigned long long tkey = 1ull;
         G.was_forced = G.forced != 0ull;
         G.was_carried = !G.was_forced && G.carry != 0ull;
@@ -819,29 +824,33 @@ __device__ int32_t decide(const Inst& I, MultiShared& S, Lead& G) {
         }
         return kCmdPlan;
     }
-    // (b) picks more than twice the cutoff apart: thread c tests pick c against every
-    // j < c, in FP32 against a radius widened by the rounding of the centres
-    if (tid >= 1 && tid < q) {  // (q <= kPickCap <= kMT)
-        const float2 a = S.sp[tid];
-        const float r2 = I.rconf2f;
+    // (b) picks more than twice the cutoff apart: threads 2c and 2c + 1 test pick c
+    // against the even and the odd j < c, in FP32 against a radius widened by the
+    // rounding of the centres
+    {
+        const int c = tid >> 1;  // (q <= kPickCap <= kMT / 2)
         bool hit = false;
-        int j = 0;
-        for (; j + 4 <= tid; j += 4) {
+        if (c >= 1 && c < q) {
+            const float2 a = S.sp[c];
+            const float r2 = I.rconf2f;
+            int j = tid & 1;
+            for (; j + 6 < c; j += 8) {
 #pragma unroll
-            for (int z = 0; z < 4; ++z) {
-                const float2 b = S.sp[j + z];
+                for (int z = 0; z < 4; ++z) {
+                    const float2 b = S.sp[j + 2 * z];
+                    const float dx = __fsub_rn(a.x, b.x);
+                    const float dy = __fsub_rn(a.y, b.y);
+                    hit |= __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) <= r2;
+                }
+            }
+            for (; j < c; j += 2) {
+                const float2 b = S.sp[j];
                 const float dx = __fsub_rn(a.x, b.x);
                 const float dy = __fsub_rn(a.y, b.y);
                 hit |= __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) <= r2;
             }
         }
-        for (; j < tid; ++j) {
-            const float2 b = S.sp[j];
-            const float dx = __fsub_rn(a.x, b.x);
-            const float dy = __fsub_rn(a.y, b.y);
-            hit |= __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) <= r2;
-        }
-        if (hit) atomicMin(&S.conflict_at, tid);
+        if (hit) atomicMin(&S.conflict_at, c);
     }
     __syncthreads();
     q = min(q, S.conflict_at);
@@ -884,6 +893,16 @@ template <int PREC>
 __device__ int32_t prefix_step(const Inst& I, MultiShared& S, Lead& G, uint32_t step) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int q = S.q;
+    // the next plan's level, loaded now (the tree is final: the picks' keys are in)
+    unsigned long long lv[kSelPer];
+    {
+        const int cnt = I.lvl_n[G.lsel];
+#pragma unroll
+        for (int u = 0; u < kSelPer; ++u) {
+            const int c = tid + u * kMT;
+            lv[u] = c < cnt ? __ldcg(S.lp[G.lsel] + c) : 0ull;
+        }
+    }
     // the best of the earlier picks' neighbour values, an exclusive prefix maximum
     // over the picks in order (thread j: pick j; within warps, then across them)
     if (tid == 0) S.p = q;
@@ -974,7 +993,7 @@ __device__ int32_t prefix_step(const Inst& I, MultiShared& S, Lead& G, uint32_t 
     __syncthreads();
     if (tid == 0) S.hq_n = h0 + p;
     // the next threshold and frontier now (the tree holds the round's keys)
-    const int32_t next = G.handoff ? kCmdStop : plan<PREC>(I, S, G, step, true);
+    const int32_t next = G.handoff ? kCmdStop : plan<PREC>(I, S, G, step, true, lv, true);
     if (tid == 0) S.next = next;
     return kCmdStore;
 }
@@ -1188,7 +1207,10 @@ __global__ void __launch_bounds__(kMT, 1)
             known = false;
         } else {
             if (leader) {
-                if (cmd == kCmdPlan) cmd = plan<PREC>(I, S, G, step, false);
+                if (cmd == kCmdPlan) {
+                    unsigned long long none[kSelPer];
+                    cmd = plan<PREC>(I, S, G, step, false, none, false);
+                }
                 if (tid == 0) S.cmd = cmd;
             }
             csync();  // the leader's command is out
