@@ -69,7 +69,7 @@ constexpr int kCarry = 160;       // candidates carried below a round's last fli
 constexpr int kPMin = 4;
 constexpr int kLowRounds = 4;
 constexpr int kClsSh = 32;        // angle classes whose external field is read from shared memory
-constexpr int kRankMax = 256;     // candidates sorted by rank (more: a bitonic network)
+constexpr int kRankMax = 128;     // candidates sorted by rank (more: by merging)
 constexpr int kHashQ = 2 * kPickCap;  // flips waiting to be folded into the sequence hash
 
 // One candidate island as its exact evaluation found it.
@@ -97,6 +97,9 @@ struct MultiShared {
     unsigned long long sv[kCandCap];  // candidates in "before" order: value,
     int32_t si[kCandCap];             //   island,
     int16_t so[kCandCap];             //   and slot in cand
+    unsigned long long mv[kCandCap];  // the merge sort's second buffer
+    int32_t mi[kCandCap];
+    int16_t mo[kCandCap];
     float2 sp[kPickCap];              // the first candidates' centres, in that order
     int32_t front[2][kCandCap];       // frontier of the tree search
     int32_t loc[kCandCap];            // the candidate islands this CTA found
@@ -527,16 +530,19 @@ __device__ void scan_best(const Inst& I, uint32_t step, MultiShared& S) {
     __syncthreads();
 }
 
-// S.cand[0 .. n) into "before" order in S.sv / S.si / S.so: up to kRankMax entries
-// by rank (each entry counts those that go before it; islands are distinct), more
-// by a bitonic network over the next power of two (padding entries sort last).
-// CTA-wide.
+// S.cand[0 .. n) into "before" order in S.sv / S.si / S.so. Up to kRankMax entries
+// by rank (each entry counts those that go before it, four threads an entry;
+// islands are distinct). More by merging: every warp sorts runs of 32 in registers
+// (a bitonic network over its lanes), then pairs of runs merge until one run holds
+// everything, each entry's place being its place in its own run plus the number of
+// entries of the other run that go before it (a binary search; the left run wins
+// ties, which only padding entries, past n up to a power of two, can have: they
+// sort last). CTA-wide.
 __device__ void sort_candidates(MultiShared& S, int n) {
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (n <= kRankMax) {
-        // sub consecutive threads count for one entry, each over every sub-th other
-        const int sub = n <= kMT / 4 ? 4 : 2;  // (kRankMax <= kMT / 2)
-        const int e = tid / sub, part = tid % sub;
+        // four consecutive threads count for one entry, each over every fourth other
+        const int e = tid >> 2, part = tid & 3;  // (kRankMax <= kMT / 4)
         int r = 0;
         unsigned long long v = 0ull;
         int32_t ix = 0;
@@ -544,20 +550,21 @@ __device__ void sort_candidates(MultiShared& S, int n) {
             v = S.cand[e].v;
             ix = S.cand[e].i;
             int u = part;
-            for (; u + 7 * sub < n; u += 8 * sub) {  // (eight loads in flight)
+            for (; u + 28 < n; u += 32) {  // (eight loads in flight)
                 unsigned long long w[8];
                 int32_t wi[8];
 #pragma unroll
                 for (int z = 0; z < 8; ++z) {
-                    w[z] = S.cand[u + z * sub].v;
-                    wi[z] = S.cand[u + z * sub].i;
+                    w[z] = S.cand[u + 4 * z].v;
+                    wi[z] = S.cand[u + 4 * z].i;
                 }
 #pragma unroll
                 for (int z = 0; z < 8; ++z) r += before(w[z], wi[z], v, ix) ? 1 : 0;
             }
-            for (; u < n; u += sub) r += before(S.cand[u].v, S.cand[u].i, v, ix) ? 1 : 0;
+            for (; u < n; u += 4) r += before(S.cand[u].v, S.cand[u].i, v, ix) ? 1 : 0;
         }
-        for (int o = 1; o < sub; o <<= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+        r += __shfl_xor_sync(0xffffffffu, r, 1);
+        r += __shfl_xor_sync(0xffffffffu, r, 2);
         if (e < n && part == 0) {
             S.sv[r] = v;
             S.si[r] = ix;
@@ -566,37 +573,81 @@ __device__ void sort_candidates(MultiShared& S, int n) {
         __syncthreads();
         return;
     }
-    int n2 = 1;
-    while (n2 < n) n2 <<= 1;
-    for (int t = tid; t < n2; t += kMT) {
-        const bool real = t < n;
-        S.sv[t] = real ? S.cand[t].v : 0ull;
-        S.si[t] = real ? S.cand[t].i : 0x7fffffff;
-        S.so[t] = real ? (int16_t)t : (int16_t)-1;
-    }
-    __syncthreads();
-    for (int k = 2; k <= n2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int t = tid; t < n2; t += kMT) {
-                const int o = t ^ j;
-                if (o > t) {
-                    const bool up = (t & k) == 0;
-                    const unsigned long long va = S.sv[t], vb = S.sv[o];
-                    const int32_t ia = S.si[t], ib = S.si[o];
-                    const bool swap = up ? before(vb, ib, va, ia) : before(va, ia, vb, ib);
-                    if (swap) {
-                        S.sv[t] = vb;
-                        S.sv[o] = va;
-                        S.si[t] = ib;
-                        S.si[o] = ia;
-                        const int16_t so = S.so[t];
-                        S.so[t] = S.so[o];
-                        S.so[o] = so;
-                    }
+    int n2 = 32;
+    while (n2 < n) n2 <<= 1;  // (<= kCandCap)
+    // runs of 32 in registers, into (sv, si, so)
+    for (int base = wid * 32; base < n2; base += kMT) {
+        const int t = base + lane;
+        unsigned long long v = t < n ? S.cand[t].v : 0ull;
+        int32_t ix = t < n ? S.cand[t].i : 0x7fffffff;
+        int32_t so = t < n ? t : -1;
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const unsigned long long ov = __shfl_xor_sync(0xffffffffu, v, j);
+                const int32_t oi = __shfl_xor_sync(0xffffffffu, ix, j);
+                const int32_t os = __shfl_xor_sync(0xffffffffu, so, j);
+                // the pair's lower lane keeps the entry that goes first in a block
+                // sorted forwards, the later one in a block sorted backwards
+                const bool fwd = (lane & k) == 0 || k == 32;
+                const bool lower = (lane & j) == 0;
+                const bool take = fwd == lower ? before(ov, oi, v, ix) : before(v, ix, ov, oi);
+                if (take) {
+                    v = ov;
+                    ix = oi;
+                    so = os;
                 }
             }
-            __syncthreads();
         }
+        S.sv[t] = v;
+        S.si[t] = ix;
+        S.so[t] = (int16_t)so;
+    }
+    __syncthreads();
+    // pairwise merges, between (sv, si, so) and (mv, mi, mo)
+    bool in_m = false;
+    for (int r = 32; r < n2; r <<= 1) {
+        const unsigned long long* fv = in_m ? S.mv : S.sv;
+        const int32_t* fi = in_m ? S.mi : S.si;
+        const int16_t* fo = in_m ? S.mo : S.so;
+        unsigned long long* tv = in_m ? S.sv : S.mv;
+        int32_t* ti = in_m ? S.si : S.mi;
+        int16_t* to = in_m ? S.so : S.mo;
+        for (int t = tid; t < n2; t += kMT) {
+            const unsigned long long v = fv[t];
+            const int32_t ix = fi[t];
+            const int16_t so = fo[t];
+            const int run = t / r, k = t % r;
+            const bool left = (run & 1) == 0;
+            const int other = (run ^ 1) * r;
+            // entries of the other run that go before this one (ties: the left run first)
+            int lo = 0, hi = r;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                const unsigned long long w = fv[other + mid];
+                const int32_t wi = fi[other + mid];
+                const bool goes_before = left ? before(w, wi, v, ix) : !before(v, ix, w, wi);
+                if (goes_before)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            const int dst = (run >> 1) * 2 * r + k + lo;
+            tv[dst] = v;
+            ti[dst] = ix;
+            to[dst] = so;
+        }
+        __syncthreads();
+        in_m = !in_m;
+    }
+    if (in_m) {
+        for (int t = tid; t < n; t += kMT) {
+            S.sv[t] = S.mv[t];
+            S.si[t] = S.mi[t];
+            S.so[t] = S.mo[t];
+        }
+        __syncthreads();
     }
 }
 
@@ -619,13 +670,9 @@ struct Lead {
 // on level lsel, loaded whole (its M-th largest node, unless the previous round
 // carried one or forced one). `early`: the round's stores are still to come (the
 // tree holds their keys already); a scan then waits for them (returns kCmdPlan).
-// `pre`: the level's values as this thread loaded them (node tid + u kMT), when
-// `have_pre`.
 // Returns the cluster's next command. Leader CTA-wide.
 template <int PREC>
-__device__ __forceinline__ int32_t plan(const Inst& I, MultiShared& S, Lead& G, uint32_t step,
-                                        bool early, const unsigned long long (&pre)[kSelPer],
-                                        bool have_pre) {
+__device__ int32_t plan(const Inst& I, MultiShared& S, Lead& G, uint32_t step, bool early) {
     constexpr int kB = 4;  // frontier nodes whose children a warp loads together
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
     for (;;) {
@@ -665,9 +712,8 @@ __device__ __forceinline__ int32_t plan(const Inst& I, MultiShared& S, Lead& G, 
 #pragma unroll
         for (int u = 0; u < kSelPer; ++u) {
             const int c = tid + u * kMT;
-            v[u] = have_pre ? pre[u] : (c < cnt ? __ldcg(S.lp[lsel] + c) : 0ull);
+            v[u] = c < cnt ? __ldcg(S.lp[lsel] + c) : 0ull;
         }
-        have_pre = false;  // (a retry reads the level again: it rebuilt nodes)
         unsigned long long tkey = 1ull;
         G.was_forced = G.forced != 0ull;
         G.was_carried = !G.was_forced && G.carry != 0ull;
@@ -893,16 +939,6 @@ template <int PREC>
 __device__ int32_t prefix_step(const Inst& I, MultiShared& S, Lead& G, uint32_t step) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int q = S.q;
-    // the next plan's level, loaded now (the tree is final: the picks' keys are in)
-    unsigned long long lv[kSelPer];
-    {
-        const int cnt = I.lvl_n[G.lsel];
-#pragma unroll
-        for (int u = 0; u < kSelPer; ++u) {
-            const int c = tid + u * kMT;
-            lv[u] = c < cnt ? __ldcg(S.lp[G.lsel] + c) : 0ull;
-        }
-    }
     // the best of the earlier picks' neighbour values, an exclusive prefix maximum
     // over the picks in order (thread j: pick j; within warps, then across them)
     if (tid == 0) S.p = q;
@@ -993,7 +1029,7 @@ __device__ int32_t prefix_step(const Inst& I, MultiShared& S, Lead& G, uint32_t 
     __syncthreads();
     if (tid == 0) S.hq_n = h0 + p;
     // the next threshold and frontier now (the tree holds the round's keys)
-    const int32_t next = G.handoff ? kCmdStop : plan<PREC>(I, S, G, step, true, lv, true);
+    const int32_t next = G.handoff ? kCmdStop : plan<PREC>(I, S, G, step, true);
     if (tid == 0) S.next = next;
     return kCmdStore;
 }
@@ -1207,10 +1243,7 @@ __global__ void __launch_bounds__(kMT, 1)
             known = false;
         } else {
             if (leader) {
-                if (cmd == kCmdPlan) {
-                    unsigned long long none[kSelPer];
-                    cmd = plan<PREC>(I, S, G, step, false, none, false);
-                }
+                if (cmd == kCmdPlan) cmd = plan<PREC>(I, S, G, step, false);
                 if (tid == 0) S.cmd = cmd;
             }
             csync();  // the leader's command is out
