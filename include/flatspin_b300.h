@@ -251,7 +251,8 @@ fs_status fs_set_spins_dev(fs_sim* sim, const int8_t* d_s, int64_t n);
 typedef struct {
     double sweep_ms, relax_ms;  /* summed device time of the sweeps and relaxes */
     int64_t sweep_launches, relax_launches;
-    int64_t rechecks;           /* FP64 recheck rounds of the FP32 path so far */
+    int64_t rechecks;           /* FP32 path: FP64 recheck rounds (single-flip relax) and
+                                   FP64 evaluations of candidates (multi-flip relax) so far */
     int64_t fallbacks;          /* rechecks that overflowed into a full scan */
     int64_t rounds;             /* multi-flip relax: rounds that flipped so far */
     int64_t idle_rounds;        /* multi-flip relax: candidate passes that flipped nothing */

@@ -37,7 +37,8 @@ struct InstState {
     double hx, hy;      // external field of the current step
     uint32_t step;      // thermal step index of the current step
     uint32_t pad;
-    int64_t rechecks;   // FP64 recheck rounds (FP32 path)
+    int64_t rechecks;   // FP32 path: FP64 recheck rounds (single-flip relax), FP64
+                        // evaluations of candidates (multi-flip relax)
     int64_t fallbacks;  // full-scan rechecks (candidate overflow)
     int64_t rounds;     // multi-flip relax: rounds that flipped, and iterations without a flip
     int64_t idle;

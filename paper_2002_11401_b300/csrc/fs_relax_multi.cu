@@ -450,9 +450,10 @@ __device__ void store_pick(const Inst& I, int64_t k, int snew, const Stage* stg)
 // exact value (an upper bound no higher than the one it had). The FP32 path
 // evaluates the exact sums in FP64 unless its current fields already were
 // (key64 >= 0); the step's thermal draw is the kept one, or drawn and kept (no
-// other thread evaluates island i meanwhile). Every load is issued up front.
+// other thread evaluates island i meanwhile; *nfp64 counts the FP64 evaluations).
+// Every load is issued up front.
 template <int PREC>
-__device__ __forceinline__ Cand eval_cand(const Inst& I, int64_t i, uint32_t step) {
+__device__ __forceinline__ Cand eval_cand(const Inst& I, int64_t i, uint32_t step, int* nfp64) {
     const IslandRec r = rec_load(I, i);
     const double2 pc = __ldg(&I.pos[i]);
     const double kept = I.key64[i];
@@ -468,6 +469,7 @@ __device__ __forceinline__ Cand eval_cand(const Inst& I, int64_t i, uint32_t ste
             tv = I.th64[i];
         }
         if (kept < 0.0) {
+            ++*nfp64;
             if (th && ts != step) {
                 thermal64(I, i, step, &tv.x, &tv.y);
                 I.th64[i] = tv;
@@ -1041,7 +1043,7 @@ __device__ int32_t prefix_step(const Inst& I, MultiShared& S, Lead& G, uint32_t 
 // them, past kCandCap too). Warps of all CTAs share the nodes.
 template <int PREC, int NC>
 __device__ void expand_eval(const Inst& I, MultiShared* L, MultiShared& S, int rank,
-                            uint32_t step) {
+                            uint32_t step, int* nfp64) {
     constexpr int kB = 8;
     constexpr int kW = NC * kMW;  // warps that expand
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -1114,7 +1116,8 @@ __device__ void expand_eval(const Inst& I, MultiShared* L, MultiShared& S, int r
     __syncthreads();
     const int base = S.lbase;
     const int lim = min(nloc, kCandCap - base);  // (an overflowing set is dropped by the leader)
-    for (int k = tid; k < lim; k += kMT) L->cand[base + k] = eval_cand<PREC>(I, S.loc[k], step);
+    for (int k = tid; k < lim; k += kMT)
+        L->cand[base + k] = eval_cand<PREC>(I, S.loc[k], step, nfp64);
 }
 
 // Every CTA of the cluster: the round's picks (their neighbourhoods are disjoint), a
@@ -1233,6 +1236,7 @@ __global__ void __launch_bounds__(kMT, 1)
     G.need_scan = G.was_carried = G.was_forced = G.handoff = false;
 
     int32_t cmd = kCmdPlan;  // (the leader's next step)
+    int nfp64 = 0;           // this thread's FP64 evaluations of candidates
     bool known = false;      // every CTA has the next command already (S.next)
     bool held = false;       // this warp holds a staged pick:
     int held_j = 0, held_s = 0;  // its index and new spin,
@@ -1251,7 +1255,7 @@ __global__ void __launch_bounds__(kMT, 1)
         }
         if (cmd == kCmdStop) break;
         if (cmd == kCmdExpand) {
-            expand_eval<PREC, NC>(I, L, S, rank, step);
+            expand_eval<PREC, NC>(I, L, S, rank, step, &nfp64);
             csync();  // the candidates are in
             if (leader) cmd = decide(I, S, G);
         } else if (cmd == kCmdCompute) {
@@ -1270,6 +1274,10 @@ __global__ void __launch_bounds__(kMT, 1)
         }
     }
     csync();  // (no CTA leaves while another may still reach the leader's memory)
+    // the FP64 evaluations of the candidates count as the FP32 path's exact work
+    nfp64 = __reduce_add_sync(0xffffffffu, nfp64);
+    if ((threadIdx.x & 31) == 0 && nfp64)
+        atomicAdd((unsigned long long*)&st->rechecks, (unsigned long long)nfp64);
     if (!leader) return;
     if (tid == kHashT) {
         hash_queue(S, G, step, S.hq_n);
