@@ -122,7 +122,7 @@ TRAFFIC = {
                 "sources": ("fs_sweep.cu",), "sha256_16": "6f2859ae689aa7d3"},
     "k_relax_multi": {"per": "flip", "bytes_per_unit": 11841.0,
                       "sources": ("fs_relax_multi.cu", "fs_update.cuh", "fs_common.cuh"),
-                      "sha256_16": "28d384a96c3d3628"},
+                      "sha256_16": "1d4d0713b80815b1"},
     "k_relax": {"per": "flip", "bytes_per_unit": None,
                 "sources": ("fs_relax.cu", "fs_common.cuh"), "sha256_16": ""},
 }

@@ -16,29 +16,31 @@
 //  (c) no neighbour of an earlier pick got a new value that beats it (the flipped
 //      islands themselves are no longer flippable: their field is unchanged and
 //      their spin now opposes h_par's sign).
-// (a) and (b) are checked before the round's flips; all picks that pass them are
-// flipped at once (their neighbourhoods are disjoint), (c) is checked on the new
-// values, and the picks after the first that fails are flipped back (the exact
-// integer sums return to their old values and every key is evaluated again from
-// them). A round therefore always flips at least one island, and the flip
+// (a) and (b) are checked before the round's flips; the updates of all picks that
+// pass them are computed together (their neighbourhoods are disjoint), (c) is
+// checked on the new values, and only the prefix before the first pick that fails
+// is stored. A round therefore always flips at least one island, and the flip
 // sequence, the flips per field step and the hash equal the single-flip relax's.
 //
 // The max-tree over the keys is kept as an upper bound: keys that grow are pushed
-// up with atomic maxima, keys that shrink leave their ancestors stale, and every
-// node the candidate search expands is rebuilt from its children.
+// up with atomic maxima (also those of picks that are not stored), keys that
+// shrink leave their ancestors stale, and every node the candidate search expands
+// is rebuilt from its children.
 //
 // One thread-block cluster of NC CTAs per simulation and field step. A round is
-// two cluster-wide phases, each between two cluster barriers:
-//   expand: all CTAs expand the frontier the leader chose into the candidate
-//           islands and evaluate each one exactly (value, spin, row, centre);
-//   commit: all CTAs flip the picks, one warp a pick.
+// three cluster-wide phases, each ended by a cluster barrier:
+//   expand:  all CTAs expand the frontier the leader chose into the candidate
+//            islands and evaluate each one exactly (value, spin, row, centre);
+//   compute: all CTAs compute the picks' neighbour updates into shared memory, one
+//            warp a pick, and push the keys that grow up the tree;
+//   store:   the updates of the picks before the prefix are stored.
 // The leader (rank 0) holds the round's state in its shared memory and does the
-// serial work alone between the phases: after an expand it orders and tests the
-// candidates and chooses the picks; after a commit it finds the prefix, flips the
-// rest back, and chooses the next threshold and frontier from one level of the tree
-// (loaded whole). The other CTAs reach the leader's shared memory as distributed
-// shared memory; every decision that steers the control flow is read from the
-// leader after a barrier, so all CTAs take the same path.
+// serial work alone between the phases: after an expansion it orders and tests the
+// candidates and chooses the picks; after the computation it finds the prefix and
+// plans the next round (its threshold from one tree level, loaded whole, and the
+// frontier of nodes that reach it). The other CTAs reach the leader's shared memory
+// as distributed shared memory; every decision that steers the control flow is read
+// from the leader after a barrier, so all CTAs take the same path.
 #include <cuda_runtime.h>
 #include <cooperative_groups.h>
 #include <stdint.h>
