@@ -160,10 +160,17 @@ fs_status fs_set_stream(fs_sim* sim, void* stream);
  *   value that beats it. Faster on large arrays, where many of the largest values
  *   lie far apart. A field step whose rounds stay below 4 flips for 4 rounds in a
  *   row (a chain of flips that each make a neighbour the largest) is finished by
- *   the single-flip chain.
+ *   the single-flip chain. The rounds run on a cluster of 16 CTAs (16 SMs), or on
+ *   one CTA where a cluster of 16 does not fit.
+ * FS_RELAX_MULTI_CTA: the same rounds on one CTA (one SM), e.g. beside other work.
  * FS_RELAX_AUTO (default): multi-flip rounds from 262,144 islands on.
  * Batches always use single flips. Errors: FS_ERR_INVALID. */
-typedef enum { FS_RELAX_AUTO = 0, FS_RELAX_SINGLE = 1, FS_RELAX_MULTI = 2 } fs_relax_mode;
+typedef enum {
+    FS_RELAX_AUTO = 0,
+    FS_RELAX_SINGLE = 1,
+    FS_RELAX_MULTI = 2,
+    FS_RELAX_MULTI_CTA = 3
+} fs_relax_mode;
 fs_status fs_set_relax_mode(fs_sim* sim, int32_t mode);
 
 /* Device bytes fs_set_params(sim, p) would allocate: the simulation's state (the

@@ -22,7 +22,7 @@ FS_SQUARE_OPEN, FS_PINWHEEL_DIAMOND, FS_PINWHEEL_LUCKY_KNOT, FS_ISING = 3, 4, 5,
 FS_FP64, FS_FP32_RECHECK = 0, 1
 FS_CRITERION_ASTROID, FS_CRITERION_PARALLEL = 0, 1
 FS_ENCODE_SINUSOID, FS_ENCODE_SAWTOOTH, FS_ENCODE_ROTATION = 0, 1, 2
-FS_RELAX_AUTO, FS_RELAX_SINGLE, FS_RELAX_MULTI = 0, 1, 2
+FS_RELAX_AUTO, FS_RELAX_SINGLE, FS_RELAX_MULTI, FS_RELAX_MULTI_CTA = 0, 1, 2, 3
 
 EXPORTS = (
     "fs_last_error", "fs_hash_init", "fs_create_geometry", "fs_create_custom", "fs_destroy",
@@ -325,7 +325,7 @@ class Sim:
         return out
 
     def set_relax_mode(self, mode: int):
-        """FS_RELAX_AUTO, FS_RELAX_SINGLE or FS_RELAX_MULTI."""
+        """FS_RELAX_AUTO, FS_RELAX_SINGLE, FS_RELAX_MULTI or FS_RELAX_MULTI_CTA."""
         self._check(self._lib.fs_set_relax_mode(self._h, mode))
 
     def set_field_local(self, hx, hy):

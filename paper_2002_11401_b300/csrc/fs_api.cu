@@ -218,7 +218,8 @@ extern "C" void fs_destroy(fs_sim* sim) {
 
 extern "C" fs_status fs_set_relax_mode(fs_sim* sim, int32_t mode) {
     if (!sim) return fail(nullptr, FS_ERR_INVALID, "sim is NULL");
-    if (mode != FS_RELAX_AUTO && mode != FS_RELAX_SINGLE && mode != FS_RELAX_MULTI)
+    if (mode != FS_RELAX_AUTO && mode != FS_RELAX_SINGLE && mode != FS_RELAX_MULTI &&
+        mode != FS_RELAX_MULTI_CTA)
         return fail(sim, FS_ERR_INVALID, "unknown relax mode");
     sim->relax_mode = mode;
     return FS_OK;
@@ -860,7 +861,7 @@ cudaError_t collect_profile(fs_sim* sim) {
 // Whether the simulation's relaxes run as multi-flip rounds: by choice, or (auto)
 // for arrays large enough that many of the largest keys lie far apart.
 bool relax_multi(const fs_sim* sim) {
-    if (sim->relax_mode == FS_RELAX_MULTI) return true;
+    if (sim->relax_mode == FS_RELAX_MULTI || sim->relax_mode == FS_RELAX_MULTI_CTA) return true;
     if (sim->relax_mode == FS_RELAX_SINGLE) return false;
     return sim->n >= kMultiAutoIslands;
 }
@@ -882,7 +883,7 @@ cudaError_t enqueue_steps(fs_sim* sim, int64_t K, int resweep, cudaStream_t st) 
     R.n_work = 1;
     R.prec = sim->p.precision;
     R.smem_levels = relax_smem_levels(sim->n);
-    R.multi = relax_multi(sim) ? 1 : 0;
+    R.multi = !relax_multi(sim) ? 0 : sim->relax_mode == FS_RELAX_MULTI_CTA ? 2 : 1;
     cudaError_t e;
     if (sim->profiling && sim->ev_used + 3 * (size_t)K > 30000 &&
         (e = collect_profile(sim)) != cudaSuccess)

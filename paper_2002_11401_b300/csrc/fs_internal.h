@@ -86,7 +86,7 @@ struct fs_sim {
     int32_t e64 = 0, e32 = 0;
     int lanes = 16;
     int sweep_occ = 4;  // resident sweep CTAs per SM (4 or 5), set by the autotuner
-    int relax_mode = 0; // FS_RELAX_AUTO, FS_RELAX_SINGLE or FS_RELAX_MULTI
+    int relax_mode = 0; // FS_RELAX_AUTO, FS_RELAX_SINGLE, FS_RELAX_MULTI or FS_RELAX_MULTI_CTA
     int64_t rechecks = 0, fallbacks = 0;
     int64_t rounds = 0, idle_rounds = 0;  // multi-flip relax
     int64_t round_flips = 0, handoffs = 0;

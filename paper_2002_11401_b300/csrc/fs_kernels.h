@@ -32,7 +32,8 @@ struct RelaxLaunch {
     int smem_levels;      // dynamic shared memory for the upper tree levels
     int min_blocks = 1;   // 2: the build for two resident CTAs per SM (shared GPU)
     int multi = 0;        // 1: multi-flip rounds (fs_relax_multi.cu) first, then the
-                          // single-flip kernel for what they hand off
+                          // single-flip kernel for what they hand off; 2: the same,
+                          // the rounds on one CTA
 };
 
 cudaError_t launch_ext_table(const SweepLaunch& L, cudaStream_t st);

@@ -1377,7 +1377,7 @@ cudaError_t launch_relax_multi(const RelaxLaunch& L, cudaStream_t st) {
             ready[k].store(1);
         }
     }
-    if (use_cluster[k].load())
+    if (use_cluster[k].load() && L.multi != 2)
         return k ? launch_multi<1, kNC>(L, smem, st) : launch_multi<0, kNC>(L, smem, st);
     return k ? launch_multi<1, 1>(L, smem, st) : launch_multi<0, 1>(L, smem, st);
 }

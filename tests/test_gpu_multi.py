@@ -1,4 +1,5 @@
-"""The multi-flip relax (FS_RELAX_MULTI) against the FP64 oracle, flip for flip.
+"""The multi-flip relax (FS_RELAX_MULTI, FS_RELAX_MULTI_CTA) against the FP64
+oracle, flip for flip.
 
 A round flips several of the islands with the largest LHS at once, as long as
 each is the island the single-flip relax of Sec. "Dynamics" takes next (its exact
@@ -30,9 +31,9 @@ def B():
     return binding
 
 
-def _multi(B, w, prec, **over):
+def _multi(B, w, prec, mode=None, **over):
     sim = lib_sim(w, precision=prec, **over)
-    sim.set_relax_mode(B.FS_RELAX_MULTI)
+    sim.set_relax_mode(B.FS_RELAX_MULTI if mode is None else mode)
     return sim
 
 
@@ -40,18 +41,24 @@ def _compare(B, oracle, w, hx, hy, precs=(FP64, FP32), resweeps=(True,), **over)
     S = oracle_sim(oracle, w, **over)
     ref = S.run(np.ones(S.n, dtype=np.int8), hx, hy)
     assert ref["status"] == 0
-    for prec in precs:
-        for rs in resweeps:
-            sim = _multi(B, w, prec, **over)
-            got = sim.run_protocol(hx, hy, resweep=rs)
-            d = first_divergence(ref["log_step"], ref["log_spin"], got["log_step"],
-                                 got["log_spin"])
-            assert d is None, (prec, rs, d, ref["ties"])
-            assert (got["n_flips"], got["hash"]) == (ref["n_flips"], ref["hash"])
-            np.testing.assert_array_equal(got["flips_per_step"], ref["flips_per_step"])
-            np.testing.assert_array_equal(sim.spins(), ref["spins"])
-            sim.close()
+    # the rounds on a cluster of CTAs, and on one CTA (the build that runs where a
+    # cluster does not fit)
+    for mode in (B.FS_RELAX_MULTI, B.FS_RELAX_MULTI_CTA):
+        for prec in precs:
+            for rs in resweeps:
+                _check_one(B, w, hx, hy, ref, prec, rs, mode, **over)
     return ref
+
+
+def _check_one(B, w, hx, hy, ref, prec, rs, mode, **over):
+    sim = _multi(B, w, prec, mode, **over)
+    got = sim.run_protocol(hx, hy, resweep=rs)
+    d = first_divergence(ref["log_step"], ref["log_spin"], got["log_step"], got["log_spin"])
+    assert d is None, (mode, prec, rs, d, ref["ties"])
+    assert (got["n_flips"], got["hash"]) == (ref["n_flips"], ref["hash"])
+    np.testing.assert_array_equal(got["flips_per_step"], ref["flips_per_step"])
+    np.testing.assert_array_equal(sim.spins(), ref["spins"])
+    sim.close()
 
 
 def test_square16_sequence(B, oracle):
