@@ -583,7 +583,7 @@ def main():
     relax_alg = flip_alg_bytes(avg_deg, True) * flips_timed
     relax_ach = relax_alg / relax_s / 1e9 if relax_s > 0 else 0.0
     flips_per_launch = flips_timed / relax_launches
-    relax_kernel = "k_relax_multi" if n >= 262144 else "k_relax"  # the library's automatic choice
+    relax_kernel = "k_relax_multi" if n >= 32768 else "k_relax"  # the library's automatic choice
     roof_relax = {"kernel": relax_kernel, "bound": "hbm", "achieved": relax_ach, "peak": peak,
                   "unit": "GB/s", "frac": relax_ach / peak,
                   "traffic": traffic_of(relax_kernel, flips_per_launch),

@@ -163,7 +163,7 @@ fs_status fs_set_stream(fs_sim* sim, void* stream);
  *   the single-flip chain. The rounds run on a cluster of 16 CTAs (16 SMs), or on
  *   one CTA where a cluster of 16 does not fit.
  * FS_RELAX_MULTI_CTA: the same rounds on one CTA (one SM), e.g. beside other work.
- * FS_RELAX_AUTO (default): multi-flip rounds from 262,144 islands on.
+ * FS_RELAX_AUTO (default): multi-flip rounds from 32,768 islands on.
  * Batches always use single flips. Errors: FS_ERR_INVALID. */
 typedef enum {
     FS_RELAX_AUTO = 0,

@@ -33,7 +33,7 @@ struct Arena {
 
 // Arrays of at least this many islands relax in multi-flip rounds unless the
 // simulation chooses otherwise (fs_set_relax_mode).
-constexpr int64_t kMultiAutoIslands = 262144;
+constexpr int64_t kMultiAutoIslands = 32768;
 bool relax_multi(const fs_sim* sim);
 
 int choose_lanes(double avg_groups);

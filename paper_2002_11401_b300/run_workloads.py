@@ -4,6 +4,7 @@ runs it through the C ABI and prints one JSON line of measurements.
 
   python -m paper_2002_11401_b300.run_workloads square16|pinwheel300|kagome1000 \
       [--precision fp32|fp64] [--steps K] [--resweep 0|1] [--cells N]
+      [--relax auto|single|multi|multi_cta]
   python -m paper_2002_11401_b300.run_workloads ensemble512 [--members M]
   python -m paper_2002_11401_b300.run_workloads serving [--requests R] [--rate HZ]
 """
@@ -56,13 +57,15 @@ def sweep_bytes(info, fp32: bool, resweep: bool, thermal: bool) -> int:
     return (12 if fp32 else 20) * nnz + 8 * (n + 1) + n * per_island
 
 
-def run_single(name, precision, steps, resweep, cells=0):
+def run_single(name, precision, steps, resweep, cells=0, relax="auto"):
     w = dict(I.WORKLOADS[name])
     if cells:
         w["nx"] = w["ny"] = cells
     fp32 = precision == B.FS_FP32_RECHECK
     t0 = time.perf_counter()
     sim = make_sim(w, precision)
+    sim.set_relax_mode({"auto": B.FS_RELAX_AUTO, "single": B.FS_RELAX_SINGLE,
+                        "multi": B.FS_RELAX_MULTI, "multi_cta": B.FS_RELAX_MULTI_CTA}[relax])
     build_s = time.perf_counter() - t0
     lanes = sim.autotune()
     hx, hy = I.protocol_of(w["protocol"])
@@ -225,6 +228,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=0)
     ap.add_argument("--cells", type=int, default=0, help="override the array side (cells)")
     ap.add_argument("--resweep", type=int, default=1)
+    ap.add_argument("--relax", default="auto", choices=["auto", "single", "multi", "multi_cta"])
     ap.add_argument("--members", type=int, default=512)
     ap.add_argument("--sample", type=int, default=12)
     ap.add_argument("--requests", type=int, default=1000)
@@ -237,7 +241,8 @@ def main(argv=None):
     B.load()
     prec = B.FS_FP32_RECHECK if a.precision == "fp32" else B.FS_FP64
     if a.workload in I.WORKLOADS:
-        out = run_single(a.workload, prec, a.steps, bool(a.resweep), a.cells)
+        out = run_single(a.workload, prec, a.steps, bool(a.resweep), a.cells, a.relax)
+        out["relax"] = a.relax
     elif a.workload == "ensemble512":
         out = run_ensemble(a.members, a.sample)
     elif a.workload == "serving":
