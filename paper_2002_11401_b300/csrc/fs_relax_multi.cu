@@ -59,7 +59,8 @@ namespace {
 constexpr int kMT = 512;          // threads of a multi-flip relax CTA
 constexpr int kMW = kMT / 32;
 constexpr int kCandCap = 1024;    // candidate islands per round
-constexpr int kPickCap = 256;     // picks tested per round (one a warp of a cluster of 16)
+constexpr int kPickCap = 240;     // picks tested per round (one a warp of the cluster's 15
+                                  // CTAs besides the leader, a cluster of 16)
 constexpr int kSelMax = 4096;     // thresholds are chosen on the lowest level with at most this many nodes
 constexpr int kSelPer = kSelMax / kMT;
 constexpr int kM0 = 512;          // rank of the threshold node
@@ -136,13 +137,23 @@ struct MultiShared {
 constexpr int kStageOff = (int)((sizeof(MultiShared) + 15) & ~(size_t)15);
 
 constexpr int32_t kCmdExpand = 0;   // expand the frontier into candidates
-constexpr int32_t kCmdCompute = 1;  // compute the picks' flips (q in S.q)
-constexpr int32_t kCmdStore = 4;    // store the staged flips of the prefix (p in S.p)
+constexpr int32_t kCmdCompute = 1;  // compute the picks' flips (q in S.q), then store the
+                                    // prefix's (p in S.p)
 constexpr int32_t kCmdStop = 2;     // the relax of this launch is over
 
 __device__ __forceinline__ bool before(unsigned long long va, int32_t ia, unsigned long long vb,
                                        int32_t ib) {
     return va > vb || (va == vb && ia < ib);
+}
+
+// The two halves of a cluster barrier: this thread's writes so far are released to
+// the cluster (arrive), and it waits until every thread of the cluster has arrived
+// (wait, acquiring their writes). A thread waits before it arrives again.
+__device__ __forceinline__ void cluster_arrive() {
+    asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+    asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
 }
 
 // Appends the lanes' hits (island or node `c` where `hit`) to list[*cnt ...) (the
@@ -938,9 +949,10 @@ __device__ __forceinline__ void hash_queue(const MultiShared& S, Lead& G, uint32
 // earlier pick's neighbour overtakes (c); the eager picks after it flipped back (a
 // warp a pick); the prefix logged and queued for the hash in order; the threshold
 // carried to the next round, and the next round planned (S.next: what follows the
-// stores). Returns kCmdStore. Leader CTA-wide.
-template <int PREC>
-__device__ int32_t prefix_step(const Inst& I, MultiShared& S, Lead& G, uint32_t step) {
+// stores). In a cluster it arrives at a cluster barrier once the prefix is known, so
+// that the other CTAs store the prefix meanwhile. Leader CTA-wide.
+template <int PREC, int NC>
+__device__ void prefix_step(const Inst& I, MultiShared& S, Lead& G, uint32_t step) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int q = S.q;
     // the best of the earlier picks' neighbour values, an exclusive prefix maximum
@@ -982,6 +994,9 @@ __device__ int32_t prefix_step(const Inst& I, MultiShared& S, Lead& G, uint32_t 
     }
     __syncthreads();
     const int p = S.p;
+    // the prefix is out: the other CTAs store their picks' updates while the leader
+    // goes on (it waits for that barrier before the next one)
+    if constexpr (NC > 1) cluster_arrive();
     // the eager ones among the rest flipped back (the staged ones are dropped)
     for (int j = p + wid; j < q; j += kMW) {
         const Pick pk = S.pk[j];
@@ -1035,7 +1050,6 @@ __device__ int32_t prefix_step(const Inst& I, MultiShared& S, Lead& G, uint32_t 
     // the next threshold and frontier now (the tree holds the round's keys)
     const int32_t next = G.handoff ? kCmdStop : plan<PREC>(I, S, G, step, true);
     if (tid == 0) S.next = next;
-    return kCmdStore;
 }
 
 // Every CTA of the cluster: the frontier nodes L->front[L->f_buf] expanded into the
@@ -1134,7 +1148,11 @@ __device__ bool compute_picks(const Inst& I, MultiShared* L, MultiShared& S, Lea
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int q = L->q;
     bool held = false;
-    for (int j = rank + NC * wid; j < q; j += NC * kMW) {
+    // in a cluster the leader takes no pick (it plans the next round while the other
+    // CTAs store theirs): pick j goes to CTA 1 + j % (NC - 1)
+    constexpr int kPR = NC > 1 ? NC - 1 : 1;  // CTAs that take picks
+    const int prank = NC > 1 ? rank - 1 : 0;
+    for (int j = prank + kPR * wid; prank >= 0 && j < q; j += kPR * kMW) {
         const Pick pk = L->pk[j];
         const int64_t r0 = (int64_t)pk.rowq << 2, r1 = r0 + ((int64_t)pk.rowlenq << 2);
         unsigned long long xv;
@@ -1154,8 +1172,9 @@ __device__ bool compute_picks(const Inst& I, MultiShared* L, MultiShared& S, Lea
             L->xi[j] = xi;
         }
     }
-    // the leader's hash thread (its warp's first pick, NC (kMW - 1), lies past most
-    // rounds' picks): the queued flips of the earlier rounds into the hash
+    // the leader's hash thread (in a cluster its warp has no pick; alone, its first
+    // pick, kMW - 1, lies past most rounds' picks): the queued flips of the earlier
+    // rounds into the hash
     if (rank == 0 && threadIdx.x == kHashT) {
         hash_queue(S, G, step, S.hq_n);
         S.hq_n = 0;
@@ -1239,14 +1258,13 @@ __global__ void __launch_bounds__(kMT, 1)
 
     int32_t cmd = kCmdPlan;  // (the leader's next step)
     int nfp64 = 0;           // this thread's FP64 evaluations of candidates
-    bool known = false;      // every CTA has the next command already (S.next)
+    bool ready = false;      // every CTA has the next command already (S.next)
     bool held = false;       // this warp holds a staged pick:
     int held_j = 0, held_s = 0;  // its index and new spin,
     int64_t held_k = 0;      // its island
     for (;;) {
-        if (known) {
-            csync();  // the stores are in
-            known = false;
+        if (ready) {
+            ready = false;
         } else {
             if (leader) {
                 if (cmd == kCmdPlan) cmd = plan<PREC>(I, S, G, step, false);
@@ -1260,19 +1278,27 @@ __global__ void __launch_bounds__(kMT, 1)
             expand_eval<PREC, NC>(I, L, S, rank, step, &nfp64);
             csync();  // the candidates are in
             if (leader) cmd = decide(I, S, G);
-        } else if (cmd == kCmdCompute) {
+        } else {  // kCmdCompute
             held = compute_picks<PREC, NC>(I, L, S, G, stg, rank, step, &held_j, &held_k, &held_s);
             csync();  // the picks are computed
-            if (leader) cmd = prefix_step<PREC>(I, S, G, step);
-        } else {  // kCmdStore
-            if (held && held_j < L->p) store_pick(I, held_k, held_s, stg);
-            held = false;
-            cmd = L->next;
-            if (cmd == kCmdPlan) {
-                csync();  // the prefix is stored (before the leader plans)
+            if constexpr (NC > 1) {
+                if (leader) {
+                    prefix_step<PREC, NC>(I, S, G, step);  // (arrives once the prefix is out)
+                    cluster_wait();
+                } else {
+                    // the picks before the prefix stored while the leader plans
+                    cluster_arrive();
+                    cluster_wait();  // the prefix is out
+                    if (held && held_j < L->p) store_pick(I, held_k, held_s, stg);
+                }
             } else {
-                known = true;  // (planned already: one barrier, then on)
+                prefix_step<PREC, NC>(I, S, G, step);
+                if (held && held_j < S.p) store_pick(I, held_k, held_s, stg);
             }
+            held = false;
+            csync();  // the prefix is stored, the next round planned
+            cmd = L->next;
+            ready = cmd != kCmdPlan;  // (a plan that waited for the stores comes next)
         }
     }
     csync();  // (no CTA leaves while another may still reach the leader's memory)
