@@ -120,9 +120,9 @@ TRAFFIC = {
     # step 5 of that rotation; both are scaled to a full launch by their units
     "k_sweep": {"per": "neighbour pair", "bytes_per_unit": 13.39,
                 "sources": ("fs_sweep.cu",), "sha256_16": "6f2859ae689aa7d3"},
-    "k_relax_multi": {"per": "flip", "bytes_per_unit": 11841.0,
+    "k_relax_multi": {"per": "flip", "bytes_per_unit": 11840.0,
                       "sources": ("fs_relax_multi.cu", "fs_update.cuh", "fs_common.cuh"),
-                      "sha256_16": "1d4d0713b80815b1"},
+                      "sha256_16": "482884c1584587c8"},
     "k_relax": {"per": "flip", "bytes_per_unit": None,
                 "sources": ("fs_relax.cu", "fs_common.cuh"), "sha256_16": ""},
 }
