@@ -379,8 +379,8 @@ fs_status fs_correlation(fs_sim* sim, double rmax, double bin_width, int32_t nbi
  *   sim      built simulation (fs_set_params done); its spins are not used or
  *            changed; n = its island count, at most 2,097,152 (2^21)
  *   d_spins  device, n int8 in {-1,+1} (values are not checked)
- *   d_lhs    device output, n doubles: the Eq. 5 LHS of every flippable island,
- *            0 for the others
+ *   d_lhs    device output, n doubles: the astroid left-hand side (the value
+ *            fs_get_lhs reports) of every flippable island, 0 for the others
  *   d_best   device output, one int64: the flippable island with the largest
  *            LHS (lowest index on ties), or -1 when none is flippable
  *   stream   cudaStream_t to queue on (NULL = legacy default); the call returns
