@@ -414,9 +414,12 @@ fs_status fs_batch_run_protocol(fs_sim* const* sims, int32_t n, const double* hx
 /* ---- Continuous-batching server ---------------------------------------------
  * Builder threads admit requests while their estimated device footprint fits the
  * budget and build them on side streams; every admitted request then gets a
- * stream of its own with its whole protocol queued, so requests that arrive while
- * others run start as soon as they are built and all of them overlap on the
- * device. Admission order: a request waiting longer than 10 s first (oldest
+ * stream of its own on which a graph of a few field steps of its protocol is
+ * launched again and again (two launches queued at most) until the protocol is
+ * done, so requests that arrive while others run start as soon as they are built
+ * and all of them overlap on the device. Builds run at the highest stream
+ * priority and larger requests (longer flip chains) at higher priorities than
+ * smaller ones. Admission order: a request waiting longer than 10 s first (oldest
  * first), else the least estimated work (islands x field steps). Every request
  * relaxes with the single-flip chain (FS_RELAX_SINGLE: one CTA, one SM), which
  * makes the most flips per SM on a shared device. Results equal those of running

@@ -672,16 +672,12 @@ __device__ int64_t pick_warp(const Inst& I, const Levels& L, RecheckShared& R, D
     return kPickBounds;
 }
 
-// MINB: resident CTAs per SM the build is made for. One CTA per SM (registers as
-// needed) for a relax that has the GPU to itself; two (at most 128 registers a
-// thread) for a batch with more members than SMs, so that each SM interleaves two
-// latency-bound chains (measured: 24.3M vs 20.9M flips/s on the 512-member FP32
-// ensemble; the server's requests, fewer at a time, run faster with one).
-template <int PREC, int MINB>
-__global__ void __launch_bounds__(kT, MINB)
-    k_relax(const Inst* __restrict__ tab, const int32_t* __restrict__ work, int n_work,
-            int smem_levels, int cont) {
-    extern __shared__ unsigned long long sm_levels[];
+// The relax of one simulation's field step by the whole CTA (the body of k_relax,
+// and a work item of the persistent batch kernel). sm_levels: the dynamic shared
+// memory for the upper tree levels, smem_levels bytes.
+template <int PREC>
+__device__ __forceinline__ void relax_sim(const Inst& I, int smem_levels, int cont,
+                                          unsigned long long* sm_levels) {
     __shared__ int64_t sh_k;
     __shared__ Prediction P;
     __shared__ int64_t sh_e0, sh_e1;
@@ -694,7 +690,6 @@ __global__ void __launch_bounds__(kT, MINB)
     __shared__ RecheckShared R;
     __shared__ Dirty D;
 
-    const Inst& I = tab[work[blockIdx.x]];
     InstState* st = I.st;
     // cont: launched after the multi-flip relax of the same step, which either
     // finished it (nothing to do) or handed the rest over (continue from its flips)
@@ -934,6 +929,19 @@ __global__ void __launch_bounds__(kT, MINB)
         st->init = 0;
         st->t = t + 1;
     }
+}
+
+// MINB: resident CTAs per SM the build is made for. One CTA per SM (registers as
+// needed) for a relax that has the GPU to itself; two (at most 128 registers a
+// thread) for a batch with more members than SMs, so that each SM interleaves two
+// latency-bound chains (measured: 24.3M vs 20.9M flips/s on the 512-member FP32
+// ensemble; the server's requests, fewer at a time, run faster with one).
+template <int PREC, int MINB>
+__global__ void __launch_bounds__(kT, MINB)
+    k_relax(const Inst* __restrict__ tab, const int32_t* __restrict__ work, int n_work,
+            int smem_levels, int cont) {
+    extern __shared__ unsigned long long sm_levels[];
+    relax_sim<PREC>(tab[work[blockIdx.x]], smem_levels, cont, sm_levels);
 }
 
 // Total field, LHS and its bounds for every island at the current state (FS_FP64

@@ -5,13 +5,18 @@
 //   - builder threads admit pending requests while their estimated device
 //     footprint fits the budget, and build each (geometry, h_k draw, neighbour
 //     tensors) on their own streams, overlapping the running iterations;
-//   - the builder also captures the request's whole protocol (per field step:
-//     external-field table, sweep, relax) as one CUDA graph;
+//   - the builder also captures a few field steps of the request's protocol (per
+//     field step: external-field table, sweep, relax) as one CUDA graph; the
+//     kernels take the step index from the simulation's device state, so the
+//     same graph, launched again, runs the next steps;
 //   - a worker thread launches every admitted request's graph on a stream of its
-//     own, so requests advance independently and their
-//     sweeps and relaxes overlap on the device (requests that arrive while others
-//     run start as soon as they are built); finished requests are retired as their
-//     completion events fire: final state read back, memory freed, budget
+//     own, at most two launches in flight per request and the next one as soon as
+//     one ends, so requests advance independently and their sweeps and relaxes
+//     overlap on the device (requests that arrive while others run start as soon
+//     as they are built), while the device's queues hold only a few steps of each
+//     request (a whole protocol queued at once held up every later launch, the
+//     builds' included, until it had run); finished requests are retired as
+//     their last launch ends: final state read back, memory freed, budget
 //     returned.
 // Device waits are all host-side stream synchronisations; no kernel waits on the
 // host.
@@ -51,7 +56,8 @@ struct Job {
     fs_result res{};
     double* d_hx = nullptr;
     double* d_hy = nullptr;
-    cudaGraphExec_t exec = nullptr;  // the request's whole protocol, one launch
+    cudaGraphExec_t exec = nullptr;  // kChunk field steps of the request's protocol
+    int64_t launches = 0;            // launches of it that run the whole protocol
 };
 
 // Device bytes of one request before it is built: per island ~156 B of state
@@ -89,6 +95,11 @@ size_t estimate_bytes(const fs_request& r) {
 // first), else the one with the least estimated work (islands x field steps), so
 // that short requests are not queued behind long ones and long ones still start.
 constexpr double kAgeS = 10.0;
+
+// Field steps a request's graph holds; the worker keeps at most kInFlight launches
+// of it queued.
+constexpr int64_t kChunk = 8;
+constexpr int kInFlight = 2;
 
 double work_of(const fs_request& r) { return islands_of(r) * (double)std::max<int64_t>(r.K, 1); }
 
@@ -201,8 +212,9 @@ void builder_loop(fs_server* S, int which) {
             S->cv_build.notify_all();
             continue;
         }
-        // descriptor and fresh state on the device, then the protocol captured as one
-        // graph (K field steps: external-field table, sweep, relax)
+        // descriptor and fresh state on the device, then kChunk field steps captured
+        // as one graph (external-field table, sweep, relax per step; a kernel whose
+        // step lies past K returns at once)
         if (st == FS_OK) {
             Inst I = sim->inst;
             I.phx = j->d_hx;
@@ -226,7 +238,9 @@ void builder_loop(fs_server* S, int which) {
                       cudaStreamBeginCapture(bst, cudaStreamCaptureModeThreadLocal) ==
                           cudaSuccess;
             if (ok) {
-                const cudaError_t le = enqueue_steps(sim, j->req.K, 1, bst);
+                const int64_t c = std::min<int64_t>(std::max<int64_t>(j->req.K, 1), kChunk);
+                j->launches = std::max<int64_t>((j->req.K + c - 1) / c, 1);
+                const cudaError_t le = enqueue_steps(sim, j->req.K > 0 ? c : 0, 1, bst);
                 const cudaError_t ce = cudaStreamEndCapture(bst, &graph);
                 ok = le == cudaSuccess && ce == cudaSuccess && graph &&
                      cudaGraphInstantiate(&j->exec, graph, 0) == cudaSuccess;
@@ -262,19 +276,58 @@ void builder_loop(fs_server* S, int which) {
     }
 }
 
-// The worker: every admitted request's protocol graph is launched on a stream of
-// its own, followed by an event; requests therefore advance independently and
-// their kernels overlap on the device. Completion is found by polling the events.
+// The worker: every admitted request's graph is launched on a stream of its own,
+// each launch followed by an event, kInFlight at most queued; requests therefore
+// advance independently and their kernels overlap on the device. Progress and
+// completion are found by polling the events.
 void worker_loop(fs_server* S) {
     cudaSetDevice(S->device);
     struct Active {
         std::shared_ptr<Job> job;
-        cudaStream_t stream;
-        cudaEvent_t done;
+        cudaStream_t stream = nullptr;
+        int prio = 0;
+        cudaEvent_t ev[kInFlight] = {};
+        int64_t launched = 0, ended = 0;  // launches queued, launches ended
+        cudaError_t err = cudaSuccess;
     };
     std::vector<Active> active;
-    std::vector<cudaStream_t> free_streams;
+    std::map<int, std::vector<cudaStream_t>> free_streams;  // by priority
     std::vector<cudaEvent_t> free_events;
+    // Larger requests run at higher stream priorities (the builders' level excepted):
+    // their flip chains are the longest, and a relax launch of a higher priority takes
+    // the next free SM before the CTAs of the other requests' sweeps.
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    auto prio_of = [&](int64_t n) {
+        const int levels = std::max(0, prio_lo - prio_hi - 1);  // below the builders'
+        const double lg = std::log2((double)std::max<int64_t>(n, 1));
+        const int up = std::min(levels, std::max(0, (int)(lg - 14.0) / 2));
+        return prio_lo - up;
+    };
+    auto take_event = [&](cudaEvent_t* e) {
+        if (!free_events.empty()) {
+            *e = free_events.back();
+            free_events.pop_back();
+            return true;
+        }
+        return cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    };
+    auto give_back = [&](Active& a) {
+        if (a.stream) free_streams[a.prio].push_back(a.stream);
+        for (cudaEvent_t& e : a.ev)
+            if (e) free_events.push_back(e);
+    };
+    // queues launches until kInFlight are in flight or all are queued
+    auto top_up = [&](Active& a) {
+        const Job& j = *a.job;
+        while (a.err == cudaSuccess && a.launched < j.launches &&
+               a.launched - a.ended < kInFlight) {
+            cudaError_t e = cudaGraphLaunch(j.exec, a.stream);
+            if (e == cudaSuccess) e = cudaEventRecord(a.ev[a.launched % kInFlight], a.stream);
+            if (e != cudaSuccess) a.err = e;
+            ++a.launched;
+        }
+    };
     for (;;) {
         std::vector<std::shared_ptr<Job>> joining;
         {
@@ -292,26 +345,24 @@ void worker_loop(fs_server* S) {
             }
         }
         for (auto& j : joining) {
-            Active a{j, nullptr, nullptr};
-            if (!free_streams.empty()) {
-                a.stream = free_streams.back();
-                free_streams.pop_back();
-            } else if (cudaStreamCreateWithFlags(&a.stream, cudaStreamNonBlocking) !=
+            Active a;
+            a.job = j;
+            a.prio = prio_of(j->sim->n);
+            auto& pool = free_streams[a.prio];
+            if (!pool.empty()) {
+                a.stream = pool.back();
+                pool.pop_back();
+            } else if (cudaStreamCreateWithPriority(&a.stream, cudaStreamNonBlocking, a.prio) !=
                        cudaSuccess) {
                 a.stream = nullptr;
             }
-            if (!free_events.empty()) {
-                a.done = free_events.back();
-                free_events.pop_back();
-            } else if (cudaEventCreateWithFlags(&a.done, cudaEventDisableTiming) != cudaSuccess) {
-                a.done = nullptr;
-            }
+            bool ok = a.stream != nullptr;
+            for (cudaEvent_t& e : a.ev) ok = ok && take_event(&e);
             fs_sim* sim = j->sim;
-            bool ok = a.stream && a.done;
             if (ok) {
                 sim->stream = a.stream;
-                ok = cudaGraphLaunch(j->exec, a.stream) == cudaSuccess &&
-                     cudaEventRecord(a.done, a.stream) == cudaSuccess;
+                top_up(a);
+                ok = a.err == cudaSuccess;
             }
             if (!ok) {
                 if (a.stream) cudaStreamSynchronize(a.stream);
@@ -322,25 +373,31 @@ void worker_loop(fs_server* S) {
                 S->used -= j->reserved;
                 S->cv_build.notify_all();
                 finish(S, j, FS_ERR_CUDA);
-                if (a.stream) free_streams.push_back(a.stream);
-                if (a.done) free_events.push_back(a.done);
+                give_back(a);
                 continue;
             }
             active.push_back(a);
         }
-        // retire finished requests
+        // advance every request; retire the finished ones
         std::vector<Active> keep;
         for (auto& a : active) {
-            const cudaError_t q = cudaEventQuery(a.done);
-            if (q == cudaErrorNotReady) {
+            while (a.err == cudaSuccess && a.ended < a.launched) {
+                const cudaError_t q = cudaEventQuery(a.ev[a.ended % kInFlight]);
+                if (q == cudaErrorNotReady) break;
+                if (q != cudaSuccess) a.err = q;
+                ++a.ended;
+            }
+            top_up(a);
+            if (a.err == cudaSuccess && a.ended < a.job->launches) {
                 keep.push_back(a);
                 continue;
             }
             auto& j = a.job;
             // the request's work has ended: read its state (and spins) back now; a
             // copy into pageable memory queued earlier would have blocked this thread
+            cudaError_t e = a.err;
+            if (e != cudaSuccess) cudaStreamSynchronize(a.stream);
             InstState& st = j->sim->state_host;
-            cudaError_t e = q;
             if (e == cudaSuccess)
                 e = cudaMemcpy(&st, j->sim->d_state, sizeof(InstState), cudaMemcpyDeviceToHost);
             if (e == cudaSuccess && j->spins_out)
@@ -356,8 +413,7 @@ void worker_loop(fs_server* S) {
             S->used -= bytes;
             S->cv_build.notify_all();
             finish(S, j, status);
-            free_streams.push_back(a.stream);
-            free_events.push_back(a.done);
+            give_back(a);
         }
         active.swap(keep);
     }
@@ -367,10 +423,10 @@ void worker_loop(fs_server* S) {
         fs_destroy(a.job->sim);
         a.job->sim = nullptr;
         finish(S, a.job, FS_ERR_STATE);
-        free_streams.push_back(a.stream);
-        free_events.push_back(a.done);
+        give_back(a);
     }
-    for (cudaStream_t st : free_streams) cudaStreamDestroy(st);
+    for (auto& pool : free_streams)
+        for (cudaStream_t st : pool.second) cudaStreamDestroy(st);
     for (cudaEvent_t e : free_events) cudaEventDestroy(e);
 }
 
@@ -392,9 +448,14 @@ extern "C" fs_status fs_server_create(size_t hbm_budget, int32_t max_active, fs_
     const int nb = 8;  // builder threads, each with its own stream
     S->build_st.resize(nb, nullptr);
     bool ok = cudaStreamCreateWithFlags(&S->main_st, cudaStreamNonBlocking) == cudaSuccess;
+    // builds run at the highest stream priority: their kernels and copies are short
+    // steps between host synchronisations, which would otherwise wait behind the
+    // running requests' sweeps for every SM they need
+    int prio_lo = 0, prio_hi = 0;
+    if (ok) ok = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) == cudaSuccess;
     for (int b = 0; b < nb && ok; ++b)
-        ok = cudaStreamCreateWithFlags(&S->build_st[(size_t)b], cudaStreamNonBlocking) ==
-             cudaSuccess;
+        ok = cudaStreamCreateWithPriority(&S->build_st[(size_t)b], cudaStreamNonBlocking,
+                                          prio_hi) == cudaSuccess;
     if (!ok) {
         delete S;
         return FS_ERR_CUDA;

@@ -1,95 +1,30 @@
 // fs_sweep.cu - the full field-and-margin sweep (Sec. "Dynamics": at each
 // simulation step the total field on every island is calculated; Eq. 2, 3, 5, 6).
 //
-// One warp owns 32 consecutive islands (one node of the first tree level).
-// Sub-warps of W lanes stream one CSR row each: every lane reads a group of four
-// entries with 16-byte loads (column indices, then the fixed-point (P, Q)
-// coefficients), gathers the four spins, and accumulates the exact integer sums
-// s_j P_ij and s_j Q_ij; a shuffle butterfly inside the sub-warp finishes the row.
-// The per-row sums are staged in shared memory so that lane q then evaluates
-// island q: external and thermal fields, Eq. 5/6, the argmax key. A warp max
-// gives the first tree level; the last warp to finish a group of 32 sibling
-// nodes builds their parent (fenced counter), so the whole max-tree is ready
-// when the kernel ends.
-//
-// With resweep off, the exact sums kept up to date by the flips are read instead
-// of recomputed; integer sums make both modes bit-identical.
+// One warp owns 32 consecutive islands (one node of the first tree level); the
+// task itself (row sums, evaluation, keys, the tree above it) is sweep_task in
+// fs_sweep_task.cuh. One launch covers every task of every simulation of a table,
+// so the whole max-tree is ready when the kernel ends.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "fs_common.cuh"
 #include "fs_kernels.h"
+#include "fs_sweep_task.cuh"
 
 namespace fs {
 
 namespace {
 
-constexpr int kSweepThreads = 256;
-constexpr int kSweepWarps = kSweepThreads / 32;
-
-__device__ __forceinline__ int find_inst(const int64_t* __restrict__ start, int n_inst,
-                                         int64_t task) {
-    int lo = 0, hi = n_inst - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (start[mid] <= task)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ int sgn_sel(int8_t s, int v) { return s > 0 ? v : -v; }
-__device__ __forceinline__ long long sgn_sel(int8_t s, long long v) { return s > 0 ? v : -v; }
-
-// Warp maximum of 64-bit keys (every lane gets it): the largest upper half, then
-// among those the largest lower half.
-__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v) {
-    const unsigned hi = (unsigned)(v >> 32), lo = (unsigned)v;
-    const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
-    const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
-    return ((unsigned long long)mh << 32) | ml;
-}
-
-// Called by a full warp after lane 0 wrote node `idx` of level `lev`: the last
-// of its siblings to arrive builds the parent, and so on up to the root.
-__device__ void propagate_up(const Inst& I, unsigned* __restrict__ tcnt, int lev, int64_t idx) {
-    const int lane = threadIdx.x & 31;
-    while (lev + 1 < I.nlev) {
-        const int64_t parent = idx >> 5;
-        const int64_t first = parent << 5;
-        const int64_t last = min((int64_t)I.lvl_n[lev], first + 32);
-        const unsigned nchild = (unsigned)(last - first);
-        __threadfence();
-        unsigned old = 0;
-        if (lane == 0) old = atomicAdd(&tcnt[I.lvl_off[lev + 1] + parent], 1u);
-        old = __shfl_sync(0xffffffffu, old, 0);
-        if (old + 1 != nchild) return;
-        if (lane == 0) tcnt[I.lvl_off[lev + 1] + parent] = 0u;
-        __threadfence();
-        unsigned long long v = 0ull;
-        if (first + lane < last) v = __ldcg(&I.tree[I.lvl_off[lev] + first + lane]);
-        v = warp_max_key(v);
-        if (lane == 0) I.tree[I.lvl_off[lev + 1] + parent] = v;
-        ++lev;
-        idx = parent;
-    }
-}
-
-// MODE 0: margins only (exact sums kept by the flips); MODE 1: resweep the sums of
-// the simulation's width. A simulation whose state says `init` (sums not set up
-// yet) is swept in any mode, and on the FP32 path both widths are summed.
 // OCC resident CTAs per SM: 4 (registers as needed) or 5 (at most 51 registers a
 // thread, some spilled): the latter puts 5920 warps on the 148 SMs, one wave for
-// an array of up to 189,000 islands. The autotuner picks.
+// an array of up to 189,000 islands. The autotuner picks. MODE as sweep_task.
 template <int PREC, int W, int MODE, int OCC>
 __global__ void __launch_bounds__(kSweepThreads, OCC)
     k_sweep(const Inst* __restrict__ tab, const int64_t* __restrict__ task_start, int n_inst,
             int64_t total_tasks, unsigned* const* __restrict__ tcnts) {
     __shared__ int sums32[PREC == 1 ? kSweepWarps : 1][32][2];
     __shared__ long long sums64[kSweepWarps][32][2];
-    const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int64_t gw = (blockIdx.x * (int64_t)kSweepThreads + threadIdx.x) >> 5;
     if (gw >= total_tasks) return;
@@ -99,146 +34,8 @@ __global__ void __launch_bounds__(kSweepThreads, OCC)
     const int64_t t = st->t;
     if (st->status != ST_OK || t >= I.K) return;
     const int64_t lt = gw - task_start[inst];
-    const int64_t r0 = lt << 5;
-    const bool init = st->init != 0;
-    const bool SUM32 = PREC == 1 && (MODE == 1 || init);
-    const bool SUM64 = PREC == 0 ? (MODE == 1 || init) : init;
-
-    if (SUM32 || SUM64) {
-        constexpr int R = 32 / W;
-        const int sub = lane / W, sl = lane % W;
-        const int4* __restrict__ col4 = reinterpret_cast<const int4*>(I.col);
-        for (int q = sub; q < 32; q += R) {
-            const int64_t i = r0 + q;
-            int bp = 0, bq = 0;
-            long long ap = 0, aq = 0;
-            if (i < I.n) {
-                const int64_t g0 = __ldg(&I.rp[i]) >> 2, g1 = __ldg(&I.rp[i + 1]) >> 2;
-                for (int64_t g = g0 + sl; g < g1; g += W) {
-                    const int4 c = __ldg(&col4[g]);
-                    const int8_t s0 = __ldg(&I.s[c.x]), s1 = __ldg(&I.s[c.y]);
-                    const int8_t s2 = __ldg(&I.s[c.z]), s3 = __ldg(&I.s[c.w]);
-                    if (PREC == 1 && SUM32) {
-                        const int4* p4 = reinterpret_cast<const int4*>(I.pq32) + 2 * g;
-                        const int4 a = __ldg(p4), b = __ldg(p4 + 1);
-                        bp += sgn_sel(s0, a.x) + sgn_sel(s1, a.z) + sgn_sel(s2, b.x) +
-                              sgn_sel(s3, b.z);
-                        bq += sgn_sel(s0, a.y) + sgn_sel(s1, a.w) + sgn_sel(s2, b.y) +
-                              sgn_sel(s3, b.w);
-                    }
-                    if (SUM64) {
-                        const longlong2* p = I.pq64 + 4 * g;
-                        const longlong2 v0 = __ldg(p), v1 = __ldg(p + 1);
-                        const longlong2 v2 = __ldg(p + 2), v3 = __ldg(p + 3);
-                        ap += sgn_sel(s0, v0.x) + sgn_sel(s1, v1.x) + sgn_sel(s2, v2.x) +
-                              sgn_sel(s3, v3.x);
-                        aq += sgn_sel(s0, v0.y) + sgn_sel(s1, v1.y) + sgn_sel(s2, v2.y) +
-                              sgn_sel(s3, v3.y);
-                    }
-                }
-            }
-#pragma unroll
-            for (int o = W / 2; o > 0; o >>= 1) {
-                if (SUM32) {
-                    bp += __shfl_xor_sync(0xffffffffu, bp, o);
-                    bq += __shfl_xor_sync(0xffffffffu, bq, o);
-                }
-                if (SUM64) {
-                    ap += __shfl_xor_sync(0xffffffffu, ap, o);
-                    aq += __shfl_xor_sync(0xffffffffu, aq, o);
-                }
-            }
-            if (sl == 0) {
-                if (PREC == 1 && SUM32) {
-                    sums32[wib][q][0] = bp;
-                    sums32[wib][q][1] = bq;
-                }
-                if (SUM64) {
-                    sums64[wib][q][0] = ap;
-                    sums64[wib][q][1] = aq;
-                }
-            }
-        }
-        __syncwarp();
-    }
-
-    const int64_t i = r0 + lane;
-    unsigned long long node = 0ull;
-    if (i < I.n) {
-        const uint32_t step = I.step0 + (uint32_t)t;
-        const int si = I.s[i];
-        const uint16_t ci = I.cls[i];
-        const float2 rbc = I.rbc32[i];
-        const int64_t ra = __ldg(&I.rp[i]), rb = __ldg(&I.rp[i + 1]);
-        // the external field on the island's frame: the class table of the global
-        // field, or with a local or spatial field the island's own projection,
-        // kept for the relax
-        double2 e64 = I.ext64[ci];
-        float2 e32 = I.ext32[ci];
-        if (I.exti64) {
-            const double2 lab = ext_lab(I, i, step, I.phx[t], I.phy[t]);
-            e64 = ext_proj(lab.x, lab.y, I.cs64[ci]);
-            e32 = make_float2(__double2float_rn(e64.x), __double2float_rn(e64.y));
-            I.exti64[i] = e64;
-            I.exti32[i] = e32;
-        }
-        float2 th = make_float2(0.0f, 0.0f);
-        if (I.sigma > 0.0) {
-            th = thermal32(I, i, step);
-            I.th32[i] = th;
-        }
-        longlong2 h64;
-        if (SUM64) {
-            h64 = make_longlong2(sums64[wib][lane][0], sums64[wib][lane][1]);
-            I.h64[i] = h64;
-        }
-        if constexpr (PREC == 1) {
-            // (without the resweep, the 32-bit sums kept by the flips)
-            const int2 h = SUM32 ? make_int2(sums32[wib][lane][0], sums32[wib][lane][1])
-                                 : rec_load(I, i).h32;
-            const float dp = __fmul_rn(__int2float_rn(h.x), I.inv32);
-            const float dq = __fmul_rn(__int2float_rn(h.y), I.inv32);
-            const Eval32 e = eval32(I, si, dp, dq, rbc, e32, th.x, th.y);
-            float lo = e.certain ? e.lo : -1.0f;
-            node = e.possible ? key32_of(e.hi, i) : 0ull;
-            double x = e.possible ? -1.0 : 0.0;
-            // An island that may be flippable may meet an exact comparison in the
-            // relax: its FP64 thermal draw is taken and kept here, off the flip chain.
-            double tp = 0.0, tq = 0.0;
-            if (I.sigma > 0.0 && e.possible) thermal64_kept(I, i, step, &tp, &tq);
-            if (e.possible && !e.certain) {
-                // within its band of the threshold or of the sign change: FP64 now
-                if (!SUM64) h64 = I.h64[i];
-                const Eval64 f = eval64(I, si, h64.x, h64.y, I.rbc64[i], e64, tp, tq);
-                x = f.flippable ? f.lhs : 0.0;
-                node = x > 0.0 ? key32_of(__double2float_ru(x), i) : 0ull;
-                lo = x > 0.0 ? __double2float_rd(x) : -1.0f;
-            }
-            I.key32[i] = node;
-            I.key64[i] = x;
-            rec_store(I, i, h, lo, si, rbc, ra, rb, ci);
-        } else {
-            if (!SUM64) h64 = I.h64[i];
-            const float dp = __fmul_rn(__ll2float_rn(h64.x), I.inv64f);
-            const float dq = __fmul_rn(__ll2float_rn(h64.y), I.inv64f);
-            const Eval32 e = eval32(I, si, dp, dq, rbc, e32, th.x, th.y);
-            double x = 0.0;
-            if (e.possible) {
-                double tp = 0.0, tq = 0.0;
-                if (I.sigma > 0.0) thermal64_kept(I, i, step, &tp, &tq);
-                const Eval64 f = eval64(I, si, h64.x, h64.y, I.rbc64[i], e64, tp, tq);
-                if (f.flippable) x = f.lhs;
-            }
-            I.key64[i] = x;
-            node = x > 0.0 ? key32_of(__double2float_ru(x), i) : 0ull;
-            I.key32[i] = node;
-            rec_store(I, i, make_int2(0, 0), x > 0.0 ? __double2float_rd(x) : -1.0f, si, rbc, ra,
-                      rb, ci);
-        }
-    }
-    node = warp_max_key(node);
-    if (lane == 0) I.tree[I.lvl_off[0] + lt] = node;
-    propagate_up(I, tcnts[inst], 0, lt);
+    sweep_task<PREC, W, MODE, false>(I, tcnts[inst], t, lt, st->init != 0,
+                                     sums32[PREC == 1 ? wib : 0], sums64[wib]);
 }
 
 // Projections of the current step's external field on every angle class of every
