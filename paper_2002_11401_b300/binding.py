@@ -23,6 +23,7 @@ FS_FP64, FS_FP32_RECHECK = 0, 1
 FS_CRITERION_ASTROID, FS_CRITERION_PARALLEL = 0, 1
 FS_ENCODE_SINUSOID, FS_ENCODE_SAWTOOTH, FS_ENCODE_ROTATION = 0, 1, 2
 FS_RELAX_AUTO, FS_RELAX_SINGLE, FS_RELAX_MULTI, FS_RELAX_MULTI_CTA = 0, 1, 2, 3
+FS_BATCH_AUTO, FS_BATCH_PERSISTENT, FS_BATCH_PER_STEP = 0, 1, 2
 
 EXPORTS = (
     "fs_last_error", "fs_hash_init", "fs_create_geometry", "fs_create_custom", "fs_destroy",
@@ -34,6 +35,7 @@ EXPORTS = (
     "fs_set_profiling", "fs_get_profile", "fs_eval_argmax_static", "fs_autotune",
     "fs_workspace_bytes", "fs_bind_workspace", "fs_set_field_local", "fs_set_field_spatial",
     "fs_set_sigma_series", "fs_encode", "fs_correlation", "fs_set_relax_mode",
+    "fs_batch_run_protocol_ex",
 )
 
 
@@ -115,6 +117,7 @@ def load():
             "fs_get_info": ([P, P], i32),
             "fs_get_csr": ([P, P, P, P, P], i32),
             "fs_batch_run_protocol": ([P, i32, P, P, i64, i32, P, P, P, P], i32),
+            "fs_batch_run_protocol_ex": ([P, i32, P, P, i64, i32, i32, P, P, P, P], i32),
             "fs_server_create": ([C.c_size_t, i32, P], i32),
             "fs_server_submit": ([P, P, P], i32),
             "fs_server_poll": ([P, u64, P], i32),
@@ -380,8 +383,10 @@ def encode(kind: int, inputs, period: int, h_lo: float, h_hi: float, angle_deg: 
     return hx[:m * period].copy(), hy[:m * period].copy()
 
 
-def batch_run_protocol(sims, hx, hy, *, resweep: bool = True, with_counts: bool = False):
-    """Runs every simulation of `sims` through one protocol together."""
+def batch_run_protocol(sims, hx, hy, *, resweep: bool = True, with_counts: bool = False,
+                       schedule: int = FS_BATCH_AUTO):
+    """Runs every simulation of `sims` through one protocol together (schedule:
+    FS_BATCH_AUTO, FS_BATCH_PERSISTENT or FS_BATCH_PER_STEP)."""
     lib = load()
     n = len(sims)
     handles = (C.c_void_p * n)(*[s.handle for s in sims])
@@ -392,8 +397,8 @@ def batch_run_protocol(sims, hx, hy, *, resweep: bool = True, with_counts: bool 
     hs = np.full(n, hash_init(), dtype=np.uint64)
     stv = np.zeros(n, dtype=np.int32)
     fps = np.zeros(n * K, dtype=np.int64) if with_counts else None
-    st = lib.fs_batch_run_protocol(handles, n, _p(hx), _p(hy), K, int(bool(resweep)), _p(nf),
-                                   _p(hs), _p(stv), _p(fps))
+    st = lib.fs_batch_run_protocol_ex(handles, n, _p(hx), _p(hy), K, int(bool(resweep)),
+                                      int(schedule), _p(nf), _p(hs), _p(stv), _p(fps))
     if st != FS_OK:
         raise FsError(st, lib.fs_last_error(sims[0].handle).decode())
     out = dict(n_flips=nf, hash=hs, status=stv)

@@ -36,6 +36,32 @@ struct RelaxLaunch {
                           // the rounds on one CTA
 };
 
+// The work queue of the persistent batch kernel: one entry per member, in the
+// order of `work` (largest members first), in device memory.
+struct PersistLaunch {
+    const Inst* tab;
+    const int32_t* work;        // [n]: member at each queue position
+    const int64_t* task_start;  // [members + 1]: first 32-island task of each member
+    unsigned* const* tcnts;     // [members]: tree arrival counters
+    int n;                      // queue positions (members)
+    int prec, resweep, lanes_per_row;
+    int smem_levels;            // dynamic shared memory of the relax's upper tree levels
+    int32_t* state;             // [n]: kQ* below
+    uint32_t* chunk;            // [n]: next sweep chunk of the member's current field step
+    uint32_t* nchunk;           // [n]: sweep chunks per field step
+    int32_t* ctl;               // [4]: members done, fault, progress beat, (unused)
+};
+constexpr int32_t kQSweep = 0;  // the field step's sweep: chunks to claim
+constexpr int32_t kQReady = 1;  // swept: the relax is next
+constexpr int32_t kQRelax = 2;  // relaxing
+constexpr int32_t kQDone = 3;   // protocol finished (or stopped by a status)
+
+// Queues the persistent batch protocol (state initialised from the members'
+// device states; the first step's external-field table must be queued before).
+// Returns cudaErrorInvalidConfiguration when the kernel cannot be resident with
+// this much shared memory (the caller then uses per-step launches).
+cudaError_t launch_batch_persist(const PersistLaunch& L, cudaStream_t st);
+
 cudaError_t launch_ext_table(const SweepLaunch& L, cudaStream_t st);
 cudaError_t launch_sweep(const SweepLaunch& L, cudaStream_t st);
 cudaError_t launch_relax(const RelaxLaunch& L, cudaStream_t st);

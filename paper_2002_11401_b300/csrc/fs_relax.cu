@@ -38,6 +38,7 @@
 
 #include "fs_common.cuh"
 #include "fs_kernels.h"
+#include "fs_sweep_task.cuh"
 #include "fs_update.cuh"
 
 namespace fs {
@@ -674,10 +675,12 @@ __device__ int64_t pick_warp(const Inst& I, const Levels& L, RecheckShared& R, D
 
 // The relax of one simulation's field step by the whole CTA (the body of k_relax,
 // and a work item of the persistent batch kernel). sm_levels: the dynamic shared
-// memory for the upper tree levels, smem_levels bytes.
+// memory for the upper tree levels, smem_levels bytes. beat (or NULL): a counter
+// raised every 256 flips, so that CTAs waiting for work see that this one is
+// still making progress.
 template <int PREC>
 __device__ __forceinline__ void relax_sim(const Inst& I, int smem_levels, int cont,
-                                          unsigned long long* sm_levels) {
+                                          unsigned long long* sm_levels, unsigned* beat) {
     __shared__ int64_t sh_k;
     __shared__ Prediction P;
     __shared__ int64_t sh_e0, sh_e1;
@@ -873,6 +876,7 @@ __device__ __forceinline__ void relax_sim(const Inst& I, int smem_levels, int co
         ++flips;
         demotions = 0;
         par ^= 1;
+        if (beat != nullptr && threadIdx.x == 0 && (flips & 255) == 0) atomicAdd(beat, 1u);
         if (threadIdx.x == kHashThread) hash = fnv_flip(hash, step, (uint32_t)k);
         // every neighbour i of k: add 2 s_k(new) (P_ik, Q_ik), new key, tree update
         const int snew = sh_snew;
@@ -941,7 +945,7 @@ __global__ void __launch_bounds__(kT, MINB)
     k_relax(const Inst* __restrict__ tab, const int32_t* __restrict__ work, int n_work,
             int smem_levels, int cont) {
     extern __shared__ unsigned long long sm_levels[];
-    relax_sim<PREC>(tab[work[blockIdx.x]], smem_levels, cont, sm_levels);
+    relax_sim<PREC>(tab[work[blockIdx.x]], smem_levels, cont, sm_levels, nullptr);
 }
 
 // Total field, LHS and its bounds for every island at the current state (FS_FP64
@@ -981,6 +985,230 @@ __global__ void k_eval_all(const Inst* __restrict__ tab, double hx, double hy, u
         lhs[i] = e.lhs;
         lo[i] = e.lhs;
         hi[i] = e.lhs;
+    }
+}
+
+// ---- Persistent batch kernel ------------------------------------------------
+// Every member of a batch advances its own protocol (Sec. "Simulation framework":
+// ensembles and parameter sweeps), inside one launch: a CTA takes whatever work is
+// ready — first the relax of a member whose field step has been swept (members in
+// queue order, largest first), else a chunk of a member's sweep — so that one
+// member's relax (a latency-bound chain on one SM) overlaps other members' sweeps
+// (bandwidth-bound), and no member waits for another's field step. A member's
+// steps are the same kernels' work as in per-step launches (the sweep task, the
+// single-flip relax), in the same order, so its results are those of a solo run.
+//
+// Hand-offs between CTAs: the warp that completes a sweep's tree marks the member
+// ready; the CTA that relaxed it computes the next step's external-field table,
+// resets its chunk counter and marks it sweeping; claims are atomics, each side
+// fenced, so that the claimer sees everything the previous owner wrote. The spins
+// are read through the coherent path (other CTAs flip them within this launch).
+// A CTA that finds no work sleeps and looks again; it stops when every member is
+// done, or, having seen no progress anywhere (no item finished, no relax's
+// 256-flip beat) for kIdleLimitNs, it sets the fault word and stops (the host
+// reports FS_ERR_BOUNDS).
+constexpr int kChunkPerWarp = 4;               // tasks a warp sweeps per claimed chunk
+constexpr int kChunkTasks = kNW * kChunkPerWarp;
+constexpr unsigned long long kIdleLimitNs = 10000000000ull;  // 10 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int32_t ld_volatile(const int32_t* p) {
+    return *reinterpret_cast<const volatile int32_t*>(p);
+}
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
+    return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+
+__global__ void k_persist_init(PersistLaunch A) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= A.n) return;
+    const int m = A.work[p];
+    const Inst& I = A.tab[m];
+    const InstState* st = I.st;
+    const int64_t tasks = A.task_start[m + 1] - A.task_start[m];
+    A.nchunk[p] = (uint32_t)((tasks + kChunkTasks - 1) / kChunkTasks);
+    A.chunk[p] = 0u;
+    const bool done = st->status != ST_OK || st->t >= I.K;
+    A.state[p] = done ? kQDone : kQSweep;
+    if (done) atomicAdd(&A.ctl[0], 1);
+}
+
+template <int PREC, int W, int MODE>
+__global__ void __launch_bounds__(kT, 2) k_batch_persist(PersistLaunch A) {
+    extern __shared__ unsigned long long sm_levels[];
+    __shared__ int sums32[PREC == 1 ? kNW : 1][32][2];
+    __shared__ long long sums64[kNW][32][2];
+    __shared__ int32_t q_kind, q_pos, q_best, q_stop;
+    __shared__ uint32_t q_chunk;
+    __shared__ int64_t q_t;
+    __shared__ int32_t q_init, q_next;
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    int32_t* const n_done = &A.ctl[0];
+    int32_t* const fault = &A.ctl[1];
+    unsigned* const beat = reinterpret_cast<unsigned*>(&A.ctl[2]);
+    unsigned seen = 0u;                     // (thread 0) the progress beat last seen
+    unsigned long long quiet_since = 0ull;  // (thread 0) when it last changed
+    unsigned nap = 64u;                     // ns to sleep after a pass without work
+    int aff = -1;   // the member this CTA last relaxed or swept: its work is tried first
+    for (;;) {
+        // The next item: the member this CTA worked on last (its relax when its sweep
+        // is done, else a chunk of its sweep), else the first member in queue order
+        // (largest first) with either: the longest chains are kept moving first.
+        if (tid == 0) {
+            q_kind = 0;
+            if (aff >= 0) {
+                const int32_t sa = ld_volatile(&A.state[aff]);
+                if (sa == kQReady && atomicCAS(&A.state[aff], kQReady, kQRelax) == kQReady) {
+                    q_kind = 1;
+                    q_pos = aff;
+                } else if (sa == kQSweep && ld_volatile(&A.chunk[aff]) < A.nchunk[aff]) {
+                    const uint32_t c = atomicAdd(&A.chunk[aff], 1u);
+                    if (c < A.nchunk[aff]) {
+                        q_kind = 2;
+                        q_pos = aff;
+                        q_chunk = c;
+                    }
+                }
+            }
+            q_best = 0x7fffffff;
+        }
+        __syncthreads();
+        if (q_kind == 0) {
+            for (int p = tid; p < A.n; p += kT) {
+                const int32_t sp = ld_volatile(&A.state[p]);
+                if (sp == kQReady || (sp == kQSweep && ld_volatile(&A.chunk[p]) < A.nchunk[p])) {
+                    atomicMin(&q_best, p);
+                    break;
+                }
+            }
+            __syncthreads();
+            if (tid == 0 && q_best != 0x7fffffff) {
+                const int p = q_best;
+                if (ld_volatile(&A.state[p]) == kQReady) {
+                    if (atomicCAS(&A.state[p], kQReady, kQRelax) == kQReady) {
+                        q_kind = 1;
+                        q_pos = p;
+                    }
+                } else {
+                    const uint32_t c = atomicAdd(&A.chunk[p], 1u);
+                    if (c < A.nchunk[p]) {
+                        q_kind = 2;
+                        q_pos = p;
+                        q_chunk = c;
+                    }
+                }
+                if (q_kind == 0) q_kind = -1;  // lost a race for it: look again at once
+            }
+            __syncthreads();
+        }
+        if (q_kind == -1) continue;
+        if (q_kind == 0) {
+            aff = -1;
+            // nothing to take: finished, faulted, or wait
+            if (tid == 0) {
+                q_stop = 0;
+                if (ld_volatile(n_done) >= A.n || ld_volatile(fault) != 0) {
+                    q_stop = 1;
+                } else {
+                    const unsigned b = ld_volatile(reinterpret_cast<const uint32_t*>(beat));
+                    const unsigned long long now = global_ns();
+                    if (b != seen || quiet_since == 0ull) {
+                        seen = b;
+                        quiet_since = now;
+                    } else if (now - quiet_since > kIdleLimitNs) {
+                        atomicExch(fault, 1);
+                        q_stop = 1;
+                    }
+                }
+            }
+            __syncthreads();
+            if (q_stop) return;
+            __nanosleep(nap);
+            nap = min(nap * 2u, 4096u);
+            continue;
+        }
+        nap = 64u;
+        aff = q_pos;
+        if (tid == 0) {
+            __threadfence();  // (acquire: the claim observed the previous owner's release)
+            const Inst& I = A.tab[A.work[q_pos]];
+            q_t = I.st->t;
+            q_init = I.st->init;
+        }
+        __syncthreads();
+        __threadfence();  // (every thread, before it reads the member's state)
+        const int m = A.work[q_pos];
+        const Inst& I = A.tab[m];
+        if (q_kind == 2) {
+            // a chunk of the member's sweep: warp w takes tasks chunk * kChunkTasks +
+            // u * kNW + w, so that the CTA streams neighbouring rows together
+            const int64_t tasks = A.task_start[m + 1] - A.task_start[m];
+            for (int u = 0; u < kChunkPerWarp; ++u) {
+                const int64_t lt = (int64_t)q_chunk * kChunkTasks + u * kNW + wid;
+                if (lt >= tasks) break;
+                const bool root = sweep_task<PREC, W, MODE, true>(
+                    I, A.tcnts[m], q_t, lt, q_init != 0, sums32[PREC == 1 ? wid : 0], sums64[wid]);
+                if (root && lane == 0) {  // the tree is complete: the relax is next
+                    __threadfence();
+                    atomicExch(&A.state[q_pos], kQReady);
+                    atomicAdd(beat, 1u);
+                }
+            }
+            __syncthreads();
+            continue;  // (a completed tree: this CTA tries the member's relax first)
+        }
+        // the member's relax, then its next field step
+        relax_sim<PREC>(I, A.smem_levels, 0, sm_levels, beat);
+        __threadfence();  // (every thread's stores, before the member changes hands)
+        __syncthreads();
+        if (tid == 0) {
+            const InstState* st = I.st;
+            q_next = st->status == ST_OK && st->t < I.K ? 1 : 0;
+            q_t = st->t;
+        }
+        __syncthreads();
+        if (q_next) {
+            // the next step's external field on every angle class
+            const double hx = I.phx[q_t], hy = I.phy[q_t];
+            for (int c = tid; c < I.nclass; c += kT) {
+                const double2 e = ext_proj(hx, hy, I.cs64[c]);
+                I.ext64[c] = e;
+                I.ext32[c] = make_float2(__double2float_rn(e.x), __double2float_rn(e.y));
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            if (q_next) {
+                atomicExch(&A.chunk[q_pos], 0u);
+                __threadfence();
+                atomicExch(&A.state[q_pos], kQSweep);
+            } else {
+                atomicExch(&A.state[q_pos], kQDone);
+                atomicAdd(n_done, 1);
+            }
+            atomicAdd(beat, 1u);
+        }
+        __syncthreads();
+    }
+}
+
+template <int PREC, int MODE>
+void* persist_fn(int W) {
+    switch (W) {
+        case 4:
+            return (void*)k_batch_persist<PREC, 4, MODE>;
+        case 8:
+            return (void*)k_batch_persist<PREC, 8, MODE>;
+        case 16:
+            return (void*)k_batch_persist<PREC, 16, MODE>;
+        default:
+            return (void*)k_batch_persist<PREC, 32, MODE>;
     }
 }
 
@@ -1045,6 +1273,32 @@ cudaError_t launch_relax(const RelaxLaunch& L, cudaStream_t st) {
             k_relax<0, 1><<<g, kT, sm, st>>>(L.tab, L.work, L.n_work, sm, cont);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_batch_persist(const PersistLaunch& L, cudaStream_t st) {
+    if (L.n == 0) return cudaSuccess;
+    void* fn = L.prec == 1 ? (L.resweep ? persist_fn<1, 1>(L.lanes_per_row)
+                                        : persist_fn<1, 0>(L.lanes_per_row))
+                           : (L.resweep ? persist_fn<0, 1>(L.lanes_per_row)
+                                        : persist_fn<0, 0>(L.lanes_per_row));
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         L.smem_levels);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kT,
+                                                           (size_t)L.smem_levels)) != cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    k_persist_init<<<(L.n + 255) / 256, 256, 0, st>>>(L);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // every CTA resident at once (no CTA waits for a particular other one, so this
+    // is for speed, not for progress)
+    void* args[] = {(void*)&L};
+    return cudaLaunchKernel(fn, dim3((unsigned)(per_sm * nsm)), dim3(kT), args,
+                            (size_t)L.smem_levels, st);
 }
 
 cudaError_t launch_eval_all(const Inst* tab, int64_t n, double hx, double hy, uint32_t step,

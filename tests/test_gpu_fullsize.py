@@ -141,11 +141,12 @@ def test_kagome1000_fields_at_full_size(B, oracle):
         assert max(np.abs(hp - op).max(), np.abs(hq - oq).max()) <= tol * scale
 
 
-def test_ensemble512_members_match_oracle(B):
+@pytest.mark.parametrize("schedule", [1, 2])  # FS_BATCH_PERSISTENT, FS_BATCH_PER_STEP
+def test_ensemble512_members_match_oracle(B, schedule):
     members, proto = I.ensemble_workload()
     hx, hy = I.protocol_of(proto)
     sims = [lib_sim(m, precision=1) for m in members]
-    out = B.batch_run_protocol(sims, hx, hy, with_counts=True)
+    out = B.batch_run_protocol(sims, hx, hy, with_counts=True, schedule=schedule)
     assert (out["status"] == 0).all()
     for q in (0, 37, 211, 500):
         g = gold(f"ensemble512_member{q}")

@@ -307,7 +307,8 @@ def test_log_shorter_than_flips(B):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-def test_batch_equals_solo_and_oracle(B, oracle, prec):
+@pytest.mark.parametrize("schedule", [1, 2])  # FS_BATCH_PERSISTENT, FS_BATCH_PER_STEP
+def test_batch_equals_solo_and_oracle(B, oracle, prec, schedule):
     rng = np.random.default_rng(4)
     sides = rng.integers(3, 15, size=12)
     hx, hy = I.ramp_protocol(50, 45.0, 0.3)
@@ -315,7 +316,8 @@ def test_batch_equals_solo_and_oracle(B, oracle, prec):
     for q, s in enumerate(sides):
         w = small(I.SQUARE, int(s), seed=1000 + q)
         members.append((w, lib_sim(w, precision=prec)))
-    out = B.batch_run_protocol([m for _, m in members], hx, hy, with_counts=True)
+    out = B.batch_run_protocol([m for _, m in members], hx, hy, with_counts=True,
+                               schedule=schedule)
     for q, (w, _) in enumerate(members):
         S = oracle_sim(oracle, w)
         ref = S.run(np.ones(S.n, dtype=np.int8), hx, hy)
@@ -324,6 +326,54 @@ def test_batch_equals_solo_and_oracle(B, oracle, prec):
         np.testing.assert_array_equal(out["flips_per_step"][q], ref["flips_per_step"])
         solo = lib_sim(w, precision=prec).run_protocol(hx, hy)
         assert solo["hash"] == ref["hash"]
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_persistent_batch_mixed_members_match_oracle(B, oracle, prec):
+    """The persistent schedule on members of every geometry and of very different
+    sizes (a one-node tree of 24 islands up to ~20,000 islands, whose sweep spans many
+    claimed chunks), with and without thermal noise, more members than one CTA each
+    can hold at once: every member's flips per step, flip count and hash equal the
+    oracle's, and the final spins equal a per-step batch run's."""
+    rng = np.random.default_rng(9)
+    hx, hy = I.ramp_protocol(40, 30.0, 0.3)
+    ws = []
+    kinds = [I.SQUARE, I.PINWHEEL, I.KAGOME]
+    for q in range(20):
+        kind = kinds[q % 3]
+        n = int(rng.integers(3, 30))
+        ws.append(small(kind, n, seed=2000 + q, sigma_th=0.004 if q % 4 == 1 else 0.0))
+    ws.append(small(I.SQUARE, 3, seed=2100))    # 24 islands: a one-node tree
+    ws.append(small(I.KAGOME, 80, seed=2101))   # 19,519 islands
+    sims = [lib_sim(w, precision=prec) for w in ws]
+    out = B.batch_run_protocol(sims, hx, hy, with_counts=True, schedule=1)
+    assert (out["status"] == 0).all()
+    spins = [s.spins() for s in sims]
+    sims2 = [lib_sim(w, precision=prec) for w in ws]
+    B.batch_run_protocol(sims2, hx, hy, schedule=2)
+    for q, w in enumerate(ws):
+        S = oracle_sim(oracle, w)
+        ref = S.run(np.ones(S.n, dtype=np.int8), hx, hy)
+        assert int(out["hash"][q]) == ref["hash"], q
+        assert out["n_flips"][q] == ref["n_flips"], q
+        np.testing.assert_array_equal(out["flips_per_step"][q], ref["flips_per_step"])
+        np.testing.assert_array_equal(spins[q], sims2[q].spins())
+
+
+def test_persistent_batch_twice_in_a_row(B, oracle):
+    """Two persistent protocols in a row on the same members (the second continues
+    from the first's final state, with a new step offset): both equal solo runs."""
+    hx, hy = I.ramp_protocol(30, 45.0, 0.3)
+    ws = [small(I.SQUARE, n, seed=2200 + n) for n in (4, 9, 17, 33)]
+    sims = [lib_sim(w, precision=FP32) for w in ws]
+    solo = [lib_sim(w, precision=FP32) for w in ws]
+    for rep in range(2):
+        out = B.batch_run_protocol(sims, hx, hy, schedule=1)
+        for q, s in enumerate(solo):
+            r = s.run_protocol(hx, hy)
+            assert int(out["n_flips"][q]) == r["n_flips"]
+        for q in range(len(ws)):
+            np.testing.assert_array_equal(sims[q].spins(), solo[q].spins())
 
 
 # ---------------------------------------------------------------------------

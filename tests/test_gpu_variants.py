@@ -195,6 +195,10 @@ def test_batch_members_with_local_fields(B, oracle):
         sim.set_field_local(lhx, np.zeros_like(lhx))
         sims.append(sim)
         refs.append(S.run(np.ones(S.n, dtype=np.int8), hx, hy, lhx=lhx, lhy=np.zeros_like(lhx)))
+    # the persistent schedule takes no local fields; the default falls back to per step
+    with pytest.raises(B.FsError) as e:
+        B.batch_run_protocol(sims, hx, hy, schedule=B.FS_BATCH_PERSISTENT)
+    assert e.value.code == B.FS_ERR_INVALID
     out = B.batch_run_protocol(sims, hx, hy)
     for q, ref in enumerate(refs):
         assert int(out["hash"][q]) == ref["hash"] and int(out["n_flips"][q]) == ref["n_flips"]
