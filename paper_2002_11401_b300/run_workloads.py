@@ -5,7 +5,8 @@ runs it through the C ABI and prints one JSON line of measurements.
   python -m paper_2002_11401_b300.run_workloads square16|pinwheel300|kagome1000 \
       [--precision fp32|fp64] [--steps K] [--resweep 0|1] [--cells N]
       [--relax auto|single|multi|multi_cta]
-  python -m paper_2002_11401_b300.run_workloads ensemble512 [--members M]
+  python -m paper_2002_11401_b300.run_workloads ensemble512 [--members M] [--steps K]
+      [--schedule per_step|persistent|auto]
   python -m paper_2002_11401_b300.run_workloads serving [--requests R] [--rate HZ]
 """
 from __future__ import annotations
@@ -115,18 +116,22 @@ def step_barrier(fps, slots=2 * 148):
             "steps": int(fps.shape[1]), "slots": slots}
 
 
-def run_ensemble(members, sample):
+def run_ensemble(members, sample, steps=0, schedule="per_step"):
     mem, proto = I.ensemble_workload()
     mem = mem[:members]
     hx, hy = I.protocol_of(proto)
+    if steps:
+        hx, hy = hx[:steps], hy[:steps]
+    sched = {"auto": B.FS_BATCH_AUTO, "persistent": B.FS_BATCH_PERSISTENT,
+             "per_step": B.FS_BATCH_PER_STEP}[schedule]
     out = {"workload": f"ensemble of {len(mem)} square arrays (sides 20..200), "
-                       f"{len(hx)}-step 45-degree ramp"}
+                       f"{len(hx)}-step 45-degree ramp", "schedule": schedule}
     hashes = {}
     for prec, tag in ((B.FS_FP32_RECHECK, "fp32"), (B.FS_FP64, "fp64")):
         sims = [make_sim(m, prec) for m in mem]
         out["islands"] = int(sum(s.n for s in sims))
         t0 = time.perf_counter()
-        res = B.batch_run_protocol(sims, hx, hy, with_counts=tag == "fp32")
+        res = B.batch_run_protocol(sims, hx, hy, with_counts=tag == "fp32", schedule=sched)
         dt = time.perf_counter() - t0
         flips = int(res["n_flips"].sum())
         hashes[tag] = res["hash"].copy()
@@ -230,6 +235,7 @@ def main(argv=None):
     ap.add_argument("--resweep", type=int, default=1)
     ap.add_argument("--relax", default="auto", choices=["auto", "single", "multi", "multi_cta"])
     ap.add_argument("--members", type=int, default=512)
+    ap.add_argument("--schedule", default="per_step", choices=["auto", "persistent", "per_step"])
     ap.add_argument("--sample", type=int, default=12)
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--rate", type=float, default=200.0)
@@ -244,7 +250,7 @@ def main(argv=None):
         out = run_single(a.workload, prec, a.steps, bool(a.resweep), a.cells, a.relax)
         out["relax"] = a.relax
     elif a.workload == "ensemble512":
-        out = run_ensemble(a.members, a.sample)
+        out = run_ensemble(a.members, a.sample, a.steps, a.schedule)
     elif a.workload == "serving":
         out = run_serving(a.requests, a.rate, a.budget_gb, a.check)
     else:
