@@ -418,16 +418,21 @@ fs_status fs_eval_argmax_static(const fs_sim* sim, const int8_t* d_spins, double
  *   with a local or spatial field (FS_ERR_INVALID).
  * FS_BATCH_PER_STEP: per field step one sweep launch over every member's rows,
  *   then one relax launch with a CTA per member.
- * FS_BATCH_AUTO: per step (measured faster on the 512-member ensemble: 1.26 s
- *   against 1.42 s, FP32; a relax CTA holds half an SM's registers, so a CTA
- *   sweeping beside it has a fraction of the warps the sweep kernel runs with).
+ * FS_BATCH_TWO_CHAINS: the same launches for two halves of the members (taken
+ *   alternately by size), each half with its own chain of field steps, so that one
+ *   half's relaxes may overlap the other's sweeps.
+ * FS_BATCH_AUTO: per step, in two chains from twice as many members as SMs
+ *   (measured faster on the 512-member ensemble: 1.25 s in two chains, 1.26 s in
+ *   one, 1.42 s persistent, FP32; a relax CTA holds half an SM's registers, so a
+ *   CTA sweeping beside it has a fraction of the warps the sweep kernel runs with).
  * The sweep's lanes per CSR row are timed on the batch's own rows first (for a
  * batch whose sweep is long enough). A persistent run in which no work finished
  * anywhere for 10 s stops with FS_ERR_BOUNDS. */
 typedef enum {
     FS_BATCH_AUTO = 0,
     FS_BATCH_PERSISTENT = 1,
-    FS_BATCH_PER_STEP = 2
+    FS_BATCH_PER_STEP = 2,
+    FS_BATCH_TWO_CHAINS = 3
 } fs_batch_schedule;
 
 fs_status fs_batch_run_protocol_ex(fs_sim* const* sims, int32_t n, const double* hx,

@@ -23,7 +23,7 @@ FS_FP64, FS_FP32_RECHECK = 0, 1
 FS_CRITERION_ASTROID, FS_CRITERION_PARALLEL = 0, 1
 FS_ENCODE_SINUSOID, FS_ENCODE_SAWTOOTH, FS_ENCODE_ROTATION = 0, 1, 2
 FS_RELAX_AUTO, FS_RELAX_SINGLE, FS_RELAX_MULTI, FS_RELAX_MULTI_CTA = 0, 1, 2, 3
-FS_BATCH_AUTO, FS_BATCH_PERSISTENT, FS_BATCH_PER_STEP = 0, 1, 2
+FS_BATCH_AUTO, FS_BATCH_PERSISTENT, FS_BATCH_PER_STEP, FS_BATCH_TWO_CHAINS = 0, 1, 2, 3
 
 EXPORTS = (
     "fs_last_error", "fs_hash_init", "fs_create_geometry", "fs_create_custom", "fs_destroy",
@@ -386,7 +386,7 @@ def encode(kind: int, inputs, period: int, h_lo: float, h_hi: float, angle_deg: 
 def batch_run_protocol(sims, hx, hy, *, resweep: bool = True, with_counts: bool = False,
                        schedule: int = FS_BATCH_AUTO):
     """Runs every simulation of `sims` through one protocol together (schedule:
-    FS_BATCH_AUTO, FS_BATCH_PERSISTENT or FS_BATCH_PER_STEP)."""
+    FS_BATCH_AUTO, FS_BATCH_PERSISTENT, FS_BATCH_PER_STEP or FS_BATCH_TWO_CHAINS)."""
     lib = load()
     n = len(sims)
     handles = (C.c_void_p * n)(*[s.handle for s in sims])

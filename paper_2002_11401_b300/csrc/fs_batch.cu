@@ -193,7 +193,7 @@ extern "C" fs_status fs_batch_run_protocol_ex(fs_sim* const* sims, int32_t n, co
     if (!sims || n <= 0 || !sims[0]) return FS_ERR_INVALID;
     fs_sim* lead = sims[0];
     if (K < 0 || (K > 0 && (!hx || !hy)) || !n_flips || !seq_hash || !status ||
-        schedule < FS_BATCH_AUTO || schedule > FS_BATCH_PER_STEP) {
+        schedule < FS_BATCH_AUTO || schedule > FS_BATCH_TWO_CHAINS) {
         lead->err = "bad batch arguments";
         return FS_ERR_INVALID;
     }
@@ -226,6 +226,14 @@ extern "C" fs_status fs_batch_run_protocol_ex(fs_sim* const* sims, int32_t n, co
     // 1.68 s on FP64), whose relax CTAs (128 registers a thread, two per SM) leave a
     // sweeping CTA a fraction of the SM's warps and share its L1 with the chains
     const bool persist = schedule == FS_BATCH_PERSISTENT;
+    // FS_BATCH_AUTO: two chains from twice as many members as SMs (512-member
+    // ensemble: 1.252 s against 1.265 s in one chain, FP32; 1.601 s against 1.623 s,
+    // FP64), else one
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const bool two = n >= 2 && (schedule == FS_BATCH_TWO_CHAINS ||
+                                (schedule == FS_BATCH_AUTO && n >= 2 * nsm));
     // graphs cannot be captured on the legacy default stream: run the batch on a
     // stream of its own, ordered after the lead's queued work
     cudaStream_t st = nullptr;
@@ -299,8 +307,44 @@ extern "C" fs_status fs_batch_run_protocol_ex(fs_sim* const* sims, int32_t n, co
     int levels = 1024;
     for (int i = 0; i < n; ++i) levels = std::max(levels, relax_smem_levels(v[(size_t)i]->n));
     if ((e = prepare_relax(prec, levels)) != cudaSuccess) return bail(e, "relax setup");
+    // two chains: the members alternately by size into two tables, each with its
+    // own field steps, forked from and joined to st in the graph
+    BatchTable half[2];
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    struct ChainGuard {
+        cudaStream_t* s;
+        cudaEvent_t* a;
+        cudaEvent_t* b;
+        ~ChainGuard() {
+            if (*s) {
+                cudaStreamSynchronize(*s);
+                cudaStreamDestroy(*s);
+            }
+            if (*a) cudaEventDestroy(*a);
+            if (*b) cudaEventDestroy(*b);
+        }
+    } chain_guard{&st2, &ev_fork, &ev_join};
+    if (two) {
+        std::vector<fs_sim*> vs[2];
+        std::vector<Inst> ds[2];
+        for (int q = 0; q < n; ++q) {
+            const int m = B.h_work[(size_t)q];  // (largest first)
+            vs[q & 1].push_back(v[(size_t)m]);
+            ds[q & 1].push_back(descs[(size_t)m]);
+        }
+        for (int c = 0; c < 2; ++c) {
+            if ((e = half[c].upload(vs[c], ds[c], st)) != cudaSuccess) return bail(e, "upload");
+            half[c].lanes = B.lanes;
+            half[c].occ = B.occ;
+        }
+        if ((e = cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming)) != cudaSuccess)
+            return bail(e, "streams");
+    }
     // capture the whole protocol in one graph: one persistent launch, or the field
-    // steps' launches
+    // steps' launches (in one chain or two)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
@@ -308,6 +352,15 @@ extern "C" fs_status fs_batch_run_protocol_ex(fs_sim* const* sims, int32_t n, co
     cudaError_t le = cudaSuccess;
     if (persist && K > 0) {
         le = B.enqueue_persistent(prec, resweep ? 1 : 0, levels, st);
+    } else if (two) {
+        le = cudaEventRecord(ev_fork, st);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(st2, ev_fork, 0);
+        for (int64_t t = 0; t < K && le == cudaSuccess; ++t) {
+            le = half[0].enqueue_step(prec, resweep ? 1 : 0, levels, st);
+            if (le == cudaSuccess) le = half[1].enqueue_step(prec, resweep ? 1 : 0, levels, st2);
+        }
+        if (le == cudaSuccess) le = cudaEventRecord(ev_join, st2);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(st, ev_join, 0);
     } else {
         for (int64_t t = 0; t < K && le == cudaSuccess; ++t)
             le = B.enqueue_step(prec, resweep ? 1 : 0, levels, st);
@@ -346,6 +399,8 @@ extern "C" fs_status fs_batch_run_protocol_ex(fs_sim* const* sims, int32_t n, co
     if (e != cudaSuccess) return bail(e, "protocol");
     tmp.release(st);
     B.mem.release(st);
+    half[0].mem.release(st);
+    half[1].mem.release(st);
     fs_status worst = FS_OK;
     for (int i = 0; i < n; ++i) {
         const InstState& S = states[(size_t)i];

@@ -123,7 +123,7 @@ def run_ensemble(members, sample, steps=0, schedule="per_step"):
     if steps:
         hx, hy = hx[:steps], hy[:steps]
     sched = {"auto": B.FS_BATCH_AUTO, "persistent": B.FS_BATCH_PERSISTENT,
-             "per_step": B.FS_BATCH_PER_STEP}[schedule]
+             "per_step": B.FS_BATCH_PER_STEP, "two_chains": B.FS_BATCH_TWO_CHAINS}[schedule]
     out = {"workload": f"ensemble of {len(mem)} square arrays (sides 20..200), "
                        f"{len(hx)}-step 45-degree ramp", "schedule": schedule}
     hashes = {}
@@ -235,7 +235,7 @@ def main(argv=None):
     ap.add_argument("--resweep", type=int, default=1)
     ap.add_argument("--relax", default="auto", choices=["auto", "single", "multi", "multi_cta"])
     ap.add_argument("--members", type=int, default=512)
-    ap.add_argument("--schedule", default="per_step", choices=["auto", "persistent", "per_step"])
+    ap.add_argument("--schedule", default="per_step", choices=["auto", "persistent", "per_step", "two_chains"])
     ap.add_argument("--sample", type=int, default=12)
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--rate", type=float, default=200.0)

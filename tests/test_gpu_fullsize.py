@@ -141,7 +141,7 @@ def test_kagome1000_fields_at_full_size(B, oracle):
         assert max(np.abs(hp - op).max(), np.abs(hq - oq).max()) <= tol * scale
 
 
-@pytest.mark.parametrize("schedule", [1, 2])  # FS_BATCH_PERSISTENT, FS_BATCH_PER_STEP
+@pytest.mark.parametrize("schedule", [0, 1, 2])  # FS_BATCH_AUTO (two chains), _PERSISTENT, _PER_STEP
 def test_ensemble512_members_match_oracle(B, schedule):
     members, proto = I.ensemble_workload()
     hx, hy = I.protocol_of(proto)

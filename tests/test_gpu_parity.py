@@ -307,7 +307,7 @@ def test_log_shorter_than_flips(B):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-@pytest.mark.parametrize("schedule", [1, 2])  # FS_BATCH_PERSISTENT, FS_BATCH_PER_STEP
+@pytest.mark.parametrize("schedule", [1, 2, 3])  # FS_BATCH_PERSISTENT, _PER_STEP, _TWO_CHAINS
 def test_batch_equals_solo_and_oracle(B, oracle, prec, schedule):
     rng = np.random.default_rng(4)
     sides = rng.integers(3, 15, size=12)
