@@ -412,8 +412,9 @@ def test_server_results_equal_solo_runs_and_oracle(B, oracle):
                            spins_out=buf)
             entries.append((t, r, prec, hx, hy, buf))
         if wave < 2:
-            time.sleep(0.05)
-            # requests of the earlier waves still in flight when the next arrives
+            # a short pause (the wave's requests are admitted and start), then the
+            # requests still in flight when the next wave arrives
+            time.sleep(0.002)
             for e in entries:
                 if e[0] not in seen:
                     res = srv.poll(e[0])
