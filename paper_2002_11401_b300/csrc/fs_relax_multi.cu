@@ -72,7 +72,7 @@ constexpr int kCarry = 160;       // candidates carried below a round's last fli
 constexpr int kPMin = 4;
 constexpr int kLowRounds = 4;
 constexpr int kClsSh = 32;        // angle classes whose external field is read from shared memory
-constexpr int kRankMax = 128;     // candidates sorted by rank (more: by merging)
+constexpr int kRankMax = kMT / 2;  // candidates sorted by rank (more: by merging)
 constexpr int kHashQ = 2 * kPickCap;  // flips waiting to be folded into the sequence hash
 
 // One candidate island as its exact evaluation found it.
@@ -546,7 +546,7 @@ __device__ void scan_best(const Inst& I, uint32_t step, MultiShared& S) {
 }
 
 // S.cand[0 .. n) into "before" order in S.sv / S.si / S.so. Up to kRankMax entries
-// by rank (each entry counts those that go before it, four threads an entry;
+// by rank (each entry counts those that go before it, kMT / n threads an entry;
 // islands are distinct). More by merging: every warp sorts runs of 32 in registers
 // (a bitonic network over its lanes), then pairs of runs merge until one run holds
 // everything, each entry's place being its place in its own run plus the number of
@@ -556,31 +556,36 @@ __device__ void scan_best(const Inst& I, uint32_t step, MultiShared& S) {
 __device__ void sort_candidates(MultiShared& S, int n) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (n <= kRankMax) {
-        // four consecutive threads count for one entry, each over every fourth other
-        const int e = tid >> 2, part = tid & 3;  // (kRankMax <= kMT / 4)
-        int r = 0;
+        // kMT / n consecutive threads count for one entry (at least two), each over
+        // every tpc-th other, their counts summed in S.mi
+        const int tpc = kMT / n;
+        const int e = tid / tpc, part = tid - e * tpc;
+        for (int c = tid; c < n; c += kMT) S.mi[c] = 0;
+        __syncthreads();
         unsigned long long v = 0ull;
         int32_t ix = 0;
         if (e < n) {
             v = S.cand[e].v;
             ix = S.cand[e].i;
+            int r = 0;
             int u = part;
-            for (; u + 28 < n; u += 32) {  // (eight loads in flight)
+            for (; u + 7 * tpc < n; u += 8 * tpc) {  // (eight loads in flight)
                 unsigned long long w[8];
                 int32_t wi[8];
 #pragma unroll
                 for (int z = 0; z < 8; ++z) {
-                    w[z] = S.cand[u + 4 * z].v;
-                    wi[z] = S.cand[u + 4 * z].i;
+                    w[z] = S.cand[u + z * tpc].v;
+                    wi[z] = S.cand[u + z * tpc].i;
                 }
 #pragma unroll
                 for (int z = 0; z < 8; ++z) r += before(w[z], wi[z], v, ix) ? 1 : 0;
             }
-            for (; u < n; u += 4) r += before(S.cand[u].v, S.cand[u].i, v, ix) ? 1 : 0;
+            for (; u < n; u += tpc) r += before(S.cand[u].v, S.cand[u].i, v, ix) ? 1 : 0;
+            if (r) atomicAdd(&S.mi[e], r);
         }
-        r += __shfl_xor_sync(0xffffffffu, r, 1);
-        r += __shfl_xor_sync(0xffffffffu, r, 2);
+        __syncthreads();
         if (e < n && part == 0) {
+            const int r = S.mi[e];
             S.sv[r] = v;
             S.si[r] = ix;
             S.so[r] = (int16_t)e;
