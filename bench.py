@@ -122,7 +122,7 @@ TRAFFIC = {
                 "sources": ("fs_sweep.cu", "fs_sweep_task.cuh"), "sha256_16": "7f6360002b4626ed"},
     "k_relax_multi": {"per": "flip", "bytes_per_unit": 11840.0,
                       "sources": ("fs_relax_multi.cu", "fs_update.cuh", "fs_common.cuh"),
-                      "sha256_16": "482884c1584587c8"},
+                      "sha256_16": "a9765cd257c11bd4"},
     "k_relax": {"per": "flip", "bytes_per_unit": None,
                 "sources": ("fs_relax.cu", "fs_common.cuh"), "sha256_16": ""},
 }
