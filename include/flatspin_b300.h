@@ -426,8 +426,16 @@ fs_status fs_eval_argmax_static(const fs_sim* sim, const int8_t* d_spins, double
  *   one, 1.42 s persistent, FP32; a relax CTA holds half an SM's registers, so a
  *   CTA sweeping beside it has a fraction of the warps the sweep kernel runs with).
  * The sweep's lanes per CSR row are timed on the batch's own rows first (for a
- * batch whose sweep is long enough). A persistent run in which no work finished
- * anywhere for 10 s stops with FS_ERR_BOUNDS. */
+ * batch whose sweep is long enough).
+ *   hx, hy   host, K doubles each: the external field of every field step
+ *   resweep  1: the dipolar sums recomputed in every field step's sweep; 0: the
+ *            exact sums the flips keep are used (the same bits)
+ * Errors: FS_ERR_INVALID (NULL arrays, n <= 0, an unknown schedule, members of
+ * different precisions, a local, spatial or thermal series shorter than K, or the
+ * persistent schedule with a local or spatial field), FS_ERR_STATE (a member
+ * without parameters), FS_ERR_CUDA, FS_ERR_BOUNDS (a persistent run in which no
+ * work finished anywhere for 10 s), else the first member's failing status (each
+ * member's own in status[]). */
 typedef enum {
     FS_BATCH_AUTO = 0,
     FS_BATCH_PERSISTENT = 1,
