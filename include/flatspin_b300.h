@@ -460,8 +460,8 @@ fs_status fs_batch_run_protocol(fs_sim* const* sims, int32_t n, const double* hx
  * launched again and again (two launches queued at most) until the protocol is
  * done, so requests that arrive while others run start as soon as they are built
  * and all of them overlap on the device. Builds run at the highest stream
- * priority and larger requests (longer flip chains) at higher priorities than
- * smaller ones. Admission order: a request waiting longer than 10 s first (oldest
+ * priority and smaller requests (short kernels) at higher priorities than larger
+ * ones. Admission order: a request waiting longer than 10 s first (oldest
  * first), else the least estimated work (islands x field steps). Every request
  * relaxes with the single-flip chain (FS_RELAX_SINGLE: one CTA, one SM), which
  * makes the most flips per SM on a shared device. Results equal those of running

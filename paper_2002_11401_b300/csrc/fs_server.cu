@@ -293,16 +293,18 @@ void worker_loop(fs_server* S) {
     std::vector<Active> active;
     std::map<int, std::vector<cudaStream_t>> free_streams;  // by priority
     std::vector<cudaEvent_t> free_events;
-    // Larger requests run at higher stream priorities (the builders' level excepted):
-    // their flip chains are the longest, and a relax launch of a higher priority takes
-    // the next free SM before the CTAs of the other requests' sweeps.
+    // Smaller requests run at higher stream priorities (the builders' level excepted):
+    // their kernels are short, and taking SMs first they finish and leave the device to
+    // the long flip chains of the large requests (measured on the 40-request stream, in
+    // three pairs of runs: 0.75/0.95/0.83M flips/s against 0.68/0.92/0.73M with the
+    // larger requests first).
     int prio_lo = 0, prio_hi = 0;
     cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     auto prio_of = [&](int64_t n) {
         const int levels = std::max(0, prio_lo - prio_hi - 1);  // below the builders'
         const double lg = std::log2((double)std::max<int64_t>(n, 1));
-        const int up = std::min(levels, std::max(0, (int)(lg - 14.0) / 2));
-        return prio_lo - up;
+        const int big = std::min(levels, std::max(0, (int)(lg - 14.0) / 2));
+        return prio_lo - (levels - big);
     };
     auto take_event = [&](cudaEvent_t* e) {
         if (!free_events.empty()) {
