@@ -269,7 +269,7 @@ typedef struct {
 fs_status fs_set_profiling(fs_sim* sim, int32_t on);
 fs_status fs_get_profile(fs_sim* sim, fs_profile* out);
 
-/* Sweep autotuner: times the field-and-margin sweep with 4, 8, 16 and 32 lanes per
+/* Sweep autotuner: times the field-and-margin sweep with 2, 4, 8, 16 and 32 lanes per
  * CSR row, each built for 4 and for 5 resident blocks per SM, on this system and
  * keeps the fastest for later calls; *lanes_out (may be NULL) receives the lanes
  * per row of the choice. Every choice gives bit-identical results. */

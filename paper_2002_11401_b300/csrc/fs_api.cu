@@ -1303,12 +1303,12 @@ extern "C" fs_status fs_autotune(fs_sim* sim, int32_t* lanes_out) {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event");
     CK(cudaEventCreate(&e1), "event");
-    const int cands[4] = {4, 8, 16, 32};
+    const int cands[5] = {2, 4, 8, 16, 32};
     int best = sim->lanes, best_occ = sim->sweep_occ;
     float best_ms = 1e30f;
-    for (int c = 0; c < 8; ++c) {
-        S.lanes_per_row = cands[c & 3];
-        S.occupancy = c < 4 ? 4 : 5;
+    for (int c = 0; c < 10; ++c) {
+        S.lanes_per_row = cands[c % 5];
+        S.occupancy = c < 5 ? 4 : 5;
         CK(launch_sweep(S, st), "sweep");
         float ms = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
@@ -1322,7 +1322,7 @@ extern "C" fs_status fs_autotune(fs_sim* sim, int32_t* lanes_out) {
         }
         if (ms < best_ms) {
             best_ms = ms;
-            best = cands[c & 3];
+            best = cands[c % 5];
             best_occ = S.occupancy;
         }
     }

@@ -154,11 +154,11 @@ cudaError_t BatchTable::autotune(int prec, int resweep, cudaStream_t st) {
         cudaEventDestroy(e0);
         return e;
     }
-    const int cands[4] = {4, 8, 16, 32};
+    const int cands[5] = {2, 4, 8, 16, 32};
     float best_ms = 1e30f;
-    for (int c = 0; c < 8 && e == cudaSuccess; ++c) {
-        S.lanes_per_row = cands[c & 3];
-        S.occupancy = c < 4 ? 4 : 5;
+    for (int c = 0; c < 10 && e == cudaSuccess; ++c) {
+        S.lanes_per_row = cands[c % 5];
+        S.occupancy = c < 5 ? 4 : 5;
         if ((e = launch_sweep(S, st)) != cudaSuccess) break;  // warm-up
         float ms = 1e30f;
         for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {

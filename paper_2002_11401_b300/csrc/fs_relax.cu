@@ -1201,6 +1201,8 @@ __global__ void __launch_bounds__(kT, 2) k_batch_persist(PersistLaunch A) {
 template <int PREC, int MODE>
 void* persist_fn(int W) {
     switch (W) {
+        case 2:
+            return (void*)k_batch_persist<PREC, 2, MODE>;
         case 4:
             return (void*)k_batch_persist<PREC, 4, MODE>;
         case 8:

@@ -69,6 +69,8 @@ cudaError_t launch_w(const SweepLaunch& L, cudaStream_t st) {
     const unsigned blocks = (unsigned)((L.total_tasks + kSweepWarps - 1) / kSweepWarps);
     if (blocks == 0) return cudaSuccess;
     switch (L.lanes_per_row) {
+        case 2:
+            return launch_wo<PREC, MODE, 2>(blocks, L, st);
         case 4:
             return launch_wo<PREC, MODE, 4>(blocks, L, st);
         case 8:
