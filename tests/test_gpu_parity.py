@@ -360,6 +360,20 @@ def test_persistent_batch_mixed_members_match_oracle(B, oracle, prec):
         np.testing.assert_array_equal(spins[q], sims2[q].spins())
 
 
+def test_batch_schedule_arguments(B):
+    """An unknown schedule is refused; an empty protocol runs on every schedule and
+    flips nothing."""
+    sims = [lib_sim(small(I.SQUARE, n, seed=2300 + n), precision=FP32) for n in (4, 6)]
+    hx, hy = I.ramp_protocol(10, 45.0, 0.3)
+    with pytest.raises(B.FsError) as e:
+        B.batch_run_protocol(sims, hx, hy, schedule=7)
+    assert e.value.code == B.FS_ERR_INVALID
+    for sched in (B.FS_BATCH_AUTO, B.FS_BATCH_PERSISTENT, B.FS_BATCH_PER_STEP,
+                  B.FS_BATCH_TWO_CHAINS):
+        out = B.batch_run_protocol(sims, hx[:0], hy[:0], schedule=sched)
+        assert (out["n_flips"] == 0).all() and (out["status"] == 0).all()
+
+
 def test_persistent_batch_twice_in_a_row(B, oracle):
     """Two persistent protocols in a row on the same members (the second continues
     from the first's final state, with a new step offset): both equal solo runs."""
