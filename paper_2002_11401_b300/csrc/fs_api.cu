@@ -885,12 +885,6 @@ cudaError_t enqueue_steps(fs_sim* sim, int64_t K, int resweep, cudaStream_t st) 
     R.smem_levels = relax_smem_levels(sim->n);
     R.multi = !relax_multi(sim) ? 0 : sim->relax_mode == FS_RELAX_MULTI_CTA ? 2 : 1;
     cudaError_t e;
-    // a small array's steps in one CTA (not with per-kernel timing, a local or
-    // spatial field, or without the dipolar resweep)
-    if (small_protocol_fits(sim->n) && !sim->profiling && !sim->inst.exti64 && resweep &&
-        !relax_multi(sim))
-        return launch_small_protocol(sim->d_inst, sim->d_tcnts, sim->p.precision,
-                                     R.smem_levels, K, st);
     if (sim->profiling && sim->ev_used + 3 * (size_t)K > 30000 &&
         (e = collect_profile(sim)) != cudaSuccess)
         return e;

@@ -62,14 +62,6 @@ constexpr int32_t kQDone = 3;   // protocol finished (or stopped by a status)
 // this much shared memory (the caller then uses per-step launches).
 cudaError_t launch_batch_persist(const PersistLaunch& L, cudaStream_t st);
 
-// Small arrays (small_protocol_fits): nsteps field steps of the simulation tab[0]
-// in one CTA (table, sweep with 4 lanes a row and the dipolar resweep, single-flip
-// relax); prepare_small_protocol sets its shared-memory limit (before any capture).
-bool small_protocol_fits(int64_t n);
-cudaError_t prepare_small_protocol();
-cudaError_t launch_small_protocol(const Inst* tab, unsigned* const* tcnts, int prec,
-                                  int smem_levels, int64_t nsteps, cudaStream_t st);
-
 cudaError_t launch_ext_table(const SweepLaunch& L, cudaStream_t st);
 cudaError_t launch_sweep(const SweepLaunch& L, cudaStream_t st);
 cudaError_t launch_relax(const RelaxLaunch& L, cudaStream_t st);

@@ -1198,55 +1198,6 @@ __global__ void __launch_bounds__(kT, 2) k_batch_persist(PersistLaunch A) {
     }
 }
 
-// ---- Small arrays: a protocol's field steps in one CTA ------------------------
-// For an array of a few thousand islands a field step's kernels each take a few
-// microseconds, less than launching them: one CTA runs nsteps field steps of one
-// simulation (the steps past K return at once), each the external-field table,
-// the sweep (the CTA's warps over the array's tasks, the tree built by the last
-// arrivals as in the sweep kernel) and the single-flip relax, with barriers between.
-// The same work as the per-step launches, in the same order, so the same bits.
-constexpr int64_t kSmallIslands = 4096;  // arrays up to this size take this kernel
-
-template <int PREC>
-__global__ void __launch_bounds__(kT, 1)
-    k_small_protocol(const Inst* tab, unsigned* const* tcnts, int smem_levels, int64_t nsteps) {
-    extern __shared__ unsigned long long sm_levels[];
-    __shared__ int sums32[PREC == 1 ? kNW : 1][32][2];
-    __shared__ long long sums64[kNW][32][2];
-    __shared__ int64_t s_t;
-    __shared__ int32_t s_go, s_init;
-    const Inst& I = tab[0];
-    InstState* st = I.st;
-    const int tid = threadIdx.x, wid = tid >> 5;
-    const int64_t tasks = (I.n + 31) / 32;
-    unsigned* const tcnt = tcnts[0];
-    for (int64_t k = 0; k < nsteps; ++k) {
-        if (tid == 0) {
-            s_t = st->t;
-            s_go = st->status == ST_OK && s_t < I.K ? 1 : 0;
-            s_init = st->init;
-        }
-        __syncthreads();
-        if (!s_go) return;
-        const int64_t t = s_t;
-        // the step's external field on every angle class
-        const double hx = I.phx[t], hy = I.phy[t];
-        for (int c = tid; c < I.nclass; c += kT) {
-            const double2 e = ext_proj(hx, hy, I.cs64[c]);
-            I.ext64[c] = e;
-            I.ext32[c] = make_float2(__double2float_rn(e.x), __double2float_rn(e.y));
-        }
-        __syncthreads();
-        // the sweep (spins through the coherent path: this CTA flips them)
-        for (int64_t lt = wid; lt < tasks; lt += kNW)
-            sweep_task<PREC, 4, 1, true>(I, tcnt, t, lt, s_init != 0,
-                                         sums32[PREC == 1 ? wid : 0], sums64[wid]);
-        __syncthreads();
-        relax_sim<PREC>(I, smem_levels, 0, sm_levels, nullptr);
-        __syncthreads();
-    }
-}
-
 template <int PREC, int MODE>
 void* persist_fn(int W) {
     switch (W) {
@@ -1323,38 +1274,6 @@ cudaError_t launch_relax(const RelaxLaunch& L, cudaStream_t st) {
         else
             k_relax<0, 1><<<g, kT, sm, st>>>(L.tab, L.work, L.n_work, sm, cont);
     }
-    return cudaGetLastError();
-}
-
-bool small_protocol_fits(int64_t n) { return n <= kSmallIslands; }
-
-// Sets the small-array kernels' dynamic shared-memory limit (once; before any
-// capture, so that their launches can be captured).
-cudaError_t prepare_small_protocol() {
-    static std::atomic<int> done{0};
-    static std::mutex mu;
-    if (done.load()) return cudaSuccess;
-    std::lock_guard<std::mutex> g(mu);
-    if (done.load()) return cudaSuccess;
-    const int smem = 96 * 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_small_protocol<0>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_small_protocol<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smem);
-    if (e == cudaSuccess) done.store(1);
-    return e;
-}
-
-cudaError_t launch_small_protocol(const Inst* tab, unsigned* const* tcnts, int prec,
-                                  int smem_levels, int64_t nsteps, cudaStream_t st) {
-    if (nsteps <= 0) return cudaSuccess;
-    cudaError_t e = prepare_small_protocol();
-    if (e != cudaSuccess) return e;
-    if (prec == 1)
-        k_small_protocol<1><<<1, kT, smem_levels, st>>>(tab, tcnts, smem_levels, nsteps);
-    else
-        k_small_protocol<0><<<1, kT, smem_levels, st>>>(tab, tcnts, smem_levels, nsteps);
     return cudaGetLastError();
 }
 

@@ -443,8 +443,7 @@ extern "C" fs_status fs_server_create(size_t hbm_budget, int32_t max_active, fs_
     cudaGetDevice(&S->device);
     // the relax kernel's shared-memory limit is set before any capture
     if (prepare_relax(0, relax_smem_max()) != cudaSuccess ||
-        prepare_relax(1, relax_smem_max()) != cudaSuccess ||
-        prepare_small_protocol() != cudaSuccess) {
+        prepare_relax(1, relax_smem_max()) != cudaSuccess) {
         delete S;
         return FS_ERR_CUDA;
     }
