@@ -94,64 +94,144 @@ __device__ __forceinline__ bool sweep_task(const Inst& I, unsigned* __restrict__
         constexpr int R = 32 / W;
         const int sub = lane / W, sl = lane % W;
         const int4* __restrict__ col4 = reinterpret_cast<const int4*>(I.col);
-        for (int q = sub; q < 32; q += R) {
-            const int64_t i = r0 + q;
-            int bp = 0, bq = 0;
-            long long ap = 0, aq = 0;
-            if (i < I.n) {
-                const int64_t g0 = __ldg(&I.rp[i]) >> 2, g1 = __ldg(&I.rp[i + 1]) >> 2;
-                for (int64_t g = g0 + sl; g < g1; g += W) {
-                    const int4 c = __ldg(&col4[g]);
-                    int8_t s0, s1, s2, s3;
+        // The FP32 sums alone (the FP32 path's sweeps after the first): a sub-warp's
+        // rows two at a time (q and q + R, the sub-warp holds W rows, an even number),
+        // their groups loaded side by side so that twice a lane's loads are in flight;
+        // a row past its end contributes zero coefficients. With 64-bit sums one row
+        // at a time (registers).
+        if (!SUM64) {
+            for (int q = sub; q < 32; q += 2 * R) {
+                const int64_t ia = r0 + q, ib = r0 + q + R;
+                int64_t ga = 0, ea = 0, gb = 0, eb = 0;
+                if (ia < I.n) {
+                    ga = (__ldg(&I.rp[ia]) >> 2) + sl;
+                    ea = __ldg(&I.rp[ia + 1]) >> 2;
+                }
+                if (ib < I.n) {
+                    gb = (__ldg(&I.rp[ib]) >> 2) + sl;
+                    eb = __ldg(&I.rp[ib + 1]) >> 2;
+                }
+                int bpa = 0, bqa = 0, bpb = 0, bqb = 0;
+                for (; ga < ea || gb < eb; ga += W, gb += W) {
+                    const bool va = ga < ea, vb = gb < eb;
+                    const int4 z4 = make_int4(0, 0, 0, 0);
+                    const int4 ca = va ? __ldg(&col4[ga]) : z4;
+                    const int4 cb = vb ? __ldg(&col4[gb]) : z4;
+                    const int4* pa = reinterpret_cast<const int4*>(I.pq32) + 2 * ga;
+                    const int4* pb = reinterpret_cast<const int4*>(I.pq32) + 2 * gb;
+                    const int4 xa = va ? __ldg(pa) : z4, ya = va ? __ldg(pa + 1) : z4;
+                    const int4 xb = vb ? __ldg(pb) : z4, yb = vb ? __ldg(pb + 1) : z4;
+                    int8_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
                     if constexpr (COHERENT) {
-                        s0 = I.s[c.x];
-                        s1 = I.s[c.y];
-                        s2 = I.s[c.z];
-                        s3 = I.s[c.w];
+                        if (va) {
+                            a0 = I.s[ca.x];
+                            a1 = I.s[ca.y];
+                            a2 = I.s[ca.z];
+                            a3 = I.s[ca.w];
+                        }
+                        if (vb) {
+                            b0 = I.s[cb.x];
+                            b1 = I.s[cb.y];
+                            b2 = I.s[cb.z];
+                            b3 = I.s[cb.w];
+                        }
                     } else {
-                        s0 = __ldg(&I.s[c.x]);
-                        s1 = __ldg(&I.s[c.y]);
-                        s2 = __ldg(&I.s[c.z]);
-                        s3 = __ldg(&I.s[c.w]);
+                        if (va) {
+                            a0 = __ldg(&I.s[ca.x]);
+                            a1 = __ldg(&I.s[ca.y]);
+                            a2 = __ldg(&I.s[ca.z]);
+                            a3 = __ldg(&I.s[ca.w]);
+                        }
+                        if (vb) {
+                            b0 = __ldg(&I.s[cb.x]);
+                            b1 = __ldg(&I.s[cb.y]);
+                            b2 = __ldg(&I.s[cb.z]);
+                            b3 = __ldg(&I.s[cb.w]);
+                        }
                     }
-                    if (PREC == 1 && SUM32) {
-                        const int4* p4 = reinterpret_cast<const int4*>(I.pq32) + 2 * g;
-                        const int4 a = __ldg(p4), b = __ldg(p4 + 1);
-                        bp += sgn_sel(s0, a.x) + sgn_sel(s1, a.z) + sgn_sel(s2, b.x) +
-                              sgn_sel(s3, b.z);
-                        bq += sgn_sel(s0, a.y) + sgn_sel(s1, a.w) + sgn_sel(s2, b.y) +
-                              sgn_sel(s3, b.w);
+                    bpa += sgn_sel(a0, xa.x) + sgn_sel(a1, xa.z) + sgn_sel(a2, ya.x) +
+                           sgn_sel(a3, ya.z);
+                    bqa += sgn_sel(a0, xa.y) + sgn_sel(a1, xa.w) + sgn_sel(a2, ya.y) +
+                           sgn_sel(a3, ya.w);
+                    bpb += sgn_sel(b0, xb.x) + sgn_sel(b1, xb.z) + sgn_sel(b2, yb.x) +
+                           sgn_sel(b3, yb.z);
+                    bqb += sgn_sel(b0, xb.y) + sgn_sel(b1, xb.w) + sgn_sel(b2, yb.y) +
+                           sgn_sel(b3, yb.w);
+                }
+#pragma unroll
+                for (int o = W / 2; o > 0; o >>= 1) {
+                    bpa += __shfl_xor_sync(0xffffffffu, bpa, o);
+                    bqa += __shfl_xor_sync(0xffffffffu, bqa, o);
+                    bpb += __shfl_xor_sync(0xffffffffu, bpb, o);
+                    bqb += __shfl_xor_sync(0xffffffffu, bqb, o);
+                }
+                if (sl == 0) {
+                    s32[q][0] = bpa;
+                    s32[q][1] = bqa;
+                    s32[q + R][0] = bpb;
+                    s32[q + R][1] = bqb;
+                }
+            }
+        } else {
+            for (int q = sub; q < 32; q += R) {
+                const int64_t i = r0 + q;
+                int bp = 0, bq = 0;
+                long long ap = 0, aq = 0;
+                if (i < I.n) {
+                    const int64_t g0 = __ldg(&I.rp[i]) >> 2, g1 = __ldg(&I.rp[i + 1]) >> 2;
+                    for (int64_t g = g0 + sl; g < g1; g += W) {
+                        const int4 c = __ldg(&col4[g]);
+                        int8_t s0, s1, s2, s3;
+                        if constexpr (COHERENT) {
+                            s0 = I.s[c.x];
+                            s1 = I.s[c.y];
+                            s2 = I.s[c.z];
+                            s3 = I.s[c.w];
+                        } else {
+                            s0 = __ldg(&I.s[c.x]);
+                            s1 = __ldg(&I.s[c.y]);
+                            s2 = __ldg(&I.s[c.z]);
+                            s3 = __ldg(&I.s[c.w]);
+                        }
+                        if (PREC == 1 && SUM32) {
+                            const int4* p4 = reinterpret_cast<const int4*>(I.pq32) + 2 * g;
+                            const int4 a = __ldg(p4), b = __ldg(p4 + 1);
+                            bp += sgn_sel(s0, a.x) + sgn_sel(s1, a.z) + sgn_sel(s2, b.x) +
+                                  sgn_sel(s3, b.z);
+                            bq += sgn_sel(s0, a.y) + sgn_sel(s1, a.w) + sgn_sel(s2, b.y) +
+                                  sgn_sel(s3, b.w);
+                        }
+                        if (SUM64) {
+                            const longlong2* p = I.pq64 + 4 * g;
+                            const longlong2 v0 = __ldg(p), v1 = __ldg(p + 1);
+                            const longlong2 v2 = __ldg(p + 2), v3 = __ldg(p + 3);
+                            ap += sgn_sel(s0, v0.x) + sgn_sel(s1, v1.x) + sgn_sel(s2, v2.x) +
+                                  sgn_sel(s3, v3.x);
+                            aq += sgn_sel(s0, v0.y) + sgn_sel(s1, v1.y) + sgn_sel(s2, v2.y) +
+                                  sgn_sel(s3, v3.y);
+                        }
+                    }
+                }
+    #pragma unroll
+                for (int o = W / 2; o > 0; o >>= 1) {
+                    if (SUM32) {
+                        bp += __shfl_xor_sync(0xffffffffu, bp, o);
+                        bq += __shfl_xor_sync(0xffffffffu, bq, o);
                     }
                     if (SUM64) {
-                        const longlong2* p = I.pq64 + 4 * g;
-                        const longlong2 v0 = __ldg(p), v1 = __ldg(p + 1);
-                        const longlong2 v2 = __ldg(p + 2), v3 = __ldg(p + 3);
-                        ap += sgn_sel(s0, v0.x) + sgn_sel(s1, v1.x) + sgn_sel(s2, v2.x) +
-                              sgn_sel(s3, v3.x);
-                        aq += sgn_sel(s0, v0.y) + sgn_sel(s1, v1.y) + sgn_sel(s2, v2.y) +
-                              sgn_sel(s3, v3.y);
+                        ap += __shfl_xor_sync(0xffffffffu, ap, o);
+                        aq += __shfl_xor_sync(0xffffffffu, aq, o);
                     }
                 }
-            }
-#pragma unroll
-            for (int o = W / 2; o > 0; o >>= 1) {
-                if (SUM32) {
-                    bp += __shfl_xor_sync(0xffffffffu, bp, o);
-                    bq += __shfl_xor_sync(0xffffffffu, bq, o);
-                }
-                if (SUM64) {
-                    ap += __shfl_xor_sync(0xffffffffu, ap, o);
-                    aq += __shfl_xor_sync(0xffffffffu, aq, o);
-                }
-            }
-            if (sl == 0) {
-                if (PREC == 1 && SUM32) {
-                    s32[q][0] = bp;
-                    s32[q][1] = bq;
-                }
-                if (SUM64) {
-                    s64[q][0] = ap;
-                    s64[q][1] = aq;
+                if (sl == 0) {
+                    if (PREC == 1 && SUM32) {
+                        s32[q][0] = bp;
+                        s32[q][1] = bq;
+                    }
+                    if (SUM64) {
+                        s64[q][0] = ap;
+                        s64[q][1] = aq;
+                    }
                 }
             }
         }
