@@ -118,8 +118,8 @@ TRAFFIC = {
     # (profiles/), valid while the listed sources are unchanged (sha256 prefix): the sweep
     # capture is of its 8-lanes-a-row build on kagome 300x300, the multi-flip one of field
     # step 5 of that rotation; both are scaled to a full launch by their units
-    "k_sweep": {"per": "neighbour pair", "bytes_per_unit": 13.47,
-                "sources": ("fs_sweep.cu", "fs_sweep_task.cuh"), "sha256_16": "554d69c5537b0d3d"},
+    "k_sweep": {"per": "neighbour pair", "bytes_per_unit": 13.45,
+                "sources": ("fs_sweep.cu", "fs_sweep_task.cuh"), "sha256_16": "76cfa28bdbad0bac"},
     "k_relax_multi": {"per": "flip", "bytes_per_unit": 11840.0,
                       "sources": ("fs_relax_multi.cu", "fs_update.cuh", "fs_common.cuh"),
                       "sha256_16": "a9765cd257c11bd4"},
