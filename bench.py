@@ -614,7 +614,11 @@ def main():
                        "sweep_lanes_per_row": lanes},
             "field_steps_per_s": field_steps,
             "roofline": roof_relax, "roofline_sweep": roof_sweep,
-            "gpu_launches": args.steps * (3 * CHUNK + 1),
+            # per field step: the external-field table, the sweep, the relax (with the
+            # multi-flip rounds also the single-flip continuation, which returns at once
+            # unless a step is handed over); per bench step one copy-out of the results
+            "gpu_launches": args.steps * ((4 if relax_kernel == "k_relax_multi" else 3) * CHUNK
+                                          + 1),
             "fp64_rechecks_per_flip": rechecks / max(flips_timed, 1)}
     if relax_kernel == "k_relax_multi" and not args.no_e2e:
         line["multi_flip_rounds"] = None  # filled from the host-buffer pass below
