@@ -83,9 +83,11 @@ def flip_alg_bytes(degree: float, fp32: bool) -> float:
     return degree * (42.0 if fp32 else 70.0)
 
 
-def sweep_bytes(n: int, nnz: int, fp32: bool, resweep: bool, thermal: bool) -> int:
+def sweep_bytes(n: int, nnz: int, fp32: bool, resweep: bool, thermal: bool,
+                col16: bool = False) -> int:
     """Bytes of one sweep as this implementation lays its arrays out. Per pair: the
-    column index and the (P, Q) coefficients of the path's width (4 + 8 or 4 + 16);
+    column index and the (P, Q) coefficients of the path's width (4 + 8 or 4 + 16;
+    with col16, the FP32 path's 16-bit column offsets: 2 + 8);
     per row: its pointer (8). Per island: spin, angle class, 1/(b h_k) and
     1/(c h_k) read (1 + 2 + 8); the relax's 32-byte record, key and exact value
     written (32 + 8 + 8); on the FP64 path the 64-bit sums written (or, without the
@@ -95,7 +97,8 @@ def sweep_bytes(n: int, nnz: int, fp32: bool, resweep: bool, thermal: bool) -> i
                   + (8 if fp32 and not resweep else 0) + (8 if thermal else 0))
     if not resweep:
         return n * per_island
-    return (12 if fp32 else 20) * nnz + 8 * (n + 1) + n * per_island
+    per_pair = (10 if col16 else 12) if fp32 else 20
+    return per_pair * nnz + 8 * (n + 1) + n * per_island
 
 
 def flip_layout_bytes(degree: float, fp32: bool) -> float:
@@ -116,13 +119,13 @@ def flip_layout_bytes(degree: float, fp32: bool) -> float:
 TRAFFIC = {
     # DRAM bytes (read + write) per unit from one small-case ncu capture of the kernel
     # (profiles/), valid while the listed sources are unchanged (sha256 prefix): the sweep
-    # capture is of its 8-lanes-a-row build on kagome 300x300, the multi-flip one of field
+    # capture is of its 4-lanes-a-row build on kagome 300x300, the multi-flip one of field
     # step 5 of that rotation; both are scaled to a full launch by their units
-    "k_sweep": {"per": "neighbour pair", "bytes_per_unit": 13.45,
-                "sources": ("fs_sweep.cu", "fs_sweep_task.cuh"), "sha256_16": "76cfa28bdbad0bac"},
-    "k_relax_multi": {"per": "flip", "bytes_per_unit": 11840.0,
+    "k_sweep": {"per": "neighbour pair", "bytes_per_unit": 11.41,
+                "sources": ("fs_sweep.cu", "fs_sweep_task.cuh"), "sha256_16": "0b37c859b8c89d8a"},
+    "k_relax_multi": {"per": "flip", "bytes_per_unit": 11716.0,
                       "sources": ("fs_relax_multi.cu", "fs_update.cuh", "fs_common.cuh"),
-                      "sha256_16": "a9765cd257c11bd4"},
+                      "sha256_16": "adfeb495ca5714f7"},
     "k_relax": {"per": "flip", "bytes_per_unit": None,
                 "sources": ("fs_relax.cu", "fs_common.cuh"), "sha256_16": ""},
 }
@@ -380,7 +383,8 @@ def timed_protocol(torch, B, w, prec, repeats, warm, golden_name=None):
     res["sweep"] = {"us_per_launch": sw * 1e3, "alg_bytes_per_launch": alg,
                     "achieved_gbs": alg / (sw / 1e3) / 1e9, "frac": alg / (sw / 1e3) / 1e9 / peak,
                     "layout_bytes_per_launch": sweep_bytes(info.n, info.nnz, fp32, True,
-                                                           w["sigma_th"] > 0)}
+                                                           w["sigma_th"] > 0,
+                                                           bool(info.col_offsets16))}
     res["relax_share"] = prof["relax_ms"] / ms_prof
     sim.close()
     return res
@@ -594,7 +598,8 @@ def main():
                   "unit": "GB/s", "frac": sweep_alg / (sweep_launch_ms / 1e3) / 1e9 / peak,
                   "traffic": traffic_of("k_sweep", nnz), "peak_kind": peak_kind,
                   "avg_launch_ms": sweep_launch_ms, "bytes_per_launch": sweep_alg,
-                  "layout_bytes_per_launch": sweep_bytes(n, nnz, True, True, True),
+                  "layout_bytes_per_launch": sweep_bytes(n, nnz, True, True, True,
+                                                         bool(info.col_offsets16)),
                   "share_of_step": prof["sweep_ms"] / ms if ms > 0 else None}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

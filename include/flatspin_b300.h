@@ -109,6 +109,10 @@ typedef struct {
     int32_t e64, e32;  /* fixed-point exponents: value = integer * 2^-e */
     int64_t device_bytes;
     double band_rel, band_abs; /* FP32 error band of the LHS: rel * LHS + abs */
+    int32_t col_offsets16; /* 1: the FP32 path's sweeps and multi-flip rounds read
+                            * each neighbour as its row island plus a 16-bit offset
+                            * (every offset fits), 0: the 32-bit column indices */
+    int32_t reserved_info;  /* 0 */
 } fs_info;
 
 /* Last error message of `sim` (or of the last failed create call when sim is

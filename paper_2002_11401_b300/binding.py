@@ -57,7 +57,8 @@ class fs_params(C.Structure):
 class fs_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nnz_padded", C.c_int64),
                 ("max_degree", C.c_int32), ("e64", C.c_int32), ("e32", C.c_int32),
-                ("device_bytes", C.c_int64), ("band_rel", C.c_double), ("band_abs", C.c_double)]
+                ("device_bytes", C.c_int64), ("band_rel", C.c_double), ("band_abs", C.c_double),
+                ("col_offsets16", C.c_int32), ("reserved_info", C.c_int32)]
 
 
 class fs_profile(C.Structure):

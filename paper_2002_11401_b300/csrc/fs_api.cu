@@ -290,7 +290,7 @@ static PlanBytes plan_bytes(int64_t n, size_t ncls, int64_t ncell, int64_t nnzp,
     // neighbour tensors (the 32-bit ones are scratch on the FP64 path)
     S(8 * (n + 1)), S(4 * nnzp), S(16 * nnzp), S(8 * nnzp);
     if (fp32)
-        S(8 * nnzp), S(4 * nnzp);
+        S(8 * nnzp), S(4 * nnzp), S(2 * nnzp);  // (with the 16-bit column offsets)
     else
         T(8 * nnzp), T(4 * nnzp);
     // islands, classes, relax state
@@ -478,6 +478,16 @@ fs_status fs_build_sim(fs_sim* sim) {
     o.pq32 = pq32;
     o.qt32 = qt32;
     CK(build_fill(in, w, o, st), "fill");
+    // The FP32 sweeps read 16-bit column offsets instead of col when every one fits
+    // (lattice orderings keep neighbours close in index); read back below.
+    int16_t* dcol = nullptr;
+    int32_t dcol_over = 1;
+    if (p.precision == FS_FP32_RECHECK) {
+        CK(palloc((void**)&dcol, 2 * nnzp), "alloc");
+        CK(build_dcol(n, rp, col, dcol, &w.stats->dcol_over, st), "offsets");
+        CK(cudaMemcpyAsync(&dcol_over, &w.stats->dcol_over, 4, cudaMemcpyDeviceToHost, st),
+           "stats");
+    }
     I.rp = rp;
     I.col = col;
     I.pq64 = pq64;
@@ -528,6 +538,7 @@ fs_status fs_build_sim(fs_sim* sim) {
         CK(cudaMemcpyAsync(pos, hp.data(), 16 * n, cudaMemcpyHostToDevice, st), "upload");
         CK(cudaStreamSynchronize(st), "upload");  // (the host copy goes out of scope)
         I.pos = pos;
+        I.dcol = dcol_over == 0 ? dcol : nullptr;
         const double rc = 2.0 * p.cutoff * sim->a;
         I.rconf2 = rc * rc * (1.0 + 1e-6);
         // the same test on FP32 centres: each coordinate is within ext 2^-24 of its
@@ -1182,6 +1193,7 @@ extern "C" fs_status fs_get_info(const fs_sim* csim, fs_info* out) {
     out->band_rel = std::max(sim->inst.pow_rel_p, sim->inst.pow_rel_q) + sim->inst.div_rel +
                     sim->inst.dh_rel;
     out->band_abs = sim->inst.dh_abs;
+    out->col_offsets16 = sim->inst.dcol != nullptr ? 1 : 0;
     // unpadded nnz: count non-self entries
     std::vector<int64_t> rp((size_t)sim->n + 1);
     std::vector<int32_t> col((size_t)sim->nnzp);

@@ -339,4 +339,26 @@ cudaError_t build_fill(const BuildIn& in, BuildWork& w, const BuildOut& o, cudaS
     return cudaGetLastError();
 }
 
+// One warp per row: the row's column offsets from its own island, 16 bits each.
+__global__ void k_dcol(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                       int16_t* __restrict__ dcol, int32_t* __restrict__ over) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    bool bad = false;
+    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += 32) {
+        const int64_t d = (int64_t)col[e] - i;
+        bad = bad || d < -32768 || d > 32767;
+        dcol[e] = (int16_t)d;
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(over, 1);
+}
+
+cudaError_t build_dcol(int64_t n, const int64_t* rp, const int32_t* col, int16_t* dcol,
+                       int32_t* over, cudaStream_t st) {
+    const int64_t threads = n * 32;
+    k_dcol<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(n, rp, col, dcol, over);
+    return cudaGetLastError();
+}
+
 }  // namespace fs

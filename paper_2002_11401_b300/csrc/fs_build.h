@@ -9,7 +9,7 @@ namespace fs {
 struct BuildStats {
     unsigned long long bound_bits;  // max_i sum_j 2 alpha / r_ij^3 (double bits)
     int32_t max_deg;                // max padded degree
-    int32_t pad;
+    int32_t dcol_over;              // some col[e] - i does not fit 16 bits
 };
 
 struct BuildIn {
@@ -53,5 +53,9 @@ cudaError_t build_cells(const BuildIn& in, BuildWork& w, cudaStream_t st);
 cudaError_t build_degrees(const BuildIn& in, BuildWork& w, cudaStream_t st);
 cudaError_t build_rows(const BuildIn& in, BuildWork& w, int64_t* rp, cudaStream_t st);
 cudaError_t build_fill(const BuildIn& in, BuildWork& w, const BuildOut& o, cudaStream_t st);
+// dcol[e] = col[e] - i for every entry e of row i; sets *over when one does not fit
+// 16 bits (those entries are then left truncated and dcol is not to be used).
+cudaError_t build_dcol(int64_t n, const int64_t* rp, const int32_t* col, int16_t* dcol,
+                       int32_t* over, cudaStream_t st);
 
 }  // namespace fs

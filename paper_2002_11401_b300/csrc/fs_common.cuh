@@ -82,6 +82,9 @@ struct Inst {
     const long long* qt64;  // transposed Q: field of the row island on col, col's frame
     const int2* pq32;       // (P, Q) in 2^-e32 fixed point
     const int* qt32;
+    // col[e] - i for row i as 16-bit offsets (FP32 path, when every offset fits;
+    // else null): what the FP32 sweeps read instead of col
+    const int16_t* dcol;
     // islands
     int8_t* s;
     const double2* rbc64;   // (1 / (b h_k), 1 / (c h_k)) per island, FP64

@@ -308,7 +308,10 @@ __device__ __forceinline__ void pass_compute(const Inst& I, int64_t k, int snew,
         Upd u;
         u.i = -1;
         if (e < r1) {
-            const int32_t i = __ldg(&I.col[e]);
+            // (the FP32 path reads the 16-bit column offsets the sweep streams)
+            const int32_t i = PREC == 1 && I.dcol != nullptr
+                                  ? (int32_t)k + (int32_t)__ldg(&I.dcol[e])
+                                  : __ldg(&I.col[e]);
             const long long dp = __ldg(&I.pq64[e].x), dq = __ldg(&I.qt64[e]);
             int dp32 = 0, dq32 = 0;
             if constexpr (PREC == 1) {

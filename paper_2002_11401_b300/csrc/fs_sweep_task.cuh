@@ -5,7 +5,8 @@
 // the persistent batch kernel (tasks claimed by whichever CTA is free).
 //
 // Sub-warps of W lanes stream one CSR row each: every lane reads a group of four
-// entries with 16-byte loads (column indices, then the fixed-point (P, Q)
+// entries with 16-byte loads (column indices, or on the FP32 path their 16-bit
+// offsets from the row's island in 8 bytes, then the fixed-point (P, Q)
 // coefficients), gathers the four spins, and accumulates the exact integer sums
 // s_j P_ij and s_j Q_ij; a shuffle butterfly inside the sub-warp finishes the row.
 // The per-row sums are staged in shared memory so that lane q then evaluates
@@ -72,6 +73,104 @@ __device__ bool propagate_up(const Inst& I, unsigned* __restrict__ tcnt, int lev
     return true;
 }
 
+// The FP32 sums alone (the FP32 path's sweeps after the first) for the 32 rows from
+// r0: a sub-warp's rows two at a time (q and q + R; the sub-warp holds W rows, an
+// even number), their groups loaded side by side so that twice a lane's loads are
+// in flight; a row past its end contributes zero coefficients. D16: the columns
+// come from the 16-bit offsets (I.dcol, 8 bytes a group of four) instead of col
+// (16 bytes). Results to s32[q] by the sub-warp's first lane.
+template <int W, bool COHERENT, bool D16>
+__device__ __forceinline__ void sum32_rows(const Inst& I, int64_t r0, int (*s32)[2]) {
+    constexpr int R = 32 / W;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / W, sl = lane % W;
+    const int4* __restrict__ col4 = reinterpret_cast<const int4*>(I.col);
+    const int2* __restrict__ dcol4 = reinterpret_cast<const int2*>(I.dcol);
+    for (int q = sub; q < 32; q += 2 * R) {
+        const int64_t ia = r0 + q, ib = r0 + q + R;
+        int64_t ga = 0, ea = 0, gb = 0, eb = 0;
+        if (ia < I.n) {
+            ga = (__ldg(&I.rp[ia]) >> 2) + sl;
+            ea = __ldg(&I.rp[ia + 1]) >> 2;
+        }
+        if (ib < I.n) {
+            gb = (__ldg(&I.rp[ib]) >> 2) + sl;
+            eb = __ldg(&I.rp[ib + 1]) >> 2;
+        }
+        int bpa = 0, bqa = 0, bpb = 0, bqb = 0;
+        for (; ga < ea || gb < eb; ga += W, gb += W) {
+            const bool va = ga < ea, vb = gb < eb;
+            const int4 z4 = make_int4(0, 0, 0, 0);
+            int4 ca = z4, cb = z4;
+            if constexpr (D16) {
+                // four offsets in 8 bytes, added to the row's island
+                const int2 da = va ? __ldg(&dcol4[ga]) : make_int2(0, 0);
+                const int2 db = vb ? __ldg(&dcol4[gb]) : make_int2(0, 0);
+                ca = make_int4((int)ia + (int)(short)(da.x & 0xffff), (int)ia + (da.x >> 16),
+                               (int)ia + (int)(short)(da.y & 0xffff), (int)ia + (da.y >> 16));
+                cb = make_int4((int)ib + (int)(short)(db.x & 0xffff), (int)ib + (db.x >> 16),
+                               (int)ib + (int)(short)(db.y & 0xffff), (int)ib + (db.y >> 16));
+            } else {
+                ca = va ? __ldg(&col4[ga]) : z4;
+                cb = vb ? __ldg(&col4[gb]) : z4;
+            }
+            const int4* pa = reinterpret_cast<const int4*>(I.pq32) + 2 * ga;
+            const int4* pb = reinterpret_cast<const int4*>(I.pq32) + 2 * gb;
+            const int4 xa = va ? __ldg(pa) : z4, ya = va ? __ldg(pa + 1) : z4;
+            const int4 xb = vb ? __ldg(pb) : z4, yb = vb ? __ldg(pb + 1) : z4;
+            int8_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+            if constexpr (COHERENT) {
+                if (va) {
+                    a0 = I.s[ca.x];
+                    a1 = I.s[ca.y];
+                    a2 = I.s[ca.z];
+                    a3 = I.s[ca.w];
+                }
+                if (vb) {
+                    b0 = I.s[cb.x];
+                    b1 = I.s[cb.y];
+                    b2 = I.s[cb.z];
+                    b3 = I.s[cb.w];
+                }
+            } else {
+                if (va) {
+                    a0 = __ldg(&I.s[ca.x]);
+                    a1 = __ldg(&I.s[ca.y]);
+                    a2 = __ldg(&I.s[ca.z]);
+                    a3 = __ldg(&I.s[ca.w]);
+                }
+                if (vb) {
+                    b0 = __ldg(&I.s[cb.x]);
+                    b1 = __ldg(&I.s[cb.y]);
+                    b2 = __ldg(&I.s[cb.z]);
+                    b3 = __ldg(&I.s[cb.w]);
+                }
+            }
+            bpa += sgn_sel(a0, xa.x) + sgn_sel(a1, xa.z) + sgn_sel(a2, ya.x) +
+                   sgn_sel(a3, ya.z);
+            bqa += sgn_sel(a0, xa.y) + sgn_sel(a1, xa.w) + sgn_sel(a2, ya.y) +
+                   sgn_sel(a3, ya.w);
+            bpb += sgn_sel(b0, xb.x) + sgn_sel(b1, xb.z) + sgn_sel(b2, yb.x) +
+                   sgn_sel(b3, yb.z);
+            bqb += sgn_sel(b0, xb.y) + sgn_sel(b1, xb.w) + sgn_sel(b2, yb.y) +
+                   sgn_sel(b3, yb.w);
+        }
+#pragma unroll
+        for (int o = W / 2; o > 0; o >>= 1) {
+            bpa += __shfl_xor_sync(0xffffffffu, bpa, o);
+            bqa += __shfl_xor_sync(0xffffffffu, bqa, o);
+            bpb += __shfl_xor_sync(0xffffffffu, bpb, o);
+            bqb += __shfl_xor_sync(0xffffffffu, bqb, o);
+        }
+        if (sl == 0) {
+            s32[q][0] = bpa;
+            s32[q][1] = bqa;
+            s32[q + R][0] = bpb;
+            s32[q + R][1] = bqb;
+        }
+    }
+}
+
 // One warp's task: islands 32 lt .. 32 lt + 31 of simulation I at protocol step t
 // (its state's `init`: the sums are set up from scratch). MODE 0: margins only
 // (exact sums kept by the flips); MODE 1: resweep the sums of the simulation's
@@ -94,84 +193,13 @@ __device__ __forceinline__ bool sweep_task(const Inst& I, unsigned* __restrict__
         constexpr int R = 32 / W;
         const int sub = lane / W, sl = lane % W;
         const int4* __restrict__ col4 = reinterpret_cast<const int4*>(I.col);
-        // The FP32 sums alone (the FP32 path's sweeps after the first): a sub-warp's
-        // rows two at a time (q and q + R, the sub-warp holds W rows, an even number),
-        // their groups loaded side by side so that twice a lane's loads are in flight;
-        // a row past its end contributes zero coefficients. With 64-bit sums one row
-        // at a time (registers).
+        // The FP32 sums alone two rows at a time (sum32_rows); with 64-bit sums one
+        // row at a time (registers).
         if (!SUM64) {
-            for (int q = sub; q < 32; q += 2 * R) {
-                const int64_t ia = r0 + q, ib = r0 + q + R;
-                int64_t ga = 0, ea = 0, gb = 0, eb = 0;
-                if (ia < I.n) {
-                    ga = (__ldg(&I.rp[ia]) >> 2) + sl;
-                    ea = __ldg(&I.rp[ia + 1]) >> 2;
-                }
-                if (ib < I.n) {
-                    gb = (__ldg(&I.rp[ib]) >> 2) + sl;
-                    eb = __ldg(&I.rp[ib + 1]) >> 2;
-                }
-                int bpa = 0, bqa = 0, bpb = 0, bqb = 0;
-                for (; ga < ea || gb < eb; ga += W, gb += W) {
-                    const bool va = ga < ea, vb = gb < eb;
-                    const int4 z4 = make_int4(0, 0, 0, 0);
-                    const int4 ca = va ? __ldg(&col4[ga]) : z4;
-                    const int4 cb = vb ? __ldg(&col4[gb]) : z4;
-                    const int4* pa = reinterpret_cast<const int4*>(I.pq32) + 2 * ga;
-                    const int4* pb = reinterpret_cast<const int4*>(I.pq32) + 2 * gb;
-                    const int4 xa = va ? __ldg(pa) : z4, ya = va ? __ldg(pa + 1) : z4;
-                    const int4 xb = vb ? __ldg(pb) : z4, yb = vb ? __ldg(pb + 1) : z4;
-                    int8_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
-                    if constexpr (COHERENT) {
-                        if (va) {
-                            a0 = I.s[ca.x];
-                            a1 = I.s[ca.y];
-                            a2 = I.s[ca.z];
-                            a3 = I.s[ca.w];
-                        }
-                        if (vb) {
-                            b0 = I.s[cb.x];
-                            b1 = I.s[cb.y];
-                            b2 = I.s[cb.z];
-                            b3 = I.s[cb.w];
-                        }
-                    } else {
-                        if (va) {
-                            a0 = __ldg(&I.s[ca.x]);
-                            a1 = __ldg(&I.s[ca.y]);
-                            a2 = __ldg(&I.s[ca.z]);
-                            a3 = __ldg(&I.s[ca.w]);
-                        }
-                        if (vb) {
-                            b0 = __ldg(&I.s[cb.x]);
-                            b1 = __ldg(&I.s[cb.y]);
-                            b2 = __ldg(&I.s[cb.z]);
-                            b3 = __ldg(&I.s[cb.w]);
-                        }
-                    }
-                    bpa += sgn_sel(a0, xa.x) + sgn_sel(a1, xa.z) + sgn_sel(a2, ya.x) +
-                           sgn_sel(a3, ya.z);
-                    bqa += sgn_sel(a0, xa.y) + sgn_sel(a1, xa.w) + sgn_sel(a2, ya.y) +
-                           sgn_sel(a3, ya.w);
-                    bpb += sgn_sel(b0, xb.x) + sgn_sel(b1, xb.z) + sgn_sel(b2, yb.x) +
-                           sgn_sel(b3, yb.z);
-                    bqb += sgn_sel(b0, xb.y) + sgn_sel(b1, xb.w) + sgn_sel(b2, yb.y) +
-                           sgn_sel(b3, yb.w);
-                }
-#pragma unroll
-                for (int o = W / 2; o > 0; o >>= 1) {
-                    bpa += __shfl_xor_sync(0xffffffffu, bpa, o);
-                    bqa += __shfl_xor_sync(0xffffffffu, bqa, o);
-                    bpb += __shfl_xor_sync(0xffffffffu, bpb, o);
-                    bqb += __shfl_xor_sync(0xffffffffu, bqb, o);
-                }
-                if (sl == 0) {
-                    s32[q][0] = bpa;
-                    s32[q][1] = bqa;
-                    s32[q + R][0] = bpb;
-                    s32[q + R][1] = bqb;
-                }
-            }
+            if (I.dcol)
+                sum32_rows<W, COHERENT, true>(I, r0, s32);
+            else
+                sum32_rows<W, COHERENT, false>(I, r0, s32);
         } else {
             for (int q = sub; q < 32; q += R) {
                 const int64_t i = r0 + q;

@@ -43,8 +43,9 @@ def make_sim(w, precision):
 
 
 def sweep_bytes(info, fp32: bool, resweep: bool, thermal: bool) -> int:
-    """Algorithmic bytes of one field-and-margin sweep. Per pair: the column index
-    and the (P, Q) coefficients of the path's width (4 + 8 or 4 + 16); per row: its
+    """Bytes one field-and-margin sweep moves as the arrays are laid out. Per pair:
+    the column index and the (P, Q) coefficients of the path's width (4 + 8 or
+    4 + 16; 2 + 8 where the FP32 path reads 16-bit column offsets); per row: its
     pointer (8). Per island: spin, angle class, 1/(b h_k) and 1/(c h_k) read
     (1 + 2 + 8); the relax's 32-byte record, key and exact value written
     (32 + 8 + 8); on the FP64 path the 64-bit sums written (or, without the
@@ -55,7 +56,8 @@ def sweep_bytes(info, fp32: bool, resweep: bool, thermal: bool) -> int:
                   + (8 if fp32 and not resweep else 0) + (8 if thermal else 0))
     if not resweep:
         return n * per_island
-    return (12 if fp32 else 20) * nnz + 8 * (n + 1) + n * per_island
+    per_pair = (10 if info.col_offsets16 else 12) if fp32 else 20
+    return per_pair * nnz + 8 * (n + 1) + n * per_island
 
 
 def run_single(name, precision, steps, resweep, cells=0, relax="auto"):

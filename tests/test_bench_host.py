@@ -23,6 +23,8 @@ def test_algorithmic_bytes_by_hand():
 def test_layout_sweep_bytes_by_hand():
     # 10 islands, 40 pairs: FP32 resweep = 12*40 + 8*11 + 59*10
     assert bench.sweep_bytes(10, 40, True, True, False) == 480 + 88 + 590
+    # the FP32 path's 16-bit column offsets: 10 B per pair
+    assert bench.sweep_bytes(10, 40, True, True, False, True) == 400 + 88 + 590
     # FP64 resweep adds the 64-bit sums (75 B per island) and 20 B per pair
     assert bench.sweep_bytes(10, 40, False, True, False) == 800 + 88 + 750
     # without the resweep only per-island bytes remain (FP32 reads its 32-bit sums)

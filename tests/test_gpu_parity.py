@@ -247,9 +247,40 @@ def test_custom_geometry_matches_oracle(B, oracle):
         sim = B.Sim.custom(x, y, t)
         sim.set_params(B.make_params(alpha=2e-3, cutoff=2.5, k_disorder=0.1, seed=3,
                                      precision=prec))
+        # (300 islands: every column offset fits 16 bits, which the FP32 path reads)
+        assert sim.info().col_offsets16 == (1 if prec == FP32 else 0)
         S = oracle.Sim(x, y, t, sim.hk(), alpha=2e-3, cutoff_abs=2.5)
         ref = S.run(np.ones(n, dtype=np.int8), hx, hy)
         got = sim.run_protocol(hx, hy)
+        assert got["hash"] == ref["hash"], first_divergence(
+            ref["log_step"], ref["log_spin"], got["log_step"], got["log_spin"])
+
+
+def test_custom_geometry_far_indices_matches_oracle(B, oracle):
+    # Islands in random order: neighbours lie up to the whole array apart in index,
+    # so the FP32 sweeps cannot use 16-bit column offsets and read the 32-bit
+    # columns (arrays of at most 32,768 islands, and lattices in their canonical
+    # order, always fit 16 bits); above 32,768 islands the multi-flip relax runs.
+    rng = np.random.default_rng(21)
+    n = 50_000
+    side = math.sqrt(n)
+    x = rng.uniform(0, side, n)
+    y = rng.uniform(0, side, n)
+    t = rng.uniform(0, math.pi, n)
+    hx, hy = I.rotation_protocol(10, 9.0, 0.11)
+    for prec in (FP32, FP64):
+        sim = B.Sim.custom(x, y, t)
+        sim.set_params(B.make_params(alpha=2e-3, cutoff=2.0, k_disorder=0.1, seed=5,
+                                     precision=prec))
+        assert sim.info().col_offsets16 == 0
+        if prec == FP32:
+            rp, col, _, _ = sim.csr()
+            rows = np.repeat(np.arange(n), np.diff(rp))
+            assert np.abs(col.astype(np.int64) - rows).max() > 32767
+            S = oracle.Sim(x, y, t, sim.hk(), alpha=2e-3, cutoff_abs=2.0)
+            ref = S.run(np.ones(n, dtype=np.int8), hx, hy)
+        got = sim.run_protocol(hx, hy)
+        assert sum(ref["flips_per_step"]) > 1000
         assert got["hash"] == ref["hash"], first_divergence(
             ref["log_step"], ref["log_spin"], got["log_step"], got["log_spin"])
 
