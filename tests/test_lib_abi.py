@@ -133,3 +133,49 @@ def test_series_and_correlation_need_parameters(lib):
     p = B.make_params(alpha=1e-3, criterion=3)
     assert lib.fs_workspace_bytes(sim.handle, ctypes.byref(p), ctypes.byref(ctypes.c_size_t())) \
         == B.FS_ERR_INVALID
+
+
+def _header_fields(src, name):
+    """Field names of `typedef struct { ... } name;` in declaration order."""
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", src).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        # "type a" or "type a, b" (no arrays or function pointers in these structs)
+        first, *others = [p.strip() for p in decl.split(",")]
+        fields += [n.lstrip("*") for n in [first.rpartition(" ")[2]] + others]
+    return fields
+
+
+@pytest.mark.parametrize("name", ["fs_params", "fs_info", "fs_profile", "fs_request",
+                                  "fs_result"])
+def test_binding_structs_match_the_header_layout(name, tmp_path):
+    """Each ctypes struct of the binding has the header's fields in its order, and
+    gcc's sizeof and offsetof of the header's struct equal ctypes' own."""
+    import shutil
+    import subprocess
+
+    from paper_2002_11401_b300 import binding as B
+
+    hdr = os.path.join(ROOT, "include", "flatspin_b300.h")
+    src = re.sub(r"/\*.*?\*/", "", open(hdr).read(), flags=re.S)
+    want = _header_fields(src, name)
+    cls = getattr(B, name)
+    assert [f[0] for f in cls._fields_] == want
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    prog = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{hdr}"',
+             "int main(void) {", f'  printf("%zu\\n", sizeof({name}));']
+    lines += [f'  printf("%zu\\n", offsetof({name}, {f}));' for f in want]
+    lines += ["  return 0;", "}"]
+    prog.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c11", str(prog), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(cls)
+    assert out[1:] == [getattr(cls, f).offset for f in want]
