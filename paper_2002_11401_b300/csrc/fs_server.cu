@@ -62,8 +62,10 @@ struct Job {
 
 // Device bytes of one request before it is built: per island ~156 B of state
 // and, per neighbour pair, the CSR entry and both coefficient widths with their
-// transposed copies (40 B); the degree is the cutoff disc's area times the array's
-// island density, plus a margin for the rounding of the rows to multiples of 4.
+// transposed copies (40 B: on the FS_FP64 path the 32-bit ones are the build's
+// scratch) and the FS_FP32_RECHECK path's 16-bit column offset (2 B); the degree
+// is the cutoff disc's area times the array's island density, plus a margin for
+// the rounding of the rows to multiples of 4.
 double islands_of(const fs_request& r) {
     const double x = r.nx, y = r.ny;
     switch (r.kind) {
@@ -88,7 +90,7 @@ size_t estimate_bytes(const fs_request& r) {
                            : r.kind == FS_ISING ? 1.0
                                                 : 2.0;
     const double deg = 1.05 * M_PI * rc * rc * density + 8.0;
-    return (size_t)(n * (deg * 40.0 + 156.0) + 16.0 * r.K + (1 << 20));
+    return (size_t)(n * (deg * 42.0 + 156.0) + 16.0 * r.K + (1 << 20));
 }
 
 // Admission order: a request that has waited longer than kAgeS goes first (oldest
